@@ -1,0 +1,254 @@
+/*
+ * Plain, slow, FP64 CPU oracle for the factorization-based DPP sampler of
+ * Poulson, "High-performance sampling of generic Determinantal Point
+ * Processes" (arXiv:1905.00165).
+ *
+ * THIS IS TEST INFRASTRUCTURE. Only the test-suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load it. It shares no code, header, table or
+ * helper with the CUDA library; the CUDA path never calls it.
+ *
+ * What is computed, and where the paper fixes it:
+ *   - Algorithm 1 ("Unblocked, right-looking, non-Hermitian DPP sampling"),
+ *     Theorem 1: for j = 0..n-1 the pivot A_jj is the conditional inclusion
+ *     probability of index j; index j is kept by a Bernoulli draw with that
+ *     probability, otherwise 1 is subtracted from the pivot (Prop. 4, element
+ *     exclusion); the column below the pivot is divided by the pivot and the
+ *     trailing block receives the rank-1 Schur-complement update (Prop. 3/4).
+ *   - The likelihood of the sample is the product of the absolute values of
+ *     the final pivots (Theorem 1, and the proof of Prop. 1 that follows it):
+ *     log P(Y) = sum_j log|d_j|.
+ *   - The Hermitian specialisation (Section 3, "the same specializations that
+ *     exist for modifying an unpivoted LU factorization into ... LDL^H"): only
+ *     the lower triangle is referenced, L is unit lower triangular and D is
+ *     real diagonal.
+ *
+ * Readings where the paper is silent (they are the library's documented
+ * conventions as well, but implemented here independently):
+ *   - Bernoulli(d): keep iff u_j < Re(d_j), u_j in (0,1).
+ *   - u_j comes from Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
+ *     numbers: as easy as 1, 2, 3", SC'11) with key = (seed lo, seed hi) and
+ *     counter = (j, instance lo, instance hi, 0); the 53-bit uniform is
+ *     u = ((x0 << 21 | x1 >> 11) + 0.5) * 2^-53.
+ *   - Hermitian pivots are real: the imaginary part is discarded.
+ *
+ * Parallelism: the rank-1 update loops over independent columns with OpenMP;
+ * each matrix entry receives exactly the operations of the definition, in the
+ * same order, so the result does not depend on the thread count.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10, from its published definition (Salmon et al., SC'11).       */
+/* ------------------------------------------------------------------------- */
+#define PHILOX_M0 0xD2511F53u
+#define PHILOX_M1 0xCD9E8D57u
+#define PHILOX_W0 0x9E3779B9u
+#define PHILOX_W1 0xBB67AE85u
+
+static void mulhilo32(uint32_t a, uint32_t b, uint32_t* hi, uint32_t* lo) {
+  uint64_t p = (uint64_t)a * (uint64_t)b;
+  *hi = (uint32_t)(p >> 32);
+  *lo = (uint32_t)p;
+}
+
+void oracle_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2],
+                          uint32_t out[4]) {
+  uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+  uint32_t k0 = key_in[0], k1 = key_in[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += PHILOX_W0;
+      k1 += PHILOX_W1;
+    }
+    uint32_t hi0, lo0, hi1, lo1;
+    mulhilo32(PHILOX_M0, c0, &hi0, &lo0);
+    mulhilo32(PHILOX_M1, c2, &hi1, &lo1);
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n1 = lo1;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    uint32_t n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+double oracle_uniform(uint64_t seed, uint64_t instance, uint64_t j) {
+  uint32_t ctr[4] = {(uint32_t)j, (uint32_t)instance, (uint32_t)(instance >> 32), 0u};
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t x[4];
+  oracle_philox4x32_10(ctr, key, x);
+  uint64_t bits53 = ((uint64_t)x[0] << 21) | (uint64_t)(x[1] >> 11);
+  return ((double)bits53 + 0.5) * 0x1.0p-53;
+}
+
+void oracle_uniforms(uint64_t seed, uint64_t instance, int64_t n, double* u) {
+  for (int64_t j = 0; j < n; ++j) u[j] = oracle_uniform(seed, instance, (uint64_t)j);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Algorithm 1: unblocked right-looking non-Hermitian sampler (real).          */
+/* A: column-major n x n with leading dimension ld, overwritten with the       */
+/* in-place LU factors of K - 1_{Y^c}. u: n uniforms. keep: n bytes (0/1).     */
+/* pivots: n final pivots d_j (after the -1 of a rejection). Returns |Y|.      */
+/* ------------------------------------------------------------------------- */
+int64_t oracle_dpp_lu_r64(int64_t n, double* A, int64_t ld, const double* u,
+                          uint8_t* keep, double* pivots, double* logp) {
+  double lp = 0.0;
+  int64_t kept = 0;
+  for (int64_t j = 0; j < n; ++j) {
+    double d = A[j + j * ld];
+    if (u[j] < d) {
+      keep[j] = 1;
+      ++kept;
+    } else {
+      keep[j] = 0;
+      d -= 1.0;
+      A[j + j * ld] = d;
+    }
+    pivots[j] = d;
+    lp += log(fabs(d));
+    for (int64_t i = j + 1; i < n; ++i) A[i + j * ld] /= d;
+#pragma omp parallel for schedule(static)
+    for (int64_t k = j + 1; k < n; ++k) {
+      const double ajk = A[j + k * ld];
+      for (int64_t i = j + 1; i < n; ++i) A[i + k * ld] -= A[i + j * ld] * ajk;
+    }
+  }
+  *logp = lp;
+  return kept;
+}
+
+/* Algorithm 1, complex: keep iff u_j < Re(d_j); log|d_j| uses the modulus. */
+int64_t oracle_dpp_lu_c128(int64_t n, double complex* A, int64_t ld,
+                           const double* u, uint8_t* keep,
+                           double complex* pivots, double* logp) {
+  double lp = 0.0;
+  int64_t kept = 0;
+  for (int64_t j = 0; j < n; ++j) {
+    double complex d = A[j + j * ld];
+    if (u[j] < creal(d)) {
+      keep[j] = 1;
+      ++kept;
+    } else {
+      keep[j] = 0;
+      d -= 1.0;
+      A[j + j * ld] = d;
+    }
+    pivots[j] = d;
+    lp += log(cabs(d));
+    for (int64_t i = j + 1; i < n; ++i) A[i + j * ld] /= d;
+#pragma omp parallel for schedule(static)
+    for (int64_t k = j + 1; k < n; ++k) {
+      const double complex ajk = A[j + k * ld];
+      for (int64_t i = j + 1; i < n; ++i) A[i + k * ld] -= A[i + j * ld] * ajk;
+    }
+  }
+  *logp = lp;
+  return kept;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Hermitian specialisation (LDL^H): only the lower triangle of A is read and  */
+/* written. On return the strictly-lower part holds L (unit diagonal implied)  */
+/* and the diagonal holds D, the final real pivots.                            */
+/* ------------------------------------------------------------------------- */
+int64_t oracle_dpp_ldl_r64(int64_t n, double* A, int64_t ld, const double* u,
+                           uint8_t* keep, double* pivots, double* logp) {
+  double lp = 0.0;
+  int64_t kept = 0;
+  for (int64_t j = 0; j < n; ++j) {
+    double d = A[j + j * ld];
+    if (u[j] < d) {
+      keep[j] = 1;
+      ++kept;
+    } else {
+      keep[j] = 0;
+      d -= 1.0;
+      A[j + j * ld] = d;
+    }
+    pivots[j] = d;
+    lp += log(fabs(d));
+    for (int64_t i = j + 1; i < n; ++i) A[i + j * ld] /= d; /* L_ij */
+    /* A_ik -= L_ij * d_j * L_kj for i >= k > j (lower triangle) */
+#pragma omp parallel for schedule(static)
+    for (int64_t k = j + 1; k < n; ++k) {
+      const double c = d * A[k + j * ld];
+      for (int64_t i = k; i < n; ++i) A[i + k * ld] -= A[i + j * ld] * c;
+    }
+  }
+  *logp = lp;
+  return kept;
+}
+
+int64_t oracle_dpp_ldl_c128(int64_t n, double complex* A, int64_t ld,
+                            const double* u, uint8_t* keep, double* pivots,
+                            double* logp) {
+  double lp = 0.0;
+  int64_t kept = 0;
+  for (int64_t j = 0; j < n; ++j) {
+    double d = creal(A[j + j * ld]); /* D is real for Hermitian K */
+    if (u[j] < d) {
+      keep[j] = 1;
+      ++kept;
+    } else {
+      keep[j] = 0;
+      d -= 1.0;
+    }
+    A[j + j * ld] = d;
+    pivots[j] = d;
+    lp += log(fabs(d));
+    for (int64_t i = j + 1; i < n; ++i) A[i + j * ld] /= d; /* L_ij */
+    /* A_ik -= L_ij * d_j * conj(L_kj) for i >= k > j */
+#pragma omp parallel for schedule(static)
+    for (int64_t k = j + 1; k < n; ++k) {
+      const double complex c = d * conj(A[k + j * ld]);
+      for (int64_t i = k; i < n; ++i) A[i + k * ld] -= A[i + j * ld] * c;
+    }
+  }
+  *logp = lp;
+  return kept;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Greedy maximum-likelihood variant (the remark after the proof of Prop. 1):  */
+/* each Bernoulli draw is replaced by its more likely outcome. Reading: keep   */
+/* iff Re(d_j) > 1/2 (a tie rejects). Real Hermitian form.                     */
+/* ------------------------------------------------------------------------- */
+int64_t oracle_dpp_ldl_greedy_r64(int64_t n, double* A, int64_t ld,
+                                  uint8_t* keep, double* pivots, double* logp) {
+  double lp = 0.0;
+  int64_t kept = 0;
+  for (int64_t j = 0; j < n; ++j) {
+    double d = A[j + j * ld];
+    if (d > 0.5) {
+      keep[j] = 1;
+      ++kept;
+    } else {
+      keep[j] = 0;
+      d -= 1.0;
+      A[j + j * ld] = d;
+    }
+    pivots[j] = d;
+    lp += log(fabs(d));
+    for (int64_t i = j + 1; i < n; ++i) A[i + j * ld] /= d;
+#pragma omp parallel for schedule(static)
+    for (int64_t k = j + 1; k < n; ++k) {
+      const double c = d * A[k + j * ld];
+      for (int64_t i = k; i < n; ++i) A[i + k * ld] -= A[i + j * ld] * c;
+    }
+  }
+  *logp = lp;
+  return kept;
+}
+
+int oracle_num_threads(void) {
+#ifdef _OPENMP
+  extern int omp_get_max_threads(void);
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}

@@ -1,0 +1,184 @@
+"""Seeded synthetic marginal kernels shaped like the paper's workloads.
+
+This module only GENERATES inputs; it holds none of the sampler's arithmetic and
+is shared by the CUDA-path tests, the oracle tests and the benchmark. Every
+generator is deterministic in its seed (numpy PCG64 Gaussians/uniforms); large
+orthogonal factors may be computed with torch on a device, which changes only
+rounding, never the distribution.
+
+Kernels (all FP64 / complex128, returned as dense n x n arrays):
+
+* ``hermitian_kernel``: K = Q diag(lam) Q^H with Q Haar-distributed (QR of a
+  Gaussian matrix with the R-diagonal phase correction of Mezzadri 2007) and
+  lam ~ Uniform(0,1), Beta(1/2,1/2), or {0,1} with exactly ``rank`` ones
+  (a projection kernel). Hermitian kernels with spectrum in [0,1] are admissible
+  (Macchi; Section 2 of the paper).
+* ``ust_grid_kernel``: the transfer-current kernel K = B_r^T (B_r B_r^T)^{-1}
+  B_r of the d x d grid graph (unit weights, vertex 0 grounded); DPP(K) is the
+  uniform spanning-tree measure (Burton-Pemantle; Figure 1 of the paper).
+* ``lu_similarity_kernel``: K = D^{-1} S D with S Hermitian as above and D a
+  log-normal diagonal; diagonal similarity preserves every principal minor, so
+  DPP(K) = DPP(S) (Prop. 2 of the paper).
+* ``lensemble_kernel``: K = L (L + I)^{-1}, L = Phi Phi^T, Phi with unit-norm
+  Gaussian rows scaled by LogUniform(0.1, 10) qualities, formed through the
+  push-through identity K = Phi (Phi^T Phi + I)^{-1} Phi^T.
+"""
+from __future__ import annotations
+
+import math
+from typing import List, Optional, Tuple
+
+import numpy as np
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.default_rng(np.random.PCG64(seed))
+
+
+def gaussian_matrix(n: int, seed: int, complex_: bool = False) -> np.ndarray:
+    rng = _rng(seed)
+    if complex_:
+        re = rng.standard_normal((n, n))
+        im = rng.standard_normal((n, n))
+        return (re + 1j * im) / math.sqrt(2.0)
+    return rng.standard_normal((n, n))
+
+
+def _haar_from_gaussian(G, device: Optional[str] = None):
+    """Q from QR of G with R-diagonal phase correction (Mezzadri 2007)."""
+    if device is not None and device != "cpu":
+        import torch
+        Gt = torch.from_numpy(G).to(device)
+        Q, R = torch.linalg.qr(Gt)
+        d = torch.diagonal(R)
+        ph = d / d.abs()
+        Q = Q * ph.unsqueeze(0)
+        return Q
+    Q, R = np.linalg.qr(G)
+    d = np.diagonal(R)
+    return Q * (d / np.abs(d))[None, :]
+
+
+def spectrum(n: int, kind: str, seed: int, rank: Optional[int] = None) -> np.ndarray:
+    rng = _rng(seed + 7919)
+    if kind == "uniform":
+        return rng.uniform(0.0, 1.0, n)
+    if kind == "beta":
+        return rng.beta(0.5, 0.5, n)
+    if kind == "projection":
+        k = n // 4 if rank is None else rank
+        lam = np.zeros(n)
+        lam[rng.permutation(n)[:k]] = 1.0
+        return lam
+    raise ValueError(kind)
+
+
+def hermitian_kernel(n: int, seed: int = 0, kind: str = "uniform",
+                     complex_: bool = False, rank: Optional[int] = None,
+                     device: Optional[str] = None, return_torch: bool = False):
+    """K = Q diag(lam) Q^H, Q Haar (orthogonal or unitary), lam per ``kind``."""
+    G = gaussian_matrix(n, seed, complex_)
+    lam = spectrum(n, kind, seed, rank)
+    Q = _haar_from_gaussian(G, device)
+    if device is not None and device != "cpu":
+        import torch
+        lt = torch.from_numpy(lam).to(Q.device, dtype=Q.real.dtype)
+        K = (Q * lt.to(Q.dtype).unsqueeze(0)) @ Q.conj().T
+        K = 0.5 * (K + K.conj().T)
+        if return_torch:
+            return K
+        return K.cpu().numpy()
+    K = (Q * lam[None, :]) @ Q.conj().T
+    return 0.5 * (K + K.conj().T)
+
+
+def diagonal_kernel(n: int, seed: int = 0) -> np.ndarray:
+    return np.diag(_rng(seed).uniform(0.0, 1.0, n))
+
+
+# --------------------------------------------------------------------------
+# Uniform spanning trees of the d x d grid graph
+# --------------------------------------------------------------------------
+def grid_edges(d: int) -> np.ndarray:
+    """Edges of the d x d grid (vertex r*d + c): right edges then down edges."""
+    edges = []
+    for r in range(d):
+        for c in range(d - 1):
+            edges.append((r * d + c, r * d + c + 1))
+    for r in range(d - 1):
+        for c in range(d):
+            edges.append((r * d + c, (r + 1) * d + c))
+    return np.array(edges, dtype=np.int64)
+
+
+def ust_grid_kernel(d: int, device: Optional[str] = None) -> Tuple[np.ndarray, np.ndarray, int]:
+    """Transfer-current kernel of the d x d grid: (K, edges, n_vertices).
+
+    n = 2 d (d - 1) edges, rank d^2 - 1. Unit weights, vertex 0 grounded.
+    """
+    edges = grid_edges(d)
+    V, E = d * d, len(edges)
+    B = np.zeros((V, E))
+    B[edges[:, 0], np.arange(E)] = 1.0
+    B[edges[:, 1], np.arange(E)] = -1.0
+    Br = B[1:, :]
+    if device is not None and device != "cpu":
+        import torch
+        Bt = torch.from_numpy(Br).to(device)
+        Lr = Bt @ Bt.T
+        X = torch.linalg.solve(Lr, Bt)
+        K = Bt.T @ X
+        K = 0.5 * (K + K.T)
+        return K.cpu().numpy(), edges, V
+    Lr = Br @ Br.T
+    X = np.linalg.solve(Lr, Br)
+    K = Br.T @ X
+    return 0.5 * (K + K.T), edges, V
+
+
+def grid_spanning_tree_log_count(d: int) -> float:
+    """log tau(d x d grid) by Kirchhoff: product of the nonzero Laplacian
+    eigenvalues (sums of path-graph eigenvalues 2 - 2 cos(pi a / d)) over V."""
+    lam = 2.0 - 2.0 * np.cos(np.pi * np.arange(d) / d)
+    s = lam[:, None] + lam[None, :]
+    s = s.ravel()[1:]  # drop the (0, 0) zero eigenvalue
+    return float(np.sum(np.log(s)) - math.log(d * d))
+
+
+# --------------------------------------------------------------------------
+# Non-Hermitian kernels with a known Hermitian twin
+# --------------------------------------------------------------------------
+def lu_similarity_kernel(n: int, seed: int = 0, sigma: float = 0.5,
+                         device: Optional[str] = None):
+    """(K, S): S = Q diag(U(0,1)) Q^T, K = D^{-1} S D, D = diag(exp(N(0, sigma^2)))."""
+    S = hermitian_kernel(n, seed, "uniform", device=device)
+    dvec = np.exp(sigma * _rng(seed + 104729).standard_normal(n))
+    K = S * (dvec[None, :] / dvec[:, None])
+    return K, S
+
+
+# --------------------------------------------------------------------------
+# Batched L-ensembles
+# --------------------------------------------------------------------------
+def lensemble_sizes(batch: int, seed: int = 0, nmin: int = 64, nmax: int = 1024) -> np.ndarray:
+    return _rng(seed).integers(nmin, nmax + 1, size=batch)
+
+
+def lensemble_kernel(n: int, seed: int, features: int = 64,
+                     qmin: float = 0.1, qmax: float = 10.0) -> np.ndarray:
+    """K = Phi (Phi^T Phi + I)^{-1} Phi^T = L (L + I)^{-1}, L = Phi Phi^T."""
+    rng = _rng(seed)
+    G = rng.standard_normal((n, features))
+    G /= np.linalg.norm(G, axis=1, keepdims=True)
+    q = np.exp(rng.uniform(math.log(qmin), math.log(qmax), n))
+    Phi = G * q[:, None]
+    M = Phi.T @ Phi + np.eye(features)
+    K = Phi @ np.linalg.solve(M, Phi.T)
+    return 0.5 * (K + K.T)
+
+
+def lensemble_batch(batch: int, seed: int = 0, nmin: int = 64, nmax: int = 1024,
+                    features: int = 64) -> List[np.ndarray]:
+    sizes = lensemble_sizes(batch, seed, nmin, nmax)
+    return [lensemble_kernel(int(m), seed * 1000003 + i + 1, features)
+            for i, m in enumerate(sizes)]
