@@ -1,0 +1,179 @@
+/*
+ * dpp.h — C ABI of the GB300 (sm_103a) factorization-based DPP sampler.
+ *
+ * Method: J. Poulson, "High-performance sampling of generic Determinantal
+ * Point Processes" (arXiv:1905.00165).
+ *   - A DPP with marginal kernel K (n x n, complex or real) is defined by
+ *     P[Y subset of the sample] = det(K_Y) (Section 2, Definition).
+ *   - Sampling is an unpivoted right-looking LU factorization of K in which
+ *     the j-th pivot d_j (the conditional inclusion probability of index j)
+ *     drives a Bernoulli draw: keep j, or subtract 1 from the pivot and reject
+ *     j; then the column is scaled and the Schur complement updated
+ *     (Algorithm 1, Theorem 1, Props. 3-5). For Hermitian K the same process
+ *     is an unpivoted LDL^H factorization with half the work (Theorem 1).
+ *   - The blocked form factors a diagonal block with the sequential decisions,
+ *     solves the two panels against it and applies a rank-nb Schur update
+ *     (Algorithms 3 and 4, Section 4).
+ *   - log P(Y) = sum_j log|d_j| over the final pivots, and on return the
+ *     factored matrix holds the LU (LDL^H) factors of K - 1_{Y^c}
+ *     (Algorithm 1's caption; Theorem 1).
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are column-major: entry (i, j) is at ptr[i + j * ld], ld >= n.
+ *     Hermitian entry points read (and write) only the lower triangle.
+ *   - Every pointer argument named "device" must point to device memory of the
+ *     current CUDA device. The caller owns every buffer; the library allocates
+ *     nothing per call and never writes the input K (unless factor_out == K).
+ *   - All work is enqueued on `stream` (a cudaStream_t passed as void*, NULL =
+ *     legacy default stream) and is asynchronous: results are valid once the
+ *     stream has been synchronised. Calls are capture-safe (no synchronisation
+ *     and no allocation inside).
+ *   - Uniforms: unless an explicit `uniforms` array is given, u_j is drawn from
+ *     Philox4x32-10 (Salmon et al., SC'11) with key = (seed & 0xffffffff,
+ *     seed >> 32), counter = (j, instance & 0xffffffff, instance >> 32, 0),
+ *     and u_j = ((x0 << 21 | x1 >> 11) + 0.5) * 2^-53, which lies in (0, 1).
+ *   - Decision: index j is kept iff u_j < Re(d_j); otherwise d_j -= 1.
+ *     Hermitian pivots are real (the imaginary part is dropped).
+ *   - Host-detectable errors are returned as dpp_status (and described by
+ *     dpp_last_error()); nothing is enqueued when a call returns an error.
+ *     Errors detected on the device are OR-ed into dpp_result.status.
+ */
+#ifndef DPP_H_
+#define DPP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DPP_ABI_VERSION 1
+
+typedef enum {
+  DPP_OK = 0,
+  DPP_ERR_INVALID_ARG = 1, /* bad size, pointer, alignment or enum       */
+  DPP_ERR_CUDA = 2,        /* a CUDA runtime call failed                 */
+  DPP_ERR_WORKSPACE = 3,   /* workspace too small or misaligned (256 B) */
+  DPP_ERR_UNSUPPORTED = 4  /* combination not implemented (see below)   */
+} dpp_status;
+
+/* Element type of K, of factor_out and of dK. */
+typedef enum {
+  DPP_R64 = 0,  /* double                                    */
+  DPP_C128 = 1  /* double complex, interleaved (re, im) pairs */
+} dpp_dtype;
+
+/* Arithmetic of the trailing Schur-complement update (step a3).
+ *   DPP_PREC_FP64   : everything in FP64.
+ *   DPP_PREC_3XTF32 : FP32 working copy; trailing update as three TF32
+ *                     tensor-core products (hi*hi + hi*lo + lo*hi) with FP32
+ *                     accumulation; pivots, decisions and log P in FP64; any
+ *                     pivot whose uniform lies within the propagated error
+ *                     bound of its threshold is recomputed in FP64 from the
+ *                     original K before its decision.                      */
+typedef enum {
+  DPP_PREC_FP64 = 0,
+  DPP_PREC_3XTF32 = 1
+} dpp_precision;
+
+/* Bits of dpp_result.status (device-side outcome of one draw). */
+#define DPP_RES_OK 0
+#define DPP_RES_NONFINITE 1     /* a pivot was NaN or Inf                     */
+#define DPP_RES_TIMEOUT 2       /* a bounded device wait expired             */
+#define DPP_RES_INADMISSIBLE 4  /* warning: a pivot left [-tol, 1 + tol]     */
+#define DPP_RES_RECOMPUTE 8     /* warning: an FP64 recompute did not reach
+                                   its target accuracy; the decision used the
+                                   best available value                       */
+
+/* Device-resident outcome of one draw (one per instance for batched calls). */
+typedef struct {
+  int32_t status;         /* DPP_RES_* bits                                  */
+  int32_t n_kept;         /* |Y|                                             */
+  int32_t n_borderline;   /* pivots recomputed in FP64 (mixed precision)     */
+  int32_t n_out_of_range; /* pivots outside [-tol, 1 + tol] before decision  */
+  double logp;            /* log P(Y) = sum_j log|d_j|                       */
+  double max_err_ratio;   /* mixed precision: max over recomputed pivots of
+                             |d_mixed - d_fp64| / tau_j (tau = error bound)  */
+} dpp_result;
+
+/* Operation selector for dpp_workspace_size. */
+typedef enum {
+  DPP_OP_SAMPLE_HERMITIAN = 0,
+  DPP_OP_SAMPLE_LU = 1,
+  DPP_OP_LOGPROB_BACKWARD = 2
+} dpp_op;
+
+/* Bytes of device workspace needed by one call of `op` at order n.
+ * Returns 0 for an unsupported combination. The workspace pointer passed to
+ * the call must be 256-byte aligned and at least this large. */
+size_t dpp_workspace_size(int32_t op, int64_t n, int32_t dtype,
+                          int32_t precision, int32_t hermitian);
+
+/* Sample DPP(K) for Hermitian K (LDL^H form of Algorithms 1 and 4).
+ *   K          device, n x n column-major (ld >= n), lower triangle read.
+ *   dtype      DPP_R64 or DPP_C128.
+ *   precision  DPP_PREC_FP64 (R64, C128) or DPP_PREC_3XTF32 (R64).
+ *   seed, instance  Philox stream (ignored if uniforms != NULL).
+ *   uniforms   device, n doubles, or NULL for Philox.
+ *   keep       device, n bytes: keep[j] = 1 iff j is in the sample.
+ *   factor_out device n x ld of dtype, or NULL. Receives L (strictly lower,
+ *              unit diagonal implied) and D (diagonal) of K - 1_{Y^c}. May
+ *              equal K for an in-place factorization. With 3XTF32 it receives
+ *              the mixed-precision factor (pivots are the FP64 ones).
+ *   pivots     device, n doubles, or NULL: final pivots d_j (after -1).
+ *   result     device, one dpp_result.
+ *   workspace  device, >= dpp_workspace_size(DPP_OP_SAMPLE_HERMITIAN, ...).
+ * Returns DPP_OK once the work is enqueued. */
+dpp_status dpp_sample_hermitian(const void* K, int64_t n, int64_t ld,
+                                int32_t dtype, int32_t precision,
+                                uint64_t seed, uint64_t instance,
+                                const double* uniforms, uint8_t* keep,
+                                void* factor_out, double* pivots,
+                                dpp_result* result, void* workspace,
+                                size_t workspace_bytes, void* stream);
+
+/* Sample DPP(K) for a general (non-Hermitian) K (Algorithm 1, blocked as in
+ * Algorithm 4). Same arguments as dpp_sample_hermitian, except that the whole
+ * of K is read, factor_out receives L (strictly lower, unit diagonal) and U
+ * (upper, with the pivots on the diagonal), and `pivots`, when not NULL,
+ * receives n doubles for DPP_R64 and 2n doubles (re, im) for DPP_C128.
+ * Precision: DPP_PREC_FP64 only. */
+dpp_status dpp_sample_lu(const void* K, int64_t n, int64_t ld, int32_t dtype,
+                         int32_t precision, uint64_t seed, uint64_t instance,
+                         const double* uniforms, uint8_t* keep,
+                         void* factor_out, double* pivots, dpp_result* result,
+                         void* workspace, size_t workspace_bytes,
+                         void* stream);
+
+/* Adjoint of log P(Y) with the sample held fixed:
+ *   dK = g * (K - 1_{Y^c})^{-H}          (g = *grad_logp, a device scalar)
+ * which is the derivative of log|det(K - 1_{Y^c})| (Theorem 1's likelihood).
+ * The factors are recomputed (no Bernoulli draws: the decisions are `keep`).
+ *   hermitian  nonzero: K Hermitian, lower triangle read; dK is returned as a
+ *              full (Hermitian) matrix.
+ *   dK         device, n x ld_dk of dtype (full matrix written).
+ * Precision: DPP_PREC_FP64. */
+dpp_status dpp_logprob_backward(const void* K, int64_t n, int64_t ld,
+                                int32_t dtype, int32_t precision,
+                                int32_t hermitian, const uint8_t* keep,
+                                const double* grad_logp, void* dK,
+                                int64_t ld_dk, void* workspace,
+                                size_t workspace_bytes, void* stream);
+
+/* Fill `out` (device, n doubles) with the Philox uniforms u_0..u_{n-1} that
+ * the samplers use for (seed, instance). */
+dpp_status dpp_uniforms(uint64_t seed, uint64_t instance, int64_t n,
+                        double* out, void* stream);
+
+/* Thread-local description of the last host-side error ("" if none). */
+const char* dpp_last_error(void);
+
+/* DPP_ABI_VERSION of the loaded library. */
+int32_t dpp_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DPP_H_ */

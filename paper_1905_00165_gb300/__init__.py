@@ -1,0 +1,197 @@
+"""GB300-native factorization-based DPP sampler (arXiv:1905.00165).
+
+Thin torch-facing wrappers over the C ABI in ``include/dpp.h``. torch provides
+device memory and streams; the sampler itself runs in the library's sm_103a
+kernels. Functions here only marshal arguments (column-major views, workspace
+buffers, the current stream).
+"""
+from __future__ import annotations
+
+from typing import Optional
+
+from . import _lib
+from ._lib import (DPP_C128, DPP_OP_LOGPROB_BACKWARD, DPP_OP_SAMPLE_HERMITIAN,
+                   DPP_OP_SAMPLE_LU, DPP_PREC_3XTF32, DPP_PREC_FP64, DPP_R64,
+                   DPPError, PRECISIONS, decode_result, load, workspace_size)
+
+__all__ = ["sample_hermitian", "sample_lu", "logprob_backward", "uniforms",
+           "Sample", "DPPLogProb", "DPPError", "load", "workspace_size"]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dtype_code(t) -> int:
+    torch = _torch()
+    if t.dtype == torch.float64:
+        return DPP_R64
+    if t.dtype == torch.complex128:
+        return DPP_C128
+    raise TypeError(f"K must be float64 or complex128, got {t.dtype}")
+
+
+def colmajor(K):
+    """(tensor, ld): a tensor whose storage holds K column-major."""
+    n = K.shape[0]
+    if K.dim() != 2 or K.shape[1] != n:
+        raise ValueError("K must be square")
+    if n == 0:
+        return K.contiguous(), 1
+    if K.stride(0) == 1 and K.stride(1) >= n:
+        return K, K.stride(1)
+    return K.t().contiguous().t(), n
+
+
+def empty_colmajor(n: int, dtype, device):
+    """An n x n tensor with column-major storage (ld = n)."""
+    torch = _torch()
+    return torch.empty((n, n), dtype=dtype, device=device).t()
+
+
+def _stream(device):
+    torch = _torch()
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+class Sample:
+    """Device-resident outcome of one draw. ``result()`` synchronises."""
+
+    def __init__(self, keep, pivots, factor, raw):
+        self.keep = keep
+        self.pivots = pivots
+        self.factor = factor
+        self.raw = raw
+        self._res = None
+
+    def result(self) -> dict:
+        if self._res is None:
+            self._res = decode_result(bytes(self.raw.cpu().numpy().tobytes()))
+        return self._res
+
+    @property
+    def logp(self) -> float:
+        return self.result()["logp"]
+
+    @property
+    def status(self) -> int:
+        return self.result()["status"]
+
+
+def _sample(hermitian: bool, K, seed: int, instance: int, precision: str, uniforms,
+            factor: bool, workspace, out_keep=None):
+    torch = _torch()
+    L = load()
+    if not K.is_cuda:
+        raise ValueError("K must be a CUDA tensor")
+    prec = PRECISIONS[precision]
+    dt = _dtype_code(K)
+    Kc, ld = colmajor(K)
+    n = K.shape[0]
+    dev = K.device
+    keep = out_keep if out_keep is not None else torch.empty(n, dtype=torch.uint8, device=dev)
+    npiv = 2 * n if (not hermitian and dt == DPP_C128) else n
+    piv = torch.empty(max(npiv, 1), dtype=torch.float64, device=dev)
+    fac = None
+    if factor:
+        # factor_out shares K's leading dimension: use ld = n for both
+        if ld != n and n:
+            Kc, ld = Kc.t().contiguous().t(), n
+        fac = empty_colmajor(n, K.dtype, dev)
+    raw = torch.zeros(_lib.RESULT_BYTES, dtype=torch.uint8, device=dev)
+    op = DPP_OP_SAMPLE_HERMITIAN if hermitian else DPP_OP_SAMPLE_LU
+    need = workspace_size(op, n, dt, prec, 1 if hermitian else 0)
+    if need == 0:
+        raise DPPError(_lib.DPP_ERR_UNSUPPORTED, f"unsupported: dtype={K.dtype} precision={precision}")
+    ws = workspace if workspace is not None else torch.empty(need, dtype=torch.uint8, device=dev)
+    if uniforms is not None:
+        uniforms = uniforms.to(device=dev, dtype=torch.float64).contiguous()
+        assert uniforms.numel() == n
+    f = L.dpp_sample_hermitian if hermitian else L.dpp_sample_lu
+    st = f(Kc.data_ptr() if n else None, n, ld, dt, prec, seed, instance,
+           None if uniforms is None else uniforms.data_ptr(), keep.data_ptr() if n else None,
+           None if fac is None else fac.data_ptr(), piv.data_ptr(), raw.data_ptr(),
+           ws.data_ptr(), ws.numel(), _stream(dev))
+    _lib.check(st)
+    return Sample(keep, piv[:npiv], fac, raw)
+
+
+def sample_hermitian(K, seed: int = 0, instance: int = 0, precision: str = "fp64",
+                     uniforms=None, factor: bool = False, workspace=None) -> Sample:
+    """Draw Y ~ DPP(K) for Hermitian K (LDL^H form; lower triangle read)."""
+    return _sample(True, K, seed, instance, precision, uniforms, factor, workspace)
+
+
+def sample_lu(K, seed: int = 0, instance: int = 0, precision: str = "fp64",
+              uniforms=None, factor: bool = False, workspace=None) -> Sample:
+    """Draw Y ~ DPP(K) for general K (LU form of Algorithm 1)."""
+    return _sample(False, K, seed, instance, precision, uniforms, factor, workspace)
+
+
+def uniforms(seed: int, instance: int, n: int, device="cuda"):
+    """The Philox uniforms u_0..u_{n-1} the samplers draw for (seed, instance)."""
+    torch = _torch()
+    out = torch.empty(max(n, 1), dtype=torch.float64, device=device)
+    _lib.check(load().dpp_uniforms(seed, instance, n, out.data_ptr(), _stream(out.device)))
+    return out[:n]
+
+
+def logprob_backward(K, keep, grad_logp=None, hermitian: bool = True, workspace=None):
+    """dK = g (K - 1_{Y^c})^{-H} (the adjoint of log P(Y) with Y fixed)."""
+    torch = _torch()
+    L = load()
+    dt = _dtype_code(K)
+    Kc, ld = colmajor(K)
+    n = K.shape[0]
+    dev = K.device
+    g = grad_logp if grad_logp is not None else torch.ones((), dtype=torch.float64, device=dev)
+    g = g.to(device=dev, dtype=torch.float64).reshape(1).contiguous()
+    dK = empty_colmajor(n, K.dtype, dev)
+    ldd = dK.stride(1) if n else 1
+    need = workspace_size(DPP_OP_LOGPROB_BACKWARD, n, dt, DPP_PREC_FP64, 1 if hermitian else 0)
+    if need == 0:
+        raise DPPError(_lib.DPP_ERR_UNSUPPORTED, "unsupported backward configuration")
+    ws = workspace if workspace is not None else torch.empty(need, dtype=torch.uint8, device=dev)
+    keep = keep.to(device=dev, dtype=torch.uint8).contiguous()
+    st = L.dpp_logprob_backward(Kc.data_ptr() if n else None, n, ld, dt, DPP_PREC_FP64,
+                                1 if hermitian else 0, keep.data_ptr() if n else None,
+                                g.data_ptr(), dK.data_ptr() if n else None, ldd,
+                                ws.data_ptr(), ws.numel(), _stream(dev))
+    _lib.check(st)
+    return dK
+
+
+def _make_autograd():
+    torch = _torch()
+
+    class _DPPLogProb(torch.autograd.Function):
+        """log P(Y) = log|det(K - 1_{Y^c})| for a fixed sample Y.
+
+        forward: the factorization with the decisions forced to ``keep``
+        (the sampler's own kernels, uniforms that force each decision).
+        backward: dK = g (K - 1_{Y^c})^{-H} from the library's adjoint, with
+        the factors recomputed rather than stored.
+        """
+
+        @staticmethod
+        def forward(ctx, K, keep, hermitian: bool = True):
+            u = torch.where(keep.to(torch.bool), torch.tensor(-1e300, dtype=torch.float64, device=K.device),
+                            torch.tensor(1e300, dtype=torch.float64, device=K.device))
+            s = _sample(hermitian, K.detach(), 0, 0, "fp64", u, False, None)
+            ctx.save_for_backward(K.detach(), keep)
+            ctx.hermitian = hermitian
+            raw = s.raw
+            logp = raw[16:24].view(torch.float64).reshape(())
+            return logp.clone()
+
+        @staticmethod
+        def backward(ctx, g):
+            K, keep = ctx.saved_tensors
+            dK = logprob_backward(K, keep, g.detach(), hermitian=ctx.hermitian)
+            return dK, None, None
+
+    return _DPPLogProb
+
+
+DPPLogProb = _make_autograd()

@@ -1,0 +1,90 @@
+"""ctypes binding over libdpp_gb300.so (the C ABI declared in include/dpp.h).
+
+Argument marshalling only: every step of the sampler runs in the library's
+CUDA kernels. torch supplies device memory and the current stream. There is no
+fallback: if the library is missing or cannot run, the call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import struct
+from typing import Optional
+
+from . import build as _build
+
+# enums mirrored from include/dpp.h
+DPP_OK, DPP_ERR_INVALID_ARG, DPP_ERR_CUDA, DPP_ERR_WORKSPACE, DPP_ERR_UNSUPPORTED = range(5)
+DPP_R64, DPP_C128 = 0, 1
+DPP_PREC_FP64, DPP_PREC_3XTF32 = 0, 1
+DPP_OP_SAMPLE_HERMITIAN, DPP_OP_SAMPLE_LU, DPP_OP_LOGPROB_BACKWARD = 0, 1, 2
+DPP_RES_NONFINITE, DPP_RES_TIMEOUT, DPP_RES_INADMISSIBLE, DPP_RES_RECOMPUTE = 1, 2, 4, 8
+RESULT_BYTES = 32
+RESULT_FMT = "<iiiidd"
+
+PRECISIONS = {"fp64": DPP_PREC_FP64, "3xtf32": DPP_PREC_3XTF32}
+
+_lib = None
+
+
+class DPPError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"dpp status {status}: {msg}")
+        self.status = status
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(path: Optional[str] = None):
+    """Load the shared library (build it first with ``build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"{path} is missing: build the CUDA library first "
+            "(python -c 'import __graft_entry__ as g; g.build()')")
+    L = ctypes.CDLL(path)
+    vp, i32, i64, u64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_size_t
+    L.dpp_abi_version.argtypes = []
+    L.dpp_abi_version.restype = i32
+    L.dpp_last_error.argtypes = []
+    L.dpp_last_error.restype = ctypes.c_char_p
+    L.dpp_workspace_size.argtypes = [i32, i64, i32, i32, i32]
+    L.dpp_workspace_size.restype = sz
+    for name in ("dpp_sample_hermitian", "dpp_sample_lu"):
+        f = getattr(L, name)
+        f.argtypes = [vp, i64, i64, i32, i32, u64, u64, vp, vp, vp, vp, vp, vp, sz, vp]
+        f.restype = i32
+    L.dpp_logprob_backward.argtypes = [vp, i64, i64, i32, i32, i32, vp, vp, vp, i64, vp, sz, vp]
+    L.dpp_logprob_backward.restype = i32
+    L.dpp_uniforms.argtypes = [u64, u64, i64, vp, vp]
+    L.dpp_uniforms.restype = i32
+    _lib = L
+    return L
+
+
+def last_error() -> str:
+    return load().dpp_last_error().decode()
+
+
+def check(status: int) -> None:
+    if status != DPP_OK:
+        raise DPPError(status, last_error())
+
+
+def workspace_size(op: int, n: int, dtype: int, precision: int, hermitian: int = 1) -> int:
+    return int(load().dpp_workspace_size(op, n, dtype, precision, hermitian))
+
+
+def decode_result(raw: bytes) -> dict:
+    status, kept, border, oor, logp, ratio = struct.unpack(RESULT_FMT, raw)
+    return {"status": status, "n_kept": kept, "n_borderline": border,
+            "n_out_of_range": oor, "logp": logp, "max_err_ratio": ratio}
+
+
+def ptr(t) -> Optional[int]:
+    return None if t is None else t.data_ptr()

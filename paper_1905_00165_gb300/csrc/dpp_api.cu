@@ -1,0 +1,189 @@
+// C ABI of the sampler library: argument validation, workspace carving and
+// dispatch to the FP64 / mixed-precision / adjoint implementations.
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+
+#include "dpp.h"
+#include "dpp_internal.h"
+
+namespace dpp {
+
+static thread_local std::string g_last_error;
+
+static dpp_status fail(dpp_status s, const char* msg) {
+  g_last_error = msg;
+  return s;
+}
+
+static dpp_status fail_cuda(cudaError_t e, const char* where) {
+  char buf[256];
+  snprintf(buf, sizeof(buf), "%s: %s", where, cudaGetErrorString(e));
+  g_last_error = buf;
+  return DPP_ERR_CUDA;
+}
+
+cudaError_t dev_info(DevInfo* out) {
+  static thread_local DevInfo cache[64];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (cache[dev].device != dev) {
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    cache[dev].device = dev;
+    cache[dev].sm_count = sms;
+  }
+  *out = cache[dev];
+  return cudaSuccess;
+}
+
+static bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+// Validation shared by the two samplers.
+static dpp_status check_draw(const void* K, int64_t n, int64_t ld, int32_t dtype,
+                             uint8_t* keep, void* factor_out, dpp_result* result,
+                             void* workspace, size_t ws_bytes, size_t ws_need) {
+  if (n < 0) return fail(DPP_ERR_INVALID_ARG, "n must be >= 0");
+  if (n > (int64_t)0x7fffffff) return fail(DPP_ERR_INVALID_ARG, "n too large");
+  if (ld < (n > 1 ? n : 1)) return fail(DPP_ERR_INVALID_ARG, "ld must be >= max(1, n)");
+  if (dtype != DPP_R64 && dtype != DPP_C128) return fail(DPP_ERR_INVALID_ARG, "unknown dtype");
+  if (!result) return fail(DPP_ERR_INVALID_ARG, "result must not be NULL");
+  if (n > 0 && (!K || !keep)) return fail(DPP_ERR_INVALID_ARG, "K and keep must not be NULL");
+  const size_t esz = dtype == DPP_C128 ? 16 : 8;
+  if (n > 0 && !aligned(K, esz)) return fail(DPP_ERR_INVALID_ARG, "K misaligned");
+  if (factor_out && !aligned(factor_out, esz))
+    return fail(DPP_ERR_INVALID_ARG, "factor_out misaligned");
+  if (!aligned(result, 8)) return fail(DPP_ERR_INVALID_ARG, "result misaligned");
+  if (ws_need == 0) return fail(DPP_ERR_UNSUPPORTED, "unsupported dtype/precision combination");
+  if (!workspace || !aligned(workspace, 256))
+    return fail(DPP_ERR_WORKSPACE, "workspace must be non-NULL and 256-byte aligned");
+  if (ws_bytes < ws_need) return fail(DPP_ERR_WORKSPACE, "workspace too small");
+  return DPP_OK;
+}
+
+}  // namespace dpp
+
+using namespace dpp;
+
+extern "C" {
+
+int32_t dpp_abi_version(void) { return DPP_ABI_VERSION; }
+
+const char* dpp_last_error(void) { return g_last_error.c_str(); }
+
+size_t dpp_workspace_size(int32_t op, int64_t n, int32_t dtype, int32_t precision,
+                          int32_t hermitian) {
+  if (n < 0 || (dtype != DPP_R64 && dtype != DPP_C128)) return 0;
+  switch (op) {
+    case DPP_OP_SAMPLE_HERMITIAN:
+      if (precision == DPP_PREC_FP64) return ws_fp64(n, dtype, true, true);
+      if (precision == DPP_PREC_3XTF32 && dtype == DPP_R64) return ws_mixed(n);
+      return 0;
+    case DPP_OP_SAMPLE_LU:
+      if (precision == DPP_PREC_FP64) return ws_fp64(n, dtype, false, true);
+      return 0;
+    case DPP_OP_LOGPROB_BACKWARD:
+      if (precision == DPP_PREC_FP64) return ws_backward(n, dtype, hermitian != 0);
+      return 0;
+    default:
+      return 0;
+  }
+}
+
+static dpp_status sample_common(bool hermitian, const void* K, int64_t n, int64_t ld,
+                                int32_t dtype, int32_t precision, uint64_t seed,
+                                uint64_t instance, const double* uniforms, uint8_t* keep,
+                                void* factor_out, double* pivots, dpp_result* result,
+                                void* workspace, size_t ws_bytes, void* stream) {
+  g_last_error.clear();
+  const size_t need = dpp_workspace_size(hermitian ? DPP_OP_SAMPLE_HERMITIAN : DPP_OP_SAMPLE_LU,
+                                         n, dtype, precision, hermitian);
+  dpp_status st = check_draw(K, n, ld, dtype, keep, factor_out, result, workspace, ws_bytes, need);
+  if (st != DPP_OK) return st;
+  DrawArgs a;
+  a.K = K;
+  a.n = n;
+  a.ld = ld;
+  a.dtype = dtype;
+  a.seed = seed;
+  a.instance = instance;
+  a.uniforms = uniforms;
+  a.keep = keep;
+  a.factor_out = factor_out;
+  a.pivots_user = pivots;
+  a.result = result;
+  a.stream = static_cast<cudaStream_t>(stream);
+  Workspace ws;
+  ws.base = static_cast<char*>(workspace);
+  ws.size = ws_bytes;
+  cudaError_t e;
+  if (precision == DPP_PREC_FP64) {
+    e = sample_fp64(a, hermitian, ws);
+  } else {
+    if (factor_out == K && factor_out) {
+      // the mixed path reads K in FP64 for recomputes: it must stay intact
+      return fail(DPP_ERR_INVALID_ARG, "mixed precision cannot factor in place (factor_out == K)");
+    }
+    e = sample_mixed(a, ws);
+  }
+  if (e != cudaSuccess) return fail_cuda(e, hermitian ? "dpp_sample_hermitian" : "dpp_sample_lu");
+  return DPP_OK;
+}
+
+dpp_status dpp_sample_hermitian(const void* K, int64_t n, int64_t ld, int32_t dtype,
+                                int32_t precision, uint64_t seed, uint64_t instance,
+                                const double* uniforms, uint8_t* keep, void* factor_out,
+                                double* pivots, dpp_result* result, void* workspace,
+                                size_t workspace_bytes, void* stream) {
+  return sample_common(true, K, n, ld, dtype, precision, seed, instance, uniforms, keep,
+                       factor_out, pivots, result, workspace, workspace_bytes, stream);
+}
+
+dpp_status dpp_sample_lu(const void* K, int64_t n, int64_t ld, int32_t dtype, int32_t precision,
+                         uint64_t seed, uint64_t instance, const double* uniforms, uint8_t* keep,
+                         void* factor_out, double* pivots, dpp_result* result, void* workspace,
+                         size_t workspace_bytes, void* stream) {
+  return sample_common(false, K, n, ld, dtype, precision, seed, instance, uniforms, keep,
+                       factor_out, pivots, result, workspace, workspace_bytes, stream);
+}
+
+dpp_status dpp_logprob_backward(const void* K, int64_t n, int64_t ld, int32_t dtype,
+                                int32_t precision, int32_t hermitian, const uint8_t* keep,
+                                const double* grad_logp, void* dK, int64_t ld_dk,
+                                void* workspace, size_t workspace_bytes, void* stream) {
+  g_last_error.clear();
+  if (precision != DPP_PREC_FP64)
+    return fail(DPP_ERR_UNSUPPORTED, "dpp_logprob_backward supports DPP_PREC_FP64 only");
+  if (n < 0 || ld < (n > 1 ? n : 1) || ld_dk < (n > 1 ? n : 1))
+    return fail(DPP_ERR_INVALID_ARG, "bad n / ld / ld_dk");
+  if (dtype != DPP_R64 && dtype != DPP_C128) return fail(DPP_ERR_INVALID_ARG, "unknown dtype");
+  if (n > 0 && (!K || !keep || !grad_logp || !dK))
+    return fail(DPP_ERR_INVALID_ARG, "K, keep, grad_logp and dK must not be NULL");
+  const size_t need = dpp_workspace_size(DPP_OP_LOGPROB_BACKWARD, n, dtype, precision, hermitian);
+  if (!workspace || !aligned(workspace, 256))
+    return fail(DPP_ERR_WORKSPACE, "workspace must be non-NULL and 256-byte aligned");
+  if (workspace_bytes < need) return fail(DPP_ERR_WORKSPACE, "workspace too small");
+  if (n == 0) return DPP_OK;
+  Workspace ws;
+  ws.base = static_cast<char*>(workspace);
+  ws.size = workspace_bytes;
+  cudaError_t e = logprob_backward(K, n, ld, dtype, hermitian != 0, keep, grad_logp, dK, ld_dk,
+                                   ws, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return fail_cuda(e, "dpp_logprob_backward");
+  return DPP_OK;
+}
+
+dpp_status dpp_uniforms(uint64_t seed, uint64_t instance, int64_t n, double* out, void* stream) {
+  g_last_error.clear();
+  if (n < 0) return fail(DPP_ERR_INVALID_ARG, "n must be >= 0");
+  if (n > 0 && !out) return fail(DPP_ERR_INVALID_ARG, "out must not be NULL");
+  cudaError_t e = fill_uniforms(seed, instance, n, out, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return fail_cuda(e, "dpp_uniforms");
+  return DPP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,161 @@
+// Device-side building blocks shared by the sampler kernels: scalar traits
+// for real/complex FP64 and FP32, the Philox4x32-10 uniform, bounded waits on
+// device flags and the per-draw result record.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dpp.h"
+
+namespace dpp {
+
+// ---------------------------------------------------------------------------
+// Scalars
+// ---------------------------------------------------------------------------
+struct cdouble {
+  double re, im;
+};
+
+__host__ __device__ inline cdouble mk(double r, double i) { return {r, i}; }
+
+template <class T>
+struct Sc;
+
+template <>
+struct Sc<double> {
+  static constexpr bool cplx = false;
+  __device__ static inline double zero() { return 0.0; }
+  __device__ static inline double from_real(double r) { return r; }
+  __device__ static inline double re(double a) { return a; }
+  __device__ static inline double im(double) { return 0.0; }
+  __device__ static inline double conj(double a) { return a; }
+  __device__ static inline double add(double a, double b) { return a + b; }
+  __device__ static inline double sub(double a, double b) { return a - b; }
+  __device__ static inline double mul(double a, double b) { return a * b; }
+  // a - b * c
+  __device__ static inline double fnms(double a, double b, double c) { return fma(-b, c, a); }
+  // a - b * conj(c)
+  __device__ static inline double fnms_conj(double a, double b, double c) { return fma(-b, c, a); }
+  __device__ static inline double div_real(double a, double d) { return a / d; }
+  __device__ static inline double div(double a, double b) { return a / b; }
+  __device__ static inline double abs2(double a) { return a * a; }
+  __device__ static inline double absv(double a) { return fabs(a); }
+  __device__ static inline bool finite(double a) { return isfinite(a); }
+};
+
+template <>
+struct Sc<cdouble> {
+  static constexpr bool cplx = true;
+  __device__ static inline cdouble zero() { return {0.0, 0.0}; }
+  __device__ static inline cdouble from_real(double r) { return {r, 0.0}; }
+  __device__ static inline double re(cdouble a) { return a.re; }
+  __device__ static inline double im(cdouble a) { return a.im; }
+  __device__ static inline cdouble conj(cdouble a) { return {a.re, -a.im}; }
+  __device__ static inline cdouble add(cdouble a, cdouble b) { return {a.re + b.re, a.im + b.im}; }
+  __device__ static inline cdouble sub(cdouble a, cdouble b) { return {a.re - b.re, a.im - b.im}; }
+  __device__ static inline cdouble mul(cdouble a, cdouble b) {
+    return {fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re)};
+  }
+  __device__ static inline cdouble fnms(cdouble a, cdouble b, cdouble c) {
+    // a - b*c
+    double r = fma(-b.re, c.re, a.re);
+    r = fma(b.im, c.im, r);
+    double i = fma(-b.re, c.im, a.im);
+    i = fma(-b.im, c.re, i);
+    return {r, i};
+  }
+  __device__ static inline cdouble fnms_conj(cdouble a, cdouble b, cdouble c) {
+    // a - b*conj(c)
+    double r = fma(-b.re, c.re, a.re);
+    r = fma(-b.im, c.im, r);
+    double i = fma(b.re, c.im, a.im);
+    i = fma(-b.im, c.re, i);
+    return {r, i};
+  }
+  __device__ static inline cdouble div_real(cdouble a, double d) { return {a.re / d, a.im / d}; }
+  __device__ static inline cdouble div(cdouble a, cdouble b) {
+    // Smith's algorithm (scaled complex division)
+    if (fabs(b.re) >= fabs(b.im)) {
+      double r = b.im / b.re, den = b.re + b.im * r;
+      return {(a.re + a.im * r) / den, (a.im - a.re * r) / den};
+    } else {
+      double r = b.re / b.im, den = b.re * r + b.im;
+      return {(a.re * r + a.im) / den, (a.im * r - a.re) / den};
+    }
+  }
+  __device__ static inline double abs2(cdouble a) { return a.re * a.re + a.im * a.im; }
+  __device__ static inline double absv(cdouble a) { return hypot(a.re, a.im); }
+  __device__ static inline bool finite(cdouble a) { return isfinite(a.re) && isfinite(a.im); }
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of the
+// multiply/xor bijection with a Weyl-sequence key schedule.
+// ---------------------------------------------------------------------------
+__device__ inline void philox4x32_10(uint32_t& x0, uint32_t& x1, uint32_t& x2,
+                                     uint32_t& x3, uint32_t k0, uint32_t k1) {
+  const uint32_t kMulA = 0xD2511F53u, kMulB = 0xCD9E8D57u;
+  const uint32_t kWeylA = 0x9E3779B9u, kWeylB = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hA = __umulhi(kMulA, x0), lA = kMulA * x0;
+    const uint32_t hB = __umulhi(kMulB, x2), lB = kMulB * x2;
+    const uint32_t y0 = hB ^ x1 ^ k0;
+    const uint32_t y2 = hA ^ x3 ^ k1;
+    x0 = y0;
+    x1 = lB;
+    x2 = y2;
+    x3 = lA;
+    k0 += kWeylA;
+    k1 += kWeylB;
+  }
+}
+
+// u_j in (0,1) with 53 random bits, counter (j, instance), key = seed.
+__device__ inline double philox_uniform(uint64_t seed, uint64_t instance, uint64_t j) {
+  uint32_t x0 = (uint32_t)j, x1 = (uint32_t)instance, x2 = (uint32_t)(instance >> 32), x3 = 0u;
+  philox4x32_10(x0, x1, x2, x3, (uint32_t)seed, (uint32_t)(seed >> 32));
+  const uint64_t bits = ((uint64_t)x0 << 21) | (uint64_t)(x1 >> 11);
+  return ((double)bits + 0.5) * 0x1.0p-53;
+}
+
+// ---------------------------------------------------------------------------
+// Bounded waits. Every spin in this library gives up after kWaitNs of
+// wall-clock time (device %globaltimer), reports DPP_RES_TIMEOUT and returns.
+// ---------------------------------------------------------------------------
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
+
+__device__ inline unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ inline unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ inline void st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Spin (one thread) until *flag >= target. Returns false on timeout.
+__device__ inline bool wait_geq(const unsigned* flag, unsigned target) {
+  if (ld_acquire(flag) >= target) return true;
+  const unsigned long long t0 = global_ns();
+  unsigned sleep = 32;
+  while (true) {
+    if (ld_acquire(flag) >= target) return true;
+    if (global_ns() - t0 > kWaitNs) return false;
+    __nanosleep(sleep);
+    if (sleep < 1024) sleep <<= 1;
+  }
+}
+
+// Status word that any kernel may OR bits into.
+__device__ inline void flag_status(dpp_result* r, int bits) { atomicOr(&r->status, bits); }
+
+}  // namespace dpp

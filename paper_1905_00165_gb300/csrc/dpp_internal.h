@@ -1,0 +1,75 @@
+// Host-side internal interface between the C ABI (dpp_api.cu) and the kernel
+// translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "dpp.h"
+
+namespace dpp {
+
+// Inner panel width of the sequential decisions: one warp owns the
+// kPanel x kPanel diagonal block (one row per lane).
+constexpr int kPanel = 32;
+// Threads per CTA of the panel kernels.
+constexpr int kPanelThreads = 256;
+
+struct Workspace {
+  char* base = nullptr;
+  size_t size = 0;
+  size_t used = 0;
+  // Carve `bytes` (256-byte aligned); returns nullptr when out of space.
+  void* take(size_t bytes) {
+    size_t off = (used + 255) & ~size_t(255);
+    if (off + bytes > size) return nullptr;
+    used = off + bytes;
+    return base + off;
+  }
+};
+
+inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// Per-device properties cached on first use.
+struct DevInfo {
+  int device = -1;
+  int sm_count = 0;
+};
+cudaError_t dev_info(DevInfo* out);
+
+// Common arguments of one draw.
+struct DrawArgs {
+  const void* K;
+  int64_t n, ld;
+  int32_t dtype;
+  uint64_t seed, instance;
+  const double* uniforms;
+  uint8_t* keep;
+  void* factor_out;
+  double* pivots_user;
+  dpp_result* result;
+  cudaStream_t stream;
+};
+
+// FP64 samplers (dpp_fp64.cu).
+size_t ws_fp64(int64_t n, int32_t dtype, bool hermitian, bool own_matrix);
+cudaError_t sample_fp64(const DrawArgs& a, bool hermitian, Workspace ws);
+
+// Mixed-precision Hermitian sampler (dpp_mixed.cu).
+size_t ws_mixed(int64_t n);
+cudaError_t sample_mixed(const DrawArgs& a, Workspace ws);
+
+// Adjoint (dpp_backward.cu).
+size_t ws_backward(int64_t n, int32_t dtype, bool hermitian);
+cudaError_t logprob_backward(const void* K, int64_t n, int64_t ld, int32_t dtype,
+                             bool hermitian, const uint8_t* keep,
+                             const double* grad, void* dK, int64_t ld_dk,
+                             Workspace ws, cudaStream_t stream);
+
+// Result initialisation and uniform generation (dpp_fp64.cu).
+cudaError_t init_result(dpp_result* r, cudaStream_t s);
+cudaError_t fill_uniforms(uint64_t seed, uint64_t instance, int64_t n, double* out,
+                          cudaStream_t s);
+
+}  // namespace dpp

@@ -1,0 +1,75 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports
+every function include/dpp.h declares, and rejects bad arguments before
+enqueueing anything."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1905_00165_gb300 as dpp
+from paper_1905_00165_gb300 import _lib
+from paper_1905_00165_gb300 import build as cuda_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    cuda_build.build()
+    return dpp.load()
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "dpp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dpp_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("dpp_sample_hermitian", "dpp_sample_lu", "dpp_logprob_backward",
+                     "dpp_workspace_size", "dpp_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(L):
+    for name in _declared_functions():
+        assert hasattr(L, name), name
+
+
+def test_abi_version(L):
+    assert L.dpp_abi_version() == 1
+
+
+def test_workspace_sizes(L):
+    for op in (0, 1):
+        for dt in (0, 1):
+            assert dpp.workspace_size(op, 1000, dt, 0, 1) > 1000 * 1000 * 8
+    assert dpp.workspace_size(0, 0, 0, 0, 1) > 0
+    assert dpp.workspace_size(0, 100, 7, 0, 1) == 0  # unknown dtype
+    assert dpp.workspace_size(9, 100, 0, 0, 1) == 0  # unknown op
+    assert dpp.workspace_size(1, 100, 0, 1, 0) == 0  # LU has no mixed path
+
+
+def _call(L, K=None, n=4, ld=4, dtype=0, prec=0, keep=None, res=None, ws=None, wsb=0):
+    return L.dpp_sample_hermitian(K, n, ld, dtype, prec, 0, 0, None, keep, None, None, res, ws, wsb, None)
+
+
+def test_invalid_arguments_rejected_on_host(L):
+    fake = 4096  # never dereferenced: validation fails first
+    assert _call(L, n=-1) == _lib.DPP_ERR_INVALID_ARG
+    assert "n must be" in dpp._lib.last_error()
+    assert _call(L, K=fake, n=4, ld=3, keep=fake, res=fake) == _lib.DPP_ERR_INVALID_ARG
+    assert _call(L, K=fake, n=4, ld=4, dtype=5, keep=fake, res=fake) == _lib.DPP_ERR_INVALID_ARG
+    assert _call(L, K=None, n=4, keep=fake, res=fake) == _lib.DPP_ERR_INVALID_ARG
+    assert _call(L, K=fake, n=4, keep=fake, res=None) == _lib.DPP_ERR_INVALID_ARG
+    assert _call(L, K=fake + 4, n=4, keep=fake, res=fake) == _lib.DPP_ERR_INVALID_ARG  # misaligned
+    # workspace: missing, misaligned, too small
+    assert _call(L, K=fake, n=4, keep=fake, res=fake) == _lib.DPP_ERR_WORKSPACE
+    assert _call(L, K=fake, n=4, keep=fake, res=fake, ws=fake + 8, wsb=1 << 20) == _lib.DPP_ERR_WORKSPACE
+    assert _call(L, K=fake, n=4, keep=fake, res=fake, ws=fake, wsb=16) == _lib.DPP_ERR_WORKSPACE
+    # unsupported precision for complex input
+    assert _call(L, K=fake, n=4, dtype=1, prec=1, keep=fake, res=fake, ws=fake, wsb=1 << 30) == \
+        _lib.DPP_ERR_UNSUPPORTED
+    assert L.dpp_uniforms(0, 0, -1, None, None) == _lib.DPP_ERR_INVALID_ARG

@@ -149,10 +149,14 @@ def grid_spanning_tree_log_count(d: int) -> float:
 # Non-Hermitian kernels with a known Hermitian twin
 # --------------------------------------------------------------------------
 def lu_similarity_kernel(n: int, seed: int = 0, sigma: float = 0.5,
-                         device: Optional[str] = None):
-    """(K, S): S = Q diag(U(0,1)) Q^T, K = D^{-1} S D, D = diag(exp(N(0, sigma^2)))."""
-    S = hermitian_kernel(n, seed, "uniform", device=device)
-    dvec = np.exp(sigma * _rng(seed + 104729).standard_normal(n))
+                         device: Optional[str] = None, complex_: bool = False):
+    """(K, S): S = Q diag(U(0,1)) Q^H, K = D^{-1} S D with D = diag(exp(N(0, sigma^2)))
+    (times a uniform phase exp(i theta) when ``complex_``)."""
+    S = hermitian_kernel(n, seed, "uniform", device=device, complex_=complex_)
+    rng = _rng(seed + 104729)
+    dvec = np.exp(sigma * rng.standard_normal(n))
+    if complex_:
+        dvec = dvec * np.exp(1j * rng.uniform(0.0, 2 * np.pi, n))
     K = S * (dvec[None, :] / dvec[:, None])
     return K, S
 
