@@ -166,6 +166,28 @@ dpp_status dpp_logprob_backward(const void* K, int64_t n, int64_t ld,
 dpp_status dpp_uniforms(uint64_t seed, uint64_t instance, int64_t n,
                         double* out, void* stream);
 
+/* Per-kernel timing. While profiling is on (between dpp_profile_start and
+ * dpp_profile_stop), every kernel launch of the library is bracketed by CUDA
+ * events recorded on the stream it is launched on. dpp_profile_stop waits for
+ * those events, writes one entry per kernel category that ran (at most
+ * max_entries) and returns the number written. `flops` and `bytes` are the
+ * ALGORITHMIC work of the recorded launches (e.g. m^2 b real flops for a
+ * rank-b lower-triangular Schur update of order m), not executed instructions.
+ * Profiling is process-wide and not meant for concurrent callers. */
+typedef struct {
+  char name[32];
+  int64_t launches;
+  double total_ms;
+  double flops;
+  double bytes;
+} dpp_kernel_stat;
+
+void dpp_profile_start(void);
+int32_t dpp_profile_stop(dpp_kernel_stat* out, int32_t max_entries);
+
+/* Number of kernels this library has enqueued since it was loaded. */
+uint64_t dpp_launch_count(void);
+
 /* Thread-local description of the last host-side error ("" if none). */
 const char* dpp_last_error(void);
 

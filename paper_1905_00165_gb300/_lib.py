@@ -63,6 +63,12 @@ def load(path: Optional[str] = None):
     L.dpp_logprob_backward.restype = i32
     L.dpp_uniforms.argtypes = [u64, u64, i64, vp, vp]
     L.dpp_uniforms.restype = i32
+    L.dpp_profile_start.argtypes = []
+    L.dpp_profile_start.restype = None
+    L.dpp_profile_stop.argtypes = [vp, i32]
+    L.dpp_profile_stop.restype = i32
+    L.dpp_launch_count.argtypes = []
+    L.dpp_launch_count.restype = ctypes.c_uint64
     _lib = L
     return L
 
@@ -88,3 +94,29 @@ def decode_result(raw: bytes) -> dict:
 
 def ptr(t) -> Optional[int]:
     return None if t is None else t.data_ptr()
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64),
+                ("total_ms", ctypes.c_double), ("flops", ctypes.c_double),
+                ("bytes", ctypes.c_double)]
+
+
+def profile_start() -> None:
+    load().dpp_profile_start()
+
+
+def profile_stop() -> dict:
+    """{category: {launches, total_ms, flops, bytes}} for the profiled window."""
+    arr = (KernelStat * 16)()
+    k = load().dpp_profile_stop(ctypes.cast(arr, ctypes.c_void_p), 16)
+    out = {}
+    for i in range(k):
+        s = arr[i]
+        out[s.name.decode()] = {"launches": int(s.launches), "total_ms": float(s.total_ms),
+                                "flops": float(s.flops), "bytes": float(s.bytes)}
+    return out
+
+
+def launch_count() -> int:
+    return int(load().dpp_launch_count())

@@ -18,6 +18,7 @@
 
 #include "dpp_device.cuh"
 #include "dpp_internal.h"
+#include "dpp_profile.h"
 
 namespace dpp {
 namespace {
@@ -463,8 +464,11 @@ cudaError_t run_fp64(const DrawArgs& a, bool herm, Workspace ws) {
     if (g < 1) g = 1;
     if (g > cap) g = cap;
     void* args[] = {&pa};
-    e = cudaLaunchCooperativeKernel((const void*)panel, dim3((unsigned)g), dim3(kPanelThreads),
-                                    args, 0, a.stream);
+    {
+      ProfScope ps(kProfPanel, a.stream);
+      e = cudaLaunchCooperativeKernel((const void*)panel, dim3((unsigned)g), dim3(kPanelThreads),
+                                      args, 0, a.stream);
+    }
     if (e != cudaSuccess) return e;
     if (m > 0) {
       UpdArgs ua;
@@ -486,7 +490,15 @@ cudaError_t run_fp64(const DrawArgs& a, bool herm, Workspace ws) {
         ua.ldb_op = lda;
       }
       const int64_t nt = herm ? ua.tiles * (ua.tiles + 1) / 2 : ua.tiles * ua.tiles;
-      upd<<<(unsigned)nt, 256, upd_smem, a.stream>>>(ua);
+      // algorithmic work: m^2 b real multiply-adds pairs (LDL^H lower half) or
+      // 2 m^2 b (LU); complex multiplies cost 4x
+      const double cf = Sc<T>::cplx ? 4.0 : 1.0;
+      const double fl = cf * (herm ? 1.0 : 2.0) * (double)m * (double)m * (double)b;
+      const double by = (double)esz * (herm ? 1.0 : 2.0) * (double)m * (double)m;
+      {
+        ProfScope ps(kProfUpdateFp64, a.stream, fl, by);
+        upd<<<(unsigned)nt, 256, upd_smem, a.stream>>>(ua);
+      }
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
   }
@@ -501,6 +513,7 @@ cudaError_t run_fp64(const DrawArgs& a, bool herm, Workspace ws) {
 }  // namespace
 
 cudaError_t init_result(dpp_result* r, cudaStream_t s) {
+  ProfScope ps(kProfOther, s);
   k_init_result<<<1, 1, 0, s>>>(r);
   return cudaGetLastError();
 }
@@ -509,6 +522,7 @@ cudaError_t fill_uniforms(uint64_t seed, uint64_t instance, int64_t n, double* o
   if (n <= 0) return cudaSuccess;
   int64_t g = (n + 255) / 256;
   if (g > 4096) g = 4096;
+  ProfScope ps(kProfOther, s);
   k_uniforms<<<(unsigned)g, 256, 0, s>>>(seed, instance, n, out);
   return cudaGetLastError();
 }
