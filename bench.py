@@ -44,6 +44,10 @@ def parse():
     p.add_argument("--precision", default="auto", choices=["auto", "fp64", "3xtf32"])
     p.add_argument("--cpu-sample-n", type=int, default=3072,
                    help="order of the leading block the CPU oracle samples")
+    p.add_argument("--update", default="tc", choices=["tc", "simt"],
+                   help="mixed path trailing update: tcgen05 3xTF32 or SIMT FP32")
+    p.add_argument("--gen", default="gpu", choices=["gpu", "cpu"],
+                   help="where the input kernel's Haar factor is computed")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-fp64-ref", action="store_true")
@@ -207,12 +211,16 @@ def main():
     if prec_name == "auto":
         prec_name = "3xtf32" if dpp.workspace_size(0, n, 0, 1, 1) > 0 else "fp64"
     prec = dpp.PRECISIONS[prec_name]
+    _lib.set_tuning(_lib.DPP_TUNE_UPDATE_KERNEL, 0 if args.update == "tc" else 1)
     steps = args.steps if args.steps is not None else (20 if prec_name != "fp64" else 4)
     warmup = max(args.warmup, 3)
 
     # ---- inputs (resident before timing) --------------------------------
     t_gen = time.perf_counter()
-    Kd = W.hermitian_kernel(n, seed=0, kind=args.kind, device=str(dev), return_torch=True)
+    if args.gen == "gpu":
+        Kd = W.hermitian_kernel(n, seed=0, kind=args.kind, device=str(dev), return_torch=True)
+    else:
+        Kd = torch.from_numpy(W.hermitian_kernel(n, seed=0, kind=args.kind)).to(dev)
     Kd = Kd.contiguous()  # symmetric: row-major storage == column-major K
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
@@ -362,6 +370,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": f"hermitian_real_{args.kind}_n{n}", "n": n,
                        "precision": prec_name,
+                       "update_kernel": args.update if prec_name != "fp64" else "simt_fp64",
                        "kernel": f"Q diag(lam) Q^T, Haar Q (seed 0), lam~{args.kind}",
                        "seeds": f"Philox seed = step index (+ rank offset)",
                        "l2_policy": "inputs larger than L2 (2 GiB FP64 K), no flush",

@@ -161,6 +161,25 @@ dpp_status dpp_logprob_backward(const void* K, int64_t n, int64_t ld,
                                 int64_t ld_dk, void* workspace,
                                 size_t workspace_bytes, void* stream);
 
+/* Process-wide tuning knobs (read at each call; not for concurrent changes).
+ *   DPP_TUNE_TAU_SAFETY   c in the mixed-precision borderline bound
+ *                         tau_j = c * 2^-22 * sqrt(j + 1) * (K_jj + s_j),
+ *                         s_j = sum_{k<j} |L_jk|^2 |d_k|            (default 8)
+ *   DPP_TUNE_OUTER_BLOCK  outer block width of the mixed path: the trailing
+ *                         update contracts this many columns at once (32..256,
+ *                         multiple of 32; default 256)
+ *   DPP_TUNE_UPDATE_KERNEL  mixed-path trailing update: 0 = tensor cores
+ *                         (tcgen05, 3xTF32), 1 = SIMT FP32 (default 0)
+ * Returns DPP_ERR_INVALID_ARG for an unknown key or out-of-range value. */
+typedef enum {
+  DPP_TUNE_TAU_SAFETY = 0,
+  DPP_TUNE_OUTER_BLOCK = 1,
+  DPP_TUNE_UPDATE_KERNEL = 2
+} dpp_tune_key;
+
+dpp_status dpp_set_tuning(int32_t key, double value);
+double dpp_get_tuning(int32_t key);
+
 /* Fill `out` (device, n doubles) with the Philox uniforms u_0..u_{n-1} that
  * the samplers use for (seed, instance). */
 dpp_status dpp_uniforms(uint64_t seed, uint64_t instance, int64_t n,

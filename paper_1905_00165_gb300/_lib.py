@@ -67,6 +67,10 @@ def load(path: Optional[str] = None):
     L.dpp_profile_start.restype = None
     L.dpp_profile_stop.argtypes = [vp, i32]
     L.dpp_profile_stop.restype = i32
+    L.dpp_set_tuning.argtypes = [i32, ctypes.c_double]
+    L.dpp_set_tuning.restype = i32
+    L.dpp_get_tuning.argtypes = [i32]
+    L.dpp_get_tuning.restype = ctypes.c_double
     L.dpp_launch_count.argtypes = []
     L.dpp_launch_count.restype = ctypes.c_uint64
     _lib = L
@@ -116,6 +120,17 @@ def profile_stop() -> dict:
         out[s.name.decode()] = {"launches": int(s.launches), "total_ms": float(s.total_ms),
                                 "flops": float(s.flops), "bytes": float(s.bytes)}
     return out
+
+
+DPP_TUNE_TAU_SAFETY, DPP_TUNE_OUTER_BLOCK, DPP_TUNE_UPDATE_KERNEL = 0, 1, 2
+
+
+def set_tuning(key: int, value: float) -> None:
+    check(load().dpp_set_tuning(key, float(value)))
+
+
+def get_tuning(key: int) -> float:
+    return float(load().dpp_get_tuning(key))
 
 
 def launch_count() -> int:

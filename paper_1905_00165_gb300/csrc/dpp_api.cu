@@ -177,6 +177,38 @@ dpp_status dpp_logprob_backward(const void* K, int64_t n, int64_t ld, int32_t dt
   return DPP_OK;
 }
 
+dpp_status dpp_set_tuning(int32_t key, double value) {
+  g_last_error.clear();
+  switch (key) {
+    case DPP_TUNE_TAU_SAFETY:
+      if (!(value > 0.0 && value < 1e6)) return fail(DPP_ERR_INVALID_ARG, "tau safety out of range");
+      g_tuning.tau_safety = value;
+      return DPP_OK;
+    case DPP_TUNE_OUTER_BLOCK: {
+      const int v = (int)value;
+      if ((double)v != value || v < 32 || v > kMaxOuterBlock || v % 32 != 0)
+        return fail(DPP_ERR_INVALID_ARG, "outer block must be a multiple of 32 in [32, 256]");
+      g_tuning.outer_block = v;
+      return DPP_OK;
+    }
+    case DPP_TUNE_UPDATE_KERNEL:
+      if (value != 0.0 && value != 1.0) return fail(DPP_ERR_INVALID_ARG, "update kernel is 0 or 1");
+      g_tuning.update_kernel = (int)value;
+      return DPP_OK;
+    default:
+      return fail(DPP_ERR_INVALID_ARG, "unknown tuning key");
+  }
+}
+
+double dpp_get_tuning(int32_t key) {
+  switch (key) {
+    case DPP_TUNE_TAU_SAFETY: return g_tuning.tau_safety;
+    case DPP_TUNE_OUTER_BLOCK: return (double)g_tuning.outer_block;
+    case DPP_TUNE_UPDATE_KERNEL: return (double)g_tuning.update_kernel;
+    default: return -1.0;
+  }
+}
+
 dpp_status dpp_uniforms(uint64_t seed, uint64_t instance, int64_t n, double* out, void* stream) {
   g_last_error.clear();
   if (n < 0) return fail(DPP_ERR_INVALID_ARG, "n must be >= 0");

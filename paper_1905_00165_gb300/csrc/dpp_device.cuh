@@ -90,6 +90,61 @@ struct Sc<cdouble> {
 };
 
 // ---------------------------------------------------------------------------
+// Double-float ("df64") values: an unevaluated sum hi + lo of two floats with
+// about 48 significant bits, built from the error-free transformations TwoSum
+// (Knuth) and TwoProduct-by-FMA (Dekker / Ogita-Rump-Oishi). Used where an
+// FP64 accumulation would otherwise sit on a latency-critical FP32 path.
+// Every operation uses explicit _rn intrinsics so no contraction can break
+// the transformations.
+// ---------------------------------------------------------------------------
+struct f2 {
+  float hi, lo;
+};
+
+__device__ inline f2 make_f2(float hi, float lo) { return {hi, lo}; }
+
+__device__ inline f2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+
+__device__ inline f2 fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ inline f2 f2_from_double(double x) {
+  const float hi = __double2float_rn(x);
+  return {hi, __double2float_rn(x - (double)hi)};
+}
+
+__device__ inline double f2_to_double(f2 a) { return (double)a.hi + (double)a.lo; }
+
+// a + c (c a float)
+__device__ inline f2 f2_add_f(f2 a, float c) {
+  const f2 s = two_sum(a.hi, c);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+
+// a - w * l with the product formed exactly (w * l = p + pe)
+__device__ inline f2 f2_sub_prod(f2 a, float w, float l) {
+  const float p = __fmul_rn(w, l);
+  const float pe = __fmaf_rn(w, l, -p);
+  const f2 s = two_sum(a.hi, -p);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fsub_rn(a.lo, pe)));
+}
+
+// a + w * l
+__device__ inline f2 f2_add_prod(f2 a, float w, float l) {
+  const float p = __fmul_rn(w, l);
+  const float pe = __fmaf_rn(w, l, -p);
+  const f2 s = two_sum(a.hi, p);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, pe)));
+}
+
+// ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of the
 // multiply/xor bijection with a Weyl-sequence key schedule.
 // ---------------------------------------------------------------------------

@@ -56,9 +56,27 @@ struct DrawArgs {
 size_t ws_fp64(int64_t n, int32_t dtype, bool hermitian, bool own_matrix);
 cudaError_t sample_fp64(const DrawArgs& a, bool hermitian, Workspace ws);
 
+// Process-wide tuning knobs (dpp_set_tuning).
+struct Tuning {
+  double tau_safety = 8.0;  // c in the borderline bound
+  int outer_block = 256;    // mixed path: columns contracted per trailing update
+  int update_kernel = 0;    // 0 = tcgen05 3xTF32, 1 = SIMT FP32
+};
+extern Tuning g_tuning;
+constexpr int kMaxOuterBlock = 256;
+
 // Mixed-precision Hermitian sampler (dpp_mixed.cu).
 size_t ws_mixed(int64_t n);
 cudaError_t sample_mixed(const DrawArgs& a, Workspace ws);
+
+// Trailing update C -= W L^T on the lower triangle of rows/cols [r0, n) of the
+// FP32 column-major C (ldc), with the W and L operands given as TF32 hi/lo
+// splits in row-major [n x ldk] buffers (first kdim columns used), on tcgen05
+// tensor cores (dpp_tc.cu). kdim must be a multiple of 32; ldk * 4 bytes must
+// be a multiple of 16; the operand buffers must be 16-byte aligned.
+cudaError_t outer_update_tc(float* C, int64_t ldc, int64_t n, int64_t r0, int kdim,
+                            const float* Wh, const float* Wl, const float* Lh,
+                            const float* Ll, int ldk, int* err_flag, cudaStream_t s);
 
 // Adjoint (dpp_backward.cu).
 size_t ws_backward(int64_t n, int32_t dtype, bool hermitian);

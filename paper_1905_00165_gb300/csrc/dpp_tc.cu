@@ -1,0 +1,338 @@
+// Trailing Schur-complement update of the mixed-precision sampler on the
+// fifth-generation tensor cores (tcgen05, sm_103a):
+//
+//     C[i, c] -= sum_t W[i, t] L[c, t]      (lower triangle, i >= c)
+//
+// which is the rank-NB update A22 -= W L21^T = L21 D1 L21^T of the blocked
+// LDL^T sampler (Algorithm 3's Schur complement, Hermitian form), i.e. the
+// "asymptotically all of the work" contraction of Section 4.
+//
+// Precision: 3xTF32. W = Wh + Wl and L = Lh + Ll are pre-split into TF32
+// pairs by the panel kernel; each k-step issues Wh Lh^T + Wh Ll^T + Wl Lh^T
+// into one FP32 accumulator in tensor memory (the dropped Wl Ll^T term is
+// ~2^-22 relative).
+//
+// Structure (one 128 x 128 output tile per CTA, 128 threads):
+//   warp 0 / lane 0 : TMA producer, 3-stage ring of {Wh, Wl, Lh, Ll} tiles
+//                     (128 rows x 32 fp32 = 128 B rows, SWIZZLE_128B)
+//   warp 1          : allocates 128 TMEM columns; lane 0 issues tcgen05.mma
+//                     (M = 128, N = 128, K = 8) and tcgen05.commit
+//   warps 0-3       : epilogue, tcgen05.ld 32x32b (row = TMEM lane) then a
+//                     coalesced read-modify-write of the column-major C.
+// Every mbarrier wait is bounded; on expiry the kernel records an error,
+// drains what it issued, frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "dpp_device.cuh"
+#include "dpp_internal.h"
+
+namespace dpp {
+namespace {
+
+constexpr int kBM = 128;
+constexpr int kBN = 128;
+constexpr int kBK = 32;  // fp32 elements per k-block (= one 128-byte swizzle row)
+constexpr int kStages = 3;
+constexpr int kTileBytes = kBM * kBK * 4;  // 16 KiB
+constexpr int kStageBytes = 4 * kTileBytes;
+constexpr int kThreads = 128;
+constexpr int kTmemCols = 128;
+constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256;
+
+__device__ inline uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ inline void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ inline void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ inline bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on phase `parity` of an mbarrier.
+__device__ inline bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (true) {
+    if (mbar_try(bar, parity)) return true;
+    if (global_ns() - t0 > kWaitNs) return false;
+  }
+}
+
+__device__ inline void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                   uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes, 8-row swizzle atoms 1024 bytes apart.
+__device__ inline uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)(16u >> 4) << 16;    // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024u >> 4) << 32;  // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;             // descriptor version
+  d |= (uint64_t)2 << 61;             // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::tf32: D = F32, A = B = TF32, both K-major,
+// N = kBN, M = kBM.
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kBN >> 3) << 17) |
+                            ((uint32_t)(kBM >> 4) << 24);
+
+__device__ inline void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ inline void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   bar)
+               : "memory");
+}
+
+__device__ inline void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct TcArgs {
+  float* C;
+  int64_t ldc, n, r0;
+  int kblocks;
+  int64_t tiles;
+  int* err;
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_update_tc(const __grid_constant__ CUtensorMap tWh, const __grid_constant__ CUtensorMap tWl,
+                const __grid_constant__ CUtensorMap tLh, const __grid_constant__ CUtensorMap tLl,
+                TcArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // 1024-byte aligned operand ring, then the barriers
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + kStages * kStageBytes);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + kStages;
+  uint64_t* done = bars + 2 * kStages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 1);
+  __shared__ int s_fail;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  // lower-triangle tile of the trailing block
+  const int64_t x = blockIdx.x;
+  int64_t tr = (int64_t)((sqrt(8.0 * (double)x + 1.0) - 1.0) * 0.5);
+  while (tr * (tr + 1) / 2 > x) --tr;
+  while ((tr + 1) * (tr + 2) / 2 <= x) ++tr;
+  const int64_t tc = x - tr * (tr + 1) / 2;
+  const int64_t i0 = a.r0 + tr * kBM, c0 = a.r0 + tc * kBN;
+
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    mbar_init(smem_u32(done), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const int KB = a.kblocks;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer ----
+    int issued = 0;
+    for (int kb = 0; kb < KB; ++kb) {
+      const int s = kb % kStages;
+      const uint32_t ph = (uint32_t)((kb / kStages) & 1);
+      if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1u)) {
+        atomicExch(&s_fail, 1);
+        break;
+      }
+      unsigned char* st = base + s * kStageBytes;
+      const uint32_t fb = smem_u32(&full[s]);
+      mbar_expect_tx(fb, kStageBytes);
+      const int kx = kb * kBK;
+      tma_load_2d(smem_u32(st + 0 * kTileBytes), &tWh, kx, (int)i0, fb);
+      tma_load_2d(smem_u32(st + 1 * kTileBytes), &tWl, kx, (int)i0, fb);
+      tma_load_2d(smem_u32(st + 2 * kTileBytes), &tLh, kx, (int)c0, fb);
+      tma_load_2d(smem_u32(st + 3 * kTileBytes), &tLl, kx, (int)c0, fb);
+      issued = kb + 1;
+    }
+    // drain: every issued stage must have landed before the CTA may exit
+    for (int kb = (issued > kStages ? issued - kStages : 0); kb < issued; ++kb)
+      mbar_wait(smem_u32(&full[kb % kStages]), (uint32_t)((kb / kStages) & 1));
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer ----
+    bool ok = true;
+    for (int kb = 0; kb < KB && ok; ++kb) {
+      const int s = kb % kStages;
+      const uint32_t ph = (uint32_t)((kb / kStages) & 1);
+      if (!mbar_wait(smem_u32(&full[s]), ph)) {
+        atomicExch(&s_fail, 1);
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      unsigned char* st = base + s * kStageBytes;
+      const uint32_t aH = smem_u32(st + 0 * kTileBytes), aL = smem_u32(st + 1 * kTileBytes);
+      const uint32_t bH = smem_u32(st + 2 * kTileBytes), bL = smem_u32(st + 3 * kTileBytes);
+#pragma unroll
+      for (int kk = 0; kk < kBK / 8; ++kk) {
+        const uint32_t off = kk * 32;  // 8 tf32 = 32 bytes along K
+        mma_tf32(tmem, sw128_desc(aH + off), sw128_desc(bH + off), (kb > 0 || kk > 0) ? 1u : 0u);
+        mma_tf32(tmem, sw128_desc(aH + off), sw128_desc(bL + off), 1u);
+        mma_tf32(tmem, sw128_desc(aL + off), sw128_desc(bH + off), 1u);
+      }
+      mma_commit(smem_u32(&empty[s]));
+    }
+    mma_commit(smem_u32(done));
+  }
+  __syncwarp();
+
+  // ---- epilogue: all four warps ----
+  const bool ready = mbar_wait(smem_u32(done), 0);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!ready) atomicExch(&s_fail, 1);
+  __syncthreads();
+  if (!s_fail) {
+    const int64_t row = i0 + warp * 32 + lane;
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+    for (int ch = 0; ch < kBN / 32; ++ch) {
+      float v[32];
+      tmem_ld32(trow + (uint32_t)(ch * 32), v);
+      const int64_t cb = c0 + ch * 32;
+      if (row < a.n) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          const int64_t col = cb + c;
+          if (col < a.n && row >= col) {
+            float* p = a.C + row + col * a.ldc;
+            *p -= v[c];
+          }
+        }
+      }
+    }
+  } else if (threadIdx.x == 0) {
+    atomicExch(a.err, 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTmemCols)
+                 : "memory");
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap* m, const float* ptr, int64_t rows, int ldk) {
+  auto enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)ldk, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ldk * sizeof(float)};
+  cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)kBM};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(ptr), dims, strides,
+                   box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+cudaError_t outer_update_tc(float* C, int64_t ldc, int64_t n, int64_t r0, int kdim,
+                            const float* Wh, const float* Wl, const float* Lh, const float* Ll,
+                            int ldk, int* err_flag, cudaStream_t s) {
+  if (kdim % kBK != 0 || kdim <= 0 || kdim > ldk) return cudaErrorInvalidValue;
+  if ((ldk * sizeof(float)) % 16 != 0) return cudaErrorInvalidValue;
+  const int64_t m = n - r0;
+  if (m <= 0) return cudaSuccess;
+  if (n > 0x7fffffff) return cudaErrorInvalidValue;
+  CUtensorMap tWh, tWl, tLh, tLl;
+  if (!make_map(&tWh, Wh, n, ldk) || !make_map(&tWl, Wl, n, ldk) || !make_map(&tLh, Lh, n, ldk) ||
+      !make_map(&tLl, Ll, n, ldk))
+    return cudaErrorInvalidValue;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e =
+        cudaFuncSetAttribute(k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  TcArgs a;
+  a.C = C;
+  a.ldc = ldc;
+  a.n = n;
+  a.r0 = r0;
+  a.kblocks = kdim / kBK;
+  a.tiles = (m + kBM - 1) / kBM;
+  a.err = err_flag;
+  const int64_t nt = a.tiles * (a.tiles + 1) / 2;
+  k_update_tc<<<(unsigned)nt, kThreads, kSmemBytes, s>>>(tWh, tWl, tLh, tLl, a);
+  return cudaGetLastError();
+}
+
+}  // namespace dpp

@@ -1,0 +1,140 @@
+"""Mixed-precision (3xTF32 / FP32 SIMT) Hermitian path against the FP64 oracle.
+
+The mixed path must draw the oracle's set on every decision whose uniform is
+farther than 1e-9 from the pivot: outside its borderline band an FP32-derived
+pivot cannot flip a decision, and inside it the pivot is recomputed in FP64.
+log P(Y) is reported against the oracle with a relative tolerance of 1e-6
+(FP32 working precision of the factors; the pivots themselves are FP64).
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import oracle as O
+from tests._parity import compare_draw, pre_decision_pivots
+
+pytestmark = pytest.mark.gpu
+
+MIXED_LOGP_RTOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def dpp():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1905_00165_gb300 as m
+    return m
+
+
+@pytest.fixture(params=[1, 0], ids=["simt", "tcgen05"])
+def update_kernel(request, dpp):
+    from paper_1905_00165_gb300 import _lib
+    old = _lib.get_tuning(_lib.DPP_TUNE_UPDATE_KERNEL)
+    _lib.set_tuning(_lib.DPP_TUNE_UPDATE_KERNEL, request.param)
+    yield request.param
+    _lib.set_tuning(_lib.DPP_TUNE_UPDATE_KERNEL, old)
+
+
+def _run(dpp, K, seed=0, uniforms=None, factor=False):
+    import torch
+    Kd = torch.from_numpy(np.ascontiguousarray(K)).cuda()
+    u = None if uniforms is None else torch.from_numpy(uniforms).cuda()
+    s = dpp.sample_hermitian(Kd, seed=seed, precision="3xtf32", uniforms=u, factor=factor)
+    torch.cuda.synchronize()
+    return s
+
+
+@pytest.mark.parametrize("n", [1, 31, 33, 100, 257, 300, 600, 1100])
+def test_mixed_parity(dpp, update_kernel, n):
+    from paper_1905_00165_gb300 import _lib
+    K = W.hermitian_kernel(n, seed=n + 3, kind="uniform")
+    for seed in range(3):
+        u = O.uniforms(seed, 0, n)
+        ref = O.sample_ldl(K, u)
+        s = _run(dpp, K, seed)
+        r = s.result()
+        assert r["status"] & (_lib.DPP_RES_TIMEOUT | _lib.DPP_RES_NONFINITE | _lib.DPP_RES_RECOMPUTE) == 0, r
+        compare_draw(s.keep.cpu().numpy(), r["logp"], s.pivots.cpu().numpy(), ref, u,
+                     logp_rtol=MIXED_LOGP_RTOL, piv_atol=1e-4)
+
+
+def test_forced_borderline_pivots_are_recomputed(dpp, update_kernel):
+    """Uniforms placed 1e-8 from the oracle's pivots (on the side that keeps the
+    oracle's decision): every one lies inside the mixed path's error band, so
+    each must be recomputed in FP64 and decided exactly."""
+    from paper_1905_00165_gb300 import _lib
+    n = 700
+    K = W.hermitian_kernel(n, seed=21, kind="beta")
+    u = O.uniforms(4, 0, n)
+    ref = O.sample_ldl(K, u)
+    pre = pre_decision_pivots(ref)
+    targets = [0, 5, 31, 32, 40, 255, 256, 300, 511, 600, 699]
+    for j in targets:
+        u[j] = pre[j] - 1e-8 if ref.keep[j] else pre[j] + 1e-8
+    ref2 = O.sample_ldl(K, u)
+    assert np.array_equal(ref2.keep, ref.keep)
+    s = _run(dpp, K, uniforms=u)
+    r = s.result()
+    assert r["status"] & (_lib.DPP_RES_TIMEOUT | _lib.DPP_RES_RECOMPUTE) == 0, r
+    assert r["n_borderline"] >= len(targets) - 1, r  # pivot 0 is exact in any precision
+    assert np.array_equal(s.keep.cpu().numpy(), ref2.keep)
+    assert abs(r["logp"] - ref2.logp) <= MIXED_LOGP_RTOL * abs(ref2.logp)
+    gp = s.pivots.cpu().numpy()
+    for j in targets:
+        assert abs(gp[j] - ref2.pivots[j]) < 1e-10, (j, gp[j], ref2.pivots[j])
+
+
+def test_mixed_projection_and_spanning_trees(dpp, update_kernel):
+    n = 640
+    K = W.hermitian_kernel(n, seed=2, kind="projection")
+    for seed in range(3):
+        assert int(_run(dpp, K, seed).keep.sum().item()) == n // 4
+    d = 16
+    K, edges, V = W.ust_grid_kernel(d)
+    ref = -W.grid_spanning_tree_log_count(d)
+    for seed in range(3):
+        s = _run(dpp, K, seed)
+        keep = s.keep.cpu().numpy().astype(bool)
+        assert O.is_spanning_tree(edges[keep], V)
+        assert abs(s.logp - ref) < MIXED_LOGP_RTOL * abs(ref)
+
+
+def test_tensor_core_update_matches_simt(dpp):
+    """Same forced decisions through both trailing-update kernels: the mixed
+    factors agree to FP32-level accuracy."""
+    import torch
+    from paper_1905_00165_gb300 import _lib
+    n = 900
+    K = W.hermitian_kernel(n, seed=5, kind="beta")
+    keep = O.sample_ldl(K, O.uniforms(1, 0, n)).keep
+    u = O.forced_uniforms(keep)
+    facs = []
+    old = _lib.get_tuning(_lib.DPP_TUNE_UPDATE_KERNEL)
+    try:
+        for kern in (1, 0):
+            _lib.set_tuning(_lib.DPP_TUNE_UPDATE_KERNEL, kern)
+            s = _run(dpp, K, uniforms=u, factor=True)
+            facs.append(np.tril(s.factor.cpu().numpy()))
+    finally:
+        _lib.set_tuning(_lib.DPP_TUNE_UPDATE_KERNEL, old)
+    ref = O.sample_ldl(K, u).A
+    err_simt = np.max(np.abs(facs[0] - np.tril(ref)))
+    err_tc = np.max(np.abs(facs[1] - np.tril(ref)))
+    assert err_simt < 1e-4 and err_tc < 1e-4, (err_simt, err_tc)
+
+
+def test_outer_block_sizes(dpp):
+    from paper_1905_00165_gb300 import _lib
+    n = 520
+    K = W.hermitian_kernel(n, seed=9, kind="uniform")
+    u = O.uniforms(3, 0, n)
+    ref = O.sample_ldl(K, u)
+    old = _lib.get_tuning(_lib.DPP_TUNE_OUTER_BLOCK)
+    try:
+        for nb in (32, 64, 128, 256):
+            _lib.set_tuning(_lib.DPP_TUNE_OUTER_BLOCK, nb)
+            s = _run(dpp, K, 3)
+            r = s.result()
+            compare_draw(s.keep.cpu().numpy(), r["logp"], None, ref, u, logp_rtol=MIXED_LOGP_RTOL)
+    finally:
+        _lib.set_tuning(_lib.DPP_TUNE_OUTER_BLOCK, old)
