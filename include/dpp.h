@@ -151,7 +151,9 @@ dpp_status dpp_sample_lu(const void* K, int64_t n, int64_t ld, int32_t dtype,
  * which is the derivative of log|det(K - 1_{Y^c})| (Theorem 1's likelihood).
  * The factors are recomputed (no Bernoulli draws: the decisions are `keep`).
  *   hermitian  nonzero: K Hermitian, lower triangle read; dK is returned as a
- *              full (Hermitian) matrix.
+ *              full (Hermitian) matrix, the gradient with respect to K taken
+ *              as a general matrix (a symmetric perturbation E of K changes
+ *              log P(Y) by Re tr(dK^H E)).
  *   dK         device, n x ld_dk of dtype (full matrix written).
  * Precision: DPP_PREC_FP64. */
 dpp_status dpp_logprob_backward(const void* K, int64_t n, int64_t ld,
