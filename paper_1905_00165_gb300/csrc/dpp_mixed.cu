@@ -42,26 +42,6 @@ __device__ inline float tf32_rna(float x) {
   return __uint_as_float(r);
 }
 
-struct MixedPanelArgs {
-  const double* K;
-  int64_t ldk;
-  float* A;
-  int64_t lda, n, q, p;
-  int b, NB;
-  const double* uniforms;
-  uint64_t seed, inst;
-  uint8_t* keep;
-  double* piv;
-  double* kd;
-  double* s;
-  float *Wk, *Lk, *Wh, *Wl, *Lh, *Ll;
-  dpp_result* res;
-  unsigned* flag;
-  unsigned epoch;
-  double tol, tau_c;
-  RecomputeArgs rc;
-};
-
 __global__ void __launch_bounds__(256) k_convert(const double* K, int64_t ldk, float* A,
                                                  int64_t lda, int64_t n, double* kd, double* s) {
   for (int64_t j = blockIdx.x; j < n; j += gridDim.x) {
@@ -83,162 +63,101 @@ __global__ void __launch_bounds__(256) k_export(const float* A, int64_t lda, con
   }
 }
 
-// Panel of the mixed path: decisions on the 32 x 32 diagonal block (CTA 0,
-// warp 0), then the FP32 panel solve for every row below (all CTAs).
+// One cooperative launch per outer block [p, p + NBp) of the mixed path.
 //
-// The decision loop runs in FP32 (FP64 instructions cost ~64 cycles per warp
-// on this part, and the loop is a strict sequential chain): the running
-// diagonal is a double-float (~48 bits), the Bernoulli test u < d and the
-// borderline test |u - d| <= tau are evaluated in FP32 with tau widened by the
-// FP32 rounding of u and d (2^-22 absolute). Outside the band the FP32 test
-// and the FP64 test cannot disagree; inside it the pivot is recomputed in FP64
-// from K and decided in FP64. Final pivots and log|d| are then formed in FP64,
-// once per panel, in parallel over the lanes.
-__global__ void __launch_bounds__(kPanelThreads) k_panel_mixed(MixedPanelArgs a) {
-  __shared__ float blk[kPanel][kPanel + 1];
-  __shared__ float srd[kPanel];
-  __shared__ int s_ok;
-  float* A = a.A;
-  const int b = a.b;
-  const int64_t q = a.q, lda = a.lda;
+// CTA 0 owns the rows of the outer block's diagonal block and runs ahead
+// through its 32-wide inner panels: left-looking update of the panel from the
+// block's earlier panels, the sequential decisions (warp 0), and the panel
+// solve of its remaining rows; after each panel it releases two flags (the
+// panel's L11 and pivots; the rows the next panel needs). CTAs 1..G-1 own the
+// rows below the outer block and stream behind CTA 0 (update, wait, solve),
+// serving FP64 recompute requests while they wait.
+struct OuterArgs {
+  const double* K;
+  int64_t ldk;
+  float* A;
+  int64_t lda, n, p;
+  int NBp, NB;
+  const double* uniforms;
+  uint64_t seed, inst;
+  uint8_t* keep;
+  double* piv;
+  double* kd;
+  double* s;
+  float *Wk, *Lk, *Wh, *Wl, *Lh, *Ll;
+  float* rdv;  // FP32 reciprocal of each final pivot
+  dpp_result* res;
+  unsigned epoch0;  // epoch of the first inner panel of this block
+  double tol;
+  float tau0;
+  int64_t wrow0, wrows;  // worker w >= 1 owns rows [wrow0 + (w-1) wrows, ... + wrows)
+  RecomputeArgs rc;
+};
 
-  if (blockIdx.x == 0) {
-    for (int idx = threadIdx.x; idx < kPanel * kPanel; idx += blockDim.x) {
-      const int i = idx % kPanel, k = idx / kPanel;
-      float v = 0.f;
-      if (i < b && k < b) v = (k <= i) ? A[(q + i) + (q + k) * lda] : A[(q + k) + (q + i) * lda];
-      blk[i][k] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      const int lane = threadIdx.x;
-      double u = 2.0;
-      float uf = 2.f, si = 0.f, kf = 0.f;
-      f2 dd = {0.f, 0.f};
-      if (lane < b) {
-        u = a.uniforms ? a.uniforms[q + lane] : philox_uniform(a.seed, a.inst, (uint64_t)(q + lane));
-        uf = (float)u;
-        dd = f2_from_double(a.kd[q + lane]);
-        si = (float)a.s[q + lane];
-        kf = (float)a.K[(q + lane) + (q + lane) * a.ldk];
-      }
-      const float tau0 = (float)(a.tau_c * kUEff);
-      int border = 0, seq = 0;
-      float max_ratio = 0.f;
-      bool rc_failed = false;
-      bool mykeep = false;
-      for (int j = 0; j < b; ++j) {
-        const float ph = __shfl_sync(kFull, dd.hi, j);
-        const float uj = __shfl_sync(kFull, uf, j);
-        const float sj = __shfl_sync(kFull, si, j);
-        const float kj = __shfl_sync(kFull, kf, j);
-        const float tau = tau0 * sqrtf((float)(q + j + 1)) * (fabsf(kj) + sj) + 0x1.0p-22f;
-        bool kp;
-        float df;
-        if (fabsf(uj - ph) <= tau) {
-          // Borderline: recompute d_j in FP64 from K with the worker CTAs and
-          // decide in FP64.
-          const double p64 = f2_to_double(make_f2(ph, __shfl_sync(kFull, dd.lo, j)));
-          if (lane < j) a.piv[q + lane] = f2_to_double(dd);
-          double pe = p64, est = 0.0;
-          const bool ok = recompute_leader(a.rc, blk, b, j, a.epoch, &seq, &pe, &est);
-          const double ujd = __shfl_sync(kFull, u, j);
-          kp = ujd < pe;
-          const double dfin = kp ? pe : pe - 1.0;
-          df = (float)dfin;
-          if (lane == j) dd = f2_from_double(dfin);
-          ++border;
-          const float ratio = (float)(fabs(pe - p64) / (double)tau);
-          max_ratio = fmaxf(max_ratio, ratio);
-          if (!ok || est > fabs(ujd - pe)) rc_failed = true;
-        } else {
-          kp = uj < ph;
-          df = kp ? ph : ph - 1.0f;
-          if (lane == j && !kp) dd = f2_add_f(dd, -1.0f);
-        }
-        const float rd = 1.0f / df;
-        __syncwarp();
-        if (lane > j && lane < b) {
-          const float w = blk[lane][j];
-          const float l = w * rd;
-          for (int k = j + 1; k < b; ++k) blk[lane][k] = fmaf(-l, blk[j][k], blk[lane][k]);
-          blk[lane][j] = l;
-          dd = f2_sub_prod(dd, w, l);
-          si += fabsf(w * l);
-        }
-        if (lane == j) mykeep = kp;
-        if (lane == 0) {
-          blk[j][j] = df;
-          a.keep[q + j] = kp ? 1 : 0;
-        }
-        __syncwarp();
-      }
-      // final pivots (FP64), likelihood and bookkeeping, one lane per row
-      double lp = 0.0;
-      int kept = 0, oor = 0, bad = 0;
-      if (lane < b) {
-        const double d = f2_to_double(dd);
-        const double pre = mykeep ? d : d + 1.0;
-        a.piv[q + lane] = d;
-        srd[lane] = (float)(1.0 / d);
-        lp = log(fabs(d));
-        kept = mykeep ? 1 : 0;
-        oor = (pre < -a.tol || pre > 1.0 + a.tol) ? 1 : 0;
-        bad = isfinite(d) ? 0 : 1;
-      } else {
-        srd[lane] = 1.f;
-      }
-      lp = warp_sum(lp);
+enum { kCtlRows = 8 };  // control word: rows of the outer block solved through epoch
+
+constexpr int kThreadsOuter = 256;
+constexpr size_t kOuterDynSmem = sizeof(float) * kMaxOuterBlock * kPanel;  // staged Lk
+
+// A[i, q+c] -= sum_{t < kk} Wk[i, t] Lk[q+c, t] for rows [r_lo, r_hi), c < b,
+// restricted to i >= q + c. sLk[t][c] holds Lk rows [q, q+b) (staged by the
+// caller). Items are (row, group of 8 columns).
+__device__ void inner_update(const OuterArgs& a, const float* sLk, int64_t q, int b, int kk,
+                             int64_t r_lo, int64_t r_hi, int tid, int nthr) {
+  if (kk <= 0) return;
+  const int64_t rows = r_hi - r_lo;
+  for (int64_t it = tid; it < rows * 4; it += nthr) {
+    const int64_t i = r_lo + it / 4;
+    const int c0 = (int)(it % 4) * 8;
+    if (c0 >= b) continue;
+    float acc[8];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        kept += __shfl_xor_sync(kFull, kept, o);
-        oor += __shfl_xor_sync(kFull, oor, o);
-        bad |= __shfl_xor_sync(kFull, bad, o);
-      }
-      if (lane == 0) {
-        dpp_result* r = a.res;
-        r->logp += lp;
-        if (kept) atomicAdd(&r->n_kept, kept);
-        if (oor) {
-          atomicAdd(&r->n_out_of_range, oor);
-          atomicOr(&r->status, DPP_RES_INADMISSIBLE);
-        }
-        if (bad) atomicOr(&r->status, DPP_RES_NONFINITE);
-        if (border) {
-          atomicAdd(&r->n_borderline, border);
-          if ((double)max_ratio > r->max_err_ratio) r->max_err_ratio = (double)max_ratio;
-        }
-        if (rc_failed) atomicOr(&r->status, DPP_RES_RECOMPUTE);
+    for (int cc = 0; cc < 8; ++cc) acc[cc] = 0.f;
+    const float4* wr = reinterpret_cast<const float4*>(a.Wk + i * (int64_t)a.NB);
+    for (int t4 = 0; t4 < kk / 4; ++t4) {
+      const float4 w = __ldcg(wr + t4);
+      const float wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float4 l0 = *reinterpret_cast<const float4*>(&sLk[(4 * t4 + e) * kPanel + c0]);
+        const float4 l1 = *reinterpret_cast<const float4*>(&sLk[(4 * t4 + e) * kPanel + c0 + 4]);
+        acc[0] = fmaf(wv[e], l0.x, acc[0]);
+        acc[1] = fmaf(wv[e], l0.y, acc[1]);
+        acc[2] = fmaf(wv[e], l0.z, acc[2]);
+        acc[3] = fmaf(wv[e], l0.w, acc[3]);
+        acc[4] = fmaf(wv[e], l1.x, acc[4]);
+        acc[5] = fmaf(wv[e], l1.y, acc[5]);
+        acc[6] = fmaf(wv[e], l1.z, acc[6]);
+        acc[7] = fmaf(wv[e], l1.w, acc[7]);
       }
     }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < kPanel * kPanel; idx += blockDim.x) {
-      const int i = idx % kPanel, k = idx / kPanel;
-      if (i < b && k <= i) A[(q + i) + (q + k) * lda] = blk[i][k];
+#pragma unroll
+    for (int cc = 0; cc < 8; ++cc) {
+      const int c = c0 + cc;
+      if (c < b && i >= q + c) a.A[i + (q + c) * a.lda] -= acc[cc];
     }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) recompute_release_done(a.rc, a.epoch);
-  } else {
-    // Serve recompute requests until CTA 0 reports the decisions done.
-    if (!recompute_follower(a.rc, a.epoch, &s_ok)) return;
-    for (int idx = threadIdx.x; idx < kPanel * kPanel; idx += blockDim.x) {
-      const int i = idx % kPanel, k = idx / kPanel;
-      if (i < b && k < i) blk[i][k] = __ldcg(&A[(q + i) + (q + k) * lda]);
-    }
-    if (threadIdx.x < kPanel) {
-      const double d = threadIdx.x < b ? __ldcg(&a.piv[q + threadIdx.x]) : 1.0;
-      srd[threadIdx.x] = (float)(1.0 / d);
-    }
-    __syncthreads();
   }
+}
 
-  // Panel solve for rows below the block (FP32): w = a L11^{-T}, l = w / d.
-  const int64_t m = a.n - q - b;
+// Stage Lk rows [q, q+b), columns t < kk, into sLk[t][c].
+__device__ void stage_lk(const OuterArgs& a, float* sLk, int64_t q, int b, int kk, int tid,
+                         int nthr) {
+  for (int idx = tid; idx < kk * kPanel; idx += nthr) {
+    const int t = idx % kk, c = idx / kk;
+    sLk[t * kPanel + c] = (c < b) ? __ldcg(&a.Lk[(q + c) * (int64_t)a.NB + t]) : 0.f;
+  }
+}
+
+// Panel solve of rows [r_lo, r_hi) against the factored 32 x 32 block:
+// w = a L11^{-T} (FP32), l = w / d; writes L into A, W/L (and their TF32
+// hi/lo splits) into the row-major operand buffers, and folds sum w l into
+// the FP64 running diagonal.
+__device__ void panel_solve(const OuterArgs& a, const float (*sL)[kPanel + 1], const float* srd,
+                            int64_t q, int b, int64_t r_lo, int64_t r_hi, int tid, int nthr) {
   const int t0 = (int)(q - a.p);
-  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < m;
-       r += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = q + b + r;
+  float* A = a.A;
+  const int64_t lda = a.lda;
+  for (int64_t i = r_lo + tid; i < r_hi; i += nthr) {
     float w[kPanel];
 #pragma unroll
     for (int k = 0; k < kPanel; ++k) w[k] = (k < b) ? A[i + (q + k) * lda] : 0.f;
@@ -246,7 +165,7 @@ __global__ void __launch_bounds__(kPanelThreads) k_panel_mixed(MixedPanelArgs a)
     for (int k = 1; k < kPanel; ++k) {
       if (k < b) {
 #pragma unroll
-        for (int t = 0; t < k; ++t) w[k] = fmaf(-w[t], blk[k][t], w[k]);
+        for (int t = 0; t < k; ++t) w[k] = fmaf(-w[t], sL[k][t], w[k]);
       }
     }
     float l[kPanel];
@@ -275,20 +194,264 @@ __global__ void __launch_bounds__(kPanelThreads) k_panel_mixed(MixedPanelArgs a)
     float4* llo = reinterpret_cast<float4*>(a.Ll + off);
 #pragma unroll
     for (int v = 0; v < kPanel / 4; ++v) {
-      float4 W4 = make_float4(w[4 * v], w[4 * v + 1], w[4 * v + 2], w[4 * v + 3]);
-      float4 L4 = make_float4(l[4 * v], l[4 * v + 1], l[4 * v + 2], l[4 * v + 3]);
-      float4 WH = make_float4(tf32_rna(W4.x), tf32_rna(W4.y), tf32_rna(W4.z), tf32_rna(W4.w));
-      float4 LH = make_float4(tf32_rna(L4.x), tf32_rna(L4.y), tf32_rna(L4.z), tf32_rna(L4.w));
-      float4 WL = make_float4(tf32_rna(W4.x - WH.x), tf32_rna(W4.y - WH.y), tf32_rna(W4.z - WH.z),
-                              tf32_rna(W4.w - WH.w));
-      float4 LL = make_float4(tf32_rna(L4.x - LH.x), tf32_rna(L4.y - LH.y), tf32_rna(L4.z - LH.z),
-                              tf32_rna(L4.w - LH.w));
+      const float4 W4 = make_float4(w[4 * v], w[4 * v + 1], w[4 * v + 2], w[4 * v + 3]);
+      const float4 L4 = make_float4(l[4 * v], l[4 * v + 1], l[4 * v + 2], l[4 * v + 3]);
+      const float4 WH = make_float4(tf32_rna(W4.x), tf32_rna(W4.y), tf32_rna(W4.z), tf32_rna(W4.w));
+      const float4 LH = make_float4(tf32_rna(L4.x), tf32_rna(L4.y), tf32_rna(L4.z), tf32_rna(L4.w));
+      const float4 WL = make_float4(tf32_rna(W4.x - WH.x), tf32_rna(W4.y - WH.y),
+                                    tf32_rna(W4.z - WH.z), tf32_rna(W4.w - WH.w));
+      const float4 LL = make_float4(tf32_rna(L4.x - LH.x), tf32_rna(L4.y - LH.y),
+                                    tf32_rna(L4.z - LH.z), tf32_rna(L4.w - LH.w));
       wk[v] = W4;
       lk[v] = L4;
       wh[v] = WH;
       wlo[v] = WL;
       lh[v] = LH;
       llo[v] = LL;
+    }
+  }
+}
+
+// Per-outer-block bookkeeping kept by CTA 0 (shared memory).
+struct BlockLog {
+  float dhi[kMaxOuterBlock];
+  float dlo[kMaxOuterBlock];
+  unsigned char kp[kMaxOuterBlock];
+  int border;
+  float max_ratio;
+  int rc_failed;
+};
+
+// Borderline step (rare path, kept out of the unrolled loop): recompute the
+// pivot of local index j in FP64 and decide in FP64. The rows of the block
+// must be in blk. Returns the final FP64 pivot; *kp receives the decision.
+__device__ __noinline__ double borderline_step(const OuterArgs& a, float (*blk)[kPanel + 1], int b,
+                                               int64_t q, int j, unsigned epoch, int* seq,
+                                               f2 dd_j, double u_j, float tau, bool* kp,
+                                               BlockLog* bl) {
+  const int lane = threadIdx.x & 31;
+  const double p64 = f2_to_double(dd_j);
+  double pe = p64, est = 0.0;
+  const bool ok = recompute_leader(a.rc, blk, b, q, j, epoch, seq, &pe, &est);
+  const bool keep = u_j < pe;
+  *kp = keep;
+  if (lane == 0) {
+    bl->border += 1;
+    const float ratio = (float)(fabs(pe - p64) / (double)tau);
+    if (ratio > bl->max_ratio) bl->max_ratio = ratio;
+    if (!ok || est > fabs(u_j - pe)) bl->rc_failed = 1;
+  }
+  return keep ? pe : pe - 1.0;
+}
+
+__global__ void __launch_bounds__(kThreadsOuter) k_outer_mixed(OuterArgs a) {
+  extern __shared__ __align__(16) float sLk[];  // [kMaxOuterBlock][kPanel]
+  __shared__ float sL[kPanel][kPanel + 1];
+  __shared__ float srd[kPanel];
+  __shared__ BlockLog bl;
+  __shared__ int s_ok;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t p = a.p, n = a.n;
+  const int64_t pend = p + a.NBp;
+  float* A = a.A;
+  const int64_t lda = a.lda;
+
+  if (blockIdx.x == 0) {
+    if (tid == 0) {
+      bl.border = 0;
+      bl.max_ratio = 0.f;
+      bl.rc_failed = 0;
+    }
+    int seq = 0;
+    for (int64_t q = p; q < pend; q += kPanel) {
+      const int b = (int)((pend - q) < kPanel ? (pend - q) : kPanel);
+      const int kk = (int)(q - p);
+      const unsigned epoch = a.epoch0 + (unsigned)((q - p) / kPanel);
+      // (A) left-looking update of this panel's columns for the block's rows
+      stage_lk(a, sLk, q, b, kk, tid, kThreadsOuter);
+      __syncthreads();
+      inner_update(a, sLk, q, b, kk, q, pend, tid, kThreadsOuter);
+      __syncthreads();
+      // (B) decisions, warp 0, rows of the diagonal block in registers
+      if (warp == 0) {
+        float r[kPanel];
+#pragma unroll
+        for (int k = 0; k < kPanel; ++k) {
+          float v = 0.f;
+          if (lane < b && k < b)
+            v = (k <= lane) ? A[(q + lane) + (q + k) * lda] : A[(q + k) + (q + lane) * lda];
+          r[k] = v;
+        }
+        double u = 2.0;
+        float uf = 2.f, si = 0.f, kf = 0.f, sq = 1.f;
+        f2 dd = {0.f, 0.f};
+        if (lane < b) {
+          u = a.uniforms ? a.uniforms[q + lane]
+                         : philox_uniform(a.seed, a.inst, (uint64_t)(q + lane));
+          uf = (float)u;
+          dd = f2_from_double(a.kd[q + lane]);
+          si = (float)a.s[q + lane];
+          kf = (float)a.K[(q + lane) + (q + lane) * a.ldk];
+          sq = sqrtf((float)(q + lane + 1));
+        }
+        bool mykeep = false;
+#pragma unroll
+        for (int j = 0; j < kPanel; ++j) {
+          if (j < b) {
+            const float ph = __shfl_sync(kFull, dd.hi, j);
+            const float uj = __shfl_sync(kFull, uf, j);
+            const float sj = __shfl_sync(kFull, si, j);
+            const float kj = __shfl_sync(kFull, kf, j);
+            const float sqj = __shfl_sync(kFull, sq, j);
+            const float tau = a.tau0 * sqj * (fabsf(kj) + sj) + 0x1.0p-22f;
+            bool kp;
+            float df;
+            if (fabsf(uj - ph) <= tau) {
+              // rows to shared memory for the recompute leader
+#pragma unroll
+              for (int k = 0; k < kPanel; ++k) sL[lane][k] = r[k];
+              if (lane < j) a.piv[q + lane] = f2_to_double(dd);
+              __syncwarp();
+              const f2 ddj = make_f2(ph, __shfl_sync(kFull, dd.lo, j));
+              const double uj64 = __shfl_sync(kFull, u, j);
+              const double dfin = borderline_step(a, sL, b, q, j, epoch, &seq, ddj, uj64, tau, &kp, &bl);
+              df = (float)dfin;
+              if (lane == j) dd = f2_from_double(dfin);
+            } else {
+              kp = uj < ph;
+              df = kp ? ph : ph - 1.0f;
+              if (lane == j && !kp) dd = f2_add_f(dd, -1.0f);
+            }
+            const float rd = 1.0f / df;
+            const float wj = r[j];
+            const float l = wj * rd;
+            const bool act = (lane > j) && (lane < b);
+#pragma unroll
+            for (int k = j + 1; k < kPanel; ++k) {
+              const float pk = __shfl_sync(kFull, r[k], j);
+              if (act) r[k] = fmaf(-l, pk, r[k]);
+            }
+            if (act) {
+              r[j] = l;
+              dd = f2_sub_prod(dd, wj, l);
+              si += fabsf(wj * l);
+            }
+            if (lane == j) {
+              r[j] = df;
+              mykeep = kp;
+            }
+          }
+        }
+        // publish the block: L11 (lower), pivots, reciprocals
+#pragma unroll
+        for (int k = 0; k < kPanel; ++k) {
+          sL[lane][k] = r[k];
+          if (lane < b && k <= lane) A[(q + lane) + (q + k) * lda] = r[k];
+        }
+        if (lane < b) {
+          const double d = f2_to_double(dd);
+          a.piv[q + lane] = d;
+          a.keep[q + lane] = mykeep ? 1 : 0;
+          const float rdl = (float)(1.0 / d);
+          srd[lane] = rdl;
+          a.rdv[q + lane] = rdl;
+          bl.dhi[kk + lane] = dd.hi;
+          bl.dlo[kk + lane] = dd.lo;
+          bl.kp[kk + lane] = mykeep ? 1 : 0;
+        } else {
+          srd[lane] = 1.f;
+        }
+      }
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) recompute_release_done(a.rc, epoch);
+      // (C) panel solve of the block's remaining rows
+      panel_solve(a, sL, srd, q, b, q + b, pend, tid, kThreadsOuter);
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) st_release(&a.rc.ctrl[kCtlRows], epoch);
+    }
+    // likelihood and bookkeeping of the block (FP64, one pivot per thread)
+    double lp = 0.0;
+    int kept = 0, oor = 0, bad = 0;
+    for (int i = tid; i < a.NBp; i += kThreadsOuter) {
+      const double d = (double)bl.dhi[i] + (double)bl.dlo[i];
+      const double pre = bl.kp[i] ? d : d + 1.0;
+      lp += log(fabs(d));
+      kept += bl.kp[i];
+      oor += (pre < -a.tol || pre > 1.0 + a.tol) ? 1 : 0;
+      bad |= isfinite(d) ? 0 : 1;
+    }
+    lp = warp_sum(lp);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      kept += __shfl_xor_sync(kFull, kept, o);
+      oor += __shfl_xor_sync(kFull, oor, o);
+      bad |= __shfl_xor_sync(kFull, bad, o);
+    }
+    __shared__ double s_lp[kThreadsOuter / 32];
+    __shared__ int s_cnt[3][kThreadsOuter / 32];
+    if (lane == 0) {
+      s_lp[warp] = lp;
+      s_cnt[0][warp] = kept;
+      s_cnt[1][warp] = oor;
+      s_cnt[2][warp] = bad;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double L = 0.0;
+      int K = 0, O = 0, B = 0;
+      for (int w = 0; w < kThreadsOuter / 32; ++w) {
+        L += s_lp[w];
+        K += s_cnt[0][w];
+        O += s_cnt[1][w];
+        B |= s_cnt[2][w];
+      }
+      dpp_result* r = a.res;
+      r->logp += L;
+      if (K) atomicAdd(&r->n_kept, K);
+      if (O) {
+        atomicAdd(&r->n_out_of_range, O);
+        atomicOr(&r->status, DPP_RES_INADMISSIBLE);
+      }
+      if (B) atomicOr(&r->status, DPP_RES_NONFINITE);
+      if (bl.border) {
+        atomicAdd(&r->n_borderline, bl.border);
+        if ((double)bl.max_ratio > r->max_err_ratio) r->max_err_ratio = (double)bl.max_ratio;
+      }
+      if (bl.rc_failed) atomicOr(&r->status, DPP_RES_RECOMPUTE);
+    }
+    return;
+  }
+
+  // ---- workers: rows below the outer block ----
+  const int64_t w = blockIdx.x - 1;
+  int64_t r_lo = a.wrow0 + w * a.wrows;
+  int64_t r_hi = r_lo + a.wrows;
+  if (r_lo > n) r_lo = n;
+  if (r_hi > n) r_hi = n;
+  for (int64_t q = p; q < pend; q += kPanel) {
+    const int b = (int)((pend - q) < kPanel ? (pend - q) : kPanel);
+    const int kk = (int)(q - p);
+    const unsigned epoch = a.epoch0 + (unsigned)((q - p) / kPanel);
+    if (kk > 0 && r_lo < r_hi) {
+      if (tid == 0) s_ok = rc_wait_geq(a.rc, &a.rc.ctrl[kCtlRows], epoch - 1) ? 1 : 0;
+      __syncthreads();
+      if (!s_ok) return;
+      stage_lk(a, sLk, q, b, kk, tid, kThreadsOuter);
+      __syncthreads();
+      inner_update(a, sLk, q, b, kk, r_lo, r_hi, tid, kThreadsOuter);
+    }
+    if (!recompute_follower(a.rc, epoch, &s_ok)) return;
+    if (r_lo < r_hi) {
+      for (int idx = tid; idx < kPanel * kPanel; idx += kThreadsOuter) {
+        const int i = idx % kPanel, k = idx / kPanel;
+        sL[i][k] = (i < b && k < i) ? __ldcg(&A[(q + i) + (q + k) * lda]) : 0.f;
+      }
+      if (tid < kPanel) srd[tid] = tid < b ? __ldcg(&a.rdv[q + tid]) : 1.f;
+      __syncthreads();
+      panel_solve(a, sL, srd, q, b, r_lo, r_hi, tid, kThreadsOuter);
+      __syncthreads();
     }
   }
 }
@@ -380,6 +543,7 @@ struct MixedLayout {
   float* A32;
   float *Wk, *Lk, *Wh, *Wl, *Lh, *Ll;
   double *kd, *s, *piv;
+  float* rdv;
   unsigned* flag;
   int* err;
   RecomputeScratch rs;
@@ -401,11 +565,12 @@ bool carve(Workspace& ws, int64_t n, int NB, MixedLayout* L) {
   L->kd = static_cast<double*>(ws.take(sizeof(double) * nn));
   L->s = static_cast<double*>(ws.take(sizeof(double) * nn));
   L->piv = static_cast<double*>(ws.take(sizeof(double) * nn));
+  L->rdv = static_cast<float*>(ws.take(sizeof(float) * nn));
   L->flag = static_cast<unsigned*>(ws.take(256));
   L->err = reinterpret_cast<int*>(L->flag) + 16;
   if (!recompute_carve(ws, n, &L->rs)) return false;
   return L->A32 && L->Wk && L->Lk && L->Wh && L->Wl && L->Lh && L->Ll && L->kd && L->s &&
-         L->piv && L->flag;
+         L->piv && L->rdv && L->flag;
 }
 
 }  // namespace
@@ -436,73 +601,73 @@ cudaError_t sample_mixed(const DrawArgs& a, Workspace ws) {
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   static int cap = 0;
-  if (cap == 0) cap = coop_capacity(k_panel_mixed, kPanelThreads);
+  if (cap == 0) {
+    cudaError_t ea = cudaFuncSetAttribute(k_outer_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)kOuterDynSmem);
+    if (ea != cudaSuccess) return ea;
+    DevInfo di;
+    if ((ea = dev_info(&di)) != cudaSuccess) return ea;
+    int per_sm = 0;
+    ea = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_outer_mixed, kThreadsOuter,
+                                                       kOuterDynSmem);
+    if (ea != cudaSuccess) return ea;
+    cap = per_sm * di.sm_count;
+    if (cap > kMaxCoopCtas) cap = kMaxCoopCtas;
+    if (cap < 2) return cudaErrorLaunchOutOfResources;
+  }
   unsigned epoch = 1;
   const bool use_tc = g_tuning.update_kernel == 0;
+  const int64_t min_workers = 64;  // recomputes are served by the workers
   for (int64_t p = 0; p < n; p += NB) {
     const int NBp = (int)((n - p) < NB ? (n - p) : NB);
-    for (int64_t q = p; q < p + NBp; q += kPanel, ++epoch) {
-      const int b = (int)((n - q) < kPanel ? (n - q) : kPanel);
-      if (q > p) {
-        // left-looking inner update of columns [q, q+b) from [p, q)
-        F32Args u;
-        u.C = L.A32;
-        u.ldc = L.ld32;
-        u.row0 = q;
-        u.n = n;
-        u.col0 = q;
-        u.col1 = q + b;
-        u.Aop = L.Wk;
-        u.Bop = L.Lk;
-        u.ldk = NB;
-        u.kk = (int)(q - p);
-        u.tiles_r = (n - q + kT - 1) / kT;
-        const double fl = 2.0 * (double)(n - q) * (double)b * (double)u.kk;
-        ProfScope ps(kProfUpdateF32, a.stream, fl, 0.0);
-        k_f32_update<false><<<(unsigned)u.tiles_r, 256, 0, a.stream>>>(u);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-      }
-      MixedPanelArgs pa;
-      pa.K = K;
-      pa.ldk = a.ld;
-      pa.A = L.A32;
-      pa.lda = L.ld32;
-      pa.n = n;
-      pa.q = q;
-      pa.p = p;
-      pa.b = b;
-      pa.NB = NB;
-      pa.uniforms = a.uniforms;
-      pa.seed = a.seed;
-      pa.inst = a.instance;
-      pa.keep = a.keep;
-      pa.piv = L.piv;
-      pa.kd = L.kd;
-      pa.s = L.s;
-      pa.Wk = L.Wk;
-      pa.Lk = L.Lk;
-      pa.Wh = L.Wh;
-      pa.Wl = L.Wl;
-      pa.Lh = L.Lh;
-      pa.Ll = L.Ll;
-      pa.res = a.result;
-      pa.flag = L.flag;
-      pa.epoch = epoch;
-      pa.tol = 1e-3;
-      pa.tau_c = g_tuning.tau_safety;
-      pa.rc = recompute_args(L.rs, K, a.ld, L.A32, L.ld32, L.piv, a.keep, n, q, a.result);
-      // at least two CTAs: CTA 0 decides, the others serve FP64 recomputes
-      int64_t g = (n - q - b + 63) / 64;
-      if (g < 2) g = 2;
-      if (g > cap) g = cap;
-      pa.rc.grid = (int)g;
-      void* args[] = {&pa};
+    {
+      OuterArgs oa;
+      oa.K = K;
+      oa.ldk = a.ld;
+      oa.A = L.A32;
+      oa.lda = L.ld32;
+      oa.n = n;
+      oa.p = p;
+      oa.NBp = NBp;
+      oa.NB = NB;
+      oa.uniforms = a.uniforms;
+      oa.seed = a.seed;
+      oa.inst = a.instance;
+      oa.keep = a.keep;
+      oa.piv = L.piv;
+      oa.kd = L.kd;
+      oa.s = L.s;
+      oa.Wk = L.Wk;
+      oa.Lk = L.Lk;
+      oa.Wh = L.Wh;
+      oa.Wl = L.Wl;
+      oa.Lh = L.Lh;
+      oa.Ll = L.Ll;
+      oa.rdv = L.rdv;
+      oa.res = a.result;
+      oa.epoch0 = epoch;
+      oa.tol = 1e-3;
+      oa.tau0 = (float)(g_tuning.tau_safety * 0x1.0p-22);
+      const int64_t mw = n - p - NBp;
+      int64_t nw = (mw + 127) / 128;
+      int64_t want = (n + 255) / 256;
+      if (want > min_workers) want = min_workers;
+      if (nw < want) nw = want;
+      if (nw < 1) nw = 1;
+      if (nw > cap - 1) nw = cap - 1;
+      oa.wrow0 = p + NBp;
+      oa.wrows = (mw + nw - 1) / nw;
+      if (oa.wrows < 1) oa.wrows = 1;
+      oa.rc = recompute_args(L.rs, K, a.ld, L.A32, L.ld32, L.piv, a.keep, n, p, a.result);
+      oa.rc.grid = (int)(nw + 1);
+      void* args[] = {&oa};
       {
         ProfScope ps(kProfPanel, a.stream);
-        e = cudaLaunchCooperativeKernel((const void*)k_panel_mixed, dim3((unsigned)g),
-                                        dim3(kPanelThreads), args, 0, a.stream);
+        e = cudaLaunchCooperativeKernel((const void*)k_outer_mixed, dim3((unsigned)(nw + 1)),
+                                        dim3(kThreadsOuter), args, kOuterDynSmem, a.stream);
       }
       if (e != cudaSuccess) return e;
+      epoch += (unsigned)((NBp + kPanel - 1) / kPanel);
     }
     const int64_t r0 = p + NBp;
     if (r0 < n) {

@@ -29,7 +29,7 @@ namespace dpp {
 
 // control words (unsigned[32] in the workspace)
 enum { kCtlReq = 0, kCtlG = 1, kCtlAck = 2, kCtlDone = 3, kCtlBarCount = 4, kCtlBarGen = 5,
-       kCtlAbort = 6 };
+       kCtlAbort = 6, kCtlQ = 7 };
 
 struct RecomputeScratch {
   unsigned* ctrl = nullptr;
@@ -167,7 +167,7 @@ __device__ inline bool recompute_serve(const RecomputeArgs& a, unsigned id) {
   const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
   const int w = blockIdx.x - 1, nw = a.grid - 1;
   const int64_t g = (int64_t)ld_acquire(&a.ctrl[kCtlG]);
-  const int64_t q = a.q;
+  const int64_t q = (int64_t)ld_acquire(&a.ctrl[kCtlQ]);
   const int64_t nblk = (g + 31) / 32;
   const float* A = a.A;
   const int64_t lda = a.lda;
@@ -178,46 +178,58 @@ __device__ inline bool recompute_serve(const RecomputeArgs& a, unsigned id) {
     a.ell[c] = (double)A[g + c * lda];
   if (!rc_worker_barrier(a, &s_flag)) return false;
 
-  // R1: x0 = L_P^{-T} ell, blocks from the last one down (owner t % nw == w)
+  // R1: x0 = L_P^{-T} ell (FP32 arithmetic: any x0 is admissible, its residual
+  // is computed exactly below), blocks from the last one down (owner t % nw == w)
   {
     int64_t t = nblk - 1;
     if (nblk > 0) t -= ((nblk - 1 - w) % nw + nw) % nw;
     for (; t >= 0; t -= nw) {
       const int nc = (int)((g - 32 * t) < 32 ? (g - 32 * t) : 32);
-      double acc = 0.0;
+      float acc = 0.f;
       bool ok = true;
       for (int64_t s = nblk - 1 - wp; s > t; s -= 8) {
         if (lane == 0) ok = rc_wait_geq(a, &a.flag_x[s], id);
         ok = __shfl_sync(0xffffffffu, ok, 0);
         if (!ok) break;
         const int nr = (int)((g - 32 * s) < 32 ? (g - 32 * s) : 32);
+        float tile[32];
+#pragma unroll
         for (int c = 0; c < 32; ++c)
-          sT[wp][c][lane] = (lane < nr && c < nc) ? __ldcg(&A[(32 * s + lane) + (32 * t + c) * lda]) : 0.f;
+          tile[c] = (lane < nr && c < nc) ? __ldcg(&A[(32 * s + lane) + (32 * t + c) * lda]) : 0.f;
+#pragma unroll
+        for (int c = 0; c < 32; ++c) sT[wp][c][lane] = tile[c];
         __syncwarp();
-        const double xs = (lane < nr) ? __ldcg(&a.x0[32 * s + lane]) : 0.0;
+        const float xs = (lane < nr) ? (float)__ldcg(&a.x0[32 * s + lane]) : 0.f;
+#pragma unroll
         for (int i = 0; i < 32; ++i) {
-          const double xi = __shfl_sync(0xffffffffu, xs, i);
-          acc = fma((double)sT[wp][lane][i], xi, acc);
+          const float xi = __shfl_sync(0xffffffffu, xs, i);
+          acc = fmaf(sT[wp][lane][i], xi, acc);
         }
         __syncwarp();
       }
-      spart[wp][lane] = acc;
+      spart[wp][lane] = (double)acc;
       __syncthreads();
       if (ld_acquire(&a.ctrl[kCtlAbort]) != 0) return false;
       if (wp == 0) {
-        double y = 0.0;
+        float y = 0.f;
         if (lane < nc) {
-          y = a.ell[32 * t + lane];
-          for (int k = 0; k < 8; ++k) y -= spart[k][lane];
+          double yd = a.ell[32 * t + lane];
+          for (int k = 0; k < 8; ++k) yd -= spart[k][lane];
+          y = (float)yd;
         }
+        float tile[32];
+#pragma unroll
         for (int c = 0; c < 32; ++c)
-          sT[0][c][lane] = (lane < nc && c < nc) ? __ldcg(&A[(32 * t + lane) + (32 * t + c) * lda]) : 0.f;
+          tile[c] = (lane < nc && c < nc) ? __ldcg(&A[(32 * t + lane) + (32 * t + c) * lda]) : 0.f;
+#pragma unroll
+        for (int c = 0; c < 32; ++c) sT[0][c][lane] = tile[c];
         __syncwarp();
-        for (int i = nc - 1; i >= 0; --i) {
-          const double xi = __shfl_sync(0xffffffffu, y, i);
-          if (lane < i) y = fma(-(double)sT[0][lane][i], xi, y);  // L[32t+i, 32t+lane]
+#pragma unroll
+        for (int i = 31; i >= 0; --i) {
+          const float xi = __shfl_sync(0xffffffffu, y, i);
+          if (i < nc && lane < i) y = fmaf(-sT[0][lane][i], xi, y);  // L[32t+i, 32t+lane]
         }
-        if (lane < nc) a.x0[32 * t + lane] = y;
+        if (lane < nc) a.x0[32 * t + lane] = (double)y;
         __threadfence();
         __syncwarp();
         if (lane == 0) st_release(&a.flag_x[t], id);
@@ -272,39 +284,47 @@ __device__ inline bool recompute_serve(const RecomputeArgs& a, unsigned id) {
   }
   if (!rc_worker_barrier(a, &s_flag)) return false;
 
-  // R3: v = L_P^{-1} r, e = sum v^2 / d, blocks from the first one up
+  // R3: v = L_P^{-1} r (FP32 arithmetic on the small residual), e = sum v^2 / d,
+  // blocks from the first one up
   double esum = 0.0;
   for (int64_t t = w; t < nblk; t += nw) {
     const int nr = (int)((g - 32 * t) < 32 ? (g - 32 * t) : 32);
-    double acc = 0.0;
+    float acc = 0.f;
     bool ok = true;
     for (int64_t s = wp; s < t; s += 8) {
       if (lane == 0) ok = rc_wait_geq(a, &a.flag_v[s], id);
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (!ok) break;
-      const double vs = __ldcg(&a.v[32 * s + lane]);
-      for (int c = 0; c < 32; ++c) {
-        const double vc = __shfl_sync(0xffffffffu, vs, c);
-        if (lane < nr) acc = fma((double)__ldcg(&A[(32 * t + lane) + (32 * s + c) * lda]), vc, acc);
-      }
+      float tile[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        tile[c] = (lane < nr) ? __ldcg(&A[(32 * t + lane) + (32 * s + c) * lda]) : 0.f;
+      const float vs = (float)__ldcg(&a.v[32 * s + lane]);
+#pragma unroll
+      for (int c = 0; c < 32; ++c) acc = fmaf(tile[c], __shfl_sync(0xffffffffu, vs, c), acc);
     }
-    spart[wp][lane] = acc;
+    spart[wp][lane] = (double)acc;
     __syncthreads();
     if (ld_acquire(&a.ctrl[kCtlAbort]) != 0) return false;
     if (wp == 0) {
-      double y = 0.0;
+      float y = 0.f;
       if (lane < nr) {
-        y = __ldcg(&a.r[32 * t + lane]);
-        for (int k = 0; k < 8; ++k) y -= spart[k][lane];
+        double yd = __ldcg(&a.r[32 * t + lane]);
+        for (int k = 0; k < 8; ++k) yd -= spart[k][lane];
+        y = (float)yd;
       }
-      for (int c = 0; c < nr; ++c) {
-        const double vc = __shfl_sync(0xffffffffu, y, c);
-        if (lane > c && lane < nr)
-          y = fma(-(double)__ldcg(&A[(32 * t + lane) + (32 * t + c) * lda]), vc, y);
+      float tile[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        tile[c] = (lane < nr && c < nr) ? __ldcg(&A[(32 * t + lane) + (32 * t + c) * lda]) : 0.f;
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        const float vc = __shfl_sync(0xffffffffu, y, c);
+        if (c < nr && lane > c && lane < nr) y = fmaf(-tile[c], vc, y);
       }
       if (lane < nr) {
-        a.v[32 * t + lane] = y;
-        esum += y * y / a.piv[32 * t + lane];
+        a.v[32 * t + lane] = (double)y;
+        esum += (double)y * (double)y / a.piv[32 * t + lane];
       }
       __threadfence();
       __syncwarp();
@@ -378,9 +398,10 @@ __device__ inline bool recompute_follower(const RecomputeArgs& a, unsigned epoch
 // carries l = L[g, q:g] in its first j entries. Returns the recomputed
 // pivot in *pe and an error estimate in *est (lane-uniform).
 __device__ inline bool recompute_leader(const RecomputeArgs& a, float (*blk)[kPanel + 1], int b,
-                                        int j, unsigned epoch, int* seq, double* pe, double* est) {
+                                        int64_t q, int j, unsigned epoch, int* seq, double* pe,
+                                        double* est) {
   const int lane = threadIdx.x & 31;
-  const int64_t q = a.q, g = q + j;
+  const int64_t g = q + j;
   for (int c = 0; c < j; ++c)
     if (lane > c && lane <= j) a.A[(q + lane) + (q + c) * a.lda] = blk[lane][c];
   if (lane < j) a.ell[q + lane] = (double)blk[j][lane];
@@ -392,6 +413,7 @@ __device__ inline bool recompute_leader(const RecomputeArgs& a, float (*blk)[kPa
   if (a.grid < 2) ok = false;
   if (ok && lane == 0) {
     atomicExch(&a.ctrl[kCtlG], (unsigned)g);
+    atomicExch(&a.ctrl[kCtlQ], (unsigned)q);
     __threadfence();
     st_release(&a.ctrl[kCtlReq], id);
     ok = rc_wait_geq(a, &a.ctrl[kCtlAck], id);

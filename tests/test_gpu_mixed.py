@@ -138,3 +138,41 @@ def test_outer_block_sizes(dpp):
             compare_draw(s.keep.cpu().numpy(), r["logp"], None, ref, u, logp_rtol=MIXED_LOGP_RTOL)
     finally:
         _lib.set_tuning(_lib.DPP_TUNE_OUTER_BLOCK, old)
+
+
+def _pivot_error_ratios(dpp, K, seed):
+    """|d_mixed - d_fp64| / (2^-22 sqrt(j+1) (K_jj + s_j)) for every pivot of one
+    draw, with the mixed path forced onto the FP64 path's decisions."""
+    import torch
+    n = K.shape[0]
+    Kd = torch.from_numpy(np.ascontiguousarray(K)).cuda()
+    s64 = dpp.sample_hermitian(Kd, seed=seed, precision="fp64", factor=True)
+    keep = s64.keep.cpu().numpy()
+    u = torch.from_numpy(O.forced_uniforms(keep)).cuda()
+    smx = dpp.sample_hermitian(Kd, precision="3xtf32", uniforms=u)
+    torch.cuda.synchronize()
+    d64 = s64.pivots.cpu().numpy()
+    dmx = smx.pivots.cpu().numpy()
+    F = s64.factor.cpu().numpy()
+    L = np.tril(F, -1)
+    s = (L * L) @ np.abs(d64)
+    scale = 2.0 ** -22 * np.sqrt(np.arange(n) + 1.0) * (np.abs(np.diag(K)) + s)
+    return np.abs(dmx - d64) / scale
+
+
+def test_borderline_band_has_margin(dpp):
+    """The band tau_j = c 2^-22 sqrt(j+1) (K_jj + s_j) must exceed the mixed
+    path's actual pivot error by a wide margin: over every pivot of several
+    draws of the workload shapes, the error stays below c / 8."""
+    from paper_1905_00165_gb300 import _lib
+    c = _lib.get_tuning(_lib.DPP_TUNE_TAU_SAFETY)
+    worst = 0.0
+    for n, kind, seed in [(2048, "beta", 0), (2048, "projection", 1), (3000, "uniform", 2)]:
+        K = W.hermitian_kernel(n, seed=seed, kind=kind)
+        r = _pivot_error_ratios(dpp, K, seed)
+        worst = max(worst, float(r.max()))
+    d = 20
+    K, _, _ = W.ust_grid_kernel(d)
+    worst = max(worst, float(_pivot_error_ratios(dpp, K, 3).max()))
+    print(f"max pivot error / (2^-22 sqrt(j+1)(K_jj+s_j)) = {worst:.3e}, c = {c}")
+    assert worst < c / 8.0
