@@ -100,67 +100,86 @@ constexpr int kThreadsOuter = 256;
 constexpr size_t kOuterDynSmem = sizeof(float) * kMaxOuterBlock * kPanel;  // staged Lk
 
 // A[i, q+c] -= sum_{t < kk} Wk[i, t] Lk[q+c, t] for rows [r_lo, r_hi), c < b,
-// restricted to i >= q + c. sLk[t][c] holds Lk rows [q, q+b) (staged by the
-// caller). Items are (row, group of 8 columns).
-__device__ void inner_update(const OuterArgs& a, const float* sLk, int64_t q, int b, int kk,
-                             int64_t r_lo, int64_t r_hi, int tid, int nthr) {
-  if (kk <= 0) return;
-  const int64_t rows = r_hi - r_lo;
-  for (int64_t it = tid; it < rows * 4; it += nthr) {
-    const int64_t i = r_lo + it / 4;
-    const int c0 = (int)(it % 4) * 8;
-    if (c0 >= b) continue;
-    float acc[8];
+// restricted to i >= q + c, as a shared-memory tiled product: 64-row tiles,
+// 32-deep chunks of W staged k-major in sW (coalesced row loads), L read from
+// sLk[t][c] (staged by the caller); each thread owns 2 rows x 4 columns.
+constexpr int kSwLd = 65;
+__device__ void inner_update(const OuterArgs& a, const float* sLk, float* sW, int64_t q, int b,
+                             int kk, int64_t r_lo, int64_t r_hi, int tid) {
+  if (kk <= 0 || r_lo >= r_hi) return;
+  const int ty = tid / 8, tx = tid % 8;
+  for (int64_t i0 = r_lo; i0 < r_hi; i0 += 64) {
+    float acc[2][4];
 #pragma unroll
-    for (int cc = 0; cc < 8; ++cc) acc[cc] = 0.f;
-    const float4* wr = reinterpret_cast<const float4*>(a.Wk + i * (int64_t)a.NB);
-    for (int t4 = 0; t4 < kk / 4; ++t4) {
-      const float4 w = __ldcg(wr + t4);
-      const float wv[4] = {w.x, w.y, w.z, w.w};
+    for (int rr = 0; rr < 2; ++rr)
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const float4 l0 = *reinterpret_cast<const float4*>(&sLk[(4 * t4 + e) * kPanel + c0]);
-        const float4 l1 = *reinterpret_cast<const float4*>(&sLk[(4 * t4 + e) * kPanel + c0 + 4]);
-        acc[0] = fmaf(wv[e], l0.x, acc[0]);
-        acc[1] = fmaf(wv[e], l0.y, acc[1]);
-        acc[2] = fmaf(wv[e], l0.z, acc[2]);
-        acc[3] = fmaf(wv[e], l0.w, acc[3]);
-        acc[4] = fmaf(wv[e], l1.x, acc[4]);
-        acc[5] = fmaf(wv[e], l1.y, acc[5]);
-        acc[6] = fmaf(wv[e], l1.z, acc[6]);
-        acc[7] = fmaf(wv[e], l1.w, acc[7]);
+      for (int cc = 0; cc < 4; ++cc) acc[rr][cc] = 0.f;
+    for (int k0 = 0; k0 < kk; k0 += 32) {
+      const int kc = (kk - k0) < 32 ? (kk - k0) : 32;
+      for (int idx = tid; idx < 64 * 8; idx += kThreadsOuter) {
+        const int r = idx / 8, f = idx % 8;
+        const int64_t i = i0 + r;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < r_hi && 4 * f < kc)
+          v = __ldcg(reinterpret_cast<const float4*>(a.Wk + i * (int64_t)a.NB + k0 + 4 * f));
+        sW[(4 * f + 0) * kSwLd + r] = v.x;
+        sW[(4 * f + 1) * kSwLd + r] = v.y;
+        sW[(4 * f + 2) * kSwLd + r] = v.z;
+        sW[(4 * f + 3) * kSwLd + r] = v.w;
       }
+      __syncthreads();
+      for (int t = 0; t < kc; ++t) {
+        const float w0 = sW[t * kSwLd + 2 * ty], w1 = sW[t * kSwLd + 2 * ty + 1];
+        const float4 l = *reinterpret_cast<const float4*>(&sLk[(k0 + t) * kPanel + 4 * tx]);
+        acc[0][0] = fmaf(w0, l.x, acc[0][0]);
+        acc[0][1] = fmaf(w0, l.y, acc[0][1]);
+        acc[0][2] = fmaf(w0, l.z, acc[0][2]);
+        acc[0][3] = fmaf(w0, l.w, acc[0][3]);
+        acc[1][0] = fmaf(w1, l.x, acc[1][0]);
+        acc[1][1] = fmaf(w1, l.y, acc[1][1]);
+        acc[1][2] = fmaf(w1, l.z, acc[1][2]);
+        acc[1][3] = fmaf(w1, l.w, acc[1][3]);
+      }
+      __syncthreads();
     }
 #pragma unroll
-    for (int cc = 0; cc < 8; ++cc) {
-      const int c = c0 + cc;
-      if (c < b && i >= q + c) a.A[i + (q + c) * a.lda] -= acc[cc];
+    for (int rr = 0; rr < 2; ++rr) {
+      const int64_t i = i0 + 2 * ty + rr;
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) {
+        const int c = 4 * tx + cc;
+        if (i < r_hi && c < b && i >= q + c) a.A[i + (q + c) * a.lda] -= acc[rr][cc];
+      }
     }
   }
 }
 
 // Stage Lk rows [q, q+b), columns t < kk, into sLk[t][c].
-__device__ void stage_lk(const OuterArgs& a, float* sLk, int64_t q, int b, int kk, int tid,
-                         int nthr) {
-  for (int idx = tid; idx < kk * kPanel; idx += nthr) {
+__device__ void stage_lk(const OuterArgs& a, float* sLk, int64_t q, int b, int kk, int tid) {
+  for (int idx = tid; idx < kk * kPanel; idx += kThreadsOuter) {
     const int t = idx % kk, c = idx / kk;
     sLk[t * kPanel + c] = (c < b) ? __ldcg(&a.Lk[(q + c) * (int64_t)a.NB + t]) : 0.f;
   }
 }
 
 // Panel solve of rows [r_lo, r_hi) against the factored 32 x 32 block:
-// w = a L11^{-T} (FP32), l = w / d; writes L into A, W/L (and their TF32
-// hi/lo splits) into the row-major operand buffers, and folds sum w l into
-// the FP64 running diagonal.
+// w = a L11^{-T} (FP32), l = w / d; writes L into A (column-major, coalesced),
+// folds sum w l into the FP64 running diagonal, and writes W, L and their TF32
+// hi/lo splits row-major through a per-warp shared-memory transpose so every
+// store is a full 128-byte row segment. All threads iterate together.
 __device__ void panel_solve(const OuterArgs& a, const float (*sL)[kPanel + 1], const float* srd,
-                            int64_t q, int b, int64_t r_lo, int64_t r_hi, int tid, int nthr) {
+                            float (*stage)[kPanel][kPanel + 1], int64_t q, int b, int64_t r_lo,
+                            int64_t r_hi, int tid) {
   const int t0 = (int)(q - a.p);
+  const int warp = tid >> 5, lane = tid & 31;
   float* A = a.A;
   const int64_t lda = a.lda;
-  for (int64_t i = r_lo + tid; i < r_hi; i += nthr) {
+  for (int64_t base = r_lo; base < r_hi; base += kThreadsOuter) {
+    const int64_t i = base + tid;
+    const bool valid = i < r_hi;
     float w[kPanel];
 #pragma unroll
-    for (int k = 0; k < kPanel; ++k) w[k] = (k < b) ? A[i + (q + k) * lda] : 0.f;
+    for (int k = 0; k < kPanel; ++k) w[k] = (valid && k < b) ? A[i + (q + k) * lda] : 0.f;
 #pragma unroll
     for (int k = 1; k < kPanel; ++k) {
       if (k < b) {
@@ -173,41 +192,39 @@ __device__ void panel_solve(const OuterArgs& a, const float (*sL)[kPanel + 1], c
     float ssum = 0.f;
 #pragma unroll
     for (int k = 0; k < kPanel; ++k) {
+      l[k] = w[k] * srd[k];
       if (k < b) {
-        l[k] = w[k] * srd[k];
         dsum = f2_add_prod(dsum, w[k], l[k]);
         ssum += fabsf(w[k] * l[k]);
-        A[i + (q + k) * lda] = l[k];
-      } else {
-        l[k] = 0.f;
-        w[k] = 0.f;
+        if (valid) A[i + (q + k) * lda] = l[k];
       }
     }
-    a.kd[i] -= f2_to_double(dsum);
-    a.s[i] += (double)ssum;
-    const int64_t off = i * (int64_t)a.NB + t0;
-    float4* wk = reinterpret_cast<float4*>(a.Wk + off);
-    float4* lk = reinterpret_cast<float4*>(a.Lk + off);
-    float4* wh = reinterpret_cast<float4*>(a.Wh + off);
-    float4* wlo = reinterpret_cast<float4*>(a.Wl + off);
-    float4* lh = reinterpret_cast<float4*>(a.Lh + off);
-    float4* llo = reinterpret_cast<float4*>(a.Ll + off);
+    if (valid) {
+      a.kd[i] -= f2_to_double(dsum);
+      a.s[i] += (double)ssum;
+    }
+    // row-major operand rows of this warp: base + 32 warp + rr
+    const int64_t wrow0 = base + 32 * warp;
 #pragma unroll
-    for (int v = 0; v < kPanel / 4; ++v) {
-      const float4 W4 = make_float4(w[4 * v], w[4 * v + 1], w[4 * v + 2], w[4 * v + 3]);
-      const float4 L4 = make_float4(l[4 * v], l[4 * v + 1], l[4 * v + 2], l[4 * v + 3]);
-      const float4 WH = make_float4(tf32_rna(W4.x), tf32_rna(W4.y), tf32_rna(W4.z), tf32_rna(W4.w));
-      const float4 LH = make_float4(tf32_rna(L4.x), tf32_rna(L4.y), tf32_rna(L4.z), tf32_rna(L4.w));
-      const float4 WL = make_float4(tf32_rna(W4.x - WH.x), tf32_rna(W4.y - WH.y),
-                                    tf32_rna(W4.z - WH.z), tf32_rna(W4.w - WH.w));
-      const float4 LL = make_float4(tf32_rna(L4.x - LH.x), tf32_rna(L4.y - LH.y),
-                                    tf32_rna(L4.z - LH.z), tf32_rna(L4.w - LH.w));
-      wk[v] = W4;
-      lk[v] = L4;
-      wh[v] = WH;
-      wlo[v] = WL;
-      lh[v] = LH;
-      llo[v] = LL;
+    for (int pass = 0; pass < 2; ++pass) {
+#pragma unroll
+      for (int k = 0; k < kPanel; ++k) stage[warp][lane][k] = pass == 0 ? w[k] : l[k];
+      __syncwarp();
+      float* P = pass == 0 ? a.Wk : a.Lk;
+      float* H = pass == 0 ? a.Wh : a.Lh;
+      float* Lo = pass == 0 ? a.Wl : a.Ll;
+      for (int rr = 0; rr < 32; ++rr) {
+        const int64_t row = wrow0 + rr;
+        if (row < r_hi) {
+          const float v = stage[warp][rr][lane];
+          const float h = tf32_rna(v);
+          const int64_t off = row * (int64_t)a.NB + t0 + lane;
+          P[off] = v;
+          H[off] = h;
+          Lo[off] = tf32_rna(v - h);
+        }
+      }
+      __syncwarp();
     }
   }
 }
@@ -244,12 +261,84 @@ __device__ __noinline__ double borderline_step(const OuterArgs& a, float (*blk)[
   return keep ? pe : pe - 1.0;
 }
 
-__global__ void __launch_bounds__(kThreadsOuter) k_outer_mixed(OuterArgs a) {
+// One decision step of the 32 x 32 diagonal block, local pivot J (compile
+// time, so the block rows stay in registers): lane i holds row i of the
+// block as full symmetric rows; the pivot row is broadcast by shuffles.
+struct DecCtx {
+  const OuterArgs* a;
+  float (*sL)[kPanel + 1];
+  BlockLog* bl;
+  int64_t q;
+  unsigned epoch;
+  int b;
+  int lane;
+};
+
+template <int J>
+__device__ __forceinline__ void dec_steps(const DecCtx& c, float (&r)[kPanel], f2& dd, float& si,
+                                          float uf, float kf, float sq, double u, bool& mykeep,
+                                          int& seq) {
+  if (J < c.b) {
+    const int lane = c.lane;
+    const float ph = __shfl_sync(kFull, dd.hi, J);
+    const float uj = __shfl_sync(kFull, uf, J);
+    const float sj = __shfl_sync(kFull, si, J);
+    const float kj = __shfl_sync(kFull, kf, J);
+    const float sqj = __shfl_sync(kFull, sq, J);
+    const float tau = c.a->tau0 * sqj * (fabsf(kj) + sj) + 0x1.0p-22f;
+    bool kp;
+    float df;
+    if (fabsf(uj - ph) <= tau) {
+      // rows to shared memory, decisions and FP64 pivots of [q, q + J) to
+      // global memory: the recompute reads them
+#pragma unroll
+      for (int k = 0; k < kPanel; ++k) c.sL[lane][k] = r[k];
+      if (lane < J) {
+        c.a->piv[c.q + lane] = f2_to_double(dd);
+        c.a->keep[c.q + lane] = mykeep ? 1 : 0;
+      }
+      __syncwarp();
+      const f2 ddj = make_f2(ph, __shfl_sync(kFull, dd.lo, J));
+      const double uj64 = __shfl_sync(kFull, u, J);
+      const double dfin =
+          borderline_step(*c.a, c.sL, c.b, c.q, J, c.epoch, &seq, ddj, uj64, tau, &kp, c.bl);
+      df = (float)dfin;
+      if (lane == J) dd = f2_from_double(dfin);
+    } else {
+      kp = uj < ph;
+      df = kp ? ph : ph - 1.0f;
+      if (lane == J && !kp) dd = f2_add_f(dd, -1.0f);
+    }
+    const float rd = 1.0f / df;
+    const float wj = r[J];
+    const float l = wj * rd;
+    const bool act = (lane > J) && (lane < c.b);
+#pragma unroll
+    for (int k = J + 1; k < kPanel; ++k) {
+      const float pk = __shfl_sync(kFull, r[k], J);
+      if (act) r[k] = fmaf(-l, pk, r[k]);
+    }
+    if (act) {
+      r[J] = l;
+      dd = f2_sub_prod(dd, wj, l);
+      si += fabsf(wj * l);
+    }
+    if (lane == J) {
+      r[J] = df;
+      mykeep = kp;
+    }
+  }
+  if constexpr (J + 1 < kPanel) dec_steps<J + 1>(c, r, dd, si, uf, kf, sq, u, mykeep, seq);
+}
+
+__global__ void __launch_bounds__(kThreadsOuter, 1) k_outer_mixed(OuterArgs a) {
   extern __shared__ __align__(16) float sLk[];  // [kMaxOuterBlock][kPanel]
   __shared__ float sL[kPanel][kPanel + 1];
   __shared__ float srd[kPanel];
   __shared__ BlockLog bl;
   __shared__ int s_ok;
+  __shared__ float sW[32 * kSwLd];
+  __shared__ float stage[kThreadsOuter / 32][kPanel][kPanel + 1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t p = a.p, n = a.n;
   const int64_t pend = p + a.NBp;
@@ -268,9 +357,9 @@ __global__ void __launch_bounds__(kThreadsOuter) k_outer_mixed(OuterArgs a) {
       const int kk = (int)(q - p);
       const unsigned epoch = a.epoch0 + (unsigned)((q - p) / kPanel);
       // (A) left-looking update of this panel's columns for the block's rows
-      stage_lk(a, sLk, q, b, kk, tid, kThreadsOuter);
+      stage_lk(a, sLk, q, b, kk, tid);
       __syncthreads();
-      inner_update(a, sLk, q, b, kk, q, pend, tid, kThreadsOuter);
+      inner_update(a, sLk, sW, q, b, kk, q, pend, tid);
       __syncthreads();
       // (B) decisions, warp 0, rows of the diagonal block in registers
       if (warp == 0) {
@@ -295,53 +384,15 @@ __global__ void __launch_bounds__(kThreadsOuter) k_outer_mixed(OuterArgs a) {
           sq = sqrtf((float)(q + lane + 1));
         }
         bool mykeep = false;
-#pragma unroll
-        for (int j = 0; j < kPanel; ++j) {
-          if (j < b) {
-            const float ph = __shfl_sync(kFull, dd.hi, j);
-            const float uj = __shfl_sync(kFull, uf, j);
-            const float sj = __shfl_sync(kFull, si, j);
-            const float kj = __shfl_sync(kFull, kf, j);
-            const float sqj = __shfl_sync(kFull, sq, j);
-            const float tau = a.tau0 * sqj * (fabsf(kj) + sj) + 0x1.0p-22f;
-            bool kp;
-            float df;
-            if (fabsf(uj - ph) <= tau) {
-              // rows to shared memory for the recompute leader
-#pragma unroll
-              for (int k = 0; k < kPanel; ++k) sL[lane][k] = r[k];
-              if (lane < j) a.piv[q + lane] = f2_to_double(dd);
-              __syncwarp();
-              const f2 ddj = make_f2(ph, __shfl_sync(kFull, dd.lo, j));
-              const double uj64 = __shfl_sync(kFull, u, j);
-              const double dfin = borderline_step(a, sL, b, q, j, epoch, &seq, ddj, uj64, tau, &kp, &bl);
-              df = (float)dfin;
-              if (lane == j) dd = f2_from_double(dfin);
-            } else {
-              kp = uj < ph;
-              df = kp ? ph : ph - 1.0f;
-              if (lane == j && !kp) dd = f2_add_f(dd, -1.0f);
-            }
-            const float rd = 1.0f / df;
-            const float wj = r[j];
-            const float l = wj * rd;
-            const bool act = (lane > j) && (lane < b);
-#pragma unroll
-            for (int k = j + 1; k < kPanel; ++k) {
-              const float pk = __shfl_sync(kFull, r[k], j);
-              if (act) r[k] = fmaf(-l, pk, r[k]);
-            }
-            if (act) {
-              r[j] = l;
-              dd = f2_sub_prod(dd, wj, l);
-              si += fabsf(wj * l);
-            }
-            if (lane == j) {
-              r[j] = df;
-              mykeep = kp;
-            }
-          }
-        }
+        DecCtx dc;
+        dc.a = &a;
+        dc.sL = sL;
+        dc.bl = &bl;
+        dc.q = q;
+        dc.epoch = epoch;
+        dc.b = b;
+        dc.lane = lane;
+        dec_steps<0>(dc, r, dd, si, uf, kf, sq, u, mykeep, seq);
         // publish the block: L11 (lower), pivots, reciprocals
 #pragma unroll
         for (int k = 0; k < kPanel; ++k) {
@@ -366,7 +417,7 @@ __global__ void __launch_bounds__(kThreadsOuter) k_outer_mixed(OuterArgs a) {
       __syncthreads();
       if (tid == 0) recompute_release_done(a.rc, epoch);
       // (C) panel solve of the block's remaining rows
-      panel_solve(a, sL, srd, q, b, q + b, pend, tid, kThreadsOuter);
+      panel_solve(a, sL, srd, stage, q, b, q + b, pend, tid);
       __threadfence();
       __syncthreads();
       if (tid == 0) st_release(&a.rc.ctrl[kCtlRows], epoch);
@@ -438,9 +489,9 @@ __global__ void __launch_bounds__(kThreadsOuter) k_outer_mixed(OuterArgs a) {
       if (tid == 0) s_ok = rc_wait_geq(a.rc, &a.rc.ctrl[kCtlRows], epoch - 1) ? 1 : 0;
       __syncthreads();
       if (!s_ok) return;
-      stage_lk(a, sLk, q, b, kk, tid, kThreadsOuter);
+      stage_lk(a, sLk, q, b, kk, tid);
       __syncthreads();
-      inner_update(a, sLk, q, b, kk, r_lo, r_hi, tid, kThreadsOuter);
+      inner_update(a, sLk, sW, q, b, kk, r_lo, r_hi, tid);
     }
     if (!recompute_follower(a.rc, epoch, &s_ok)) return;
     if (r_lo < r_hi) {
@@ -450,7 +501,7 @@ __global__ void __launch_bounds__(kThreadsOuter) k_outer_mixed(OuterArgs a) {
       }
       if (tid < kPanel) srd[tid] = tid < b ? __ldcg(&a.rdv[q + tid]) : 1.f;
       __syncthreads();
-      panel_solve(a, sL, srd, q, b, r_lo, r_hi, tid, kThreadsOuter);
+      panel_solve(a, sL, srd, stage, q, b, r_lo, r_hi, tid);
       __syncthreads();
     }
   }

@@ -12,13 +12,23 @@
 // into one FP32 accumulator in tensor memory (the dropped Wl Ll^T term is
 // ~2^-22 relative).
 //
-// Structure (one 128 x 128 output tile per CTA, 128 threads):
+// Accuracy: the tensor core's in-instruction FP32 accumulation is not
+// round-to-nearest, so a long chain of MMAs into one accumulator drifts. Each
+// 32-deep k-block (12 MMAs) therefore goes into a fresh TMEM accumulator that
+// the epilogue drains into FP32 registers with ordinary round-to-nearest adds.
+//
+// Structure (persistent, one CTA per SM, 320 threads, 128 x 128 tiles of the
+// lower triangle assigned round-robin):
 //   warp 0 / lane 0 : TMA producer, 3-stage ring of {Wh, Wl, Lh, Ll} tiles
-//                     (128 rows x 32 fp32 = 128 B rows, SWIZZLE_128B)
-//   warp 1          : allocates 128 TMEM columns; lane 0 issues tcgen05.mma
-//                     (M = 128, N = 128, K = 8) and tcgen05.commit
-//   warps 0-3       : epilogue, tcgen05.ld 32x32b (row = TMEM lane) then a
-//                     coalesced read-modify-write of the column-major C.
+//                     (128 rows x 32 fp32 = 128-byte rows, SWIZZLE_128B)
+//   warp 1          : allocates 4 x 128 TMEM columns (a ring of k-block
+//                     accumulators, so the MMAs run ahead of the epilogue);
+//                     lane 0 issues tcgen05.mma (M = N = 128, K = 8) and
+//                     tcgen05.commit
+//   warps 2-9       : epilogue; each thread owns half a row of the tile (64
+//                     columns): it accumulates minus every drained k-block
+//                     partial (tcgen05.ld 32x32b) in registers and adds the sum
+//                     into C at the end of the tile.
 // Every mbarrier wait is bounded; on expiry the kernel records an error,
 // drains what it issued, frees its TMEM and returns.
 #include <cuda.h>
@@ -36,8 +46,11 @@ constexpr int kBK = 32;  // fp32 elements per k-block (= one 128-byte swizzle ro
 constexpr int kStages = 3;
 constexpr int kTileBytes = kBM * kBK * 4;  // 16 KiB
 constexpr int kStageBytes = 4 * kTileBytes;
-constexpr int kThreads = 128;
-constexpr int kTmemCols = 128;
+constexpr int kThreads = 320;  // producer, MMA, 8 epilogue warps
+constexpr int kEpiThreads = 256;
+constexpr int kEpiCols = kBN / 2;  // columns per epilogue thread
+constexpr int kAccBufs = 4;                 // TMEM accumulator ring
+constexpr int kTmemCols = kAccBufs * kBN;  // all 512 columns
 constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256;
 
 __device__ inline uint32_t smem_u32(const void* p) {
@@ -137,42 +150,49 @@ struct TcArgs {
   float* C;
   int64_t ldc, n, r0;
   int kblocks;
-  int64_t tiles;
+  int64_t tiles;   // tiles along one side of the trailing block
+  int64_t ntiles;  // lower-triangle tiles
   int* err;
 };
+
+__device__ inline void tile_coords(int64_t x, int64_t* tr, int64_t* tc) {
+  int64_t r = (int64_t)((sqrt(8.0 * (double)x + 1.0) - 1.0) * 0.5);
+  while (r * (r + 1) / 2 > x) --r;
+  while ((r + 1) * (r + 2) / 2 <= x) ++r;
+  *tr = r;
+  *tc = x - r * (r + 1) / 2;
+}
+
+__device__ inline void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
 
 __global__ void __launch_bounds__(kThreads, 1)
     k_update_tc(const __grid_constant__ CUtensorMap tWh, const __grid_constant__ CUtensorMap tWl,
                 const __grid_constant__ CUtensorMap tLh, const __grid_constant__ CUtensorMap tLl,
                 TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  // 1024-byte aligned operand ring, then the barriers
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(base + kStages * kStageBytes);
-  uint64_t* full = bars;
-  uint64_t* empty = bars + kStages;
-  uint64_t* done = bars + 2 * kStages;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 1);
+  uint64_t* full = bars;                    // [kStages]
+  uint64_t* empty = bars + kStages;         // [kStages]
+  uint64_t* acc_full = bars + 2 * kStages;    // [kAccBufs]
+  uint64_t* acc_empty = acc_full + kAccBufs;  // [kAccBufs]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + kAccBufs);
   __shared__ int s_fail;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-  // lower-triangle tile of the trailing block
-  const int64_t x = blockIdx.x;
-  int64_t tr = (int64_t)((sqrt(8.0 * (double)x + 1.0) - 1.0) * 0.5);
-  while (tr * (tr + 1) / 2 > x) --tr;
-  while ((tr + 1) * (tr + 2) / 2 <= x) ++tr;
-  const int64_t tc = x - tr * (tr + 1) / 2;
-  const int64_t i0 = a.r0 + tr * kBM, c0 = a.r0 + tc * kBN;
-
   if (threadIdx.x == 0) {
     s_fail = 0;
     for (int s = 0; s < kStages; ++s) {
       mbar_init(smem_u32(&full[s]), 1);
       mbar_init(smem_u32(&empty[s]), 1);
     }
-    mbar_init(smem_u32(done), 1);
+    for (int b = 0; b < kAccBufs; ++b) {
+      mbar_init(smem_u32(&acc_full[b]), 1);
+      mbar_init(smem_u32(&acc_empty[b]), kEpiThreads);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -188,84 +208,123 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tmem = *tmem_slot;
   const int KB = a.kblocks;
 
-  if (warp == 0 && lane == 0) {
-    // ---- TMA producer ----
-    int issued = 0;
-    for (int kb = 0; kb < KB; ++kb) {
-      const int s = kb % kStages;
-      const uint32_t ph = (uint32_t)((kb / kStages) & 1);
-      if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1u)) {
-        atomicExch(&s_fail, 1);
-        break;
-      }
-      unsigned char* st = base + s * kStageBytes;
-      const uint32_t fb = smem_u32(&full[s]);
-      mbar_expect_tx(fb, kStageBytes);
-      const int kx = kb * kBK;
-      tma_load_2d(smem_u32(st + 0 * kTileBytes), &tWh, kx, (int)i0, fb);
-      tma_load_2d(smem_u32(st + 1 * kTileBytes), &tWl, kx, (int)i0, fb);
-      tma_load_2d(smem_u32(st + 2 * kTileBytes), &tLh, kx, (int)c0, fb);
-      tma_load_2d(smem_u32(st + 3 * kTileBytes), &tLl, kx, (int)c0, fb);
-      issued = kb + 1;
-    }
-    // drain: every issued stage must have landed before the CTA may exit
-    for (int kb = (issued > kStages ? issued - kStages : 0); kb < issued; ++kb)
-      mbar_wait(smem_u32(&full[kb % kStages]), (uint32_t)((kb / kStages) & 1));
-  } else if (warp == 1 && lane == 0) {
-    // ---- MMA issuer ----
-    bool ok = true;
-    for (int kb = 0; kb < KB && ok; ++kb) {
-      const int s = kb % kStages;
-      const uint32_t ph = (uint32_t)((kb / kStages) & 1);
-      if (!mbar_wait(smem_u32(&full[s]), ph)) {
-        atomicExch(&s_fail, 1);
-        ok = false;
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      unsigned char* st = base + s * kStageBytes;
-      const uint32_t aH = smem_u32(st + 0 * kTileBytes), aL = smem_u32(st + 1 * kTileBytes);
-      const uint32_t bH = smem_u32(st + 2 * kTileBytes), bL = smem_u32(st + 3 * kTileBytes);
-#pragma unroll
-      for (int kk = 0; kk < kBK / 8; ++kk) {
-        const uint32_t off = kk * 32;  // 8 tf32 = 32 bytes along K
-        mma_tf32(tmem, sw128_desc(aH + off), sw128_desc(bH + off), (kb > 0 || kk > 0) ? 1u : 0u);
-        mma_tf32(tmem, sw128_desc(aH + off), sw128_desc(bL + off), 1u);
-        mma_tf32(tmem, sw128_desc(aL + off), sw128_desc(bH + off), 1u);
-      }
-      mma_commit(smem_u32(&empty[s]));
-    }
-    mma_commit(smem_u32(done));
-  }
-  __syncwarp();
-
-  // ---- epilogue: all four warps ----
-  const bool ready = mbar_wait(smem_u32(done), 0);
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (!ready) atomicExch(&s_fail, 1);
-  __syncthreads();
-  if (!s_fail) {
-    const int64_t row = i0 + warp * 32 + lane;
-    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-#pragma unroll 1
-    for (int ch = 0; ch < kBN / 32; ++ch) {
-      float v[32];
-      tmem_ld32(trow + (uint32_t)(ch * 32), v);
-      const int64_t cb = c0 + ch * 32;
-      if (row < a.n) {
-#pragma unroll
-        for (int c = 0; c < 32; ++c) {
-          const int64_t col = cb + c;
-          if (col < a.n && row >= col) {
-            float* p = a.C + row + col * a.ldc;
-            *p -= v[c];
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- TMA producer ----
+      int64_t g = 0;  // k-blocks issued so far
+      bool ok = true;
+      for (int64_t x = blockIdx.x; x < a.ntiles && ok; x += gridDim.x) {
+        int64_t tr, tc;
+        tile_coords(x, &tr, &tc);
+        const int i0 = (int)(a.r0 + tr * kBM), c0 = (int)(a.r0 + tc * kBN);
+        for (int kb = 0; kb < KB; ++kb, ++g) {
+          const int s = (int)(g % kStages);
+          const uint32_t ph = (uint32_t)((g / kStages) & 1);
+          if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1u) || *(volatile int*)&s_fail) {
+            atomicExch(&s_fail, 1);
+            ok = false;
+            break;
           }
+          unsigned char* st = base + s * kStageBytes;
+          const uint32_t fb = smem_u32(&full[s]);
+          mbar_expect_tx(fb, kStageBytes);
+          const int kx = kb * kBK;
+          tma_load_2d(smem_u32(st + 0 * kTileBytes), &tWh, kx, i0, fb);
+          tma_load_2d(smem_u32(st + 1 * kTileBytes), &tWl, kx, i0, fb);
+          tma_load_2d(smem_u32(st + 2 * kTileBytes), &tLh, kx, c0, fb);
+          tma_load_2d(smem_u32(st + 3 * kTileBytes), &tLl, kx, c0, fb);
+        }
+      }
+      // drain: every issued stage must have landed before the CTA may exit
+      for (int64_t h = (g > kStages ? g - kStages : 0); h < g; ++h)
+        mbar_wait(smem_u32(&full[h % kStages]), (uint32_t)((h / kStages) & 1));
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer ----
+      int64_t g = 0;
+      bool ok = true;
+      for (int64_t x = blockIdx.x; x < a.ntiles && ok; x += gridDim.x) {
+        for (int kb = 0; kb < KB; ++kb, ++g) {
+          const int s = (int)(g % kStages);
+          const uint32_t ph = (uint32_t)((g / kStages) & 1);
+          const int buf = (int)(g % kAccBufs);
+          const uint32_t aph = (uint32_t)((g / kAccBufs) & 1);
+          if (!mbar_wait(smem_u32(&acc_empty[buf]), aph ^ 1u) ||
+              !mbar_wait(smem_u32(&full[s]), ph) || *(volatile int*)&s_fail) {
+            atomicExch(&s_fail, 1);
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          unsigned char* st = base + s * kStageBytes;
+          const uint32_t aH = smem_u32(st + 0 * kTileBytes), aL = smem_u32(st + 1 * kTileBytes);
+          const uint32_t bH = smem_u32(st + 2 * kTileBytes), bL = smem_u32(st + 3 * kTileBytes);
+          const uint32_t d = tmem + (uint32_t)(buf * kBN);
+#pragma unroll
+          for (int kk = 0; kk < kBK / 8; ++kk) {
+            const uint32_t off = kk * 32;  // 8 tf32 = 32 bytes along K
+            mma_tf32(d, sw128_desc(aH + off), sw128_desc(bH + off), kk > 0 ? 1u : 0u);
+            mma_tf32(d, sw128_desc(aH + off), sw128_desc(bL + off), 1u);
+            mma_tf32(d, sw128_desc(aL + off), sw128_desc(bH + off), 1u);
+          }
+          mma_commit(smem_u32(&empty[s]));
+          mma_commit(smem_u32(&acc_full[buf]));
         }
       }
     }
-  } else if (threadIdx.x == 0) {
-    atomicExch(a.err, 1);
+  } else {
+    // ---- epilogue: warps 2..9; a thread owns half a row of the tile ----
+    const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
+    const int half = (warp - 2) >> 2;
+    const int rloc = 32 * quarter + lane;
+    int64_t g = 0;
+    bool ok = true;
+    for (int64_t x = blockIdx.x; x < a.ntiles && ok; x += gridDim.x) {
+      int64_t tr, tc;
+      tile_coords(x, &tr, &tc);
+      const int64_t row = a.r0 + tr * kBM + rloc;
+      const int64_t c0 = a.r0 + tc * kBN + half * kEpiCols;
+      // columns [c0, c0 + ncol) of this row are stored (lower triangle, < n)
+      int64_t cend = c0 + kEpiCols;
+      if (cend > a.n) cend = a.n;
+      if (tr == tc && cend > row + 1) cend = row + 1;
+      const int ncol = (row < a.n && cend > c0) ? (int)(cend - c0) : 0;
+      float acc[kEpiCols];
+#pragma unroll
+      for (int c = 0; c < kEpiCols; ++c) acc[c] = 0.f;
+      for (int kb = 0; kb < KB; ++kb, ++g) {
+        const int buf = (int)(g % kAccBufs);
+        const uint32_t aph = (uint32_t)((g / kAccBufs) & 1);
+        if (!mbar_wait(smem_u32(&acc_full[buf]), aph) || *(volatile int*)&s_fail) {
+          atomicExch(&s_fail, 1);
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) +
+                               (uint32_t)(buf * kBN + half * kEpiCols);
+#pragma unroll
+        for (int ch = 0; ch < kEpiCols / 32; ++ch) {
+          float v[32];
+          tmem_ld32(taddr + (uint32_t)(ch * 32), v);
+#pragma unroll
+          for (int c = 0; c < 32; ++c) acc[ch * 32 + c] -= v[c];
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(smem_u32(&acc_empty[buf]));
+      }
+      if (!ok) break;
+      float* wp = a.C + row + c0 * a.ldc;
+#pragma unroll
+      for (int c = 0; c < kEpiCols; ++c) {
+        if (c < ncol) *wp += acc[c];
+        wp += a.ldc;
+      }
+    }
   }
+  __syncthreads();
+  if (s_fail && threadIdx.x == 0) atomicExch(a.err, 1);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 1) {
@@ -329,9 +388,14 @@ cudaError_t outer_update_tc(float* C, int64_t ldc, int64_t n, int64_t r0, int kd
   a.r0 = r0;
   a.kblocks = kdim / kBK;
   a.tiles = (m + kBM - 1) / kBM;
+  a.ntiles = a.tiles * (a.tiles + 1) / 2;
   a.err = err_flag;
-  const int64_t nt = a.tiles * (a.tiles + 1) / 2;
-  k_update_tc<<<(unsigned)nt, kThreads, kSmemBytes, s>>>(tWh, tWl, tLh, tLl, a);
+  DevInfo di;
+  cudaError_t e = dev_info(&di);
+  if (e != cudaSuccess) return e;
+  int64_t grid = di.sm_count;
+  if (grid > a.ntiles) grid = a.ntiles;
+  k_update_tc<<<(unsigned)grid, kThreads, kSmemBytes, s>>>(tWh, tWl, tLh, tLl, a);
   return cudaGetLastError();
 }
 
