@@ -71,10 +71,17 @@ typedef enum {
  *                     accumulation; pivots, decisions and log P in FP64; any
  *                     pivot whose uniform lies within the propagated error
  *                     bound of its threshold is recomputed in FP64 from the
- *                     original K before its decision.                      */
+ *                     original K before its decision.
+ *   DPP_PREC_BF16X6 : as 3XTF32, but the trailing update splits each FP32
+ *                     operand into three BF16 pieces (which represent it
+ *                     exactly) and issues the six products of combined order
+ *                     <= 2 on the BF16 tensor path: the same tensor time as
+ *                     3XTF32 with FP32-level accuracy.                      */
 typedef enum {
   DPP_PREC_FP64 = 0,
-  DPP_PREC_3XTF32 = 1
+  DPP_PREC_3XTF32 = 1,
+  DPP_PREC_BF16X6 = 2,
+  DPP_PREC_FP32 = 3  /* FP32 SIMT updates, FP64 pivots and recomputes (batched) */
 } dpp_precision;
 
 /* Bits of dpp_result.status (device-side outcome of one draw). */
@@ -113,14 +120,15 @@ size_t dpp_workspace_size(int32_t op, int64_t n, int32_t dtype,
 /* Sample DPP(K) for Hermitian K (LDL^H form of Algorithms 1 and 4).
  *   K          device, n x n column-major (ld >= n), lower triangle read.
  *   dtype      DPP_R64 or DPP_C128.
- *   precision  DPP_PREC_FP64 (R64, C128) or DPP_PREC_3XTF32 (R64).
+ *   precision  DPP_PREC_FP64 (R64, C128), DPP_PREC_3XTF32 or DPP_PREC_BF16X6
+ *              (R64).
  *   seed, instance  Philox stream (ignored if uniforms != NULL).
  *   uniforms   device, n doubles, or NULL for Philox.
  *   keep       device, n bytes: keep[j] = 1 iff j is in the sample.
  *   factor_out device n x ld of dtype, or NULL. Receives L (strictly lower,
  *              unit diagonal implied) and D (diagonal) of K - 1_{Y^c}. May
- *              equal K for an in-place factorization. With 3XTF32 it receives
- *              the mixed-precision factor (pivots are the FP64 ones).
+ *              equal K for an in-place factorization. With a mixed precision
+ *              it receives the FP32 factor (pivots are the FP64 ones).
  *   pivots     device, n doubles, or NULL: final pivots d_j (after -1).
  *   result     device, one dpp_result.
  *   workspace  device, >= dpp_workspace_size(DPP_OP_SAMPLE_HERMITIAN, ...).
@@ -145,6 +153,38 @@ dpp_status dpp_sample_lu(const void* K, int64_t n, int64_t ld, int32_t dtype,
                          void* factor_out, double* pivots, dpp_result* result,
                          void* workspace, size_t workspace_bytes,
                          void* stream);
+
+/* Many independent draws, one per Hermitian (real symmetric) kernel of its own
+ * order, in ONE persistent launch (no host synchronisation). Each CTA takes
+ * the next instance from a device work queue (largest n first) and draws it
+ * alone: left-looking 32-wide panels, FP32 SIMT updates, FP64 pivots,
+ * decisions and log P, FP64 recompute of any pivot inside the borderline band
+ * (the band of dpp_sample_hermitian). Arguments (all arrays device memory):
+ *   batch      number of instances (>= 0).
+ *   n, ld      per-instance order and leading dimension (ld >= n).
+ *   K          per-instance device pointer to the column-major FP64 kernel
+ *              (lower triangle read).
+ *   n_max      host bound on every n (instances with n > n_max are skipped
+ *              and flagged DPP_RES_NONFINITE).
+ *   precision  DPP_PREC_FP32.
+ *   instance   per-instance Philox instance id, or NULL (id = index).
+ *   keep       per-instance device pointer to n bytes (output).
+ *   uniforms   per-instance device pointer to n doubles, or NULL (Philox).
+ *   pivots     per-instance device pointer to n doubles, or NULL.
+ *   results    batch dpp_result records.
+ *   workspace  >= dpp_batched_workspace_size(batch, n_max, precision); the
+ *              launch uses as many CTAs as fit (at most two per SM).
+ * Calls that share a workspace must not overlap. */
+size_t dpp_batched_workspace_size(int32_t batch, int64_t n_max, int32_t precision);
+
+dpp_status dpp_sample_batched(int32_t batch, const int64_t* n,
+                              const double* const* K, const int64_t* ld,
+                              int64_t n_max, int32_t precision, uint64_t seed,
+                              const uint64_t* instance, uint8_t* const* keep,
+                              const double* const* uniforms,
+                              double* const* pivots, dpp_result* results,
+                              void* workspace, size_t workspace_bytes,
+                              void* stream);
 
 /* Adjoint of log P(Y) with the sample held fixed:
  *   dK = g * (K - 1_{Y^c})^{-H}          (g = *grad_logp, a device scalar)

@@ -11,11 +11,12 @@ from typing import Optional
 
 from . import _lib
 from ._lib import (DPP_C128, DPP_OP_LOGPROB_BACKWARD, DPP_OP_SAMPLE_HERMITIAN,
-                   DPP_OP_SAMPLE_LU, DPP_PREC_3XTF32, DPP_PREC_FP64, DPP_R64,
+                   DPP_OP_SAMPLE_LU, DPP_PREC_3XTF32, DPP_PREC_BF16X6, DPP_PREC_FP64, DPP_R64,
                    DPPError, PRECISIONS, decode_result, load, workspace_size)
 
-__all__ = ["sample_hermitian", "sample_lu", "logprob_backward", "uniforms",
-           "Sample", "DPPLogProb", "DPPError", "load", "workspace_size"]
+__all__ = ["sample_hermitian", "sample_lu", "sample_batched", "BatchedSampler",
+           "logprob_backward", "uniforms", "Sample", "DPPLogProb", "DPPError", "load",
+           "workspace_size"]
 
 
 def _torch():
@@ -127,6 +128,75 @@ def sample_lu(K, seed: int = 0, instance: int = 0, precision: str = "fp64",
               uniforms=None, factor: bool = False, workspace=None) -> Sample:
     """Draw Y ~ DPP(K) for general K (LU form of Algorithm 1)."""
     return _sample(False, K, seed, instance, precision, uniforms, factor, workspace)
+
+
+class BatchedSampler:
+    """Reusable device state for repeated batched draws over a fixed list of
+    real symmetric kernels (device pointer tables, outputs, workspace)."""
+
+    def __init__(self, Ks, instance=None, want_pivots: bool = False, uniforms=None):
+        torch = _torch()
+        L = load()
+        self.L = L
+        self.Ks = []
+        ns, lds = [], []
+        for K in Ks:
+            if K.dtype != torch.float64 or not K.is_cuda:
+                raise TypeError("batched kernels must be float64 CUDA tensors")
+            Kc, ld = colmajor(K)
+            self.Ks.append(Kc)
+            ns.append(K.shape[0])
+            lds.append(ld)
+        dev = Ks[0].device if Ks else torch.device("cuda")
+        self.device = dev
+        self.batch = len(Ks)
+        self.n_max = max(ns) if ns else 0
+        self.n = torch.tensor(ns, dtype=torch.int64, device=dev)
+        self.ld = torch.tensor(lds, dtype=torch.int64, device=dev)
+        self.kptr = torch.tensor([k.data_ptr() for k in self.Ks], dtype=torch.int64, device=dev)
+        self.keep = [torch.empty(max(m, 1), dtype=torch.uint8, device=dev) for m in ns]
+        self.keep_ptr = torch.tensor([k.data_ptr() for k in self.keep], dtype=torch.int64, device=dev)
+        self.pivots = None
+        self.piv_ptr = None
+        if want_pivots:
+            self.pivots = [torch.empty(max(m, 1), dtype=torch.float64, device=dev) for m in ns]
+            self.piv_ptr = torch.tensor([p.data_ptr() for p in self.pivots], dtype=torch.int64, device=dev)
+        self.u = None
+        self.u_ptr = None
+        if uniforms is not None:
+            self.u = [uu.to(device=dev, dtype=torch.float64).contiguous() for uu in uniforms]
+            self.u_ptr = torch.tensor([uu.data_ptr() for uu in self.u], dtype=torch.int64, device=dev)
+        self.inst = None
+        if instance is not None:
+            self.inst = torch.tensor(list(instance), dtype=torch.int64, device=dev)
+        self.raw = torch.zeros(max(self.batch, 1) * _lib.RESULT_BYTES, dtype=torch.uint8, device=dev)
+        need = int(L.dpp_batched_workspace_size(self.batch, self.n_max, _lib.DPP_PREC_FP32))
+        if need == 0:
+            raise DPPError(_lib.DPP_ERR_UNSUPPORTED, "batched workspace query failed")
+        self.ws = torch.empty(need, dtype=torch.uint8, device=dev)
+
+    def draw(self, seed: int = 0) -> None:
+        """Enqueue one draw of every instance on the current stream."""
+        st = self.L.dpp_sample_batched(
+            self.batch, self.n.data_ptr(), self.kptr.data_ptr(), self.ld.data_ptr(), self.n_max,
+            _lib.DPP_PREC_FP32, seed, None if self.inst is None else self.inst.data_ptr(),
+            self.keep_ptr.data_ptr(), None if self.u_ptr is None else self.u_ptr.data_ptr(),
+            None if self.piv_ptr is None else self.piv_ptr.data_ptr(), self.raw.data_ptr(),
+            self.ws.data_ptr(), self.ws.numel(), _stream(self.device))
+        _lib.check(st)
+
+    def results(self):
+        raw = self.raw.cpu().numpy().tobytes()
+        return [decode_result(raw[i * _lib.RESULT_BYTES:(i + 1) * _lib.RESULT_BYTES])
+                for i in range(self.batch)]
+
+
+def sample_batched(Ks, seed: int = 0, instance=None, want_pivots: bool = False, uniforms=None):
+    """One persistent-launch draw for each kernel in ``Ks``; returns the sampler
+    (``.keep[i]``, ``.pivots[i]``, ``.results()``)."""
+    b = BatchedSampler(Ks, instance=instance, want_pivots=want_pivots, uniforms=uniforms)
+    b.draw(seed)
+    return b
 
 
 def uniforms(seed: int, instance: int, n: int, device="cuda"):

@@ -81,7 +81,8 @@ size_t dpp_workspace_size(int32_t op, int64_t n, int32_t dtype, int32_t precisio
   switch (op) {
     case DPP_OP_SAMPLE_HERMITIAN:
       if (precision == DPP_PREC_FP64) return ws_fp64(n, dtype, true, true);
-      if (precision == DPP_PREC_3XTF32 && dtype == DPP_R64) return ws_mixed(n);
+      if ((precision == DPP_PREC_3XTF32 || precision == DPP_PREC_BF16X6) && dtype == DPP_R64)
+        return ws_mixed(n);
       return 0;
     case DPP_OP_SAMPLE_LU:
       if (precision == DPP_PREC_FP64) return ws_fp64(n, dtype, false, true);
@@ -109,6 +110,7 @@ static dpp_status sample_common(bool hermitian, const void* K, int64_t n, int64_
   a.n = n;
   a.ld = ld;
   a.dtype = dtype;
+  a.precision = precision;
   a.seed = seed;
   a.instance = instance;
   a.uniforms = uniforms;
@@ -149,6 +151,51 @@ dpp_status dpp_sample_lu(const void* K, int64_t n, int64_t ld, int32_t dtype, in
                          size_t workspace_bytes, void* stream) {
   return sample_common(false, K, n, ld, dtype, precision, seed, instance, uniforms, keep,
                        factor_out, pivots, result, workspace, workspace_bytes, stream);
+}
+
+size_t dpp_batched_workspace_size(int32_t batch, int64_t n_max, int32_t precision) {
+  if (batch < 0 || n_max < 0 || precision != DPP_PREC_FP32) return 0;
+  return ws_batched(batch, n_max, batched_default_ctas());
+}
+
+dpp_status dpp_sample_batched(int32_t batch, const int64_t* n, const double* const* K,
+                              const int64_t* ld, int64_t n_max, int32_t precision, uint64_t seed,
+                              const uint64_t* instance, uint8_t* const* keep,
+                              const double* const* uniforms, double* const* pivots,
+                              dpp_result* results, void* workspace, size_t workspace_bytes,
+                              void* stream) {
+  g_last_error.clear();
+  if (precision != DPP_PREC_FP32)
+    return fail(DPP_ERR_UNSUPPORTED, "dpp_sample_batched supports DPP_PREC_FP32 only");
+  if (batch < 0 || n_max < 0 || n_max > (1 << 20))
+    return fail(DPP_ERR_INVALID_ARG, "bad batch or n_max");
+  if (batch == 0) return DPP_OK;
+  if (!n || !K || !ld || !keep || !results)
+    return fail(DPP_ERR_INVALID_ARG, "n, K, ld, keep and results must not be NULL");
+  if (!workspace || !aligned(workspace, 256))
+    return fail(DPP_ERR_WORKSPACE, "workspace must be non-NULL and 256-byte aligned");
+  const size_t minimal = ws_batched(batch, n_max, 1);
+  if (workspace_bytes < minimal) return fail(DPP_ERR_WORKSPACE, "workspace too small");
+  BatchedArgs b;
+  b.batch = batch;
+  b.n = n;
+  b.K = K;
+  b.ld = ld;
+  b.n_max = n_max;
+  b.seed = seed;
+  b.instance = instance;
+  b.keep = keep;
+  b.uniforms = uniforms;
+  b.pivots = pivots;
+  b.results = results;
+  b.flops = 0.0;
+  b.stream = static_cast<cudaStream_t>(stream);
+  Workspace ws;
+  ws.base = static_cast<char*>(workspace);
+  ws.size = workspace_bytes;
+  cudaError_t e = sample_batched(b, ws);
+  if (e != cudaSuccess) return fail_cuda(e, "dpp_sample_batched");
+  return DPP_OK;
 }
 
 dpp_status dpp_logprob_backward(const void* K, int64_t n, int64_t ld, int32_t dtype,

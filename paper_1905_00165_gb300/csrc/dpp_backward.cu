@@ -316,6 +316,7 @@ cudaError_t run_backward(const void* K, int64_t n, int64_t ld, int32_t dtype, bo
   a.n = n;
   a.ld = ld;
   a.dtype = dtype;
+  a.precision = DPP_PREC_FP64;
   a.seed = 0;
   a.instance = 0;
   a.uniforms = u;

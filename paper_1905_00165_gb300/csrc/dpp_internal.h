@@ -43,6 +43,7 @@ struct DrawArgs {
   const void* K;
   int64_t n, ld;
   int32_t dtype;
+  int32_t precision;
   uint64_t seed, instance;
   const double* uniforms;
   uint8_t* keep;
@@ -69,14 +70,39 @@ constexpr int kMaxOuterBlock = 256;
 size_t ws_mixed(int64_t n);
 cudaError_t sample_mixed(const DrawArgs& a, Workspace ws);
 
+// Operand splits of the tensor-core trailing update.
+enum { kSplit3xTf32 = 0, kSplitBf16x6 = 1 };
+
 // Trailing update C -= W L^T on the lower triangle of rows/cols [r0, n) of the
-// FP32 column-major C (ldc), with the W and L operands given as TF32 hi/lo
-// splits in row-major [n x ldk] buffers (first kdim columns used), on tcgen05
-// tensor cores (dpp_tc.cu). kdim must be a multiple of 32; ldk * 4 bytes must
-// be a multiple of 16; the operand buffers must be 16-byte aligned.
-cudaError_t outer_update_tc(float* C, int64_t ldc, int64_t n, int64_t r0, int kdim,
-                            const float* Wh, const float* Wl, const float* Lh,
-                            const float* Ll, int ldk, int* err_flag, cudaStream_t s);
+// FP32 column-major C (ldc), on tcgen05 tensor cores (dpp_tc.cu). The W and L
+// operands are given as splits in row-major [n x ldk] buffers (first kdim
+// columns used): two TF32 pieces (fp32 storage) for kSplit3xTf32, three BF16
+// pieces for kSplitBf16x6. kdim must be a multiple of the k-block (32 / 64);
+// ldk * element size must be a multiple of 16; buffers 16-byte aligned.
+cudaError_t outer_update_tc(int mode, float* C, int64_t ldc, int64_t n, int64_t r0, int kdim,
+                            void* const* Wops, void* const* Lops, int ldk, int* err_flag,
+                            cudaStream_t s);
+
+// Batched sampler (dpp_batched.cu).
+struct BatchedArgs {
+  int32_t batch;
+  const int64_t* n;
+  const double* const* K;
+  const int64_t* ld;
+  int64_t n_max;
+  uint64_t seed;
+  const uint64_t* instance;
+  uint8_t* const* keep;
+  const double* const* uniforms;
+  double* const* pivots;
+  dpp_result* results;
+  double flops;  // algorithmic flops (profiling only; 0 if unknown)
+  cudaStream_t stream;
+};
+size_t ws_batched(int32_t batch, int64_t n_max, int ctas);
+size_t ws_batched_per_cta(int64_t n_max);
+int batched_default_ctas();
+cudaError_t sample_batched(const BatchedArgs& b, Workspace ws);
 
 // Adjoint (dpp_backward.cu).
 size_t ws_backward(int64_t n, int32_t dtype, bool hermitian);

@@ -20,6 +20,7 @@
 // left-looking from the previous inner panels of the same outer block; after
 // each outer block one rank-NB trailing update is applied to the whole
 // remaining lower triangle, which makes the dominant contraction NB deep.
+#include <cuda_bf16.h>
 #include <math.h>
 
 #include "dpp_device.cuh"
@@ -34,7 +35,6 @@ Tuning g_tuning;
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr double kUEff = 0x1.0p-22;
 
 __device__ inline float tf32_rna(float x) {
   uint32_t r;
@@ -84,8 +84,11 @@ struct OuterArgs {
   double* piv;
   double* kd;
   double* s;
-  float *Wk, *Lk, *Wh, *Wl, *Lh, *Ll;
-  float* rdv;  // FP32 reciprocal of each final pivot
+  float *Wk, *Lk;
+  void* Wop[3];  // tensor-core operand splits of W (row-major [n x NB])
+  void* Lop[3];  // ... and of L
+  int split;     // kSplit3xTf32 or kSplitBf16x6
+  float* rdv;    // FP32 reciprocal of each final pivot
   dpp_result* res;
   unsigned epoch0;  // epoch of the first inner panel of this block
   double tol;
@@ -108,28 +111,47 @@ __device__ void inner_update(const OuterArgs& a, const float* sLk, float* sW, in
                              int kk, int64_t r_lo, int64_t r_hi, int tid) {
   if (kk <= 0 || r_lo >= r_hi) return;
   const int ty = tid / 8, tx = tid % 8;
+  const int lr = tid / 8, lf = tid % 8;  // W loader: 8 float4 per row, 2 rows per thread
+  const int nchunks = (kk + 31) / 32;
   for (int64_t i0 = r_lo; i0 < r_hi; i0 += 64) {
     float acc[2][4];
 #pragma unroll
     for (int rr = 0; rr < 2; ++rr)
 #pragma unroll
       for (int cc = 0; cc < 4; ++cc) acc[rr][cc] = 0.f;
-    for (int k0 = 0; k0 < kk; k0 += 32) {
+    // software pipeline: chunk c+1 is loaded into registers while chunk c is
+    // consumed from the other shared buffer
+    float4 pre[2];
+    auto load = [&](int k0) {
       const int kc = (kk - k0) < 32 ? (kk - k0) : 32;
-      for (int idx = tid; idx < 64 * 8; idx += kThreadsOuter) {
-        const int r = idx / 8, f = idx % 8;
-        const int64_t i = i0 + r;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (i < r_hi && 4 * f < kc)
-          v = __ldcg(reinterpret_cast<const float4*>(a.Wk + i * (int64_t)a.NB + k0 + 4 * f));
-        sW[(4 * f + 0) * kSwLd + r] = v.x;
-        sW[(4 * f + 1) * kSwLd + r] = v.y;
-        sW[(4 * f + 2) * kSwLd + r] = v.z;
-        sW[(4 * f + 3) * kSwLd + r] = v.w;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int64_t i = i0 + lr + 32 * h;
+        pre[h] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < r_hi && 4 * lf < kc)
+          pre[h] = __ldcg(reinterpret_cast<const float4*>(a.Wk + i * (int64_t)a.NB + k0 + 4 * lf));
       }
-      __syncthreads();
+    };
+    auto store = [&](float* buf) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int r = lr + 32 * h;
+        buf[(4 * lf + 0) * kSwLd + r] = pre[h].x;
+        buf[(4 * lf + 1) * kSwLd + r] = pre[h].y;
+        buf[(4 * lf + 2) * kSwLd + r] = pre[h].z;
+        buf[(4 * lf + 3) * kSwLd + r] = pre[h].w;
+      }
+    };
+    load(0);
+    store(sW);
+    __syncthreads();
+    for (int c = 0; c < nchunks; ++c) {
+      const int k0 = 32 * c;
+      const int kc = (kk - k0) < 32 ? (kk - k0) : 32;
+      float* cur = sW + (c & 1) * 32 * kSwLd;
+      if (c + 1 < nchunks) load(k0 + 32);
       for (int t = 0; t < kc; ++t) {
-        const float w0 = sW[t * kSwLd + 2 * ty], w1 = sW[t * kSwLd + 2 * ty + 1];
+        const float w0 = cur[t * kSwLd + 2 * ty], w1 = cur[t * kSwLd + 2 * ty + 1];
         const float4 l = *reinterpret_cast<const float4*>(&sLk[(k0 + t) * kPanel + 4 * tx]);
         acc[0][0] = fmaf(w0, l.x, acc[0][0]);
         acc[0][1] = fmaf(w0, l.y, acc[0][1]);
@@ -140,6 +162,7 @@ __device__ void inner_update(const OuterArgs& a, const float* sLk, float* sW, in
         acc[1][2] = fmaf(w1, l.z, acc[1][2]);
         acc[1][3] = fmaf(w1, l.w, acc[1][3]);
       }
+      if (c + 1 < nchunks) store(sW + ((c + 1) & 1) * 32 * kSwLd);
       __syncthreads();
     }
 #pragma unroll
@@ -164,9 +187,10 @@ __device__ void stage_lk(const OuterArgs& a, float* sLk, int64_t q, int b, int k
 
 // Panel solve of rows [r_lo, r_hi) against the factored 32 x 32 block:
 // w = a L11^{-T} (FP32), l = w / d; writes L into A (column-major, coalesced),
-// folds sum w l into the FP64 running diagonal, and writes W, L and their TF32
-// hi/lo splits row-major through a per-warp shared-memory transpose so every
-// store is a full 128-byte row segment. All threads iterate together.
+// folds sum w l into the FP64 running diagonal, and writes W, L and their
+// tensor-core splits (TF32 pairs or BF16 triplets) row-major through a
+// per-warp shared-memory transpose so each store instruction covers one
+// contiguous row segment. All threads iterate together.
 __device__ void panel_solve(const OuterArgs& a, const float (*sL)[kPanel + 1], const float* srd,
                             float (*stage)[kPanel][kPanel + 1], int64_t q, int b, int64_t r_lo,
                             int64_t r_hi, int tid) {
@@ -211,17 +235,27 @@ __device__ void panel_solve(const OuterArgs& a, const float (*sL)[kPanel + 1], c
       for (int k = 0; k < kPanel; ++k) stage[warp][lane][k] = pass == 0 ? w[k] : l[k];
       __syncwarp();
       float* P = pass == 0 ? a.Wk : a.Lk;
-      float* H = pass == 0 ? a.Wh : a.Lh;
-      float* Lo = pass == 0 ? a.Wl : a.Ll;
+      void* const* ops = pass == 0 ? a.Wop : a.Lop;
       for (int rr = 0; rr < 32; ++rr) {
         const int64_t row = wrow0 + rr;
         if (row < r_hi) {
           const float v = stage[warp][rr][lane];
-          const float h = tf32_rna(v);
           const int64_t off = row * (int64_t)a.NB + t0 + lane;
           P[off] = v;
-          H[off] = h;
-          Lo[off] = tf32_rna(v - h);
+          if (a.split == kSplitBf16x6) {
+            // three BF16 pieces: v = b0 + b1 + b2 exactly (8 + 8 + 8 bits)
+            const __nv_bfloat16 b0 = __float2bfloat16_rn(v);
+            const float r1 = v - __bfloat162float(b0);
+            const __nv_bfloat16 b1 = __float2bfloat16_rn(r1);
+            const float r2 = r1 - __bfloat162float(b1);
+            static_cast<__nv_bfloat16*>(ops[0])[off] = b0;
+            static_cast<__nv_bfloat16*>(ops[1])[off] = b1;
+            static_cast<__nv_bfloat16*>(ops[2])[off] = __float2bfloat16_rn(r2);
+          } else {
+            const float h = tf32_rna(v);
+            static_cast<float*>(ops[0])[off] = h;
+            static_cast<float*>(ops[1])[off] = tf32_rna(v - h);
+          }
         }
       }
       __syncwarp();
@@ -241,69 +275,69 @@ struct BlockLog {
 
 // Borderline step (rare path, kept out of the unrolled loop): recompute the
 // pivot of local index j in FP64 and decide in FP64. The rows of the block
-// must be in blk. Returns the final FP64 pivot; *kp receives the decision.
-__device__ __noinline__ double borderline_step(const OuterArgs& a, float (*blk)[kPanel + 1], int b,
-                                               int64_t q, int j, unsigned epoch, int* seq,
-                                               f2 dd_j, double u_j, float tau, bool* kp,
-                                               BlockLog* bl) {
+// must be in blk.
+struct BorderOut {
+  double dfin;  // final FP64 pivot (after -1 on rejection)
+  int keep;
+  int seq;
+};
+
+__device__ __noinline__ BorderOut borderline_step(const OuterArgs& a, float (*blk)[kPanel + 1],
+                                                  int b, int64_t q, int j, unsigned epoch, int seq,
+                                                  float ph, float pl, double u_j, float tau,
+                                                  BlockLog* bl) {
   const int lane = threadIdx.x & 31;
-  const double p64 = f2_to_double(dd_j);
+  const double p64 = (double)ph + (double)pl;
   double pe = p64, est = 0.0;
-  const bool ok = recompute_leader(a.rc, blk, b, q, j, epoch, seq, &pe, &est);
+  const bool ok = recompute_leader(a.rc, blk, b, q, j, epoch, &seq, &pe, &est);
   const bool keep = u_j < pe;
-  *kp = keep;
   if (lane == 0) {
     bl->border += 1;
     const float ratio = (float)(fabs(pe - p64) / (double)tau);
     if (ratio > bl->max_ratio) bl->max_ratio = ratio;
     if (!ok || est > fabs(u_j - pe)) bl->rc_failed = 1;
   }
-  return keep ? pe : pe - 1.0;
+  BorderOut o;
+  o.dfin = keep ? pe : pe - 1.0;
+  o.keep = keep ? 1 : 0;
+  o.seq = seq;
+  return o;
 }
 
 // One decision step of the 32 x 32 diagonal block, local pivot J (compile
 // time, so the block rows stay in registers): lane i holds row i of the
-// block as full symmetric rows; the pivot row is broadcast by shuffles.
-struct DecCtx {
-  const OuterArgs* a;
-  float (*sL)[kPanel + 1];
-  BlockLog* bl;
-  int64_t q;
-  unsigned epoch;
-  int b;
-  int lane;
-};
-
+// block as a full symmetric row; the pivot row is broadcast by shuffles.
 template <int J>
-__device__ __forceinline__ void dec_steps(const DecCtx& c, float (&r)[kPanel], f2& dd, float& si,
-                                          float uf, float kf, float sq, double u, bool& mykeep,
-                                          int& seq) {
-  if (J < c.b) {
-    const int lane = c.lane;
+__device__ __forceinline__ void dec_steps(const OuterArgs& a, float (*sL)[kPanel + 1], BlockLog* bl,
+                                          int64_t q, unsigned epoch, int b, int lane, float tau0,
+                                          float (&r)[kPanel], f2& dd, float& si, float uf, float kf,
+                                          float sq, double u, bool& mykeep, int& seq) {
+  if (J < b) {
     const float ph = __shfl_sync(kFull, dd.hi, J);
     const float uj = __shfl_sync(kFull, uf, J);
     const float sj = __shfl_sync(kFull, si, J);
     const float kj = __shfl_sync(kFull, kf, J);
     const float sqj = __shfl_sync(kFull, sq, J);
-    const float tau = c.a->tau0 * sqj * (fabsf(kj) + sj) + 0x1.0p-22f;
+    const float tau = tau0 * sqj * (fabsf(kj) + sj) + 0x1.0p-22f;
     bool kp;
     float df;
     if (fabsf(uj - ph) <= tau) {
       // rows to shared memory, decisions and FP64 pivots of [q, q + J) to
       // global memory: the recompute reads them
 #pragma unroll
-      for (int k = 0; k < kPanel; ++k) c.sL[lane][k] = r[k];
+      for (int k = 0; k < kPanel; ++k) sL[lane][k] = r[k];
       if (lane < J) {
-        c.a->piv[c.q + lane] = f2_to_double(dd);
-        c.a->keep[c.q + lane] = mykeep ? 1 : 0;
+        a.piv[q + lane] = f2_to_double(dd);
+        a.keep[q + lane] = mykeep ? 1 : 0;
       }
       __syncwarp();
-      const f2 ddj = make_f2(ph, __shfl_sync(kFull, dd.lo, J));
+      const float pl = __shfl_sync(kFull, dd.lo, J);
       const double uj64 = __shfl_sync(kFull, u, J);
-      const double dfin =
-          borderline_step(*c.a, c.sL, c.b, c.q, J, c.epoch, &seq, ddj, uj64, tau, &kp, c.bl);
-      df = (float)dfin;
-      if (lane == J) dd = f2_from_double(dfin);
+      const BorderOut o = borderline_step(a, sL, b, q, J, epoch, seq, ph, pl, uj64, tau, bl);
+      seq = o.seq;
+      kp = o.keep != 0;
+      df = (float)o.dfin;
+      if (lane == J) dd = f2_from_double(o.dfin);
     } else {
       kp = uj < ph;
       df = kp ? ph : ph - 1.0f;
@@ -312,7 +346,7 @@ __device__ __forceinline__ void dec_steps(const DecCtx& c, float (&r)[kPanel], f
     const float rd = 1.0f / df;
     const float wj = r[J];
     const float l = wj * rd;
-    const bool act = (lane > J) && (lane < c.b);
+    const bool act = (lane > J) && (lane < b);
 #pragma unroll
     for (int k = J + 1; k < kPanel; ++k) {
       const float pk = __shfl_sync(kFull, r[k], J);
@@ -328,7 +362,8 @@ __device__ __forceinline__ void dec_steps(const DecCtx& c, float (&r)[kPanel], f
       mykeep = kp;
     }
   }
-  if constexpr (J + 1 < kPanel) dec_steps<J + 1>(c, r, dd, si, uf, kf, sq, u, mykeep, seq);
+  if constexpr (J + 1 < kPanel)
+    dec_steps<J + 1>(a, sL, bl, q, epoch, b, lane, tau0, r, dd, si, uf, kf, sq, u, mykeep, seq);
 }
 
 __global__ void __launch_bounds__(kThreadsOuter, 1) k_outer_mixed(OuterArgs a) {
@@ -337,7 +372,7 @@ __global__ void __launch_bounds__(kThreadsOuter, 1) k_outer_mixed(OuterArgs a) {
   __shared__ float srd[kPanel];
   __shared__ BlockLog bl;
   __shared__ int s_ok;
-  __shared__ float sW[32 * kSwLd];
+  __shared__ float sW[2 * 32 * kSwLd];
   __shared__ float stage[kThreadsOuter / 32][kPanel][kPanel + 1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t p = a.p, n = a.n;
@@ -384,15 +419,7 @@ __global__ void __launch_bounds__(kThreadsOuter, 1) k_outer_mixed(OuterArgs a) {
           sq = sqrtf((float)(q + lane + 1));
         }
         bool mykeep = false;
-        DecCtx dc;
-        dc.a = &a;
-        dc.sL = sL;
-        dc.bl = &bl;
-        dc.q = q;
-        dc.epoch = epoch;
-        dc.b = b;
-        dc.lane = lane;
-        dec_steps<0>(dc, r, dd, si, uf, kf, sq, u, mykeep, seq);
+        dec_steps<0>(a, sL, &bl, q, epoch, b, lane, a.tau0, r, dd, si, uf, kf, sq, u, mykeep, seq);
         // publish the block: L11 (lower), pivots, reciprocals
 #pragma unroll
         for (int k = 0; k < kPanel; ++k) {
@@ -592,7 +619,9 @@ struct MixedLayout {
   int64_t ld32;
   int NB;
   float* A32;
-  float *Wk, *Lk, *Wh, *Wl, *Lh, *Ll;
+  float *Wk, *Lk;
+  void* Wop[3];
+  void* Lop[3];
   double *kd, *s, *piv;
   float* rdv;
   unsigned* flag;
@@ -609,10 +638,12 @@ bool carve(Workspace& ws, int64_t n, int NB, MixedLayout* L) {
   const size_t ob = sizeof(float) * nn * (size_t)kMaxOuterBlock;
   L->Wk = static_cast<float*>(ws.take(ob));
   L->Lk = static_cast<float*>(ws.take(ob));
-  L->Wh = static_cast<float*>(ws.take(ob));
-  L->Wl = static_cast<float*>(ws.take(ob));
-  L->Lh = static_cast<float*>(ws.take(ob));
-  L->Ll = static_cast<float*>(ws.take(ob));
+  bool ops_ok = true;
+  for (int o = 0; o < 3; ++o) {
+    L->Wop[o] = ws.take(ob);
+    L->Lop[o] = ws.take(ob);
+    ops_ok = ops_ok && L->Wop[o] && L->Lop[o];
+  }
   L->kd = static_cast<double*>(ws.take(sizeof(double) * nn));
   L->s = static_cast<double*>(ws.take(sizeof(double) * nn));
   L->piv = static_cast<double*>(ws.take(sizeof(double) * nn));
@@ -620,8 +651,7 @@ bool carve(Workspace& ws, int64_t n, int NB, MixedLayout* L) {
   L->flag = static_cast<unsigned*>(ws.take(256));
   L->err = reinterpret_cast<int*>(L->flag) + 16;
   if (!recompute_carve(ws, n, &L->rs)) return false;
-  return L->A32 && L->Wk && L->Lk && L->Wh && L->Wl && L->Lh && L->Ll && L->kd && L->s &&
-         L->piv && L->rdv && L->flag;
+  return L->A32 && L->Wk && L->Lk && ops_ok && L->kd && L->s && L->piv && L->rdv && L->flag;
 }
 
 }  // namespace
@@ -668,6 +698,8 @@ cudaError_t sample_mixed(const DrawArgs& a, Workspace ws) {
   }
   unsigned epoch = 1;
   const bool use_tc = g_tuning.update_kernel == 0;
+  const int split = a.precision == DPP_PREC_BF16X6 ? kSplitBf16x6 : kSplit3xTf32;
+  const int kb_tc = split == kSplitBf16x6 ? 64 : 32;
   const int64_t min_workers = 64;  // recomputes are served by the workers
   for (int64_t p = 0; p < n; p += NB) {
     const int NBp = (int)((n - p) < NB ? (n - p) : NB);
@@ -690,10 +722,11 @@ cudaError_t sample_mixed(const DrawArgs& a, Workspace ws) {
       oa.s = L.s;
       oa.Wk = L.Wk;
       oa.Lk = L.Lk;
-      oa.Wh = L.Wh;
-      oa.Wl = L.Wl;
-      oa.Lh = L.Lh;
-      oa.Ll = L.Ll;
+      for (int o = 0; o < 3; ++o) {
+        oa.Wop[o] = L.Wop[o];
+        oa.Lop[o] = L.Lop[o];
+      }
+      oa.split = split;
       oa.rdv = L.rdv;
       oa.res = a.result;
       oa.epoch0 = epoch;
@@ -724,9 +757,9 @@ cudaError_t sample_mixed(const DrawArgs& a, Workspace ws) {
     if (r0 < n) {
       const int64_t m = n - r0;
       const double fl = (double)m * (double)m * (double)NBp;  // lower half of 2 m^2 NB
-      if (use_tc && NBp % 32 == 0) {
+      if (use_tc && NBp % kb_tc == 0) {
         ProfScope ps(kProfUpdateTc, a.stream, fl, 8.0 * (double)m * (double)m / 2.0);
-        e = outer_update_tc(L.A32, L.ld32, n, r0, NBp, L.Wh, L.Wl, L.Lh, L.Ll, NB, L.err, a.stream);
+        e = outer_update_tc(split, L.A32, L.ld32, n, r0, NBp, L.Wop, L.Lop, NB, L.err, a.stream);
         if (e != cudaSuccess) return e;
       } else {
         F32Args u;

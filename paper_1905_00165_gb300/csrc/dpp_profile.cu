@@ -28,7 +28,8 @@ std::vector<cudaEvent_t> g_pool;
 std::atomic<unsigned long long> g_launches{0};
 
 const char* kNames[kProfCategories] = {"panel_decide_solve", "update_fp64", "update_f32_simt",
-                                       "update_tc_3xtf32", "convert", "recompute", "other"};
+                                       "update_tc", "convert", "recompute", "other",
+                                       "batched"};
 
 cudaEvent_t get_event() {
   if (!g_pool.empty()) {

@@ -13,7 +13,8 @@ enum ProfCat {
   kProfConvert = 4,
   kProfRecompute = 5,
   kProfOther = 6,
-  kProfCategories = 7
+  kProfBatched = 7,
+  kProfCategories = 8
 };
 
 // Counts one launch; while profiling is on, records an event pair around the

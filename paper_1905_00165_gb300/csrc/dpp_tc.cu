@@ -5,30 +5,35 @@
 //
 // which is the rank-NB update A22 -= W L21^T = L21 D1 L21^T of the blocked
 // LDL^T sampler (Algorithm 3's Schur complement, Hermitian form), i.e. the
-// "asymptotically all of the work" contraction of Section 4.
+// contraction that carries asymptotically all of the work (Section 4).
 //
-// Precision: 3xTF32. W = Wh + Wl and L = Lh + Ll are pre-split into TF32
-// pairs by the panel kernel; each k-step issues Wh Lh^T + Wh Ll^T + Wl Lh^T
-// into one FP32 accumulator in tensor memory (the dropped Wl Ll^T term is
-// ~2^-22 relative).
+// Precision (chosen per call):
+//   3xTF32 : W = Wh + Wl, L = Lh + Ll (TF32 pairs); per 8-deep k-step
+//            Wl Lh^T + Wh Ll^T + Wh Lh^T (kind::tf32).
+//   BF16x6 : W = W0 + W1 + W2, L = L0 + L1 + L2 (three BF16 pieces, which
+//            represent an FP32 value exactly); per 16-deep k-step the six
+//            products with combined order <= 2 (kind::f16, BF16 runs at twice
+//            the TF32 rate, so this costs the same as 3xTF32 and reaches FP32
+//            accuracy). Small products are issued first.
+// Both splits are produced by the panel kernel; FP32 accumulation.
 //
 // Accuracy: the tensor core's in-instruction FP32 accumulation is not
 // round-to-nearest, so a long chain of MMAs into one accumulator drifts. Each
-// 32-deep k-block (12 MMAs) therefore goes into a fresh TMEM accumulator that
-// the epilogue drains into FP32 registers with ordinary round-to-nearest adds.
+// group of MMAs (one 32-deep k-block for 3xTF32, one 16-deep k-step for
+// BF16x6) therefore goes into a fresh TMEM accumulator that the epilogue drains
+// into FP32 registers with ordinary round-to-nearest adds.
 //
 // Structure (persistent, one CTA per SM, 320 threads, 128 x 128 tiles of the
 // lower triangle assigned round-robin):
-//   warp 0 / lane 0 : TMA producer, 3-stage ring of {Wh, Wl, Lh, Ll} tiles
-//                     (128 rows x 32 fp32 = 128-byte rows, SWIZZLE_128B)
-//   warp 1          : allocates 4 x 128 TMEM columns (a ring of k-block
-//                     accumulators, so the MMAs run ahead of the epilogue);
-//                     lane 0 issues tcgen05.mma (M = N = 128, K = 8) and
-//                     tcgen05.commit
+//   warp 0 / lane 0 : TMA producer, ring of operand stages (128 rows x 128
+//                     bytes per split, SWIZZLE_128B)
+//   warp 1          : allocates 4 x 128 TMEM columns (a ring of accumulators,
+//                     so the MMAs run ahead of the epilogue); lane 0 issues
+//                     tcgen05.mma (M = N = 128) and tcgen05.commit
 //   warps 2-9       : epilogue; each thread owns half a row of the tile (64
-//                     columns): it accumulates minus every drained k-block
-//                     partial (tcgen05.ld 32x32b) in registers and adds the sum
-//                     into C at the end of the tile.
+//                     columns): it accumulates minus every drained partial
+//                     (tcgen05.ld 32x32b) in registers and adds the sum into C
+//                     at the end of the tile.
 // Every mbarrier wait is bounded; on expiry the kernel records an error,
 // drains what it issued, frees its TMEM and returns.
 #include <cuda.h>
@@ -42,16 +47,63 @@ namespace {
 
 constexpr int kBM = 128;
 constexpr int kBN = 128;
-constexpr int kBK = 32;  // fp32 elements per k-block (= one 128-byte swizzle row)
-constexpr int kStages = 3;
-constexpr int kTileBytes = kBM * kBK * 4;  // 16 KiB
-constexpr int kStageBytes = 4 * kTileBytes;
-constexpr int kThreads = 320;  // producer, MMA, 8 epilogue warps
+constexpr int kTileBytes = kBM * 128;  // 128 rows x 128 bytes per split tile
+constexpr int kThreads = 320;          // producer, MMA, 8 epilogue warps
 constexpr int kEpiThreads = 256;
-constexpr int kEpiCols = kBN / 2;  // columns per epilogue thread
-constexpr int kAccBufs = 4;                 // TMEM accumulator ring
+constexpr int kEpiCols = kBN / 2;
+constexpr int kAccBufs = 4;
 constexpr int kTmemCols = kAccBufs * kBN;  // all 512 columns
-constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256;
+
+template <int MODE>
+struct TcCfg;
+
+// 3xTF32: 2 splits, 32 fp32 per 128-byte row, one drain per k-block of four
+// 8-deep steps (12 MMAs).
+template <>
+struct TcCfg<kSplit3xTf32> {
+  static constexpr int kOps = 2;
+  static constexpr int kBK = 32;
+  static constexpr int kStages = 3;
+  static constexpr int kSteps = 4;          // MMA k-steps per k-block
+  static constexpr int kStepsPerDrain = 4;  // drain once per k-block
+  static constexpr int kProducts = 3;
+  // D = F32 (bits 4-5 = 1), A = B = TF32 (2), K-major, N >> 3, M >> 4
+  static constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) |
+                                     ((uint32_t)(kBN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+  __device__ static void product(int p, int* ia, int* ib) {
+    const int A[3] = {1, 0, 0}, B[3] = {0, 1, 0};
+    *ia = A[p];
+    *ib = B[p];
+  }
+};
+
+// BF16x6: 3 splits, 64 bf16 per 128-byte row, one drain per 16-deep step.
+template <>
+struct TcCfg<kSplitBf16x6> {
+  static constexpr int kOps = 3;
+  static constexpr int kBK = 64;
+  static constexpr int kStages = 2;
+  static constexpr int kSteps = 4;
+  static constexpr int kStepsPerDrain = 1;
+  static constexpr int kProducts = 6;
+  // D = F32, A = B = BF16 (1), K-major, N >> 3, M >> 4
+  static constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                                     ((uint32_t)(kBN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+  __device__ static void product(int p, int* ia, int* ib) {
+    const int A[6] = {1, 0, 2, 0, 1, 0}, B[6] = {1, 2, 0, 1, 0, 0};
+    *ia = A[p];
+    *ib = B[p];
+  }
+};
+
+template <int MODE>
+__host__ __device__ constexpr int stage_bytes() {
+  return 2 * TcCfg<MODE>::kOps * kTileBytes;
+}
+template <int MODE>
+__host__ __device__ constexpr int smem_bytes() {
+  return TcCfg<MODE>::kStages * stage_bytes<MODE>() + 1024 + 256;
+}
 
 __device__ inline uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -109,20 +161,6 @@ __device__ inline uint64_t sw128_desc(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor, kind::tf32: D = F32, A = B = TF32, both K-major,
-// N = kBN, M = kBM.
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kBN >> 3) << 17) |
-                            ((uint32_t)(kBM >> 4) << 24);
-
-__device__ inline void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
-      : "memory");
-}
-
 __device__ inline void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                    bar)
@@ -146,6 +184,30 @@ __device__ inline void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+template <int MODE>
+__device__ inline void mma_issue(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
+  if (MODE == kSplit3xTf32) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(TcCfg<MODE>::kIdesc), "r"(accumulate)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(TcCfg<MODE>::kIdesc), "r"(accumulate)
+        : "memory");
+  }
+}
+
+struct TcMaps {
+  CUtensorMap W[3];
+  CUtensorMap L[3];
+};
+
 struct TcArgs {
   float* C;
   int64_t ldc, n, r0;
@@ -167,16 +229,19 @@ __device__ inline void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
+template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_update_tc(const __grid_constant__ CUtensorMap tWh, const __grid_constant__ CUtensorMap tWl,
-                const __grid_constant__ CUtensorMap tLh, const __grid_constant__ CUtensorMap tLl,
-                TcArgs a) {
+    k_update_tc(const __grid_constant__ TcMaps maps, TcArgs a) {
+  using Cfg = TcCfg<MODE>;
+  constexpr int kStages = Cfg::kStages;
+  constexpr int kStageBytes = stage_bytes<MODE>();
+  constexpr int kDrainsPerKB = Cfg::kSteps / Cfg::kStepsPerDrain;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(base + kStages * kStageBytes);
-  uint64_t* full = bars;                    // [kStages]
-  uint64_t* empty = bars + kStages;         // [kStages]
+  uint64_t* full = bars;                      // [kStages]
+  uint64_t* empty = bars + kStages;           // [kStages]
   uint64_t* acc_full = bars + 2 * kStages;    // [kAccBufs]
   uint64_t* acc_empty = acc_full + kAccBufs;  // [kAccBufs]
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + kAccBufs);
@@ -228,11 +293,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           unsigned char* st = base + s * kStageBytes;
           const uint32_t fb = smem_u32(&full[s]);
           mbar_expect_tx(fb, kStageBytes);
-          const int kx = kb * kBK;
-          tma_load_2d(smem_u32(st + 0 * kTileBytes), &tWh, kx, i0, fb);
-          tma_load_2d(smem_u32(st + 1 * kTileBytes), &tWl, kx, i0, fb);
-          tma_load_2d(smem_u32(st + 2 * kTileBytes), &tLh, kx, c0, fb);
-          tma_load_2d(smem_u32(st + 3 * kTileBytes), &tLl, kx, c0, fb);
+          const int kx = kb * Cfg::kBK;
+#pragma unroll
+          for (int o = 0; o < Cfg::kOps; ++o) {
+            tma_load_2d(smem_u32(st + o * kTileBytes), &maps.W[o], kx, i0, fb);
+            tma_load_2d(smem_u32(st + (Cfg::kOps + o) * kTileBytes), &maps.L[o], kx, c0, fb);
+          }
         }
       }
       // drain: every issued stage must have landed before the CTA may exit
@@ -242,34 +308,48 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // ---- MMA issuer ----
-      int64_t g = 0;
+      int64_t g = 0;   // k-blocks consumed
+      int64_t dg = 0;  // drains issued
       bool ok = true;
       for (int64_t x = blockIdx.x; x < a.ntiles && ok; x += gridDim.x) {
-        for (int kb = 0; kb < KB; ++kb, ++g) {
+        for (int kb = 0; kb < KB && ok; ++kb, ++g) {
           const int s = (int)(g % kStages);
           const uint32_t ph = (uint32_t)((g / kStages) & 1);
-          const int buf = (int)(g % kAccBufs);
-          const uint32_t aph = (uint32_t)((g / kAccBufs) & 1);
-          if (!mbar_wait(smem_u32(&acc_empty[buf]), aph ^ 1u) ||
-              !mbar_wait(smem_u32(&full[s]), ph) || *(volatile int*)&s_fail) {
+          if (!mbar_wait(smem_u32(&full[s]), ph) || *(volatile int*)&s_fail) {
             atomicExch(&s_fail, 1);
             ok = false;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           unsigned char* st = base + s * kStageBytes;
-          const uint32_t aH = smem_u32(st + 0 * kTileBytes), aL = smem_u32(st + 1 * kTileBytes);
-          const uint32_t bH = smem_u32(st + 2 * kTileBytes), bL = smem_u32(st + 3 * kTileBytes);
-          const uint32_t d = tmem + (uint32_t)(buf * kBN);
 #pragma unroll
-          for (int kk = 0; kk < kBK / 8; ++kk) {
-            const uint32_t off = kk * 32;  // 8 tf32 = 32 bytes along K
-            mma_tf32(d, sw128_desc(aH + off), sw128_desc(bH + off), kk > 0 ? 1u : 0u);
-            mma_tf32(d, sw128_desc(aH + off), sw128_desc(bL + off), 1u);
-            mma_tf32(d, sw128_desc(aL + off), sw128_desc(bH + off), 1u);
+          for (int dr = 0; dr < kDrainsPerKB; ++dr, ++dg) {
+            const int buf = (int)(dg % kAccBufs);
+            const uint32_t aph = (uint32_t)((dg / kAccBufs) & 1);
+            if (!mbar_wait(smem_u32(&acc_empty[buf]), aph ^ 1u)) {
+              atomicExch(&s_fail, 1);
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t d = tmem + (uint32_t)(buf * kBN);
+            bool first = true;
+#pragma unroll
+            for (int ks = 0; ks < Cfg::kStepsPerDrain; ++ks) {
+              const uint32_t off = (uint32_t)((dr * Cfg::kStepsPerDrain + ks) * 32);  // 32 B per step
+#pragma unroll
+              for (int pidx = 0; pidx < Cfg::kProducts; ++pidx) {
+                int ia, ib;
+                Cfg::product(pidx, &ia, &ib);
+                const uint32_t sa = smem_u32(st + ia * kTileBytes) + off;
+                const uint32_t sb = smem_u32(st + (Cfg::kOps + ib) * kTileBytes) + off;
+                mma_issue<MODE>(d, sw128_desc(sa), sw128_desc(sb), first ? 0u : 1u);
+                first = false;
+              }
+            }
+            mma_commit(smem_u32(&acc_full[buf]));
           }
           mma_commit(smem_u32(&empty[s]));
-          mma_commit(smem_u32(&acc_full[buf]));
         }
       }
     }
@@ -278,14 +358,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
     const int half = (warp - 2) >> 2;
     const int rloc = 32 * quarter + lane;
-    int64_t g = 0;
+    int64_t dg = 0;
     bool ok = true;
+    const int drains = KB * kDrainsPerKB;
     for (int64_t x = blockIdx.x; x < a.ntiles && ok; x += gridDim.x) {
       int64_t tr, tc;
       tile_coords(x, &tr, &tc);
       const int64_t row = a.r0 + tr * kBM + rloc;
       const int64_t c0 = a.r0 + tc * kBN + half * kEpiCols;
-      // columns [c0, c0 + ncol) of this row are stored (lower triangle, < n)
       int64_t cend = c0 + kEpiCols;
       if (cend > a.n) cend = a.n;
       if (tr == tc && cend > row + 1) cend = row + 1;
@@ -293,9 +373,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       float acc[kEpiCols];
 #pragma unroll
       for (int c = 0; c < kEpiCols; ++c) acc[c] = 0.f;
-      for (int kb = 0; kb < KB; ++kb, ++g) {
-        const int buf = (int)(g % kAccBufs);
-        const uint32_t aph = (uint32_t)((g / kAccBufs) & 1);
+      for (int dr = 0; dr < drains; ++dr, ++dg) {
+        const int buf = (int)(dg % kAccBufs);
+        const uint32_t aph = (uint32_t)((dg / kAccBufs) & 1);
         if (!mbar_wait(smem_u32(&acc_full[buf]), aph) || *(volatile int*)&s_fail) {
           atomicExch(&s_fail, 1);
           ok = false;
@@ -347,37 +427,42 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   return fn;
 }
 
-bool make_map(CUtensorMap* m, const float* ptr, int64_t rows, int ldk) {
+// Row-major [rows x ldk] operand of `esz`-byte elements, boxes of 128 rows x
+// 128 bytes, 128-byte swizzle.
+bool make_map(CUtensorMap* m, const void* ptr, int64_t rows, int ldk, int esz) {
   auto enc = get_encode();
   if (!enc) return false;
   cuuint64_t dims[2] = {(cuuint64_t)ldk, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)ldk * sizeof(float)};
-  cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)kBM};
+  cuuint64_t strides[1] = {(cuuint64_t)ldk * (cuuint64_t)esz};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)kBM};
   cuuint32_t es[2] = {1, 1};
-  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(ptr), dims, strides,
-                   box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+  CUresult r = enc(m, esz == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                   2, const_cast<void*>(ptr), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
-}  // namespace
-
-cudaError_t outer_update_tc(float* C, int64_t ldc, int64_t n, int64_t r0, int kdim,
-                            const float* Wh, const float* Wl, const float* Lh, const float* Ll,
-                            int ldk, int* err_flag, cudaStream_t s) {
-  if (kdim % kBK != 0 || kdim <= 0 || kdim > ldk) return cudaErrorInvalidValue;
-  if ((ldk * sizeof(float)) % 16 != 0) return cudaErrorInvalidValue;
+template <int MODE>
+cudaError_t launch(float* C, int64_t ldc, int64_t n, int64_t r0, int kdim, void* const* Wops,
+                   void* const* Lops, int ldk, int* err_flag, cudaStream_t s) {
+  using Cfg = TcCfg<MODE>;
+  const int esz = MODE == kSplit3xTf32 ? 4 : 2;
+  if (kdim % Cfg::kBK != 0 || kdim <= 0 || kdim > ldk) return cudaErrorInvalidValue;
+  if (((int64_t)ldk * esz) % 16 != 0) return cudaErrorInvalidValue;
   const int64_t m = n - r0;
   if (m <= 0) return cudaSuccess;
   if (n > 0x7fffffff) return cudaErrorInvalidValue;
-  CUtensorMap tWh, tWl, tLh, tLl;
-  if (!make_map(&tWh, Wh, n, ldk) || !make_map(&tWl, Wl, n, ldk) || !make_map(&tLh, Lh, n, ldk) ||
-      !make_map(&tLl, Ll, n, ldk))
-    return cudaErrorInvalidValue;
+  TcMaps maps;
+  for (int o = 0; o < Cfg::kOps; ++o) {
+    if (!make_map(&maps.W[o], Wops[o], n, ldk, esz) || !make_map(&maps.L[o], Lops[o], n, ldk, esz))
+      return cudaErrorInvalidValue;
+  }
   static bool attr = false;
   if (!attr) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    cudaError_t e = cudaFuncSetAttribute(k_update_tc<MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smem_bytes<MODE>());
     if (e != cudaSuccess) return e;
     attr = true;
   }
@@ -386,7 +471,7 @@ cudaError_t outer_update_tc(float* C, int64_t ldc, int64_t n, int64_t r0, int kd
   a.ldc = ldc;
   a.n = n;
   a.r0 = r0;
-  a.kblocks = kdim / kBK;
+  a.kblocks = kdim / Cfg::kBK;
   a.tiles = (m + kBM - 1) / kBM;
   a.ntiles = a.tiles * (a.tiles + 1) / 2;
   a.err = err_flag;
@@ -395,8 +480,20 @@ cudaError_t outer_update_tc(float* C, int64_t ldc, int64_t n, int64_t r0, int kd
   if (e != cudaSuccess) return e;
   int64_t grid = di.sm_count;
   if (grid > a.ntiles) grid = a.ntiles;
-  k_update_tc<<<(unsigned)grid, kThreads, kSmemBytes, s>>>(tWh, tWl, tLh, tLl, a);
+  k_update_tc<MODE><<<(unsigned)grid, kThreads, smem_bytes<MODE>(), s>>>(maps, a);
   return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t outer_update_tc(int mode, float* C, int64_t ldc, int64_t n, int64_t r0, int kdim,
+                            void* const* Wops, void* const* Lops, int ldk, int* err_flag,
+                            cudaStream_t s) {
+  if (mode == kSplit3xTf32)
+    return launch<kSplit3xTf32>(C, ldc, n, r0, kdim, Wops, Lops, ldk, err_flag, s);
+  if (mode == kSplitBf16x6)
+    return launch<kSplitBf16x6>(C, ldc, n, r0, kdim, Wops, Lops, ldk, err_flag, s);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace dpp

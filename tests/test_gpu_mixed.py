@@ -26,20 +26,29 @@ def dpp():
     return m
 
 
-@pytest.fixture(params=[1, 0], ids=["simt", "tcgen05"])
+_PREC = {"p": "3xtf32"}
+
+
+@pytest.fixture(params=[(1, "3xtf32"), (0, "3xtf32"), (0, "bf16x6")],
+                ids=["simt", "tcgen05-3xtf32", "tcgen05-bf16x6"])
 def update_kernel(request, dpp):
+    """Trailing-update kernel (SIMT FP32 or tensor cores) and operand split."""
     from paper_1905_00165_gb300 import _lib
+    kern, prec = request.param
     old = _lib.get_tuning(_lib.DPP_TUNE_UPDATE_KERNEL)
-    _lib.set_tuning(_lib.DPP_TUNE_UPDATE_KERNEL, request.param)
+    _lib.set_tuning(_lib.DPP_TUNE_UPDATE_KERNEL, kern)
+    _PREC["p"] = prec
     yield request.param
+    _PREC["p"] = "3xtf32"
     _lib.set_tuning(_lib.DPP_TUNE_UPDATE_KERNEL, old)
 
 
-def _run(dpp, K, seed=0, uniforms=None, factor=False):
+def _run(dpp, K, seed=0, uniforms=None, factor=False, precision=None):
     import torch
     Kd = torch.from_numpy(np.ascontiguousarray(K)).cuda()
     u = None if uniforms is None else torch.from_numpy(uniforms).cuda()
-    s = dpp.sample_hermitian(Kd, seed=seed, precision="3xtf32", uniforms=u, factor=factor)
+    s = dpp.sample_hermitian(Kd, seed=seed, precision=precision or _PREC["p"], uniforms=u,
+                             factor=factor)
     torch.cuda.synchronize()
     return s
 
@@ -111,16 +120,15 @@ def test_tensor_core_update_matches_simt(dpp):
     facs = []
     old = _lib.get_tuning(_lib.DPP_TUNE_UPDATE_KERNEL)
     try:
-        for kern in (1, 0):
+        for kern, prec in ((1, "3xtf32"), (0, "3xtf32"), (0, "bf16x6")):
             _lib.set_tuning(_lib.DPP_TUNE_UPDATE_KERNEL, kern)
-            s = _run(dpp, K, uniforms=u, factor=True)
+            s = _run(dpp, K, uniforms=u, factor=True, precision=prec)
             facs.append(np.tril(s.factor.cpu().numpy()))
     finally:
         _lib.set_tuning(_lib.DPP_TUNE_UPDATE_KERNEL, old)
-    ref = O.sample_ldl(K, u).A
-    err_simt = np.max(np.abs(facs[0] - np.tril(ref)))
-    err_tc = np.max(np.abs(facs[1] - np.tril(ref)))
-    assert err_simt < 1e-4 and err_tc < 1e-4, (err_simt, err_tc)
+    ref = np.tril(O.sample_ldl(K, u).A)
+    errs = [float(np.max(np.abs(f - ref))) for f in facs]
+    assert max(errs) < 1e-4, errs
 
 
 def test_outer_block_sizes(dpp):
@@ -140,7 +148,7 @@ def test_outer_block_sizes(dpp):
         _lib.set_tuning(_lib.DPP_TUNE_OUTER_BLOCK, old)
 
 
-def _pivot_error_ratios(dpp, K, seed):
+def _pivot_error_ratios(dpp, K, seed, precision="bf16x6"):
     """|d_mixed - d_fp64| / (2^-22 sqrt(j+1) (K_jj + s_j)) for every pivot of one
     draw, with the mixed path forced onto the FP64 path's decisions."""
     import torch
@@ -149,7 +157,7 @@ def _pivot_error_ratios(dpp, K, seed):
     s64 = dpp.sample_hermitian(Kd, seed=seed, precision="fp64", factor=True)
     keep = s64.keep.cpu().numpy()
     u = torch.from_numpy(O.forced_uniforms(keep)).cuda()
-    smx = dpp.sample_hermitian(Kd, precision="3xtf32", uniforms=u)
+    smx = dpp.sample_hermitian(Kd, precision=precision, uniforms=u)
     torch.cuda.synchronize()
     d64 = s64.pivots.cpu().numpy()
     dmx = smx.pivots.cpu().numpy()

@@ -186,3 +186,25 @@ def lensemble_batch(batch: int, seed: int = 0, nmin: int = 64, nmax: int = 1024,
     sizes = lensemble_sizes(batch, seed, nmin, nmax)
     return [lensemble_kernel(int(m), seed * 1000003 + i + 1, features)
             for i, m in enumerate(sizes)]
+
+
+def lensemble_batch_torch(batch: int, seed: int = 0, nmin: int = 64, nmax: int = 1024,
+                          features: int = 64, device: str = "cuda"):
+    """The same law as ``lensemble_batch`` built with torch on a device
+    (FP64): per kernel, unit-norm Gaussian feature rows scaled by
+    LogUniform(0.1, 10) qualities, K = Phi (Phi^T Phi + I)^{-1} Phi^T."""
+    import torch
+    sizes = lensemble_sizes(batch, seed, nmin, nmax)
+    gen = torch.Generator(device="cpu").manual_seed(seed)
+    out = []
+    eye = torch.eye(features, dtype=torch.float64, device=device)
+    for m in sizes:
+        m = int(m)
+        G = torch.randn(m, features, generator=gen, dtype=torch.float64).to(device)
+        G = G / G.norm(dim=1, keepdim=True)
+        q = torch.exp(torch.empty(m, dtype=torch.float64).uniform_(math.log(0.1), math.log(10.0),
+                                                                   generator=gen)).to(device)
+        Phi = G * q[:, None]
+        K = Phi @ torch.linalg.solve(Phi.T @ Phi + eye, Phi.T)
+        out.append(0.5 * (K + K.T))
+    return out
