@@ -141,6 +141,47 @@ dpp_status dpp_sample_hermitian(const void* K, int64_t n, int64_t ld,
                                 dpp_result* result, void* workspace,
                                 size_t workspace_bytes, void* stream);
 
+/* Bytes of the device array that holds the scratch of
+ * dpp_sample_hermitian_static, and the largest orders that fit in it. */
+#define DPP_STATIC_SCRATCH_BYTES (4u << 20)
+#define DPP_STATIC_MAX_N_R64 15418
+#define DPP_STATIC_MAX_N_C128 7942
+
+/* dpp_sample_hermitian at DPP_PREC_FP64 without any device allocation and
+ * without a workspace argument. The paper has no counterpart: this entry point
+ * serves callers that cannot allocate device memory when they sample (a
+ * serving loop whose memory is planned once at start-up, where cudaMalloc
+ * would synchronise the device or fail under memory pressure; a plain C caller
+ * that owns only K and the outputs). Its scratch (the n x 32 panel of
+ * D-scaled rows, 2n pivot doubles and a flag word: about 272 n bytes for
+ * DPP_R64, 528 n for DPP_C128) lives in one file-scope device array of
+ * DPP_STATIC_SCRATCH_BYTES bytes inside the library.
+ *   K, n, ld, dtype, seed, instance, uniforms, keep, pivots, result, stream
+ *              as in dpp_sample_hermitian.
+ *   factor_out REQUIRED (n > 0): device n x ld of dtype, owned by the caller,
+ *              receives L and D of K - 1_{Y^c}; may equal K (in place).
+ * Keep, pivots and log P are those of dpp_sample_hermitian with
+ * DPP_PREC_FP64 on the same arguments.
+ * Errors: DPP_ERR_INVALID_ARG for bad sizes, NULL or misaligned pointers;
+ * DPP_ERR_WORKSPACE (with the limit in dpp_last_error) when n is above
+ * DPP_STATIC_MAX_N_R64 / DPP_STATIC_MAX_N_C128; DPP_ERR_CUDA if the set-up or
+ * a launch fails. Nothing is enqueued on an error found on the host.
+ * Set-up: the first call on each device, made with that device current, looks
+ * up the array's device address (cudaGetSymbolAddress, which may load the
+ * library's module onto the device); make that first call before any stream
+ * capture begins. Nothing in the array needs to start at zero: the call clears
+ * its flag word on `stream` before the first kernel.
+ * Concurrency: all calls on one device share the one array, so two calls in
+ * flight at once on a device (different streams, or host threads without
+ * ordering between their streams) race on it; issue them in order, e.g. on
+ * one stream. */
+dpp_status dpp_sample_hermitian_static(const void* K, int64_t n, int64_t ld,
+                                       int32_t dtype, uint64_t seed,
+                                       uint64_t instance,
+                                       const double* uniforms, uint8_t* keep,
+                                       void* factor_out, double* pivots,
+                                       dpp_result* result, void* stream);
+
 /* Sample DPP(K) for a general (non-Hermitian) K (Algorithm 1, blocked as in
  * Algorithm 4). Same arguments as dpp_sample_hermitian, except that the whole
  * of K is read, factor_out receives L (strictly lower, unit diagonal) and U

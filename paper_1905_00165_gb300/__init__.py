@@ -14,7 +14,7 @@ from ._lib import (DPP_C128, DPP_OP_LOGPROB_BACKWARD, DPP_OP_SAMPLE_HERMITIAN,
                    DPP_OP_SAMPLE_LU, DPP_PREC_3XTF32, DPP_PREC_BF16X6, DPP_PREC_FP64, DPP_R64,
                    DPPError, PRECISIONS, decode_result, load, workspace_size)
 
-__all__ = ["sample_hermitian", "sample_lu", "sample_batched", "BatchedSampler",
+__all__ = ["sample_hermitian", "sample_hermitian_static", "sample_lu", "sample_batched", "BatchedSampler",
            "logprob_backward", "uniforms", "Sample", "DPPLogProb", "DPPError", "load",
            "workspace_size"]
 
@@ -122,6 +122,26 @@ def sample_hermitian(K, seed: int = 0, instance: int = 0, precision: str = "fp64
                      uniforms=None, factor: bool = False, workspace=None) -> Sample:
     """Draw Y ~ DPP(K) for Hermitian K (LDL^H form; lower triangle read)."""
     return _sample(True, K, seed, instance, precision, uniforms, factor, workspace)
+
+
+def sample_hermitian_static(K, factor, keep, pivots, raw, seed: int = 0, instance: int = 0,
+                            uniforms=None) -> Sample:
+    """FP64 Hermitian draw through dpp_sample_hermitian_static, which uses no
+    workspace and allocates no device memory. Every output is caller-owned:
+    ``factor`` (column-major n x n, may be K itself), ``keep`` (n uint8),
+    ``pivots`` (n float64) and ``raw`` (RESULT_BYTES uint8)."""
+    L = load()
+    dt = _dtype_code(K)
+    n = K.shape[0]
+    if n and (K.stride(0) != 1 or factor.stride(0) != 1 or factor.stride(1) != K.stride(1)):
+        raise ValueError("K and factor must be column-major with the same leading dimension")
+    ld = K.stride(1) if n else 1
+    st = L.dpp_sample_hermitian_static(
+        K.data_ptr() if n else None, n, ld, dt, seed, instance,
+        None if uniforms is None else uniforms.data_ptr(), keep.data_ptr() if n else None,
+        factor.data_ptr() if n else None, pivots.data_ptr(), raw.data_ptr(), _stream(K.device))
+    _lib.check(st)
+    return Sample(keep, pivots[:n], factor, raw)
 
 
 def sample_lu(K, seed: int = 0, instance: int = 0, precision: str = "fp64",

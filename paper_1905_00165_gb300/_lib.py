@@ -18,6 +18,8 @@ DPP_OK, DPP_ERR_INVALID_ARG, DPP_ERR_CUDA, DPP_ERR_WORKSPACE, DPP_ERR_UNSUPPORTE
 DPP_R64, DPP_C128 = 0, 1
 DPP_PREC_FP64, DPP_PREC_3XTF32, DPP_PREC_BF16X6, DPP_PREC_FP32 = 0, 1, 2, 3
 DPP_OP_SAMPLE_HERMITIAN, DPP_OP_SAMPLE_LU, DPP_OP_LOGPROB_BACKWARD = 0, 1, 2
+DPP_STATIC_SCRATCH_BYTES = 4 << 20
+DPP_STATIC_MAX_N_R64, DPP_STATIC_MAX_N_C128 = 15418, 7942
 DPP_RES_NONFINITE, DPP_RES_TIMEOUT, DPP_RES_INADMISSIBLE, DPP_RES_RECOMPUTE = 1, 2, 4, 8
 RESULT_BYTES = 32
 RESULT_FMT = "<iiiidd"
@@ -60,6 +62,8 @@ def load(path: Optional[str] = None):
         f = getattr(L, name)
         f.argtypes = [vp, i64, i64, i32, i32, u64, u64, vp, vp, vp, vp, vp, vp, sz, vp]
         f.restype = i32
+    L.dpp_sample_hermitian_static.argtypes = [vp, i64, i64, i32, u64, u64, vp, vp, vp, vp, vp, vp]
+    L.dpp_sample_hermitian_static.restype = i32
     L.dpp_batched_workspace_size.argtypes = [i32, i64, i32]
     L.dpp_batched_workspace_size.restype = sz
     L.dpp_sample_batched.argtypes = [i32, vp, vp, vp, i64, i32, u64, vp, vp, vp, vp, vp, vp, sz, vp]

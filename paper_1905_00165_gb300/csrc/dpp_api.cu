@@ -24,6 +24,12 @@ static dpp_status fail_cuda(cudaError_t e, const char* where) {
   return DPP_ERR_CUDA;
 }
 
+void clear_last_error() { g_last_error.clear(); }
+
+dpp_status set_last_error(dpp_status s, const char* msg) { return fail(s, msg); }
+
+dpp_status set_last_cuda_error(cudaError_t e, const char* where) { return fail_cuda(e, where); }
+
 cudaError_t dev_info(DevInfo* out) {
   static thread_local DevInfo cache[64];
   int dev = 0;

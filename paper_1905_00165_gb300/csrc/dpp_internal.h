@@ -38,6 +38,11 @@ struct DevInfo {
 };
 cudaError_t dev_info(DevInfo* out);
 
+// Thread-local error text read back by dpp_last_error (dpp_api.cu).
+void clear_last_error();
+dpp_status set_last_error(dpp_status s, const char* msg);
+dpp_status set_last_cuda_error(cudaError_t e, const char* where);
+
 // Common arguments of one draw.
 struct DrawArgs {
   const void* K;

@@ -73,3 +73,30 @@ def test_invalid_arguments_rejected_on_host(L):
     assert _call(L, K=fake, n=4, dtype=1, prec=1, keep=fake, res=fake, ws=fake, wsb=1 << 30) == \
         _lib.DPP_ERR_UNSUPPORTED
     assert L.dpp_uniforms(0, 0, -1, None, None) == _lib.DPP_ERR_INVALID_ARG
+
+
+def test_static_entry_limits_checked_on_host(L):
+    """The allocation-free entry point rejects orders whose scratch would not
+    fit its fixed array, and a missing factor buffer, before any CUDA call."""
+    hdr = open(os.path.join(ROOT, "include", "dpp.h")).read()
+    macros = {name: int(v) << int(sh or 0) for name, v, sh in
+              re.findall(r"#define (DPP_STATIC_\w+) \(?(\d+)u?(?: << (\d+))?", hdr)}
+    assert macros["DPP_STATIC_SCRATCH_BYTES"] == _lib.DPP_STATIC_SCRATCH_BYTES
+    assert macros["DPP_STATIC_MAX_N_R64"] == _lib.DPP_STATIC_MAX_N_R64
+    assert macros["DPP_STATIC_MAX_N_C128"] == _lib.DPP_STATIC_MAX_N_C128
+    fake = 4096  # never dereferenced: validation fails first
+    f = L.dpp_sample_hermitian_static
+    for dt, nmax in [(_lib.DPP_R64, _lib.DPP_STATIC_MAX_N_R64),
+                     (_lib.DPP_C128, _lib.DPP_STATIC_MAX_N_C128)]:
+        # the largest accepted order fills the array; one more does not fit
+        esz = 16 if dt == _lib.DPP_C128 else 8
+        a256 = lambda b: (b + 255) // 256 * 256
+        need = lambda n: a256(esz * n * 32) + a256(16 * n) + 512
+        assert need(nmax) <= _lib.DPP_STATIC_SCRATCH_BYTES < need(nmax + 1)
+        n = nmax + 1
+        assert f(fake, n, n, dt, 0, 0, None, fake, fake, None, fake, None) == _lib.DPP_ERR_WORKSPACE
+        assert "limit" in _lib.last_error()
+    assert f(fake, 4, 4, _lib.DPP_R64, 0, 0, None, fake, None, None, fake, None) == \
+        _lib.DPP_ERR_INVALID_ARG
+    assert f(fake, 4, 3, _lib.DPP_R64, 0, 0, None, fake, fake, None, fake, None) == \
+        _lib.DPP_ERR_INVALID_ARG
