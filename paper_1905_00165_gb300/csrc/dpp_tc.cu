@@ -32,8 +32,8 @@
 //                     tcgen05.mma (M = N = 128) and tcgen05.commit
 //   warps 2-9       : epilogue; each thread owns half a row of the tile (64
 //                     columns): it accumulates minus every drained partial
-//                     (tcgen05.ld 32x32b) in registers and adds the sum into C
-//                     at the end of the tile.
+//                     (tcgen05.ld 32x32b) in registers, fetches its C values
+//                     at the start of the tile and stores C + sum at its end.
 // Every mbarrier wait is bounded; on expiry the kernel records an error,
 // drains what it issued, frees its TMEM and returns.
 #include <cuda.h>
@@ -370,6 +370,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (cend > a.n) cend = a.n;
       if (tr == tc && cend > row + 1) cend = row + 1;
       const int ncol = (row < a.n && cend > c0) ? (int)(cend - c0) : 0;
+      // the tile's C values are fetched now and land while the MMAs run, so
+      // the read-modify-write at the end of the tile waits on no load
+      float cold[kEpiCols];
+      {
+        const float* rp = a.C + row + c0 * a.ldc;
+#pragma unroll
+        for (int c = 0; c < kEpiCols; ++c) cold[c] = (c < ncol) ? __ldcg(rp + c * a.ldc) : 0.f;
+      }
       float acc[kEpiCols];
 #pragma unroll
       for (int c = 0; c < kEpiCols; ++c) acc[c] = 0.f;
@@ -398,7 +406,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       float* wp = a.C + row + c0 * a.ldc;
 #pragma unroll
       for (int c = 0; c < kEpiCols; ++c) {
-        if (c < ncol) *wp += acc[c];
+        if (c < ncol) *wp = cold[c] + acc[c];
         wp += a.ldc;
       }
     }
