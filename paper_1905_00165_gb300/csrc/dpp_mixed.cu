@@ -97,7 +97,9 @@ struct OuterArgs {
   RecomputeArgs rc;
 };
 
-enum { kCtlRows = 8 };  // control word: rows of the outer block solved through epoch
+// control word: the rows of the inner panel with this epoch are final for every
+// earlier panel of the block (released before that panel's decisions start)
+enum { kCtlRows = 8 };
 
 constexpr int kThreadsOuter = 256;
 constexpr size_t kOuterDynSmem = sizeof(float) * kMaxOuterBlock * kPanel;  // staged Lk
@@ -366,14 +368,306 @@ __device__ __forceinline__ void dec_steps(const OuterArgs& a, float (*sL)[kPanel
     dec_steps<J + 1>(a, sL, bl, q, epoch, b, lane, tau0, r, dd, si, uf, kf, sq, u, mykeep, seq);
 }
 
+// ---- CTA 0 of the outer-block launch ----------------------------------------
+//
+// Right-looking lookahead over the inner panels R_0, R_1, ... of the block
+// (32 rows / columns each). Warp 0 makes the decisions of panel k and then
+// prepares only the next diagonal block: it solves the rows of R_{k+1} against
+// panel k and applies panel k's rank-32 update to the 32 x 32 block
+// R_{k+1} x R_{k+1}, so that the decisions of panel k+1 can start at once.
+// Warps 1-7 meanwhile solve the rows of R_{k+2}, ... against panel k and
+// apply its update to the rest of the block's lower triangle. Named barriers
+// order the two groups:
+//   1: panel k published (warp 0 arrives, warps 1-7 wait)
+//   2: warps 1-7 done with panel k-1 (they arrive, warp 0 waits)
+//   3: the l rows of R_{k+1} are in shared memory (warp 0 arrives)
+// Warp 0 waits on 2 before it arrives on 1, so no group can arrive twice on
+// one barrier before the other has passed it.
+constexpr int kLnLd = 36;                              // float4-aligned rows
+constexpr int kRestRows = kMaxOuterBlock - 2 * kPanel;  // rows below R_{k+1}
+constexpr int kAheadRows = kMaxOuterBlock - kPanel;     // rows below R_k
+
+__device__ __forceinline__ void nb_sync(int id) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kThreadsOuter) : "memory");
+}
+__device__ __forceinline__ void nb_arrive(int id) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(kThreadsOuter) : "memory");
+}
+
+// Forward substitution of one row against the factored 32 x 32 block:
+// w = x L11^{-T}, l = w / d, and the row's contributions sum w l (double-float)
+// and sum |w l| to its running diagonal and to the borderline scale.
+__device__ __forceinline__ void row_solve(const float (*sL)[kPanel + 1], const float* srd,
+                                          float (&w)[kPanel], float (&l)[kPanel], f2& dsum,
+                                          float& ssum) {
+#pragma unroll
+  for (int k = 1; k < kPanel; ++k) {
+#pragma unroll
+    for (int t = 0; t < k; ++t) w[k] = fmaf(-w[t], sL[k][t], w[k]);
+  }
+  dsum = {0.f, 0.f};
+  ssum = 0.f;
+#pragma unroll
+  for (int k = 0; k < kPanel; ++k) {
+    l[k] = w[k] * srd[k];
+    dsum = f2_add_prod(dsum, w[k], l[k]);
+    ssum += fabsf(w[k] * l[k]);
+  }
+}
+
+// Per-lane inputs of the decisions of the panel at q (lane = local pivot).
+__device__ __forceinline__ void lane_inputs(const OuterArgs& a, int64_t q, int b, int lane,
+                                            double& u, float& uf, float& kf, float& sq) {
+  u = 2.0;
+  uf = 2.f;
+  kf = 0.f;
+  sq = 1.f;
+  if (lane < b) {
+    u = a.uniforms ? a.uniforms[q + lane] : philox_uniform(a.seed, a.inst, (uint64_t)(q + lane));
+    uf = (float)u;
+    kf = (float)a.K[(q + lane) + (q + lane) * a.ldk];
+    sq = sqrtf((float)(q + lane + 1));
+  }
+}
+
+// CTA 0 working set (shared memory of k_outer_mixed)
+__shared__ float sL2[2][kPanel][kPanel + 1];          // L11 of panels k (k & 1)
+__shared__ float srd2[2][kPanel];                     // 1 / d of panels k (k & 1)
+__shared__ __align__(16) float sLn[kAheadRows][kLnLd];  // l rows of R_{k+1}, R_{k+2}, ...
+__shared__ float sWn[kRestRows][kPanel + 1];           // w rows of R_{k+2}, ...
+__shared__ float sB[kPanel][kPanel + 1];                // next diagonal block (warp 0)
+
+// One row of a 32 x 32 tile of the rank-32 update: ap[c * lda] -= w . ln[c]
+// for columns c <= cmax (cmax < 0: nothing), ln rows kLnLd floats apart, in
+// chunks of eight columns (loads of a chunk issued together).
+__device__ __forceinline__ void update_row_chunks(float* ap, int64_t lda, const float (&w)[kPanel],
+                                                  const float* ln, int cmax) {
+#pragma unroll 1
+  for (int c0 = 0; c0 < kPanel; c0 += 8) {
+    float acc[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c] = (c0 + c <= cmax) ? ap[(c0 + c) * lda] : 0.f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const float4* lc = reinterpret_cast<const float4*>(ln + (c0 + c) * kLnLd);
+      float sacc = 0.f;
+#pragma unroll
+      for (int t4 = 0; t4 < kPanel / 4; ++t4) {
+        const float4 v = lc[t4];
+        sacc = fmaf(w[4 * t4 + 0], v.x, sacc);
+        sacc = fmaf(w[4 * t4 + 1], v.y, sacc);
+        sacc = fmaf(w[4 * t4 + 2], v.z, sacc);
+        sacc = fmaf(w[4 * t4 + 3], v.w, sacc);
+      }
+      acc[c] -= sacc;
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+      if (c0 + c <= cmax) ap[(c0 + c) * lda] = acc[c];
+  }
+}
+
+// Warp 0, after the decisions of panel k (at q, full width): solve the rows of
+// R_{k+1} against it, share their l rows, and apply its update to the lower
+// part of R_{k+1} x R_{k+1}, which is left in sB. Returns the rows' running
+// diagonals and borderline scales.
+__device__ __noinline__ void w0_prepare_next(const OuterArgs& a, int64_t q, int kk, int64_t pend,
+                                             int buf, double* kd_out, double* s_out) {
+  const int lane = threadIdx.x & 31;
+  float* A = a.A;
+  const int64_t lda = a.lda;
+  const int64_t qn = q + kPanel;
+  const int bn = (int)((pend - qn) < kPanel ? (pend - qn) : kPanel);
+  const int64_t row = qn + lane;
+  const bool valid = lane < bn;
+  float w[kPanel], l[kPanel];
+#pragma unroll
+  for (int c = 0; c < kPanel; ++c) w[c] = valid ? A[row + (q + c) * lda] : 0.f;
+  f2 dsum;
+  float ssum;
+  row_solve(sL2[buf], srd2[buf], w, l, dsum, ssum);
+  double kdn = 0.0, sn = 0.0;
+  if (valid) {
+    float* lk = a.Lk + row * (int64_t)a.NB + kk;
+#pragma unroll
+    for (int c = 0; c < kPanel; ++c) {
+      A[row + (q + c) * lda] = l[c];
+      lk[c] = l[c];
+    }
+    kdn = a.kd[row] - f2_to_double(dsum);
+    sn = a.s[row] + (double)ssum;
+    a.kd[row] = kdn;
+    a.s[row] = sn;
+  }
+#pragma unroll
+  for (int c = 0; c < kPanel; ++c) sLn[lane][c] = l[c];
+  __syncwarp();
+  nb_arrive(3);
+  // rank-32 update of the lower part of the next diagonal block (left in A,
+  // then gathered into sB)
+  update_row_chunks(A + row + qn * lda, lda, w, &sLn[0][0], valid ? lane : -1);
+  __syncwarp();
+#pragma unroll
+  for (int c = 0; c < kPanel; ++c) sB[lane][c] = (valid && c <= lane) ? A[row + (qn + c) * lda] : 0.f;
+  __syncwarp();
+  *kd_out = kdn;
+  *s_out = sn;
+}
+
+// Warps 1-7, panel k (at q, full width, not the block's last): solve the rows
+// of R_{k+2}, ... against it and apply its rank-32 update to the block's lower
+// triangle below R_{k+1}.
+__device__ __noinline__ void wr_panel(const OuterArgs& a, int64_t q, int kk, int64_t pend, int buf,
+                                      int nP, int k) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tw = tid - 32;  // 0 .. 223
+  float* A = a.A;
+  const int64_t lda = a.lda;
+  const int64_t row = q + 2 * kPanel + tw;
+  if (tw < kRestRows && row < pend) {
+    float w[kPanel], l[kPanel];
+#pragma unroll
+    for (int c = 0; c < kPanel; ++c) w[c] = A[row + (q + c) * lda];
+    f2 dsum;
+    float ssum;
+    row_solve(sL2[buf], srd2[buf], w, l, dsum, ssum);
+    float* lk = a.Lk + row * (int64_t)a.NB + kk;
+#pragma unroll
+    for (int c = 0; c < kPanel; ++c) {
+      A[row + (q + c) * lda] = l[c];
+      lk[c] = l[c];
+      sWn[tw][c] = w[c];
+      sLn[kPanel + tw][c] = l[c];
+    }
+    a.kd[row] -= f2_to_double(dsum);
+    a.s[row] += (double)ssum;
+  }
+  nb_sync(3);
+  // 32 x 32 tiles (row block rm >= 1, column block rj <= rm, both counted
+  // from R_{k+1}), dealt round-robin to the seven warps
+  const int R = nP - k - 2;
+  const int T = R * (R + 3) / 2;
+  for (int x = warp - 1; x < T; x += kThreadsOuter / 32 - 1) {
+    int rm = 1, xx = x;
+    while (xx >= rm + 1) {
+      xx -= rm + 1;
+      ++rm;
+    }
+    const int rj = xx;
+    const int64_t i = q + kPanel + (int64_t)kPanel * rm + lane;
+    const int64_t cb = q + kPanel + (int64_t)kPanel * rj;
+    const bool vi = i < pend;
+    float w[kPanel];
+#pragma unroll
+    for (int t = 0; t < kPanel; ++t) w[t] = sWn[kPanel * (rm - 1) + lane][t];
+    update_row_chunks(A + i + cb * lda, lda, w, &sLn[kPanel * rj][0], vi ? (int)(i - cb) : -1);
+  }
+}
+
+__device__ void cta0_block(const OuterArgs& a, BlockLog& bl) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t p = a.p;
+  const int64_t pend = p + a.NBp;
+  const int nP = (a.NBp + kPanel - 1) / kPanel;
+  float* A = a.A;
+  const int64_t lda = a.lda;
+
+  if (warp == 0) {
+    float r[kPanel];
+    f2 dd = {0.f, 0.f};
+    float si = 0.f;
+    {
+      const int b = (int)((pend - p) < kPanel ? (pend - p) : kPanel);
+#pragma unroll
+      for (int k = 0; k < kPanel; ++k) {
+        float v = 0.f;
+        if (lane < b && k < b)
+          v = (k <= lane) ? A[(p + lane) + (p + k) * lda] : A[(p + k) + (p + lane) * lda];
+        r[k] = v;
+      }
+      if (lane < b) {
+        dd = f2_from_double(a.kd[p + lane]);
+        si = (float)a.s[p + lane];
+      }
+    }
+    int seq = 0;
+    for (int k = 0; k < nP; ++k) {
+      const int64_t q = p + (int64_t)kPanel * k;
+      const int b = (int)((pend - q) < kPanel ? (pend - q) : kPanel);
+      const int kk = (int)(q - p);
+      const unsigned epoch = a.epoch0 + (unsigned)k;
+      const int buf = k & 1;
+      double u;
+      float uf, kf, sq;
+      lane_inputs(a, q, b, lane, u, uf, kf, sq);
+      bool mykeep = false;
+      dec_steps<0>(a, sL2[buf], &bl, q, epoch, b, lane, a.tau0, r, dd, si, uf, kf, sq, u, mykeep,
+                   seq);
+      // publish the panel: L11 (lower), pivots, reciprocals
+#pragma unroll
+      for (int c = 0; c < kPanel; ++c) {
+        sL2[buf][lane][c] = r[c];
+        if (lane < b && c <= lane) A[(q + lane) + (q + c) * lda] = r[c];
+      }
+      if (lane < b) {
+        const double d = f2_to_double(dd);
+        a.piv[q + lane] = d;
+        a.keep[q + lane] = mykeep ? 1 : 0;
+        const float rdl = (float)(1.0 / d);
+        srd2[buf][lane] = rdl;
+        a.rdv[q + lane] = rdl;
+        bl.dhi[kk + lane] = dd.hi;
+        bl.dlo[kk + lane] = dd.lo;
+        bl.kp[kk + lane] = mykeep ? 1 : 0;
+      } else {
+        srd2[buf][lane] = 1.f;
+      }
+      __threadfence();
+      __syncwarp();
+      if (lane == 0) recompute_release_done(a.rc, epoch);
+      nb_sync(2);
+      nb_arrive(1);
+      if (k + 1 < nP) {
+        // panel k is full width here; R_{k+1} may be the ragged last one
+        const int64_t qn = q + kPanel;
+        const int bn = (int)((pend - qn) < kPanel ? (pend - qn) : kPanel);
+        const bool valid = lane < bn;
+        double kdn, sn;
+        w0_prepare_next(a, q, kk, pend, buf, &kdn, &sn);
+#pragma unroll
+        for (int c = 0; c < kPanel; ++c)
+          r[c] = (valid && c < bn) ? ((c <= lane) ? sB[lane][c] : sB[c][lane]) : 0.f;
+        __syncwarp();
+        dd = valid ? f2_from_double(kdn) : f2{0.f, 0.f};
+        si = valid ? (float)sn : 0.f;
+        // the rows of R_{k+1} are final for every earlier panel
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) st_release(&a.rc.ctrl[kCtlRows], epoch + 1);
+      }
+    }
+  } else {
+    nb_arrive(2);
+    for (int k = 0; k < nP; ++k) {
+      nb_sync(1);
+      if (k + 1 < nP) {
+        const int64_t q = p + (int64_t)kPanel * k;
+        wr_panel(a, q, (int)(q - p), pend, k & 1, nP, k);
+        __threadfence();
+        nb_arrive(2);
+      }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kThreadsOuter, 1) k_outer_mixed(OuterArgs a) {
   extern __shared__ __align__(16) float sLk[];  // [kMaxOuterBlock][kPanel]
-  __shared__ float sL[kPanel][kPanel + 1];
-  __shared__ float srd[kPanel];
   __shared__ BlockLog bl;
   __shared__ int s_ok;
   __shared__ float sW[2 * 32 * kSwLd];
   __shared__ float stage[kThreadsOuter / 32][kPanel][kPanel + 1];
+  float (*sL)[kPanel + 1] = sL2[0];
+  float* srd = srd2[0];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t p = a.p, n = a.n;
   const int64_t pend = p + a.NBp;
@@ -386,69 +680,9 @@ __global__ void __launch_bounds__(kThreadsOuter, 1) k_outer_mixed(OuterArgs a) {
       bl.max_ratio = 0.f;
       bl.rc_failed = 0;
     }
-    int seq = 0;
-    for (int64_t q = p; q < pend; q += kPanel) {
-      const int b = (int)((pend - q) < kPanel ? (pend - q) : kPanel);
-      const int kk = (int)(q - p);
-      const unsigned epoch = a.epoch0 + (unsigned)((q - p) / kPanel);
-      // (A) left-looking update of this panel's columns for the block's rows
-      stage_lk(a, sLk, q, b, kk, tid);
-      __syncthreads();
-      inner_update(a, sLk, sW, q, b, kk, q, pend, tid);
-      __syncthreads();
-      // (B) decisions, warp 0, rows of the diagonal block in registers
-      if (warp == 0) {
-        float r[kPanel];
-#pragma unroll
-        for (int k = 0; k < kPanel; ++k) {
-          float v = 0.f;
-          if (lane < b && k < b)
-            v = (k <= lane) ? A[(q + lane) + (q + k) * lda] : A[(q + k) + (q + lane) * lda];
-          r[k] = v;
-        }
-        double u = 2.0;
-        float uf = 2.f, si = 0.f, kf = 0.f, sq = 1.f;
-        f2 dd = {0.f, 0.f};
-        if (lane < b) {
-          u = a.uniforms ? a.uniforms[q + lane]
-                         : philox_uniform(a.seed, a.inst, (uint64_t)(q + lane));
-          uf = (float)u;
-          dd = f2_from_double(a.kd[q + lane]);
-          si = (float)a.s[q + lane];
-          kf = (float)a.K[(q + lane) + (q + lane) * a.ldk];
-          sq = sqrtf((float)(q + lane + 1));
-        }
-        bool mykeep = false;
-        dec_steps<0>(a, sL, &bl, q, epoch, b, lane, a.tau0, r, dd, si, uf, kf, sq, u, mykeep, seq);
-        // publish the block: L11 (lower), pivots, reciprocals
-#pragma unroll
-        for (int k = 0; k < kPanel; ++k) {
-          sL[lane][k] = r[k];
-          if (lane < b && k <= lane) A[(q + lane) + (q + k) * lda] = r[k];
-        }
-        if (lane < b) {
-          const double d = f2_to_double(dd);
-          a.piv[q + lane] = d;
-          a.keep[q + lane] = mykeep ? 1 : 0;
-          const float rdl = (float)(1.0 / d);
-          srd[lane] = rdl;
-          a.rdv[q + lane] = rdl;
-          bl.dhi[kk + lane] = dd.hi;
-          bl.dlo[kk + lane] = dd.lo;
-          bl.kp[kk + lane] = mykeep ? 1 : 0;
-        } else {
-          srd[lane] = 1.f;
-        }
-      }
-      __threadfence();
-      __syncthreads();
-      if (tid == 0) recompute_release_done(a.rc, epoch);
-      // (C) panel solve of the block's remaining rows
-      panel_solve(a, sL, srd, stage, q, b, q + b, pend, tid);
-      __threadfence();
-      __syncthreads();
-      if (tid == 0) st_release(&a.rc.ctrl[kCtlRows], epoch);
-    }
+    __syncthreads();
+    cta0_block(a, bl);
+    __syncthreads();
     // likelihood and bookkeeping of the block (FP64, one pivot per thread)
     double lp = 0.0;
     int kept = 0, oor = 0, bad = 0;
@@ -513,7 +747,7 @@ __global__ void __launch_bounds__(kThreadsOuter, 1) k_outer_mixed(OuterArgs a) {
     const int kk = (int)(q - p);
     const unsigned epoch = a.epoch0 + (unsigned)((q - p) / kPanel);
     if (kk > 0 && r_lo < r_hi) {
-      if (tid == 0) s_ok = rc_wait_geq(a.rc, &a.rc.ctrl[kCtlRows], epoch - 1) ? 1 : 0;
+      if (tid == 0) s_ok = rc_wait_geq(a.rc, &a.rc.ctrl[kCtlRows], epoch) ? 1 : 0;
       __syncthreads();
       if (!s_ok) return;
       stage_lk(a, sLk, q, b, kk, tid);
@@ -673,7 +907,7 @@ cudaError_t sample_mixed(const DrawArgs& a, Workspace ws) {
   cudaError_t e = init_result(a.result, a.stream);
   if (e != cudaSuccess || n == 0) return e;
   if ((e = cudaMemsetAsync(L.flag, 0, 256, a.stream)) != cudaSuccess) return e;
-  if ((e = recompute_reset(L.rs, a.stream)) != cudaSuccess) return e;
+  if ((e = recompute_reset(L.rs, n, a.stream)) != cudaSuccess) return e;
   const double* K = static_cast<const double*>(a.K);
   {
     ProfScope ps(kProfConvert, a.stream, 0.0, 12.0 * (double)n * (double)n / 2.0);
@@ -700,7 +934,6 @@ cudaError_t sample_mixed(const DrawArgs& a, Workspace ws) {
   const bool use_tc = g_tuning.update_kernel == 0;
   const int split = a.precision == DPP_PREC_BF16X6 ? kSplitBf16x6 : kSplit3xTf32;
   const int kb_tc = split == kSplitBf16x6 ? 64 : 32;
-  const int64_t min_workers = 64;  // recomputes are served by the workers
   for (int64_t p = 0; p < n; p += NB) {
     const int NBp = (int)((n - p) < NB ? (n - p) : NB);
     {
@@ -732,13 +965,11 @@ cudaError_t sample_mixed(const DrawArgs& a, Workspace ws) {
       oa.epoch0 = epoch;
       oa.tol = 1e-3;
       oa.tau0 = (float)(g_tuning.tau_safety * 0x1.0p-22);
+      // every other SM is a worker: they stream the rows below the block and
+      // serve the recomputes (which are bandwidth- and latency-bound)
       const int64_t mw = n - p - NBp;
-      int64_t nw = (mw + 127) / 128;
-      int64_t want = (n + 255) / 256;
-      if (want > min_workers) want = min_workers;
-      if (nw < want) nw = want;
+      int64_t nw = cap - 1;
       if (nw < 1) nw = 1;
-      if (nw > cap - 1) nw = cap - 1;
       oa.wrow0 = p + NBp;
       oa.wrows = (mw + nw - 1) / nw;
       if (oa.wrows < 1) oa.wrows = 1;

@@ -93,6 +93,31 @@ def test_forced_borderline_pivots_are_recomputed(dpp, update_kernel):
         assert abs(gp[j] - ref2.pivots[j]) < 1e-10, (j, gp[j], ref2.pivots[j])
 
 
+@pytest.mark.parametrize("precision", ["bf16x6", "3xtf32"])
+def test_forced_borderline_deep_pivots(dpp, precision):
+    """Borderline pivots deep into a larger kernel (many 32-row blocks and
+    worker CTAs in the recompute wavefronts), including the last index and
+    the first and last row of an outer block."""
+    from paper_1905_00165_gb300 import _lib
+    n = 3000
+    K = W.hermitian_kernel(n, seed=5, kind="beta")
+    u = O.uniforms(9, 0, n)
+    ref = O.sample_ldl(K, u)
+    pre = pre_decision_pivots(ref)
+    targets = [1000, 1279, 1280, 2047, 2500, 2999]
+    for j in targets:
+        u[j] = pre[j] - 1e-8 if ref.keep[j] else pre[j] + 1e-8
+    ref2 = O.sample_ldl(K, u)
+    s = _run(dpp, K, uniforms=u, precision=precision)
+    r = s.result()
+    assert r["status"] & (_lib.DPP_RES_TIMEOUT | _lib.DPP_RES_RECOMPUTE) == 0, r
+    assert r["n_borderline"] >= len(targets), r
+    assert np.array_equal(s.keep.cpu().numpy(), ref2.keep)
+    gp = s.pivots.cpu().numpy()
+    for j in targets:
+        assert abs(gp[j] - ref2.pivots[j]) < 1e-10, (j, gp[j], ref2.pivots[j])
+
+
 def test_mixed_projection_and_spanning_trees(dpp, update_kernel):
     n = 640
     K = W.hermitian_kernel(n, seed=2, kind="projection")
