@@ -100,17 +100,48 @@ struct OuterArgs {
 // control word: the rows of the inner panel with this epoch are final for every
 // earlier panel of the block (released before that panel's decisions start)
 enum { kCtlRows = 8 };
+constexpr int kSwLd = 65;
 
 constexpr int kThreadsOuter = 256;
 constexpr size_t kOuterDynSmem = sizeof(float) * kMaxOuterBlock * kPanel;  // staged Lk
+
+// Shared memory of k_outer_mixed, at file scope so that every function sees
+// its state space (a shared store can then never be taken to alias a global
+// load, and loads are not held back behind stores).
+extern __shared__ __align__(16) float g_outer_dyn[];  // staged Lk: [kMaxOuterBlock][kPanel]
+__shared__ float g_sW[2 * 32 * kSwLd];
+__shared__ float g_stage[kThreadsOuter / 32][kPanel][kPanel + 1];
+__shared__ float g_sL[kPanel][kPanel + 1];
+__shared__ float g_srd[kPanel];
+__shared__ int g_s_ok;
+
+// Copy of N elements by THREADS threads with every load issued before the
+// first store, so that the loads are in flight together (a strided loop with
+// a runtime count would wait out one load latency per element).
+template <int N, int THREADS, class LoadF, class StoreF>
+__device__ __forceinline__ void staged_copy(int tid, LoadF ld, StoreF stv) {
+  constexpr int kPer = (N + THREADS - 1) / THREADS;
+  float v[kPer];
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int e = tid + j * THREADS;
+    v[j] = e < N ? ld(e) : 0.f;
+  }
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int e = tid + j * THREADS;
+    if (e < N) stv(e, v[j]);
+  }
+}
 
 // A[i, q+c] -= sum_{t < kk} Wk[i, t] Lk[q+c, t] for rows [r_lo, r_hi), c < b,
 // restricted to i >= q + c, as a shared-memory tiled product: 64-row tiles,
 // 32-deep chunks of W staged k-major in sW (coalesced row loads), L read from
 // sLk[t][c] (staged by the caller); each thread owns 2 rows x 4 columns.
-constexpr int kSwLd = 65;
-__device__ void inner_update(const OuterArgs& a, const float* sLk, float* sW, int64_t q, int b,
-                             int kk, int64_t r_lo, int64_t r_hi, int tid) {
+__device__ void inner_update(const OuterArgs& a, int64_t q, int b, int kk, int64_t r_lo,
+                             int64_t r_hi, int tid) {
+  const float* sLk = g_outer_dyn;
+  float* sW = g_sW;
   if (kk <= 0 || r_lo >= r_hi) return;
   const int ty = tid / 8, tx = tid % 8;
   const int lr = tid / 8, lf = tid % 8;  // W loader: 8 float4 per row, 2 rows per thread
@@ -180,10 +211,28 @@ __device__ void inner_update(const OuterArgs& a, const float* sLk, float* sW, in
 }
 
 // Stage Lk rows [q, q+b), columns t < kk, into sLk[t][c].
-__device__ void stage_lk(const OuterArgs& a, float* sLk, int64_t q, int b, int kk, int tid) {
-  for (int idx = tid; idx < kk * kPanel; idx += kThreadsOuter) {
-    const int t = idx % kk, c = idx / kk;
-    sLk[t * kPanel + c] = (c < b) ? __ldcg(&a.Lk[(q + c) * (int64_t)a.NB + t]) : 0.f;
+__device__ void stage_lk(const OuterArgs& a, int64_t q, int b, int kk, int tid) {
+  float* sLk = g_outer_dyn;
+  const int n = kk * kPanel;
+  const float* Lk = a.Lk;
+  const int64_t NB = a.NB;
+  constexpr int kIn = 8;  // loads in flight per thread
+  for (int base = tid; base < n; base += kIn * kThreadsOuter) {
+    float v[kIn];
+#pragma unroll
+    for (int j = 0; j < kIn; ++j) {
+      const int idx = base + j * kThreadsOuter;
+      v[j] = 0.f;
+      if (idx < n) {
+        const int t = idx % kk, c = idx / kk;
+        if (c < b) v[j] = __ldcg(&Lk[(q + c) * NB + t]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kIn; ++j) {
+      const int idx = base + j * kThreadsOuter;
+      if (idx < n) sLk[(idx % kk) * kPanel + idx / kk] = v[j];
+    }
   }
 }
 
@@ -193,9 +242,11 @@ __device__ void stage_lk(const OuterArgs& a, float* sLk, int64_t q, int b, int k
 // tensor-core splits (TF32 pairs or BF16 triplets) row-major through a
 // per-warp shared-memory transpose so each store instruction covers one
 // contiguous row segment. All threads iterate together.
-__device__ void panel_solve(const OuterArgs& a, const float (*sL)[kPanel + 1], const float* srd,
-                            float (*stage)[kPanel][kPanel + 1], int64_t q, int b, int64_t r_lo,
+__device__ void panel_solve(const OuterArgs& a, int64_t q, int b, int64_t r_lo,
                             int64_t r_hi, int tid) {
+  const float (*sL)[kPanel + 1] = g_sL;
+  const float* srd = g_srd;
+  float (*stage)[kPanel][kPanel + 1] = g_stage;
   const int t0 = (int)(q - a.p);
   const int warp = tid >> 5, lane = tid & 31;
   float* A = a.A;
@@ -291,7 +342,12 @@ __device__ __noinline__ BorderOut borderline_step(const OuterArgs& a, float (*bl
   const int lane = threadIdx.x & 31;
   const double p64 = (double)ph + (double)pl;
   double pe = p64, est = 0.0;
-  const bool ok = recompute_leader(a.rc, blk, b, q, j, epoch, &seq, &pe, &est);
+  // the earlier panels' rows, pivots and decisions must be out in global
+  // memory before the workers read them
+  bool ready = true;
+  if (lane == 0) ready = rc_wait_geq(a.rc, &a.rc.ctrl[kCtlRows], epoch);
+  ready = __shfl_sync(kFull, ready, 0);
+  const bool ok = ready && recompute_leader(a.rc, blk, b, q, j, epoch, &seq, &pe, &est);
   const bool keep = u_j < pe;
   if (lane == 0) {
     bl->border += 1;
@@ -306,15 +362,80 @@ __device__ __noinline__ BorderOut borderline_step(const OuterArgs& a, float (*bl
   return o;
 }
 
-// One decision step of the 32 x 32 diagonal block, local pivot J (compile
-// time, so the block rows stay in registers): lane i holds row i of the
-// block as a full symmetric row; the pivot row is broadcast by shuffles.
+// One decision step of the 32 x 32 diagonal block, local pivot J: lane i
+// holds row i of the block as a full symmetric row, the pivot row is
+// broadcast by shuffles. The fast chain is unrolled (J known at compile time,
+// so the rows stay in registers) and holds no call, which keeps its code
+// small enough to run from the instruction cache on its first pass in a
+// panel; at the first pivot inside the borderline band it stops (stop = J)
+// and the panel is finished by dec_slow.
 template <int J>
-__device__ __forceinline__ void dec_steps(const OuterArgs& a, float (*sL)[kPanel + 1], BlockLog* bl,
-                                          int64_t q, unsigned epoch, int b, int lane, float tau0,
-                                          float (&r)[kPanel], f2& dd, float& si, float uf, float kf,
-                                          float sq, double u, bool& mykeep, int& seq) {
-  if (J < b) {
+__device__ __forceinline__ void dec_fast(int b, int lane, float tau0, float (&r)[kPanel], f2& dd,
+                                         float& si, float uf, float kf, float sq, bool& mykeep,
+                                         int& stop) {
+  if (J < b && stop < 0) {
+    const float ph = __shfl_sync(kFull, dd.hi, J);
+    const float uj = __shfl_sync(kFull, uf, J);
+    const float sj = __shfl_sync(kFull, si, J);
+    const float kj = __shfl_sync(kFull, kf, J);
+    const float sqj = __shfl_sync(kFull, sq, J);
+    const float tau = tau0 * sqj * (fabsf(kj) + sj) + 0x1.0p-22f;
+    if (fabsf(uj - ph) <= tau) {
+      stop = J;
+    } else {
+      const bool kp = uj < ph;
+      const float df = kp ? ph : ph - 1.0f;
+      if (lane == J && !kp) dd = f2_add_f(dd, -1.0f);
+      const float rd = 1.0f / df;
+      const float wj = r[J];
+      const float l = wj * rd;
+      const bool act = (lane > J) && (lane < b);
+#pragma unroll
+      for (int k = J + 1; k < kPanel; ++k) {
+        const float pk = __shfl_sync(kFull, r[k], J);
+        if (act) r[k] = fmaf(-l, pk, r[k]);
+      }
+      if (act) {
+        r[J] = l;
+        dd = f2_sub_prod(dd, wj, l);
+        si += fabsf(wj * l);
+      }
+      if (lane == J) {
+        r[J] = df;
+        mykeep = kp;
+      }
+    }
+  }
+  if constexpr (J + 1 < kPanel)
+    dec_fast<J + 1>(b, lane, tau0, r, dd, si, uf, kf, sq, mykeep, stop);
+}
+
+// Decision state of warp 0 handed to dec_slow through shared memory (the
+// rows of the fast chain must never have their address taken, or they would
+// leave the registers).
+struct DecState {
+  float dd_hi[kPanel], dd_lo[kPanel], si[kPanel];
+  unsigned char keep[kPanel];
+};
+
+// The rest of the panel from local pivot j0 (a borderline one) on, with a
+// runtime step index: the same arithmetic as dec_fast, predicated over all 32
+// columns, and one call site for the FP64 recompute of borderline pivots. The
+// rows come in and go out through sL (row lane in sL[lane]), the per-lane
+// state through ds.
+__device__ __noinline__ void dec_slow(const OuterArgs& a, float (*sL)[kPanel + 1], DecState* ds,
+                                      BlockLog* bl, int64_t q, unsigned epoch, int b, float tau0,
+                                      float uf, float kf, float sq, double u, int& seq, int j0) {
+  const int lane = threadIdx.x & 31;
+  float r[kPanel];
+#pragma unroll
+  for (int k = 0; k < kPanel; ++k) r[k] = sL[lane][k];
+  f2 dd = make_f2(ds->dd_hi[lane], ds->dd_lo[lane]);
+  float si = ds->si[lane];
+  bool mykeep = ds->keep[lane] != 0;
+  __syncwarp();
+#pragma unroll 1
+  for (int J = j0; J < b; ++J) {
     const float ph = __shfl_sync(kFull, dd.hi, J);
     const float uj = __shfl_sync(kFull, uf, J);
     const float sj = __shfl_sync(kFull, si, J);
@@ -346,328 +467,535 @@ __device__ __forceinline__ void dec_steps(const OuterArgs& a, float (*sL)[kPanel
       if (lane == J && !kp) dd = f2_add_f(dd, -1.0f);
     }
     const float rd = 1.0f / df;
-    const float wj = r[J];
+    float wj = 0.f;
+#pragma unroll
+    for (int k = 0; k < kPanel; ++k) wj = (k == J) ? r[k] : wj;
     const float l = wj * rd;
     const bool act = (lane > J) && (lane < b);
 #pragma unroll
-    for (int k = J + 1; k < kPanel; ++k) {
+    for (int k = 0; k < kPanel; ++k) {
       const float pk = __shfl_sync(kFull, r[k], J);
-      if (act) r[k] = fmaf(-l, pk, r[k]);
+      if (act && k > J) r[k] = fmaf(-l, pk, r[k]);
     }
+#pragma unroll
+    for (int k = 0; k < kPanel; ++k)
+      if (k == J) r[k] = act ? l : (lane == J ? df : r[k]);
     if (act) {
-      r[J] = l;
       dd = f2_sub_prod(dd, wj, l);
       si += fabsf(wj * l);
     }
-    if (lane == J) {
-      r[J] = df;
-      mykeep = kp;
-    }
+    if (lane == J) mykeep = kp;
   }
-  if constexpr (J + 1 < kPanel)
-    dec_steps<J + 1>(a, sL, bl, q, epoch, b, lane, tau0, r, dd, si, uf, kf, sq, u, mykeep, seq);
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < kPanel; ++k) sL[lane][k] = r[k];
+  ds->dd_hi[lane] = dd.hi;
+  ds->dd_lo[lane] = dd.lo;
+  ds->si[lane] = si;
+  ds->keep[lane] = mykeep ? 1 : 0;
+  __syncwarp();
 }
 
 // ---- CTA 0 of the outer-block launch ----------------------------------------
 //
-// Right-looking lookahead over the inner panels R_0, R_1, ... of the block
-// (32 rows / columns each). Warp 0 makes the decisions of panel k and then
-// prepares only the next diagonal block: it solves the rows of R_{k+1} against
-// panel k and applies panel k's rank-32 update to the 32 x 32 block
-// R_{k+1} x R_{k+1}, so that the decisions of panel k+1 can start at once.
-// Warps 1-7 meanwhile solve the rows of R_{k+2}, ... against panel k and
-// apply its update to the rest of the block's lower triangle. Named barriers
-// order the two groups:
-//   1: panel k published (warp 0 arrives, warps 1-7 wait)
-//   2: warps 1-7 done with panel k-1 (they arrive, warp 0 waits)
-//   3: the l rows of R_{k+1} are in shared memory (warp 0 arrives)
-// Warp 0 waits on 2 before it arrives on 1, so no group can arrive twice on
-// one barrier before the other has passed it.
-constexpr int kLnLd = 36;                              // float4-aligned rows
-constexpr int kRestRows = kMaxOuterBlock - 2 * kPanel;  // rows below R_{k+1}
-constexpr int kAheadRows = kMaxOuterBlock - kPanel;     // rows below R_k
+// The inner panels R_0, R_1, ... of the block (32 rows / columns each) run as
+// a pipeline around warp 0, which only makes decisions. With panel k being
+// decided:
+//   * CTA 1 (the helper) takes the block's rows from R_{k+2} on: it solves
+//     them against panel k-1, updates their column block R_k through panel
+//     k-1 (left-looking) and raises control word kCtlPre;
+//   * warps 1-7 of CTA 0 (the support warps) first write panel k-1 out to
+//     global memory and release it (kCtlDone, kCtlRows), then bring the rows
+//     of R_{k+1} up to date through panel k-1 (they are the helper's rows
+//     through its previous step): solve them against panel k-1, then update
+//     their column block R_k and their diagonal block from the stored W and
+//     L (left-looking, in 32-wide chunks); once panel k is decided they solve
+//     R_{k+1} against it and apply its rank-32 update in shared memory, and
+//     hand the result to warp 0.
+// Named barriers between warp 0 and the support warps:
+//   1  warp 0 arrives when the decisions of a panel are in shared memory;
+//   2  the support warps arrive when the inputs of the next panel are;
+//   3  support warps only (224 threads).
+// Each side arrives on one barrier only after passing the other, so neither
+// can arrive twice on a barrier before the other side has passed it.
 
-__device__ __forceinline__ void nb_sync(int id) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kThreadsOuter) : "memory");
-}
-__device__ __forceinline__ void nb_arrive(int id) {
-  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(kThreadsOuter) : "memory");
-}
+enum { kCtlPre = 9 };  // control word: the helper's step for the panel with this epoch is done
 
-// Forward substitution of one row against the factored 32 x 32 block:
-// w = x L11^{-T}, l = w / d, and the row's contributions sum w l (double-float)
-// and sum |w l| to its running diagonal and to the borderline scale.
-__device__ __forceinline__ void row_solve(const float (*sL)[kPanel + 1], const float* srd,
-                                          float (&w)[kPanel], float (&l)[kPanel], f2& dsum,
-                                          float& ssum) {
-#pragma unroll
-  for (int k = 1; k < kPanel; ++k) {
-#pragma unroll
-    for (int t = 0; t < k; ++t) w[k] = fmaf(-w[t], sL[k][t], w[k]);
-  }
-  dsum = {0.f, 0.f};
-  ssum = 0.f;
-#pragma unroll
-  for (int k = 0; k < kPanel; ++k) {
-    l[k] = w[k] * srd[k];
-    dsum = f2_add_prod(dsum, w[k], l[k]);
-    ssum += fabsf(w[k] * l[k]);
-  }
-}
+constexpr int kSupThreads = kThreadsOuter - 32;
 
-// Per-lane inputs of the decisions of the panel at q (lane = local pivot).
-__device__ __forceinline__ void lane_inputs(const OuterArgs& a, int64_t q, int b, int lane,
-                                            double& u, float& uf, float& kf, float& sq) {
-  u = 2.0;
-  uf = 2.f;
-  kf = 0.f;
-  sq = 1.f;
-  if (lane < b) {
-    u = a.uniforms ? a.uniforms[q + lane] : philox_uniform(a.seed, a.inst, (uint64_t)(q + lane));
-    uf = (float)u;
-    kf = (float)a.K[(q + lane) + (q + lane) * a.ldk];
-    sq = sqrtf((float)(q + lane + 1));
-  }
+__device__ __forceinline__ void nb_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void nb_arrive(int id, int count) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
 // CTA 0 working set (shared memory of k_outer_mixed)
-__shared__ float sL2[2][kPanel][kPanel + 1];          // L11 of panels k (k & 1)
-__shared__ float srd2[2][kPanel];                     // 1 / d of panels k (k & 1)
-__shared__ __align__(16) float sLn[kAheadRows][kLnLd];  // l rows of R_{k+1}, R_{k+2}, ...
-__shared__ float sWn[kRestRows][kPanel + 1];           // w rows of R_{k+2}, ...
-__shared__ float sB[kPanel][kPanel + 1];                // next diagonal block (warp 0)
+struct Cta0Smem {
+  // decisions of panel k (warp 0 -> support), double buffered by k & 1
+  float L11[2][kPanel][kPanel + 1];  // L (strictly lower) and D (diagonal)
+  float rd[2][kPanel];               // FP32 1 / d
+  double piv[2][kPanel];             // FP64 final pivots
+  unsigned char keep[2][kPanel];
+  // inputs of the next panel's decisions (support -> warp 0)
+  float blk[kPanel][kPanel + 1];  // symmetric diagonal block
+  double kd[kPanel];              // running diagonal (FP64)
+  double sj[kPanel];              // borderline scale
+  double u[kPanel];               // uniforms
+  float kf[kPanel];               // FP32 K_jj
+  // prefetched by the support warps while warp 0 decides
+  float X[kPanel][kPanel + 1];  // A[R_{k+1}, R_k]
+  float Y[kPanel][kPanel + 1];  // A[R_{k+1}, R_{k+1}] (lower)
+  double kdP[kPanel];
+  double sP[kPanel];
+  double uP[kPanel];
+  float kfP[kPanel];
+  // solve of R_{k+1} against panel k
+  float W[kPanel][kPanel + 1];
+  float Lr[kPanel][kPanel + 1];
+  // 32-wide chunks of the stored W and L (left-looking update)
+  float Wc[kPanel][kPanel + 1];
+  float Lc[2 * kPanel][kPanel + 1];
+};
 
-// One row of a 32 x 32 tile of the rank-32 update: ap[c * lda] -= w . ln[c]
-// for columns c <= cmax (cmax < 0: nothing), ln rows kLnLd floats apart, in
-// chunks of eight columns (loads of a chunk issued together).
-__device__ __forceinline__ void update_row_chunks(float* ap, int64_t lda, const float (&w)[kPanel],
-                                                  const float* ln, int cmax) {
-#pragma unroll 1
-  for (int c0 = 0; c0 < kPanel; c0 += 8) {
-    float acc[8];
+__shared__ Cta0Smem g_S0;
+__shared__ BlockLog g_bl;
+
+// Column-oriented forward substitution of the rows r = sw, sw + 7, ... of X
+// against the factored block of buffer buf (lane = column): w = x L11^{-T},
+// l = w / d. Writes S.W, S.Lr and subtracts sum w l from kd (FP64).
+__device__ __forceinline__ void sup_solve_rows(int buf, int bn, double* kd,
+                                               double* sj) {
+  Cta0Smem& S = g_S0;
+  const int st = threadIdx.x - 32, lane = threadIdx.x & 31, sw = st >> 5;
+  constexpr unsigned kF = 0xffffffffu;
+  float w[5];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) acc[c] = (c0 + c <= cmax) ? ap[(c0 + c) * lda] : 0.f;
+  for (int m = 0; m < 5; ++m) {
+    const int r = sw + 7 * m;
+    w[m] = (r < kPanel) ? S.X[r][lane] : 0.f;
+  }
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const float4* lc = reinterpret_cast<const float4*>(ln + (c0 + c) * kLnLd);
-      float sacc = 0.f;
+  for (int t = 0; t < kPanel; ++t) {
+    const float lt = S.L11[buf][lane][t];
 #pragma unroll
-      for (int t4 = 0; t4 < kPanel / 4; ++t4) {
-        const float4 v = lc[t4];
-        sacc = fmaf(w[4 * t4 + 0], v.x, sacc);
-        sacc = fmaf(w[4 * t4 + 1], v.y, sacc);
-        sacc = fmaf(w[4 * t4 + 2], v.z, sacc);
-        sacc = fmaf(w[4 * t4 + 3], v.w, sacc);
+    for (int m = 0; m < 5; ++m) {
+      const float wt = __shfl_sync(kF, w[m], t);
+      if (lane > t) w[m] = fmaf(-wt, lt, w[m]);
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < 5; ++m) {
+    const int r = sw + 7 * m;
+    if (r < kPanel) {
+      const bool vr = r < bn;
+      const float wv = vr ? w[m] : 0.f;
+      const float lv = wv * S.rd[buf][lane];
+      S.W[r][lane] = wv;
+      S.Lr[r][lane] = lv;
+      double ds = (double)wv * (double)lv;
+      double ss = (double)fabsf(wv * lv);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        ds += __shfl_xor_sync(kF, ds, o);
+        ss += __shfl_xor_sync(kF, ss, o);
       }
-      acc[c] -= sacc;
+      if (lane == 0 && vr) {
+        kd[r] -= ds;
+        sj[r] += ss;
+      }
     }
-#pragma unroll
-    for (int c = 0; c < 8; ++c)
-      if (c0 + c <= cmax) ap[(c0 + c) * lda] = acc[c];
   }
 }
 
-// Warp 0, after the decisions of panel k (at q, full width): solve the rows of
-// R_{k+1} against it, share their l rows, and apply its update to the lower
-// part of R_{k+1} x R_{k+1}, which is left in sB. Returns the rows' running
-// diagonals and borderline scales.
-__device__ __noinline__ void w0_prepare_next(const OuterArgs& a, int64_t q, int kk, int64_t pend,
-                                             int buf, double* kd_out, double* s_out) {
+// Support warps, while panel k (at q) is decided and k + 1 < nP: bring the
+// rows of R_{k+1} (bn rows) up to date through panel k - 1 and leave in
+// shared memory X = A[R_{k+1}, R_k], Y = A[R_{k+1}, R_{k+1}] (lower), and
+// their running diagonals, borderline scales, uniforms and K_jj.
+__device__ __noinline__ void sup_ready_next(const OuterArgs& a, int k, int64_t q,
+                                            int bn) {
+  Cta0Smem& S = g_S0;
+  const int st = threadIdx.x - 32;
+  const int64_t p = a.p, qn = q + kPanel;
+  float* A = a.A;
+  const int64_t lda = a.lda;
+  const int64_t NB = a.NB;
+  const int kk = (int)(q - p);
+  if (st < kPanel) {
+    const int i = st;
+    const bool vi = i < bn;
+    S.kdP[i] = vi ? a.kd[qn + i] : 0.0;
+    S.sP[i] = vi ? a.s[qn + i] : 0.0;
+    S.uP[i] = vi ? (a.uniforms ? a.uniforms[qn + i]
+                               : philox_uniform(a.seed, a.inst, (uint64_t)(qn + i)))
+                 : 2.0;
+    S.kfP[i] = vi ? (float)a.K[(qn + i) + (qn + i) * a.ldk] : 0.f;
+  }
+  if (k >= 1) {
+    // the rows against panel k - 1 (buffer of k - 1 still holds its L11)
+    const int64_t qp = q - kPanel;
+    const int bp = (k - 1) & 1;
+    staged_copy<kPanel * kPanel, kSupThreads>(
+        st,
+        [&](int e) {
+          const int i = e % kPanel, c = e / kPanel;
+          return i < bn ? __ldcg(&A[(qn + i) + (qp + c) * lda]) : 0.f;
+        },
+        [&](int e, float v) { S.X[e % kPanel][e / kPanel] = v; });
+    nb_sync(3, kSupThreads);
+    sup_solve_rows(bp, bn, S.kdP, S.sP);
+    nb_sync(3, kSupThreads);
+    for (int e = st; e < kPanel * kPanel; e += kSupThreads) {
+      const int i = e / kPanel, c = e % kPanel;  // consecutive threads: one row
+      if (i < bn) {
+        a.Wk[(qn + i) * NB + (kk - kPanel) + c] = S.W[i][c];
+        a.Lk[(qn + i) * NB + (kk - kPanel) + c] = S.Lr[i][c];
+      }
+    }
+    for (int e = st; e < kPanel * kPanel; e += kSupThreads) {
+      const int i = e % kPanel, c = e / kPanel;
+      if (i < bn) A[(qn + i) + (qp + c) * lda] = S.Lr[i][c];
+    }
+    nb_sync(3, kSupThreads);
+  }
+  // left-looking update through panel k - 1: outputs o < 1024 are X (i, c),
+  // the others the lower triangle of Y; at most 7 per thread
+  constexpr int kOut = kPanel * kPanel + kPanel * (kPanel + 1) / 2;
+  constexpr int kPer = (kOut + kSupThreads - 1) / kSupThreads;
+  float acc[kPer];
+  int oi[kPer], oc[kPer];
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    acc[j] = 0.f;
+    const int o = st + j * kSupThreads;
+    int i = 0, c = 0;
+    if (o < kPanel * kPanel) {
+      i = o % kPanel;
+      c = o / kPanel;
+    } else if (o < kOut) {
+      const int y = o - kPanel * kPanel;
+      i = (int)((sqrtf(8.f * (float)y + 1.f) - 1.f) * 0.5f);
+      while (i * (i + 1) / 2 > y) --i;
+      while ((i + 1) * (i + 2) / 2 <= y) ++i;
+      c = kPanel + (y - i * (i + 1) / 2);  // column index into Lc rows 32..63
+    }
+    oi[j] = i;
+    oc[j] = c;
+  }
+  for (int t0 = 0; t0 < kk; t0 += kPanel) {
+    staged_copy<3 * kPanel * kPanel, kSupThreads>(
+        st,
+        [&](int e) {
+          const int r = e / kPanel, t = e % kPanel;  // consecutive threads: one row
+          if (r < kPanel) return r < bn ? __ldcg(&a.Wk[(qn + r) * NB + t0 + t]) : 0.f;
+          if (r < 2 * kPanel) return __ldcg(&a.Lk[(q + (r - kPanel)) * NB + t0 + t]);
+          const int rr = r - 2 * kPanel;
+          return rr < bn ? __ldcg(&a.Lk[(qn + rr) * NB + t0 + t]) : 0.f;
+        },
+        [&](int e, float v) {
+          const int r = e / kPanel, t = e % kPanel;
+          if (r < kPanel) S.Wc[r][t] = v;
+          else S.Lc[r - kPanel][t] = v;
+        });
+    nb_sync(3, kSupThreads);
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      if (st + j * kSupThreads < kOut) {
+        float s = 0.f;
+#pragma unroll
+        for (int t = 0; t < kPanel; ++t) s = fmaf(S.Wc[oi[j]][t], S.Lc[oc[j]][t], s);
+        acc[j] += s;
+      }
+    }
+    nb_sync(3, kSupThreads);
+  }
+  float av[kPer];
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int o = st + j * kSupThreads;
+    const int i = oi[j], c = oc[j];
+    av[j] = 0.f;
+    if (o < kOut && i < bn)
+      av[j] = __ldcg(&A[(qn + i) + ((o < kPanel * kPanel) ? (q + c) : (qn + c - kPanel)) * lda]);
+  }
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int o = st + j * kSupThreads;
+    if (o < kOut) {
+      const int i = oi[j], c = oc[j];
+      const float v = i < bn ? av[j] - acc[j] : 0.f;
+      if (o < kPanel * kPanel) S.X[i][c] = v;
+      else S.Y[i][c - kPanel] = v;
+    }
+  }
+  // upper part of Y is never read
+  nb_sync(3, kSupThreads);
+}
+
+// The first panel of the block: its rows as the previous launches left them.
+__device__ __noinline__ void sup_load_first(const OuterArgs& a, int b0) {
+  Cta0Smem& S = g_S0;
+  const int st = threadIdx.x - 32;
+  const int64_t p = a.p;
+  const float* A = a.A;
+  const int64_t lda = a.lda;
+  staged_copy<kPanel * kPanel, kSupThreads>(
+      st,
+      [&](int e) {
+        const int i = e % kPanel, c = e / kPanel;
+        return (i < b0 && c <= i) ? __ldcg(&A[(p + i) + (p + c) * lda]) : 0.f;
+      },
+      [&](int e, float v) { S.Y[e % kPanel][e / kPanel] = v; });
+  if (st < kPanel) {
+    const int i = st;
+    const bool vi = i < b0;
+    S.kdP[i] = vi ? a.kd[p + i] : 0.0;
+    S.sP[i] = vi ? a.s[p + i] : 0.0;
+    S.uP[i] = vi ? (a.uniforms ? a.uniforms[p + i]
+                               : philox_uniform(a.seed, a.inst, (uint64_t)(p + i)))
+                 : 2.0;
+    S.kfP[i] = vi ? (float)a.K[(p + i) + (p + i) * a.ldk] : 0.f;
+  }
+}
+
+// Support warps: the inputs of the next panel's decisions from the prefetched
+// blocks. With the previous panel k (buffer buf), solve the rows of R_{k+1}
+// (w = x L11^{-T}, l = w / d) and apply the rank-32 update to the diagonal
+// block; without (the block's first panel), take the blocks as they are.
+__device__ __noinline__ void sup_prepare(int buf, int bn, bool after_panel) {
+  Cta0Smem& S = g_S0;
+  const int st = threadIdx.x - 32;
+  if (after_panel) {
+    if (st < kPanel) {
+      S.kd[st] = S.kdP[st];
+      S.sj[st] = S.sP[st];
+    }
+    nb_sync(3, kSupThreads);
+    sup_solve_rows(buf, bn, S.kd, S.sj);
+    nb_sync(3, kSupThreads);
+    // rank-32 update of the lower triangle of the diagonal block
+    for (int o = st; o < kPanel * (kPanel + 1) / 2; o += kSupThreads) {
+      int i = (int)((sqrtf(8.f * (float)o + 1.f) - 1.f) * 0.5f);
+      while (i * (i + 1) / 2 > o) --i;
+      while ((i + 1) * (i + 2) / 2 <= o) ++i;
+      const int c = o - i * (i + 1) / 2;
+      float acc = 0.f;
+#pragma unroll
+      for (int t = 0; t < kPanel; ++t) acc = fmaf(S.W[i][t], S.Lr[c][t], acc);
+      const float y = (i < bn) ? S.Y[i][c] - acc : 0.f;
+      S.blk[i][c] = y;
+      S.blk[c][i] = y;
+    }
+  } else {
+    for (int o = st; o < kPanel * kPanel; o += kSupThreads) {
+      const int i = o / kPanel, c = o % kPanel;
+      S.blk[i][c] = (c <= i) ? S.Y[i][c] : S.Y[c][i];
+    }
+    if (st < kPanel) {
+      S.kd[st] = S.kdP[st];
+      S.sj[st] = S.sP[st];
+    }
+  }
+  if (st < kPanel) {
+    S.u[st] = S.uP[st];
+    S.kf[st] = S.kfP[st];
+  }
+  nb_sync(3, kSupThreads);
+}
+
+// Support warps: panel k (at q, b rows, buffer buf) and the l rows of R_{k+1}
+// (bn rows; bn = 0 for the block's last panel) out to global memory, then
+// release both.
+__device__ __noinline__ void sup_publish(const OuterArgs& a, int64_t q, int b, int kk, int buf,
+                            int bn, unsigned epoch) {
+  Cta0Smem& S = g_S0;
+  const int st = threadIdx.x - 32;
+  float* A = a.A;
+  const int64_t lda = a.lda;
+  for (int e = st; e < kPanel * kPanel; e += kSupThreads) {
+    const int i = e % kPanel, c = e / kPanel;
+    if (i < b && c <= i) A[(q + i) + (q + c) * lda] = S.L11[buf][i][c];
+    if (i < bn) {
+      const int64_t row = q + kPanel + i;
+      const float l = S.Lr[i][c];
+      A[row + (q + c) * lda] = l;
+      a.Lk[row * (int64_t)a.NB + kk + c] = l;
+    }
+  }
+  if (st < kPanel) {
+    const int i = st;
+    if (i < b) {
+      a.piv[q + i] = S.piv[buf][i];
+      a.keep[q + i] = S.keep[buf][i];
+      a.rdv[q + i] = S.rd[buf][i];
+    }
+    if (i < bn) {
+      a.kd[q + kPanel + i] = S.kd[i];
+      a.s[q + kPanel + i] = S.sj[i];
+    }
+  }
+  __threadfence();
+  nb_sync(3, kSupThreads);
+  if (st == 0) {
+    recompute_release_done(a.rc, epoch);
+    st_release(&a.rc.ctrl[kCtlRows], epoch + 1);
+  }
+}
+
+// Warp 0: the decisions of panel k from the inputs in shared memory, results
+// back to shared memory (its own register allocation, apart from the rest of
+// the launch).
+__device__ __noinline__ void w0_decide(const OuterArgs& a, int k, int* seq_io) {
+  Cta0Smem& S = g_S0;
+  BlockLog& bl = g_bl;
   const int lane = threadIdx.x & 31;
-  float* A = a.A;
-  const int64_t lda = a.lda;
-  const int64_t qn = q + kPanel;
-  const int bn = (int)((pend - qn) < kPanel ? (pend - qn) : kPanel);
-  const int64_t row = qn + lane;
-  const bool valid = lane < bn;
-  float w[kPanel], l[kPanel];
+  const int64_t p = a.p;
+  const int64_t pend = p + a.NBp;
+  const int64_t q = p + (int64_t)kPanel * k;
+  const int b = (int)((pend - q) < kPanel ? (pend - q) : kPanel);
+  const int kk = (int)(q - p);
+  const unsigned epoch = a.epoch0 + (unsigned)k;
+  const int buf = k & 1;
+  int seq = *seq_io;
+  float r[kPanel];
 #pragma unroll
-  for (int c = 0; c < kPanel; ++c) w[c] = valid ? A[row + (q + c) * lda] : 0.f;
-  f2 dsum;
-  float ssum;
-  row_solve(sL2[buf], srd2[buf], w, l, dsum, ssum);
-  double kdn = 0.0, sn = 0.0;
-  if (valid) {
-    float* lk = a.Lk + row * (int64_t)a.NB + kk;
+  for (int c = 0; c < kPanel; ++c) r[c] = S.blk[lane][c];
+  f2 dd = f2_from_double(S.kd[lane]);
+  float si = (float)S.sj[lane];
+  const double u = S.u[lane];
+  const float uf = (float)u, kf = S.kf[lane];
+  const float sq = sqrtf((float)(q + lane + 1));
+  bool mykeep = false;
+  int stop = -1;
+  dec_fast<0>(b, lane, a.tau0, r, dd, si, uf, kf, sq, mykeep, stop);
+  if (stop >= 0) {
+    __shared__ DecState ds;
 #pragma unroll
-    for (int c = 0; c < kPanel; ++c) {
-      A[row + (q + c) * lda] = l[c];
-      lk[c] = l[c];
-    }
-    kdn = a.kd[row] - f2_to_double(dsum);
-    sn = a.s[row] + (double)ssum;
-    a.kd[row] = kdn;
-    a.s[row] = sn;
+    for (int c = 0; c < kPanel; ++c) S.L11[buf][lane][c] = r[c];
+    ds.dd_hi[lane] = dd.hi;
+    ds.dd_lo[lane] = dd.lo;
+    ds.si[lane] = si;
+    ds.keep[lane] = mykeep ? 1 : 0;
+    __syncwarp();
+    dec_slow(a, S.L11[buf], &ds, &bl, q, epoch, b, a.tau0, uf, kf, sq, u, seq, stop);
+#pragma unroll
+    for (int c = 0; c < kPanel; ++c) r[c] = S.L11[buf][lane][c];
+    dd = make_f2(ds.dd_hi[lane], ds.dd_lo[lane]);
+    si = ds.si[lane];
+    mykeep = ds.keep[lane] != 0;
+    __syncwarp();
   }
 #pragma unroll
-  for (int c = 0; c < kPanel; ++c) sLn[lane][c] = l[c];
+  for (int c = 0; c < kPanel; ++c) S.L11[buf][lane][c] = r[c];
+  if (lane < b) {
+    const double d = f2_to_double(dd);
+    S.piv[buf][lane] = d;
+    S.keep[buf][lane] = mykeep ? 1 : 0;
+    S.rd[buf][lane] = (float)(1.0 / d);
+    bl.dhi[kk + lane] = dd.hi;
+    bl.dlo[kk + lane] = dd.lo;
+    bl.kp[kk + lane] = mykeep ? 1 : 0;
+  } else {
+    S.rd[buf][lane] = 1.f;
+  }
   __syncwarp();
-  nb_arrive(3);
-  // rank-32 update of the lower part of the next diagonal block (left in A,
-  // then gathered into sB)
-  update_row_chunks(A + row + qn * lda, lda, w, &sLn[0][0], valid ? lane : -1);
-  __syncwarp();
-#pragma unroll
-  for (int c = 0; c < kPanel; ++c) sB[lane][c] = (valid && c <= lane) ? A[row + (qn + c) * lda] : 0.f;
-  __syncwarp();
-  *kd_out = kdn;
-  *s_out = sn;
+  *seq_io = seq;
 }
 
-// Warps 1-7, panel k (at q, full width, not the block's last): solve the rows
-// of R_{k+2}, ... against it and apply its rank-32 update to the block's lower
-// triangle below R_{k+1}.
-__device__ __noinline__ void wr_panel(const OuterArgs& a, int64_t q, int kk, int64_t pend, int buf,
-                                      int nP, int k) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int tw = tid - 32;  // 0 .. 223
-  float* A = a.A;
-  const int64_t lda = a.lda;
-  const int64_t row = q + 2 * kPanel + tw;
-  if (tw < kRestRows && row < pend) {
-    float w[kPanel], l[kPanel];
-#pragma unroll
-    for (int c = 0; c < kPanel; ++c) w[c] = A[row + (q + c) * lda];
-    f2 dsum;
-    float ssum;
-    row_solve(sL2[buf], srd2[buf], w, l, dsum, ssum);
-    float* lk = a.Lk + row * (int64_t)a.NB + kk;
-#pragma unroll
-    for (int c = 0; c < kPanel; ++c) {
-      A[row + (q + c) * lda] = l[c];
-      lk[c] = l[c];
-      sWn[tw][c] = w[c];
-      sLn[kPanel + tw][c] = l[c];
-    }
-    a.kd[row] -= f2_to_double(dsum);
-    a.s[row] += (double)ssum;
-  }
-  nb_sync(3);
-  // 32 x 32 tiles (row block rm >= 1, column block rj <= rm, both counted
-  // from R_{k+1}), dealt round-robin to the seven warps
-  const int R = nP - k - 2;
-  const int T = R * (R + 3) / 2;
-  for (int x = warp - 1; x < T; x += kThreadsOuter / 32 - 1) {
-    int rm = 1, xx = x;
-    while (xx >= rm + 1) {
-      xx -= rm + 1;
-      ++rm;
-    }
-    const int rj = xx;
-    const int64_t i = q + kPanel + (int64_t)kPanel * rm + lane;
-    const int64_t cb = q + kPanel + (int64_t)kPanel * rj;
-    const bool vi = i < pend;
-    float w[kPanel];
-#pragma unroll
-    for (int t = 0; t < kPanel; ++t) w[t] = sWn[kPanel * (rm - 1) + lane][t];
-    update_row_chunks(A + i + cb * lda, lda, w, &sLn[kPanel * rj][0], vi ? (int)(i - cb) : -1);
-  }
-}
-
-__device__ void cta0_block(const OuterArgs& a, BlockLog& bl) {
+__device__ void cta0_block(const OuterArgs& a) {
+  Cta0Smem& S = g_S0;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t p = a.p;
   const int64_t pend = p + a.NBp;
   const int nP = (a.NBp + kPanel - 1) / kPanel;
-  float* A = a.A;
-  const int64_t lda = a.lda;
 
   if (warp == 0) {
-    float r[kPanel];
-    f2 dd = {0.f, 0.f};
-    float si = 0.f;
-    {
-      const int b = (int)((pend - p) < kPanel ? (pend - p) : kPanel);
-#pragma unroll
-      for (int k = 0; k < kPanel; ++k) {
-        float v = 0.f;
-        if (lane < b && k < b)
-          v = (k <= lane) ? A[(p + lane) + (p + k) * lda] : A[(p + k) + (p + lane) * lda];
-        r[k] = v;
-      }
-      if (lane < b) {
-        dd = f2_from_double(a.kd[p + lane]);
-        si = (float)a.s[p + lane];
-      }
-    }
     int seq = 0;
+    for (int k = 0; k < nP; ++k) {
+      nb_sync(2, kThreadsOuter);  // inputs of panel k are in shared memory
+      w0_decide(a, k, &seq);
+      nb_arrive(1, kThreadsOuter);  // decisions of panel k are in shared memory
+    }
+  } else {
+    // the block's first panel: its rows as the previous launches left them
+    const int b0 = (int)((pend - p) < kPanel ? (pend - p) : kPanel);
+    sup_load_first(a, b0);
+    nb_sync(3, kSupThreads);
+    sup_prepare(0, b0, false);
+    if (tid == 32) st_release(&a.rc.ctrl[kCtlRows], a.epoch0);
+    nb_arrive(2, kThreadsOuter);
     for (int k = 0; k < nP; ++k) {
       const int64_t q = p + (int64_t)kPanel * k;
       const int b = (int)((pend - q) < kPanel ? (pend - q) : kPanel);
       const int kk = (int)(q - p);
       const unsigned epoch = a.epoch0 + (unsigned)k;
       const int buf = k & 1;
-      double u;
-      float uf, kf, sq;
-      lane_inputs(a, q, b, lane, u, uf, kf, sq);
-      bool mykeep = false;
-      dec_steps<0>(a, sL2[buf], &bl, q, epoch, b, lane, a.tau0, r, dd, si, uf, kf, sq, u, mykeep,
-                   seq);
-      // publish the panel: L11 (lower), pivots, reciprocals
-#pragma unroll
-      for (int c = 0; c < kPanel; ++c) {
-        sL2[buf][lane][c] = r[c];
-        if (lane < b && c <= lane) A[(q + lane) + (q + c) * lda] = r[c];
+      const bool next = k + 1 < nP;
+      const int64_t qn = q + kPanel;
+      const int bn = next ? (int)((pend - qn) < kPanel ? (pend - qn) : kPanel) : 0;
+      if (k >= 1) {
+        // panel k - 1 and the l rows of R_k out to global memory, released
+        const int64_t qp = q - kPanel;
+        sup_publish(a, qp, kPanel, kk - kPanel, buf ^ 1, b, epoch - 1);
       }
-      if (lane < b) {
-        const double d = f2_to_double(dd);
-        a.piv[q + lane] = d;
-        a.keep[q + lane] = mykeep ? 1 : 0;
-        const float rdl = (float)(1.0 / d);
-        srd2[buf][lane] = rdl;
-        a.rdv[q + lane] = rdl;
-        bl.dhi[kk + lane] = dd.hi;
-        bl.dlo[kk + lane] = dd.lo;
-        bl.kp[kk + lane] = mykeep ? 1 : 0;
+      if (next) {
+        // the helper's step for panel k - 1 covered the rows of R_{k+1}
+        if (k >= 1 && tid == 32) rc_wait_geq(a.rc, &a.rc.ctrl[kCtlPre], epoch - 1);
+        nb_sync(3, kSupThreads);
+        sup_ready_next(a, k, q, bn);
+      }
+      nb_sync(1, kThreadsOuter);  // decisions of panel k
+      if (next) {
+        sup_prepare(buf, bn, true);
+        nb_arrive(2, kThreadsOuter);
       } else {
-        srd2[buf][lane] = 1.f;
-      }
-      __threadfence();
-      __syncwarp();
-      if (lane == 0) recompute_release_done(a.rc, epoch);
-      nb_sync(2);
-      nb_arrive(1);
-      if (k + 1 < nP) {
-        // panel k is full width here; R_{k+1} may be the ragged last one
-        const int64_t qn = q + kPanel;
-        const int bn = (int)((pend - qn) < kPanel ? (pend - qn) : kPanel);
-        const bool valid = lane < bn;
-        double kdn, sn;
-        w0_prepare_next(a, q, kk, pend, buf, &kdn, &sn);
-#pragma unroll
-        for (int c = 0; c < kPanel; ++c)
-          r[c] = (valid && c < bn) ? ((c <= lane) ? sB[lane][c] : sB[c][lane]) : 0.f;
-        __syncwarp();
-        dd = valid ? f2_from_double(kdn) : f2{0.f, 0.f};
-        si = valid ? (float)sn : 0.f;
-        // the rows of R_{k+1} are final for every earlier panel
-        __threadfence();
-        __syncwarp();
-        if (lane == 0) st_release(&a.rc.ctrl[kCtlRows], epoch + 1);
-      }
-    }
-  } else {
-    nb_arrive(2);
-    for (int k = 0; k < nP; ++k) {
-      nb_sync(1);
-      if (k + 1 < nP) {
-        const int64_t q = p + (int64_t)kPanel * k;
-        wr_panel(a, q, (int)(q - p), pend, k & 1, nP, k);
-        __threadfence();
-        nb_arrive(2);
+        sup_publish(a, q, b, kk, buf, 0, epoch);
       }
     }
   }
 }
 
+// ---- CTA 1 (the helper): the block's rows from R_{k+2} on ----------------------
+__device__ __noinline__ void helper_block(const OuterArgs& a) {
+  int* s_ok = &g_s_ok;
+  const int tid = threadIdx.x;
+  const int64_t p = a.p;
+  const int64_t pend = p + a.NBp;
+  const float* A = a.A;
+  const int64_t lda = a.lda;
+  for (int64_t q = p; q < pend; q += kPanel) {
+    const int b = (int)((pend - q) < kPanel ? (pend - q) : kPanel);
+    const int kk = (int)(q - p);
+    const unsigned epoch = a.epoch0 + (unsigned)((q - p) / kPanel);
+    const int64_t r2 = q + 2 * kPanel < pend ? q + 2 * kPanel : pend;
+    if (kk > 0 && r2 < pend) {
+      // panel k - 1 is out (with kCtlDone of k - 1 and the L rows of R_k)
+      if (tid == 0) *s_ok = rc_wait_geq(a.rc, &a.rc.ctrl[kCtlRows], epoch) ? 1 : 0;
+      __syncthreads();
+      if (!*s_ok) return;
+      const int64_t qp = q - kPanel;
+      for (int idx = tid; idx < kPanel * kPanel; idx += kThreadsOuter) {
+        const int i = idx % kPanel, k = idx / kPanel;
+        g_sL[i][k] = (k < i) ? __ldcg(&A[(qp + i) + (qp + k) * lda]) : 0.f;
+      }
+      if (tid < kPanel) g_srd[tid] = __ldcg(&a.rdv[qp + tid]);
+      __syncthreads();
+      panel_solve(a, qp, kPanel, r2, pend, tid);
+      __syncthreads();
+      stage_lk(a, q, b, kk, tid);
+      __syncthreads();
+      inner_update(a, q, b, kk, r2, pend, tid);
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) st_release(&a.rc.ctrl[kCtlPre], epoch);
+    if (!recompute_follower(a.rc, epoch, s_ok)) return;
+  }
+}
+
 __global__ void __launch_bounds__(kThreadsOuter, 1) k_outer_mixed(OuterArgs a) {
-  extern __shared__ __align__(16) float sLk[];  // [kMaxOuterBlock][kPanel]
-  __shared__ BlockLog bl;
-  __shared__ int s_ok;
-  __shared__ float sW[2 * 32 * kSwLd];
-  __shared__ float stage[kThreadsOuter / 32][kPanel][kPanel + 1];
-  float (*sL)[kPanel + 1] = sL2[0];
-  float* srd = srd2[0];
+  BlockLog& bl = g_bl;
+  int& s_ok = g_s_ok;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t p = a.p, n = a.n;
   const int64_t pend = p + a.NBp;
@@ -681,7 +1009,7 @@ __global__ void __launch_bounds__(kThreadsOuter, 1) k_outer_mixed(OuterArgs a) {
       bl.rc_failed = 0;
     }
     __syncthreads();
-    cta0_block(a, bl);
+    cta0_block(a);
     __syncthreads();
     // likelihood and bookkeeping of the block (FP64, one pivot per thread)
     double lp = 0.0;
@@ -736,8 +1064,13 @@ __global__ void __launch_bounds__(kThreadsOuter, 1) k_outer_mixed(OuterArgs a) {
     return;
   }
 
+  if (blockIdx.x == 1) {
+    helper_block(a);
+    return;
+  }
+
   // ---- workers: rows below the outer block ----
-  const int64_t w = blockIdx.x - 1;
+  const int64_t w = blockIdx.x - 2;
   int64_t r_lo = a.wrow0 + w * a.wrows;
   int64_t r_hi = r_lo + a.wrows;
   if (r_lo > n) r_lo = n;
@@ -750,19 +1083,19 @@ __global__ void __launch_bounds__(kThreadsOuter, 1) k_outer_mixed(OuterArgs a) {
       if (tid == 0) s_ok = rc_wait_geq(a.rc, &a.rc.ctrl[kCtlRows], epoch) ? 1 : 0;
       __syncthreads();
       if (!s_ok) return;
-      stage_lk(a, sLk, q, b, kk, tid);
+      stage_lk(a, q, b, kk, tid);
       __syncthreads();
-      inner_update(a, sLk, sW, q, b, kk, r_lo, r_hi, tid);
+      inner_update(a, q, b, kk, r_lo, r_hi, tid);
     }
     if (!recompute_follower(a.rc, epoch, &s_ok)) return;
     if (r_lo < r_hi) {
       for (int idx = tid; idx < kPanel * kPanel; idx += kThreadsOuter) {
         const int i = idx % kPanel, k = idx / kPanel;
-        sL[i][k] = (i < b && k < i) ? __ldcg(&A[(q + i) + (q + k) * lda]) : 0.f;
+        g_sL[i][k] = (i < b && k < i) ? __ldcg(&A[(q + i) + (q + k) * lda]) : 0.f;
       }
-      if (tid < kPanel) srd[tid] = tid < b ? __ldcg(&a.rdv[q + tid]) : 1.f;
+      if (tid < kPanel) g_srd[tid] = tid < b ? __ldcg(&a.rdv[q + tid]) : 1.f;
       __syncthreads();
-      panel_solve(a, sL, srd, stage, q, b, r_lo, r_hi, tid);
+      panel_solve(a, q, b, r_lo, r_hi, tid);
       __syncthreads();
     }
   }
@@ -928,7 +1261,7 @@ cudaError_t sample_mixed(const DrawArgs& a, Workspace ws) {
     if (ea != cudaSuccess) return ea;
     cap = per_sm * di.sm_count;
     if (cap > kMaxCoopCtas) cap = kMaxCoopCtas;
-    if (cap < 2) return cudaErrorLaunchOutOfResources;
+    if (cap < 3) return cudaErrorLaunchOutOfResources;
   }
   unsigned epoch = 1;
   const bool use_tc = g_tuning.update_kernel == 0;
@@ -968,10 +1301,10 @@ cudaError_t sample_mixed(const DrawArgs& a, Workspace ws) {
       // every other SM is a worker: they stream the rows below the block and
       // serve the recomputes (which are bandwidth- and latency-bound)
       const int64_t mw = n - p - NBp;
-      int64_t nw = cap - 1;
-      if (nw < 1) nw = 1;
+      int64_t nw = cap - 1;  // CTA 0 decides, CTA 1 helps, the rest stream
       oa.wrow0 = p + NBp;
-      oa.wrows = (mw + nw - 1) / nw;
+      const int64_t ntall = nw > 1 ? nw - 1 : 1;  // CTA 1 is the helper
+      oa.wrows = (mw + ntall - 1) / ntall;
       if (oa.wrows < 1) oa.wrows = 1;
       oa.rc = recompute_args(L.rs, K, a.ld, L.A32, L.ld32, L.piv, a.keep, n, p, a.result);
       oa.rc.grid = (int)(nw + 1);
