@@ -136,6 +136,12 @@ __device__ inline f2 f2_sub_prod(f2 a, float w, float l) {
   return fast_two_sum(s.hi, __fadd_rn(s.lo, __fsub_rn(a.lo, pe)));
 }
 
+// a + b (both double-float)
+__device__ inline f2 f2_add(f2 a, f2 b) {
+  const f2 s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
 // a + w * l
 __device__ inline f2 f2_add_prod(f2 a, float w, float l) {
   const float p = __fmul_rn(w, l);

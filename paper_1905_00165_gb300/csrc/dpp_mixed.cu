@@ -564,9 +564,10 @@ __shared__ BlockLog g_bl;
 // Column-oriented forward substitution of the rows r = sw, sw + 7, ... of X
 // against the factored block of buffer buf (lane = column): w = x L11^{-T},
 // l = w / d. Writes S.W, S.Lr and subtracts sum w l from kd (FP64).
-__device__ __forceinline__ void sup_solve_rows(int buf, int bn, double* kd,
-                                               double* sj) {
+__device__ __noinline__ void sup_solve_rows(int buf, int bn, bool prefetched) {
   Cta0Smem& S = g_S0;
+  double* kd = prefetched ? S.kdP : S.kd;
+  double* sj = prefetched ? S.sP : S.sj;
   const int st = threadIdx.x - 32, lane = threadIdx.x & 31, sw = st >> 5;
   constexpr unsigned kF = 0xffffffffu;
   float w[5];
@@ -575,7 +576,8 @@ __device__ __forceinline__ void sup_solve_rows(int buf, int bn, double* kd,
     const int r = sw + 7 * m;
     w[m] = (r < kPanel) ? S.X[r][lane] : 0.f;
   }
-#pragma unroll
+  // a compact loop: this runs once per panel, cold in the instruction cache
+#pragma unroll 4
   for (int t = 0; t < kPanel; ++t) {
     const float lt = S.L11[buf][lane][t];
 #pragma unroll
@@ -593,16 +595,20 @@ __device__ __forceinline__ void sup_solve_rows(int buf, int bn, double* kd,
       const float lv = wv * S.rd[buf][lane];
       S.W[r][lane] = wv;
       S.Lr[r][lane] = lv;
-      double ds = (double)wv * (double)lv;
-      double ss = (double)fabsf(wv * lv);
+      // sum w l in double-float, sum |w l| in FP32 (FP64 arithmetic is the
+      // GPU's slowest pipe; one FP64 subtraction per row remains)
+      f2 ds = {__fmul_rn(wv, lv), 0.f};
+      ds.lo = __fmaf_rn(wv, lv, -ds.hi);
+      float ss = fabsf(wv * lv);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        ds += __shfl_xor_sync(kF, ds, o);
+        const f2 other = {__shfl_xor_sync(kF, ds.hi, o), __shfl_xor_sync(kF, ds.lo, o)};
+        ds = f2_add(ds, other);
         ss += __shfl_xor_sync(kF, ss, o);
       }
       if (lane == 0 && vr) {
-        kd[r] -= ds;
-        sj[r] += ss;
+        kd[r] -= f2_to_double(ds);
+        sj[r] += (double)ss;
       }
     }
   }
@@ -643,7 +649,7 @@ __device__ __noinline__ void sup_ready_next(const OuterArgs& a, int k, int64_t q
         },
         [&](int e, float v) { S.X[e % kPanel][e / kPanel] = v; });
     nb_sync(3, kSupThreads);
-    sup_solve_rows(bp, bn, S.kdP, S.sP);
+    sup_solve_rows(bp, bn, true);
     nb_sync(3, kSupThreads);
     for (int e = st; e < kPanel * kPanel; e += kSupThreads) {
       const int i = e / kPanel, c = e % kPanel;  // consecutive threads: one row
@@ -702,7 +708,7 @@ __device__ __noinline__ void sup_ready_next(const OuterArgs& a, int k, int64_t q
     for (int j = 0; j < kPer; ++j) {
       if (st + j * kSupThreads < kOut) {
         float s = 0.f;
-#pragma unroll
+#pragma unroll 8
         for (int t = 0; t < kPanel; ++t) s = fmaf(S.Wc[oi[j]][t], S.Lc[oc[j]][t], s);
         acc[j] += s;
       }
@@ -771,7 +777,7 @@ __device__ __noinline__ void sup_prepare(int buf, int bn, bool after_panel) {
       S.sj[st] = S.sP[st];
     }
     nb_sync(3, kSupThreads);
-    sup_solve_rows(buf, bn, S.kd, S.sj);
+    sup_solve_rows(buf, bn, false);
     nb_sync(3, kSupThreads);
     // rank-32 update of the lower triangle of the diagonal block
     for (int o = st; o < kPanel * (kPanel + 1) / 2; o += kSupThreads) {
@@ -780,7 +786,7 @@ __device__ __noinline__ void sup_prepare(int buf, int bn, bool after_panel) {
       while ((i + 1) * (i + 2) / 2 <= o) ++i;
       const int c = o - i * (i + 1) / 2;
       float acc = 0.f;
-#pragma unroll
+#pragma unroll 8
       for (int t = 0; t < kPanel; ++t) acc = fmaf(S.W[i][t], S.Lr[c][t], acc);
       const float y = (i < bn) ? S.Y[i][c] - acc : 0.f;
       S.blk[i][c] = y;
@@ -891,7 +897,7 @@ __device__ __noinline__ void w0_decide(const OuterArgs& a, int k, int* seq_io) {
     const double d = f2_to_double(dd);
     S.piv[buf][lane] = d;
     S.keep[buf][lane] = mykeep ? 1 : 0;
-    S.rd[buf][lane] = (float)(1.0 / d);
+    S.rd[buf][lane] = 1.0f / __double2float_rn(d);
     bl.dhi[kk + lane] = dd.hi;
     bl.dlo[kk + lane] = dd.lo;
     bl.kp[kk + lane] = mykeep ? 1 : 0;
