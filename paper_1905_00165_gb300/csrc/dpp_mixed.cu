@@ -553,9 +553,9 @@ struct Cta0Smem {
   // solve of R_{k+1} against panel k
   float W[kPanel][kPanel + 1];
   float Lr[kPanel][kPanel + 1];
-  // 32-wide chunks of the stored W and L (left-looking update)
+  // 32-wide chunks of the stored W and L (left-looking update), L transposed
   float Wc[kPanel][kPanel + 1];
-  float Lc[2 * kPanel][kPanel + 1];
+  __align__(16) float LcT[kPanel][2 * kPanel + 4];
 };
 
 __shared__ Cta0Smem g_S0;
@@ -664,30 +664,14 @@ __device__ __noinline__ void sup_ready_next(const OuterArgs& a, int k, int64_t q
     }
     nb_sync(3, kSupThreads);
   }
-  // left-looking update through panel k - 1: outputs o < 1024 are X (i, c),
-  // the others the lower triangle of Y; at most 7 per thread
-  constexpr int kOut = kPanel * kPanel + kPanel * (kPanel + 1) / 2;
-  constexpr int kPer = (kOut + kSupThreads - 1) / kSupThreads;
-  float acc[kPer];
-  int oi[kPer], oc[kPer];
+  // left-looking update through panel k - 1 of the 32 x 64 block [X | Y]
+  // (Y's upper part is computed and never read): support threads st < 128
+  // own row i = st / 4 and 16 consecutive columns, register-blocked.
+  const int gi = st >> 2, gc = (st & 3) * 16;
+  const bool gemm = st < 4 * kPanel;
+  float acc[16];
 #pragma unroll
-  for (int j = 0; j < kPer; ++j) {
-    acc[j] = 0.f;
-    const int o = st + j * kSupThreads;
-    int i = 0, c = 0;
-    if (o < kPanel * kPanel) {
-      i = o % kPanel;
-      c = o / kPanel;
-    } else if (o < kOut) {
-      const int y = o - kPanel * kPanel;
-      i = (int)((sqrtf(8.f * (float)y + 1.f) - 1.f) * 0.5f);
-      while (i * (i + 1) / 2 > y) --i;
-      while ((i + 1) * (i + 2) / 2 <= y) ++i;
-      c = kPanel + (y - i * (i + 1) / 2);  // column index into Lc rows 32..63
-    }
-    oi[j] = i;
-    oc[j] = c;
-  }
+  for (int j = 0; j < 16; ++j) acc[j] = 0.f;
   for (int t0 = 0; t0 < kk; t0 += kPanel) {
     staged_copy<3 * kPanel * kPanel, kSupThreads>(
         st,
@@ -701,37 +685,41 @@ __device__ __noinline__ void sup_ready_next(const OuterArgs& a, int k, int64_t q
         [&](int e, float v) {
           const int r = e / kPanel, t = e % kPanel;
           if (r < kPanel) S.Wc[r][t] = v;
-          else S.Lc[r - kPanel][t] = v;
+          else S.LcT[t][r - kPanel] = v;
         });
     nb_sync(3, kSupThreads);
+    if (gemm) {
+#pragma unroll 4
+      for (int t = 0; t < kPanel; ++t) {
+        const float w = S.Wc[gi][t];
+        const float4* lp = reinterpret_cast<const float4*>(&S.LcT[t][gc]);
 #pragma unroll
-    for (int j = 0; j < kPer; ++j) {
-      if (st + j * kSupThreads < kOut) {
-        float s = 0.f;
-#pragma unroll 8
-        for (int t = 0; t < kPanel; ++t) s = fmaf(S.Wc[oi[j]][t], S.Lc[oc[j]][t], s);
-        acc[j] += s;
+        for (int v4 = 0; v4 < 4; ++v4) {
+          const float4 l = lp[v4];
+          acc[4 * v4 + 0] = fmaf(w, l.x, acc[4 * v4 + 0]);
+          acc[4 * v4 + 1] = fmaf(w, l.y, acc[4 * v4 + 1]);
+          acc[4 * v4 + 2] = fmaf(w, l.z, acc[4 * v4 + 2]);
+          acc[4 * v4 + 3] = fmaf(w, l.w, acc[4 * v4 + 3]);
+        }
       }
     }
     nb_sync(3, kSupThreads);
   }
-  float av[kPer];
+  if (gemm) {
+    float av[16];
 #pragma unroll
-  for (int j = 0; j < kPer; ++j) {
-    const int o = st + j * kSupThreads;
-    const int i = oi[j], c = oc[j];
-    av[j] = 0.f;
-    if (o < kOut && i < bn)
-      av[j] = __ldcg(&A[(qn + i) + ((o < kPanel * kPanel) ? (q + c) : (qn + c - kPanel)) * lda]);
-  }
+    for (int j = 0; j < 16; ++j) {
+      const int c = gc + j;
+      const bool need = gi < bn && (c < kPanel || c - kPanel <= gi);
+      av[j] = need ? __ldcg(&A[(qn + gi) + ((c < kPanel) ? (q + c) : (qn + c - kPanel)) * lda])
+                   : 0.f;
+    }
 #pragma unroll
-  for (int j = 0; j < kPer; ++j) {
-    const int o = st + j * kSupThreads;
-    if (o < kOut) {
-      const int i = oi[j], c = oc[j];
-      const float v = i < bn ? av[j] - acc[j] : 0.f;
-      if (o < kPanel * kPanel) S.X[i][c] = v;
-      else S.Y[i][c - kPanel] = v;
+    for (int j = 0; j < 16; ++j) {
+      const int c = gc + j;
+      const float v = gi < bn ? av[j] - acc[j] : 0.f;
+      if (c < kPanel) S.X[gi][c] = v;
+      else S.Y[gi][c - kPanel] = (c - kPanel <= gi) ? v : 0.f;
     }
   }
   // upper part of Y is never read

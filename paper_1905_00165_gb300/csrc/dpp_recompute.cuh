@@ -147,16 +147,19 @@ __device__ inline bool rc_give_up(const RecomputeArgs& a, unsigned long long t0)
   return false;
 }
 
-// Single-thread bounded wait for *flag >= target (abort-aware).
+// Single-thread bounded wait for *flag >= target (abort-aware). The control
+// words are polled by every CTA of the launch, so the poll backs off to about
+// a microsecond and the abort flag is read only every eighth time, to keep
+// the L2 line that holds them from becoming a hot spot.
 __device__ inline bool rc_wait_geq(const RecomputeArgs& a, const unsigned* flag, unsigned target) {
   if (ld_acquire(flag) >= target) return true;
   const unsigned long long t0 = global_ns();
-  unsigned sleep = 32;
-  while (true) {
+  unsigned sleep = 64;
+  for (unsigned it = 1;; ++it) {
     if (ld_acquire(flag) >= target) return true;
-    if (rc_give_up(a, t0)) return false;
+    if ((it & 7) == 0 && rc_give_up(a, t0)) return false;
     __nanosleep(sleep);
-    if (sleep < 256) sleep <<= 1;
+    if (sleep < 1024) sleep <<= 1;
   }
 }
 
@@ -549,14 +552,14 @@ __device__ inline bool recompute_follower(const RecomputeArgs& a, unsigned epoch
     if (threadIdx.x == 0) {
       unsigned cmd = 0, id = 0;
       const unsigned long long t0 = global_ns();
-      unsigned sleep = 32;
-      while (true) {
+      unsigned sleep = 64;
+      for (unsigned it = 1;; ++it) {
         if (ld_acquire(&a.ctrl[kCtlDone]) >= epoch) { cmd = 2; break; }
         const unsigned req = ld_acquire(&a.ctrl[kCtlReq]);
         if (req >= ((epoch << 8) | (served + 1u))) { cmd = 1; id = req; break; }
-        if (rc_give_up(a, t0)) { cmd = 0; break; }
+        if ((it & 7) == 0 && rc_give_up(a, t0)) { cmd = 0; break; }
         __nanosleep(sleep);
-        if (sleep < 256) sleep <<= 1;
+        if (sleep < 1024) sleep <<= 1;
       }
       __threadfence();
       s_cmd = cmd;
