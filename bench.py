@@ -51,6 +51,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-fp64-ref", action="store_true")
+    p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--batch", type=int, default=4096,
+                   help="L-ensembles in the batched measurement (n ~ U{64..1024})")
     return p.parse_args()
 
 
@@ -118,6 +121,43 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
                 "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def bench_batched(dpp, _lib, dev, batch: int, draws: int, seed: int = 0):
+    """Batched L-ensembles: `batch` kernels K_i = L_i (L_i + I)^{-1} of orders
+    n_i ~ U{64..1024}, one persistent launch draws every instance once (FP32
+    factor, FP64 pivots and recompute). samples/s = instances drawn per second."""
+    import torch
+    import workloads as W
+    Ks = W.lensemble_batch_torch(batch, seed=seed, device=str(dev))
+    sizes = [int(K.shape[0]) for K in Ks]
+    b = dpp.BatchedSampler(Ks)
+    stream = torch.cuda.current_stream(dev)
+    for w in range(2):
+        b.draw(10**6 + w)
+    torch.cuda.synchronize()
+    _lib.profile_start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for d in range(draws):
+        b.draw(d)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = _lib.profile_stop()
+    ms = e0.elapsed_time(e1) / draws
+    res = b.results()
+    flops = sum(m ** 3 / 3.0 for m in sizes)
+    bad = sum(1 for r in res if r["status"] & (_lib.DPP_RES_TIMEOUT | _lib.DPP_RES_NONFINITE))
+    return {"metric": f"batched L-ensemble samples/s ({batch} kernels, n~U{{64..1024}})",
+            "value": batch / (ms / 1e3), "unit": "samples/s", "ms_per_draw": ms,
+            "draws": draws, "tflops_algorithmic": flops / (ms / 1e3) / 1e12,
+            "n_total": sum(sizes), "launches_per_draw":
+                sum(v["launches"] for v in prof.values()) / draws,
+            "borderline_last_draw": sum(r["n_borderline"] for r in res),
+            "failed_instances": bad,
+            "config": {"workload": "lensemble_batch", "batch": batch, "nmin": 64, "nmax": 1024,
+                       "features": 64, "quality": "LogUniform(0.1, 10)", "precision": "fp32"}}
 
 
 def dist_env():
@@ -362,6 +402,12 @@ def main():
                "steps": e2e_steps}
         del Kh, Kin
 
+    batched = None
+    if rank == 0 and not args.no_batched:
+        del wsb
+        torch.cuda.empty_cache()
+        batched = bench_batched(dpp, _lib, dev, args.batch, draws=5)
+
     cpu = None
     if rank == 0 and ws_n == 1 and not args.no_cpu:
         cpu = cpu_oracle_baseline(Kd[: args.cpu_sample_n, : args.cpu_sample_n].cpu().numpy(), n,
@@ -388,6 +434,7 @@ def main():
             "fp64_gpu_path": fp64_ref,
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "batched": batched,
             "gpu_launches": launches,
             "clocks": clk,
             "last_draw": {"status": res["status"], "n_kept": res["n_kept"],
