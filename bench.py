@@ -52,6 +52,10 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-fp64-ref", action="store_true")
     p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--suite", action="store_true",
+                   help="one JSON line per workload of the paper-shaped configurations "
+                        "(FP64 n=512; n=4096 real/complex, projection/Beta; spanning trees of "
+                        "the 64x64 grid; LU n=8192; batched L-ensembles)")
     p.add_argument("--batch", type=int, default=4096,
                    help="L-ensembles in the batched measurement (n ~ U{64..1024})")
     return p.parse_args()
@@ -160,6 +164,135 @@ def bench_batched(dpp, _lib, dev, batch: int, draws: int, seed: int = 0):
                        "features": 64, "quality": "LogUniform(0.1, 10)", "precision": "fp32"}}
 
 
+def run_suite(args):
+    """Every paper-shaped workload on one GPU: samples/s, algorithmic TFLOP/s and
+    the fraction of the peak of the pipe the dominant kernel runs on."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1905_00165_gb300 as dpp
+    from paper_1905_00165_gb300 import _lib
+    import workloads as W
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    peaks = measured_peaks()
+    bf16 = peaks.get("bf16_tflops", 1888.3)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, draws, warm=2):
+        for w in range(warm):
+            fn(10**6 + w)
+        torch.cuda.synchronize()
+        _lib.profile_start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for d in range(draws):
+            fn(d)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prof = _lib.profile_stop()
+        return e0.elapsed_time(e1) / draws, prof
+
+    def line(name, cfg, prec, ms, flops, prof, extra=None):
+        tf = flops / (ms / 1e3) / 1e12
+        if prec == "fp64":
+            peak, pipe = FP64_NOMINAL_TFLOPS, "fp64 nominal"
+        else:
+            peak, pipe = bf16 / 6.0, "bf16 measured / 6 products"
+        upd = prof.get("update_tc") or prof.get("update_fp64")
+        d = {"suite": name, "config": cfg, "precision": prec, "samples_per_s": 1e3 / ms,
+             "ms_per_draw": ms, "tflops_algorithmic": tf,
+             "frac_of_peak": tf / peak, "peak": peak, "peak_source": pipe,
+             "update_share": (upd["total_ms"] / max(1e-9, sum(v["total_ms"] for v in prof.values()))
+                              if upd else None)}
+        if extra:
+            d.update(extra)
+        print(json.dumps(d), flush=True)
+
+    def hermitian(Kd, n, prec_name, dt=0):
+        prec = dpp.PRECISIONS[prec_name]
+        need = dpp.workspace_size(0, n, dt, prec, 1)
+        ws = torch.empty(need, dtype=torch.uint8, device=dev)
+        keep = torch.empty(n, dtype=torch.uint8, device=dev)
+        raw = torch.zeros(_lib.RESULT_BYTES, dtype=torch.uint8, device=dev)
+        L = dpp.load()
+
+        def fn(seed):
+            _lib.check(L.dpp_sample_hermitian(Kd.data_ptr(), n, n, dt, prec, seed, 0, None,
+                                              keep.data_ptr(), None, None, raw.data_ptr(),
+                                              ws.data_ptr(), need, stream.cuda_stream))
+        return fn, keep, raw
+
+    # C1: FP64, n = 512, 256 draws with seeds 0..255
+    n = 512
+    Kd = torch.from_numpy(W.hermitian_kernel(n, seed=0, kind="uniform")).to(dev).contiguous()
+    fn, keep, raw = hermitian(Kd, n, "fp64")
+    ms, prof = timed(fn, 256)
+    line("C1", {"n": n, "kernel": "Haar, lam~U(0,1)", "draws": 256}, "fp64", ms, n ** 3 / 3, prof)
+    b = dpp.BatchedSampler([Kd] * 256, instance=list(range(256)))
+    ms_b, prof_b = timed(lambda s: b.draw(s), 5)
+    print(json.dumps({"suite": "C1-batched", "config": {"n": n, "instances": 256},
+                      "precision": "fp32+f64 pivots", "samples_per_s": 256e3 / ms_b,
+                      "ms_per_launch": ms_b}), flush=True)
+    del b, Kd
+
+    # C2: n = 4096, real projection / Beta, FP64 and mixed; complex Beta FP64
+    n = 4096
+    for kind in ("projection", "beta"):
+        Kd = W.hermitian_kernel(n, seed=0, kind=kind, device=str(dev), return_torch=True).contiguous()
+        for prec_name, draws in (("fp64", 4), ("bf16x6", 16)):
+            fn, keep, raw = hermitian(Kd, n, prec_name)
+            ms, prof = timed(fn, draws)
+            res = _lib.decode_result(bytes(raw.cpu().numpy().tobytes()))
+            line("C2", {"n": n, "kind": kind, "dtype": "f64"}, prec_name, ms, n ** 3 / 3, prof,
+                 {"last_draw_kept": res["n_kept"], "last_draw_borderline": res["n_borderline"]})
+        del Kd
+    Kc = W.hermitian_kernel(n, seed=0, kind="beta", complex_=True, device=str(dev),
+                            return_torch=True).contiguous()
+    fn, keep, raw = hermitian(Kc, n, "fp64", dt=1)
+    ms, prof = timed(fn, 2, warm=1)
+    line("C2", {"n": n, "kind": "beta", "dtype": "c128"}, "fp64", ms, 4 * n ** 3 / 3, prof)
+    del Kc
+
+    # C3: uniform spanning trees of the 64 x 64 grid (n = 8064, rank 4095)
+    d = 64
+    from oracle import oracle as O
+    K, edges, V = W.ust_grid_kernel(d, device=str(dev))
+    n = K.shape[0]
+    Kd = torch.from_numpy(K).to(dev).contiguous()
+    ref = -W.grid_spanning_tree_log_count(d)
+    for prec_name, draws in (("bf16x6", 64), ("fp64", 2)):
+        fn, keep, raw = hermitian(Kd, n, prec_name)
+        ms, prof = timed(fn, draws, warm=1)
+        k = keep.cpu().numpy().astype(bool)
+        res = _lib.decode_result(bytes(raw.cpu().numpy().tobytes()))
+        line("C3", {"grid": d, "n": n, "rank": V - 1}, prec_name, ms, n ** 3 / 3, prof,
+             {"last_draw_spanning_tree": bool(O.is_spanning_tree(edges[k], V)),
+              "last_draw_logp": res["logp"], "logp_expected": ref})
+    del Kd
+
+    # C4: real LU n = 8192, K = D^{-1} S D (FP64; the mixed path is Hermitian only)
+    n = 8192
+    K, S = W.lu_similarity_kernel(n, seed=0, device=str(dev))
+    Kd = torch.from_numpy(np.ascontiguousarray(K.T)).to(dev)  # column-major storage
+    need = dpp.workspace_size(1, n, 0, 0, 0)
+    ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    keep = torch.empty(n, dtype=torch.uint8, device=dev)
+    raw = torch.zeros(_lib.RESULT_BYTES, dtype=torch.uint8, device=dev)
+    L = dpp.load()
+
+    def lu(seed):
+        _lib.check(L.dpp_sample_lu(Kd.data_ptr(), n, n, 0, 0, seed, 0, None, keep.data_ptr(),
+                                   None, None, raw.data_ptr(), ws.data_ptr(), need,
+                                   stream.cuda_stream))
+    ms, prof = timed(lu, 2, warm=1)
+    line("C4", {"n": n, "kind": "D^-1 S D, lam~U(0,1), D lognormal(0,0.5)"}, "fp64", ms,
+         2 * n ** 3 / 3, prof)
+    return 0
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -229,6 +362,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.suite:
+        return run_suite(args)
     import numpy as np
     import torch
 
