@@ -153,6 +153,16 @@ def bench_batched(dpp, _lib, dev, batch: int, draws: int, seed: int = 0):
     res = b.results()
     flops = sum(m ** 3 / 3.0 for m in sizes)
     bad = sum(1 for r in res if r["status"] & (_lib.DPP_RES_TIMEOUT | _lib.DPP_RES_NONFINITE))
+    # adjoint dK_i = (K_i - 1_{Y_i^c})^{-T} of every instance's last draw (FP64)
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    n_adj = min(512, batch)
+    a0.record(stream)
+    dKs = b.logprob_backward(count=n_adj)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    ms_adj = a0.elapsed_time(a1)
+    del dKs
     return {"metric": f"batched L-ensemble samples/s ({batch} kernels, n~U{{64..1024}})",
             "value": batch / (ms / 1e3), "unit": "samples/s", "ms_per_draw": ms,
             "draws": draws, "tflops_algorithmic": flops / (ms / 1e3) / 1e12,
@@ -160,6 +170,10 @@ def bench_batched(dpp, _lib, dev, batch: int, draws: int, seed: int = 0):
                 sum(v["launches"] for v in prof.values()) / draws,
             "borderline_last_draw": sum(r["n_borderline"] for r in res),
             "failed_instances": bad,
+            "adjoint": {"instances_per_s": n_adj / (ms_adj / 1e3), "ms": ms_adj,
+                        "instances": n_adj, "precision": "fp64",
+                        "note": "dK_i = (K_i - 1_{Y_i^c})^{-T}: forced-decision FP64 "
+                                "refactorization and triangular inverses, one library call"},
             "config": {"workload": "lensemble_batch", "batch": batch, "nmin": 64, "nmax": 1024,
                        "features": 64, "quality": "LogUniform(0.1, 10)", "precision": "fp32"}}
 

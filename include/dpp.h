@@ -244,6 +244,30 @@ dpp_status dpp_logprob_backward(const void* K, int64_t n, int64_t ld,
                                 int64_t ld_dk, void* workspace,
                                 size_t workspace_bytes, void* stream);
 
+/* Adjoint of log P(Y_i) for each instance of a batch of real symmetric
+ * kernels (for instance the draws of dpp_sample_batched), Y_i fixed:
+ * dK_i = g_i (K_i - 1_{Y_i^c})^{-T}, in FP64, exactly as dpp_logprob_backward
+ * with hermitian = 1. The instances are enqueued one after another on
+ * `stream` and share the workspace (stream order makes that safe).
+ *   batch      number of instances (>= 0).
+ *   n, ld, ld_dk  HOST arrays of batch entries: order, leading dimension of
+ *              K_i (>= max(1, n_i)) and of dK_i.
+ *   K, keep, grad_logp, dK  HOST arrays of batch DEVICE pointers: K_i
+ *              (column-major, lower triangle read), keep_i (n_i bytes),
+ *              g_i (one double), dK_i (n_i x ld_dk_i doubles, written).
+ *   workspace  device, >= dpp_workspace_size(DPP_OP_LOGPROB_BACKWARD, n_max,
+ *              DPP_R64, DPP_PREC_FP64, 1) with n_max = max_i n_i.
+ * Errors: DPP_ERR_INVALID_ARG / DPP_ERR_WORKSPACE found on the host before
+ * anything is enqueued; DPP_ERR_CUDA if a launch fails (earlier instances
+ * may then already be enqueued). */
+dpp_status dpp_logprob_backward_batched(int32_t batch, const int64_t* n,
+                                        const void* const* K, const int64_t* ld,
+                                        const uint8_t* const* keep,
+                                        const double* const* grad_logp,
+                                        void* const* dK, const int64_t* ld_dk,
+                                        void* workspace, size_t workspace_bytes,
+                                        void* stream);
+
 /* Process-wide tuning knobs (read at each call; not for concurrent changes).
  *   DPP_TUNE_TAU_SAFETY   c in the mixed-precision borderline bound
  *                         tau_j = c * 2^-22 * sqrt(j + 1) * (K_jj + s_j),

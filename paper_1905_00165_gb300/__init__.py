@@ -205,6 +205,39 @@ class BatchedSampler:
             self.ws.data_ptr(), self.ws.numel(), _stream(self.device))
         _lib.check(st)
 
+    def logprob_backward(self, grad_logp=None, count=None):
+        """dK_i = g_i (K_i - 1_{Y_i^c})^{-T} for the first ``count`` instances
+        (default: all) and their last draw (FP64, one library call that
+        enqueues every instance)."""
+        import ctypes
+        import numpy as np
+        torch = _torch()
+        dev = self.device
+        B = self.batch if count is None else min(int(count), self.batch)
+        ns = [int(K.shape[0]) for K in self.Ks[:B]]
+        if grad_logp is None:
+            g = torch.ones(max(B, 1), dtype=torch.float64, device=dev)
+        else:
+            g = torch.as_tensor(grad_logp, dtype=torch.float64, device=dev).reshape(B).contiguous()
+        dKs = [empty_colmajor(m, torch.float64, dev) for m in ns]
+        n_h = np.asarray(ns, dtype=np.int64)
+        ld_h = np.asarray([K.stride(1) if m else 1 for K, m in zip(self.Ks[:B], ns)], dtype=np.int64)
+        ldd_h = np.asarray([d.stride(1) if m else 1 for d, m in zip(dKs, ns)], dtype=np.int64)
+        P = ctypes.c_void_p * max(B, 1)
+        kp = P(*[K.data_ptr() for K in self.Ks[:B]])
+        kk = P(*[k.data_ptr() for k in self.keep[:B]])
+        gp = P(*[g.data_ptr() + 8 * i for i in range(B)])
+        dp = P(*[d.data_ptr() for d in dKs])
+        need = workspace_size(DPP_OP_LOGPROB_BACKWARD, max(ns) if ns else 0, DPP_R64, DPP_PREC_FP64, 1)
+        ws = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+        st = self.L.dpp_logprob_backward_batched(
+            B, n_h.ctypes.data, ctypes.cast(kp, ctypes.c_void_p), ld_h.ctypes.data,
+            ctypes.cast(kk, ctypes.c_void_p), ctypes.cast(gp, ctypes.c_void_p),
+            ctypes.cast(dp, ctypes.c_void_p), ldd_h.ctypes.data, ws.data_ptr(), ws.numel(),
+            _stream(dev))
+        _lib.check(st)
+        return dKs
+
     def results(self):
         raw = self.raw.cpu().numpy().tobytes()
         return [decode_result(raw[i * _lib.RESULT_BYTES:(i + 1) * _lib.RESULT_BYTES])

@@ -70,6 +70,8 @@ def load(path: Optional[str] = None):
     L.dpp_sample_batched.restype = i32
     L.dpp_logprob_backward.argtypes = [vp, i64, i64, i32, i32, i32, vp, vp, vp, i64, vp, sz, vp]
     L.dpp_logprob_backward.restype = i32
+    L.dpp_logprob_backward_batched.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+    L.dpp_logprob_backward_batched.restype = i32
     L.dpp_uniforms.argtypes = [u64, u64, i64, vp, vp]
     L.dpp_uniforms.restype = i32
     L.dpp_profile_start.argtypes = []

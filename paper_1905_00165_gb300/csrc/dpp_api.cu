@@ -230,6 +230,40 @@ dpp_status dpp_logprob_backward(const void* K, int64_t n, int64_t ld, int32_t dt
   return DPP_OK;
 }
 
+dpp_status dpp_logprob_backward_batched(int32_t batch, const int64_t* n, const void* const* K,
+                                        const int64_t* ld, const uint8_t* const* keep,
+                                        const double* const* grad_logp, void* const* dK,
+                                        const int64_t* ld_dk, void* workspace,
+                                        size_t workspace_bytes, void* stream) {
+  g_last_error.clear();
+  if (batch < 0) return fail(DPP_ERR_INVALID_ARG, "batch must be >= 0");
+  if (batch == 0) return DPP_OK;
+  if (!n || !K || !ld || !keep || !grad_logp || !dK || !ld_dk)
+    return fail(DPP_ERR_INVALID_ARG, "the per-instance host arrays must not be NULL");
+  int64_t n_max = 0;
+  for (int32_t i = 0; i < batch; ++i) {
+    if (n[i] < 0 || ld[i] < (n[i] > 1 ? n[i] : 1) || ld_dk[i] < (n[i] > 1 ? n[i] : 1))
+      return fail(DPP_ERR_INVALID_ARG, "bad n / ld / ld_dk of an instance");
+    if (n[i] > 0 && (!K[i] || !keep[i] || !grad_logp[i] || !dK[i]))
+      return fail(DPP_ERR_INVALID_ARG, "NULL pointer of a non-empty instance");
+    if (n[i] > n_max) n_max = n[i];
+  }
+  const size_t need = ws_backward(n_max, DPP_R64, true);
+  if (!workspace || !aligned(workspace, 256))
+    return fail(DPP_ERR_WORKSPACE, "workspace must be non-NULL and 256-byte aligned");
+  if (workspace_bytes < need) return fail(DPP_ERR_WORKSPACE, "workspace too small for n_max");
+  for (int32_t i = 0; i < batch; ++i) {
+    if (n[i] == 0) continue;
+    Workspace ws;
+    ws.base = static_cast<char*>(workspace);
+    ws.size = workspace_bytes;
+    cudaError_t e = logprob_backward(K[i], n[i], ld[i], DPP_R64, true, keep[i], grad_logp[i],
+                                     dK[i], ld_dk[i], ws, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail_cuda(e, "dpp_logprob_backward_batched");
+  }
+  return DPP_OK;
+}
+
 dpp_status dpp_set_tuning(int32_t key, double value) {
   g_last_error.clear();
   switch (key) {
