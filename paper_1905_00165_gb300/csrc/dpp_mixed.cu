@@ -618,15 +618,29 @@ __device__ __noinline__ void sup_solve_rows(int buf, int bn, bool prefetched) {
 // rows of R_{k+1} (bn rows) up to date through panel k - 1 and leave in
 // shared memory X = A[R_{k+1}, R_k], Y = A[R_{k+1}, R_{k+1}] (lower), and
 // their running diagonals, borderline scales, uniforms and K_jj.
-__device__ __noinline__ void sup_ready_next(const OuterArgs& a, int k, int64_t q,
-                                            int bn) {
+//   1. every global load the step needs is issued at once, into registers
+//      (one memory latency instead of one per 32-wide chunk): the rows'
+//      block against panel k - 1, the stored W and L of panels 0 .. k - 2,
+//      the L rows of R_k for panel k - 1, and the current X and Y;
+//   2. the rows are solved against panel k - 1 (shared memory);
+//   3. X and Y lose sum_t W[R_{k+1}, t] L[., t] over panels 0 .. k - 1
+//      (left-looking), chunk by chunk from registers and shared memory.
+constexpr int kMaxPreChunks = kMaxOuterBlock / kPanel - 2;  // panels 0 .. k - 2, k <= 7
+constexpr int kPerChunk = (3 * kPanel * kPanel + kSupThreads - 1) / kSupThreads;
+constexpr int kPerBlk = (kPanel * kPanel + kSupThreads - 1) / kSupThreads;
+
+__device__ __noinline__ void sup_ready_next(const OuterArgs& a, int k, int64_t q, int bn) {
   Cta0Smem& S = g_S0;
   const int st = threadIdx.x - 32;
-  const int64_t p = a.p, qn = q + kPanel;
+  const int64_t p = a.p, qn = q + kPanel, qp = q - kPanel;
   float* A = a.A;
   const int64_t lda = a.lda;
   const int64_t NB = a.NB;
-  const int kk = (int)(q - p);
+  const int nch = k >= 2 ? k - 1 : 0;  // chunks already in global memory
+  const int gi = st >> 2, gc = (st & 3) * 16;
+  const bool gemm = st < 4 * kPanel;
+
+  // ---- 1. all loads in flight together ----
   if (st < kPanel) {
     const int i = st;
     const bool vi = i < bn;
@@ -637,83 +651,124 @@ __device__ __noinline__ void sup_ready_next(const OuterArgs& a, int k, int64_t q
                  : 2.0;
     S.kfP[i] = vi ? (float)a.K[(qn + i) + (qn + i) * a.ldk] : 0.f;
   }
+  float x1v[kPerBlk], lrk[kPerBlk];
+#pragma unroll
+  for (int j = 0; j < kPerBlk; ++j) {
+    const int e = st + j * kSupThreads;
+    const int i = e % kPanel, c = e / kPanel;
+    x1v[j] = (k >= 1 && e < kPanel * kPanel && i < bn) ? __ldcg(&A[(qn + i) + (qp + c) * lda])
+                                                       : 0.f;
+    const int r = e / kPanel, t = e % kPanel;  // L rows of R_k, panel k - 1
+    lrk[j] = (k >= 1 && e < kPanel * kPanel)
+                 ? __ldcg(&a.Lk[(q + r) * NB + (k - 1) * kPanel + t]) : 0.f;
+  }
+  float pre[kMaxPreChunks][kPerChunk];
+#pragma unroll
+  for (int ch = 0; ch < kMaxPreChunks; ++ch) {
+    const int t0 = ch * kPanel;
+#pragma unroll
+    for (int j = 0; j < kPerChunk; ++j) {
+      const int e = st + j * kSupThreads;
+      const int r = e / kPanel, t = e % kPanel;  // consecutive threads: one row
+      float v = 0.f;
+      if (ch < nch && e < 3 * kPanel * kPanel) {
+        if (r < kPanel) {
+          if (r < bn) v = __ldcg(&a.Wk[(qn + r) * NB + t0 + t]);
+        } else if (r < 2 * kPanel) {
+          v = __ldcg(&a.Lk[(q + (r - kPanel)) * NB + t0 + t]);
+        } else if (r - 2 * kPanel < bn) {
+          v = __ldcg(&a.Lk[(qn + (r - 2 * kPanel)) * NB + t0 + t]);
+        }
+      }
+      pre[ch][j] = v;
+    }
+  }
+  float av[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const int c = gc + j;
+    const bool need = gemm && gi < bn && (c < kPanel || c - kPanel <= gi);
+    av[j] = need ? __ldcg(&A[(qn + gi) + ((c < kPanel) ? (q + c) : (qn + c - kPanel)) * lda])
+                 : 0.f;
+  }
+
+  // ---- 2. the rows against panel k - 1 (its L11 is still in buffer (k-1)&1)
   if (k >= 1) {
-    // the rows against panel k - 1 (buffer of k - 1 still holds its L11)
-    const int64_t qp = q - kPanel;
-    const int bp = (k - 1) & 1;
-    staged_copy<kPanel * kPanel, kSupThreads>(
-        st,
-        [&](int e) {
-          const int i = e % kPanel, c = e / kPanel;
-          return i < bn ? __ldcg(&A[(qn + i) + (qp + c) * lda]) : 0.f;
-        },
-        [&](int e, float v) { S.X[e % kPanel][e / kPanel] = v; });
+#pragma unroll
+    for (int j = 0; j < kPerBlk; ++j) {
+      const int e = st + j * kSupThreads;
+      if (e < kPanel * kPanel) S.X[e % kPanel][e / kPanel] = x1v[j];
+    }
     nb_sync(3, kSupThreads);
-    sup_solve_rows(bp, bn, true);
+    sup_solve_rows((k - 1) & 1, bn, true);
     nb_sync(3, kSupThreads);
     for (int e = st; e < kPanel * kPanel; e += kSupThreads) {
       const int i = e / kPanel, c = e % kPanel;  // consecutive threads: one row
       if (i < bn) {
-        a.Wk[(qn + i) * NB + (kk - kPanel) + c] = S.W[i][c];
-        a.Lk[(qn + i) * NB + (kk - kPanel) + c] = S.Lr[i][c];
+        a.Wk[(qn + i) * NB + (k - 1) * kPanel + c] = S.W[i][c];
+        a.Lk[(qn + i) * NB + (k - 1) * kPanel + c] = S.Lr[i][c];
       }
     }
     for (int e = st; e < kPanel * kPanel; e += kSupThreads) {
       const int i = e % kPanel, c = e / kPanel;
       if (i < bn) A[(qn + i) + (qp + c) * lda] = S.Lr[i][c];
     }
-    nb_sync(3, kSupThreads);
   }
-  // left-looking update through panel k - 1 of the 32 x 64 block [X | Y]
-  // (Y's upper part is computed and never read): support threads st < 128
-  // own row i = st / 4 and 16 consecutive columns, register-blocked.
-  const int gi = st >> 2, gc = (st & 3) * 16;
-  const bool gemm = st < 4 * kPanel;
+
+  // ---- 3. left-looking update of [X | Y] (Y's upper part is never read):
+  // threads st < 128 own row gi and 16 consecutive columns gc.., register
+  // blocked; chunk ch < nch comes from registers, the last (panel k - 1)
+  // from the solve just done and from lrk
   float acc[16];
 #pragma unroll
   for (int j = 0; j < 16; ++j) acc[j] = 0.f;
-  for (int t0 = 0; t0 < kk; t0 += kPanel) {
-    staged_copy<3 * kPanel * kPanel, kSupThreads>(
-        st,
-        [&](int e) {
-          const int r = e / kPanel, t = e % kPanel;  // consecutive threads: one row
-          if (r < kPanel) return r < bn ? __ldcg(&a.Wk[(qn + r) * NB + t0 + t]) : 0.f;
-          if (r < 2 * kPanel) return __ldcg(&a.Lk[(q + (r - kPanel)) * NB + t0 + t]);
-          const int rr = r - 2 * kPanel;
-          return rr < bn ? __ldcg(&a.Lk[(qn + rr) * NB + t0 + t]) : 0.f;
-        },
-        [&](int e, float v) {
-          const int r = e / kPanel, t = e % kPanel;
-          if (r < kPanel) S.Wc[r][t] = v;
-          else S.LcT[t][r - kPanel] = v;
-        });
-    nb_sync(3, kSupThreads);
-    if (gemm) {
-#pragma unroll 4
-      for (int t = 0; t < kPanel; ++t) {
-        const float w = S.Wc[gi][t];
-        const float4* lp = reinterpret_cast<const float4*>(&S.LcT[t][gc]);
 #pragma unroll
-        for (int v4 = 0; v4 < 4; ++v4) {
-          const float4 l = lp[v4];
-          acc[4 * v4 + 0] = fmaf(w, l.x, acc[4 * v4 + 0]);
-          acc[4 * v4 + 1] = fmaf(w, l.y, acc[4 * v4 + 1]);
-          acc[4 * v4 + 2] = fmaf(w, l.z, acc[4 * v4 + 2]);
-          acc[4 * v4 + 3] = fmaf(w, l.w, acc[4 * v4 + 3]);
+  for (int ch = 0; ch <= kMaxPreChunks; ++ch) {
+    const bool from_regs = ch < nch;
+    const bool last = (k >= 1) && (ch == nch);
+    if (from_regs || last) {
+      nb_sync(3, kSupThreads);  // the previous chunk's readers are done
+      if (from_regs) {
+#pragma unroll
+        for (int j = 0; j < kPerChunk; ++j) {
+          const int e = st + j * kSupThreads;
+          if (e < 3 * kPanel * kPanel) {
+            const int r = e / kPanel, t = e % kPanel;
+            if (r < kPanel) S.Wc[r][t] = pre[ch < kMaxPreChunks ? ch : 0][j];
+            else S.LcT[t][r - kPanel] = pre[ch < kMaxPreChunks ? ch : 0][j];
+          }
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < kPerBlk; ++j) {
+          const int e = st + j * kSupThreads;
+          if (e < kPanel * kPanel) {
+            const int r = e / kPanel, t = e % kPanel;
+            S.Wc[r][t] = S.W[r][t];
+            S.LcT[t][r] = lrk[j];
+            S.LcT[t][kPanel + r] = S.Lr[r][t];
+          }
+        }
+      }
+      nb_sync(3, kSupThreads);
+      if (gemm) {
+#pragma unroll 4
+        for (int t = 0; t < kPanel; ++t) {
+          const float w = S.Wc[gi][t];
+          const float4* lp = reinterpret_cast<const float4*>(&S.LcT[t][gc]);
+#pragma unroll
+          for (int v4 = 0; v4 < 4; ++v4) {
+            const float4 l = lp[v4];
+            acc[4 * v4 + 0] = fmaf(w, l.x, acc[4 * v4 + 0]);
+            acc[4 * v4 + 1] = fmaf(w, l.y, acc[4 * v4 + 1]);
+            acc[4 * v4 + 2] = fmaf(w, l.z, acc[4 * v4 + 2]);
+            acc[4 * v4 + 3] = fmaf(w, l.w, acc[4 * v4 + 3]);
+          }
         }
       }
     }
-    nb_sync(3, kSupThreads);
   }
   if (gemm) {
-    float av[16];
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const int c = gc + j;
-      const bool need = gi < bn && (c < kPanel || c - kPanel <= gi);
-      av[j] = need ? __ldcg(&A[(qn + gi) + ((c < kPanel) ? (q + c) : (qn + c - kPanel)) * lda])
-                   : 0.f;
-    }
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
       const int c = gc + j;
@@ -722,7 +777,6 @@ __device__ __noinline__ void sup_ready_next(const OuterArgs& a, int k, int64_t q
       else S.Y[gi][c - kPanel] = (c - kPanel <= gi) ? v : 0.f;
     }
   }
-  // upper part of Y is never read
   nb_sync(3, kSupThreads);
 }
 
@@ -1260,7 +1314,7 @@ cudaError_t sample_mixed(const DrawArgs& a, Workspace ws) {
   unsigned epoch = 1;
   const bool use_tc = g_tuning.update_kernel == 0;
   const int split = a.precision == DPP_PREC_BF16X6 ? kSplitBf16x6 : kSplit3xTf32;
-  const int kb_tc = split == kSplitBf16x6 ? 64 : 32;
+  const int kb_tc = 32;  // k-block of the tensor-core update (both splits)
   for (int64_t p = 0; p < n; p += NB) {
     const int NBp = (int)((n - p) < NB ? (n - p) : NB);
     {

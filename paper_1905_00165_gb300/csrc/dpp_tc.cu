@@ -25,8 +25,9 @@
 //
 // Structure (persistent, one CTA per SM, 320 threads, 128 x 128 tiles of the
 // lower triangle assigned round-robin):
-//   warp 0 / lane 0 : TMA producer, ring of operand stages (128 rows x 128
-//                     bytes per split, SWIZZLE_128B)
+//   warp 0 / lane 0 : TMA producer, ring of operand stages (128 rows per split;
+//                     3xTF32: 128-byte rows, SWIZZLE_128B, 3 stages; BF16x6:
+//                     64-byte rows, SWIZZLE_64B, 4 stages)
 //   warp 1          : allocates 4 x 128 TMEM columns (a ring of accumulators,
 //                     so the MMAs run ahead of the epilogue); lane 0 issues
 //                     tcgen05.mma (M = N = 128) and tcgen05.commit
@@ -47,7 +48,6 @@ namespace {
 
 constexpr int kBM = 128;
 constexpr int kBN = 128;
-constexpr int kTileBytes = kBM * 128;  // 128 rows x 128 bytes per split tile
 constexpr int kThreads = 320;          // producer, MMA, 8 epilogue warps
 constexpr int kEpiThreads = 256;
 constexpr int kEpiCols = kBN / 2;
@@ -63,6 +63,7 @@ template <>
 struct TcCfg<kSplit3xTf32> {
   static constexpr int kOps = 2;
   static constexpr int kBK = 32;
+  static constexpr int kRowBytes = 128;  // SWIZZLE_128B rows
   static constexpr int kStages = 3;
   static constexpr int kSteps = 4;          // MMA k-steps per k-block
   static constexpr int kStepsPerDrain = 4;  // drain once per k-block
@@ -77,13 +78,17 @@ struct TcCfg<kSplit3xTf32> {
   }
 };
 
-// BF16x6: 3 splits, 64 bf16 per 128-byte row, one drain per 16-deep step.
+// BF16x6: 3 splits, 32 bf16 per 64-byte row (SWIZZLE_64B), so that a stage is
+// 48 KB and four stages fit: the MMAs of one 32-deep stage take about half a
+// microsecond, less than an L2 refill, so the ring must be deep. One drain per
+// 16-deep step.
 template <>
 struct TcCfg<kSplitBf16x6> {
   static constexpr int kOps = 3;
-  static constexpr int kBK = 64;
-  static constexpr int kStages = 2;
-  static constexpr int kSteps = 4;
+  static constexpr int kBK = 32;
+  static constexpr int kRowBytes = 64;
+  static constexpr int kStages = 4;
+  static constexpr int kSteps = 2;
   static constexpr int kStepsPerDrain = 1;
   static constexpr int kProducts = 6;
   // D = F32, A = B = BF16 (1), K-major, N >> 3, M >> 4
@@ -97,8 +102,12 @@ struct TcCfg<kSplitBf16x6> {
 };
 
 template <int MODE>
+__host__ __device__ constexpr int tile_bytes() {
+  return kBM * TcCfg<MODE>::kRowBytes;  // 128 rows of one split
+}
+template <int MODE>
 __host__ __device__ constexpr int stage_bytes() {
-  return 2 * TcCfg<MODE>::kOps * kTileBytes;
+  return 2 * TcCfg<MODE>::kOps * tile_bytes<MODE>();
 }
 template <int MODE>
 __host__ __device__ constexpr int smem_bytes() {
@@ -149,15 +158,17 @@ __device__ inline void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, 
       : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
-// 128 bytes, 8-row swizzle atoms 1024 bytes apart.
-__device__ inline uint64_t sw128_desc(uint32_t saddr) {
+// Shared-memory matrix descriptor: K-major operand with rows of ROW bytes
+// swizzled over ROW bytes (128 or 64), 8-row swizzle atoms 8 ROW bytes apart.
+template <int ROW>
+__device__ inline uint64_t sw_desc(uint32_t saddr) {
+  static_assert(ROW == 128 || ROW == 64, "row width");
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)(16u >> 4) << 16;    // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024u >> 4) << 32;  // stride byte offset: next 8-row group
-  d |= (uint64_t)1 << 46;             // descriptor version
-  d |= (uint64_t)2 << 61;             // 128-byte swizzle
+  d |= (uint64_t)(16u >> 4) << 16;             // leading byte offset (unused, swizzled K-major)
+  d |= (uint64_t)((8u * ROW) >> 4) << 32;      // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;                      // descriptor version
+  d |= (uint64_t)(ROW == 128 ? 2 : 4) << 61;   // 128-byte or 64-byte swizzle
   return d;
 }
 
@@ -235,6 +246,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   using Cfg = TcCfg<MODE>;
   constexpr int kStages = Cfg::kStages;
   constexpr int kStageBytes = stage_bytes<MODE>();
+  constexpr int kTileBytes = tile_bytes<MODE>();
   constexpr int kDrainsPerKB = Cfg::kSteps / Cfg::kStepsPerDrain;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
@@ -343,7 +355,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 Cfg::product(pidx, &ia, &ib);
                 const uint32_t sa = smem_u32(st + ia * kTileBytes) + off;
                 const uint32_t sb = smem_u32(st + (Cfg::kOps + ib) * kTileBytes) + off;
-                mma_issue<MODE>(d, sw128_desc(sa), sw128_desc(sb), first ? 0u : 1u);
+                mma_issue<MODE>(d, sw_desc<Cfg::kRowBytes>(sa), sw_desc<Cfg::kRowBytes>(sb),
+                                first ? 0u : 1u);
                 first = false;
               }
             }
@@ -436,17 +449,18 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 }
 
 // Row-major [rows x ldk] operand of `esz`-byte elements, boxes of 128 rows x
-// 128 bytes, 128-byte swizzle.
-bool make_map(CUtensorMap* m, const void* ptr, int64_t rows, int ldk, int esz) {
+// row_bytes bytes, swizzled over row_bytes (128 or 64).
+bool make_map(CUtensorMap* m, const void* ptr, int64_t rows, int ldk, int esz, int row_bytes) {
   auto enc = get_encode();
   if (!enc) return false;
   cuuint64_t dims[2] = {(cuuint64_t)ldk, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)ldk * (cuuint64_t)esz};
-  cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)kBM};
+  cuuint32_t box[2] = {(cuuint32_t)(row_bytes / esz), (cuuint32_t)kBM};
   cuuint32_t es[2] = {1, 1};
   CUresult r = enc(m, esz == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
                    2, const_cast<void*>(ptr), dims, strides, box, es,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   row_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -463,7 +477,8 @@ cudaError_t launch(float* C, int64_t ldc, int64_t n, int64_t r0, int kdim, void*
   if (n > 0x7fffffff) return cudaErrorInvalidValue;
   TcMaps maps;
   for (int o = 0; o < Cfg::kOps; ++o) {
-    if (!make_map(&maps.W[o], Wops[o], n, ldk, esz) || !make_map(&maps.L[o], Lops[o], n, ldk, esz))
+    if (!make_map(&maps.W[o], Wops[o], n, ldk, esz, Cfg::kRowBytes) ||
+        !make_map(&maps.L[o], Lops[o], n, ldk, esz, Cfg::kRowBytes))
       return cudaErrorInvalidValue;
   }
   static bool attr = false;
