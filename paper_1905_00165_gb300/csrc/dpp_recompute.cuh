@@ -175,14 +175,18 @@ __device__ inline bool warp_wait_words(const RecomputeArgs& a, const unsigned lo
     mine = word_has(v, id);
   }
   if (!__all_sync(kRcFull, mine)) {
+    // a short pause between polls: every warp of every worker may be waiting
+    // here, and unthrottled polling would load the L2 that the residual's
+    // streaming reads of K depend on
     const unsigned long long t0 = global_ns();
-    while (true) {
+    for (unsigned it = 1;; ++it) {
+      __nanosleep(64);
       if (!mine) {
         v = ld_relaxed_u64(w + lane);
         mine = word_has(v, id);
       }
       if (__all_sync(kRcFull, mine)) break;
-      const bool bad = lane == 0 ? rc_give_up(a, t0) : false;
+      const bool bad = (lane == 0 && (it & 7) == 0) ? rc_give_up(a, t0) : false;
       if (__shfl_sync(kRcFull, bad, 0)) {
         *out = 0.f;
         return false;
