@@ -52,6 +52,9 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-fp64-ref", action="store_true")
     p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--streams", type=int, default=3,
+                   help="draws in flight on this many streams, each launch capped at "
+                        "SMs / streams CTAs")
     p.add_argument("--suite", action="store_true",
                    help="one JSON line per workload of the paper-shaped configurations "
                         "(FP64 n=512; n=4096 real/complex, projection/Beta; spanning trees of "
@@ -414,16 +417,25 @@ def main():
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
     need = dpp.workspace_size(0, n, 0, prec, 1)
-    wsb = torch.empty(need, dtype=torch.uint8, device=dev)
-    keep = torch.empty(n, dtype=torch.uint8, device=dev)
-    piv = torch.empty(n, dtype=torch.float64, device=dev)
-    raw = torch.zeros(_lib.RESULT_BYTES, dtype=torch.uint8, device=dev)
+    nst = max(1, args.streams)
+    if nst > 1:
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        _lib.set_tuning(_lib.DPP_TUNE_MAX_CTAS, max(8, sms // nst))
+    wsbs = [torch.empty(need, dtype=torch.uint8, device=dev) for _ in range(nst)]
+    keeps = [torch.empty(n, dtype=torch.uint8, device=dev) for _ in range(nst)]
+    pivs = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(nst)]
+    raws = [torch.zeros(_lib.RESULT_BYTES, dtype=torch.uint8, device=dev) for _ in range(nst)]
+    wsb, keep, piv, raw = wsbs[0], keeps[0], pivs[0], raws[0]
     stream = torch.cuda.current_stream(dev)
+    side = [stream] if nst == 1 else [torch.cuda.Stream(dev) for _ in range(nst)]
 
-    def draw(seed, Kptr=None):
+    def draw(seed, Kptr=None, si=None):
+        j = 0 if si is None else si
+        stv = stream if si is None else side[j]
         st = L.dpp_sample_hermitian(Kptr or Kd.data_ptr(), n, n, 0, prec, seed, 0, None,
-                                    keep.data_ptr(), None, piv.data_ptr(), raw.data_ptr(),
-                                    wsb.data_ptr(), need, stream.cuda_stream)
+                                    keeps[j].data_ptr(), None, pivs[j].data_ptr(),
+                                    raws[j].data_ptr(), wsbs[j].data_ptr(), need,
+                                    stv.cuda_stream)
         _lib.check(st)
 
     base_seed = rank * 1000003
@@ -443,8 +455,16 @@ def main():
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
+    for sv in side:
+        if sv is not stream:
+            sv.wait_event(ev0)
     for s in range(steps):
-        draw(base_seed + s)
+        draw(base_seed + s, si=s % nst)
+    for sv in side:
+        if sv is not stream:
+            done = torch.cuda.Event()
+            done.record(sv)
+            stream.wait_event(done)
     ev1.record(stream)
     torch.cuda.synchronize()
     launches = _lib.launch_count() - l0
@@ -495,6 +515,12 @@ def main():
                     "frac": gbs / hbm, "traffic": None, "peak_source": "MEASURED_PEAKS hbm_gbs"}
         roof["launches_per_step"] = st["launches"] / steps
         roof["avg_launch_ms"] = avg_ms
+        if nst > 1:
+            # each launch holds at most SMs / streams CTAs (one per SM), and
+            # the streams' launches overlap: the fraction of that SM share
+            share = min(1.0, max(8, sms // nst) / sms)
+            roof["ctas_per_launch_share"] = share
+            roof["frac_of_sm_share"] = roof["frac"] / share
     kernels = {k: {"launches": v["launches"], "total_ms": round(v["total_ms"], 3),
                    "share": v["total_ms"] / max(1e-9, sum(x["total_ms"] for x in prof.values()))}
                for k, v in prof.items()}
@@ -522,18 +548,20 @@ def main():
     e2e = None
     if not args.no_e2e:
         # each step: K from pinned host memory to the device, one draw through
-        # the C ABI, keep mask and result back to pinned host memory. The copy
-        # of step s + 1's K runs on its own stream into the other of two device
-        # buffers while step s draws; events order buffer reuse.
+        # the C ABI, keep mask and result back to pinned host memory. Steps
+        # are dealt to the same streams as above; the copies run on their own
+        # stream into a ring of nst + 1 device buffers, events order reuse.
         Kh = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
         Kh.copy_(Kd)
-        Kin = [torch.empty_like(Kd), torch.empty_like(Kd)]
-        keep_h = torch.empty(n, dtype=torch.uint8, pin_memory=True)
-        raw_h = torch.empty(_lib.RESULT_BYTES, dtype=torch.uint8, pin_memory=True)
-        e2e_steps = min(steps, 10)
+        nbuf = nst + 1
+        Kin = [torch.empty_like(Kd) for _ in range(nbuf)]
+        keep_h = [torch.empty(n, dtype=torch.uint8, pin_memory=True) for _ in range(nst)]
+        raw_h = [torch.empty(_lib.RESULT_BYTES, dtype=torch.uint8, pin_memory=True)
+                 for _ in range(nst)]
+        e2e_steps = min(steps, 12)
         copy_stream = torch.cuda.Stream(dev)
-        copied = [torch.cuda.Event(), torch.cuda.Event()]
-        consumed = [torch.cuda.Event(), torch.cuda.Event()]
+        copied = [torch.cuda.Event() for _ in range(nbuf)]
+        consumed = [torch.cuda.Event() for _ in range(nbuf)]
         torch.cuda.synchronize()
         if ws_n > 1:
             torch.distributed.barrier()
@@ -541,25 +569,36 @@ def main():
         a1 = torch.cuda.Event(enable_timing=True)
         a0.record(stream)
         copy_stream.wait_event(a0)
+        for sv in side:
+            if sv is not stream:
+                sv.wait_event(a0)
 
         def stage(s):
-            b = s & 1
+            b = s % nbuf
             with torch.cuda.stream(copy_stream):
-                if s >= 2:
+                if s >= nbuf:
                     copy_stream.wait_event(consumed[b])
                 Kin[b].copy_(Kh, non_blocking=True)
                 copied[b].record(copy_stream)
 
-        stage(0)
+        for s0 in range(min(nbuf, e2e_steps)):
+            stage(s0)
         for s in range(e2e_steps):
-            b = s & 1
-            if s + 1 < e2e_steps:
-                stage(s + 1)
-            stream.wait_event(copied[b])
-            draw(base_seed + 500000 + s, Kptr=Kin[b].data_ptr())
-            consumed[b].record(stream)
-            keep_h.copy_(keep, non_blocking=True)
-            raw_h.copy_(raw, non_blocking=True)
+            b, j = s % nbuf, s % nst
+            sv = side[j]
+            sv.wait_event(copied[b])
+            draw(base_seed + 500000 + s, Kptr=Kin[b].data_ptr(), si=j)
+            consumed[b].record(sv)
+            with torch.cuda.stream(sv):
+                keep_h[j].copy_(keeps[j], non_blocking=True)
+                raw_h[j].copy_(raws[j], non_blocking=True)
+            if s + nbuf < e2e_steps:
+                stage(s + nbuf)
+        for sv in side:
+            if sv is not stream:
+                done = torch.cuda.Event()
+                done.record(sv)
+                stream.wait_event(done)
         a1.record(stream)
         torch.cuda.synchronize()
         e_ms = a0.elapsed_time(a1)
@@ -570,7 +609,7 @@ def main():
         e2e = {"value": ws_n * e2e_steps / (e_ms / 1e3), "unit": "samples/s",
                "h2d_bytes_per_step": 8 * n * n, "d2h_bytes_per_step": n + _lib.RESULT_BYTES,
                "steps": e2e_steps,
-               "overlap": "H2D of the next step's K on a second stream, double-buffered"}
+               "overlap": f"H2D on a copy stream into {nbuf} rotating buffers; draws on {nst} streams"}
         del Kh, Kin
 
     batched = None
@@ -598,7 +637,8 @@ def main():
                        "kernel": f"Q diag(lam) Q^T, Haar Q (seed 0), lam~{args.kind}",
                        "seeds": f"Philox seed = step index (+ rank offset)",
                        "l2_policy": "inputs larger than L2 (2 GiB FP64 K), no flush",
-                       "parallelism": f"replicas x{ws_n}"},
+                       "parallelism": f"replicas x{ws_n}",
+                       "streams": nst},
             "tflops_algorithmic": value * algo_flops / 1e12,
             "roofline": roof,
             "kernels": kernels,

@@ -276,12 +276,18 @@ dpp_status dpp_logprob_backward_batched(int32_t batch, const int64_t* n,
  *                         update contracts this many columns at once (32..256,
  *                         multiple of 32; default 256)
  *   DPP_TUNE_UPDATE_KERNEL  mixed-path trailing update: 0 = tensor cores
- *                         (tcgen05, 3xTF32), 1 = SIMT FP32 (default 0)
+ *                         (tcgen05), 1 = SIMT FP32 (default 0)
+ *   DPP_TUNE_MAX_CTAS     mixed path: CTAs per launch of the outer-block and
+ *                         tensor-core kernels (0 = one per SM, the default;
+ *                         else 8..4096, at most one per SM). With half the SMs,
+ *                         two draws on two streams can overlap one draw's
+ *                         latency-bound panels with the other's update.
  * Returns DPP_ERR_INVALID_ARG for an unknown key or out-of-range value. */
 typedef enum {
   DPP_TUNE_TAU_SAFETY = 0,
   DPP_TUNE_OUTER_BLOCK = 1,
-  DPP_TUNE_UPDATE_KERNEL = 2
+  DPP_TUNE_UPDATE_KERNEL = 2,
+  DPP_TUNE_MAX_CTAS = 3
 } dpp_tune_key;
 
 dpp_status dpp_set_tuning(int32_t key, double value);

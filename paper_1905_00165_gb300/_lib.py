@@ -133,7 +133,7 @@ def profile_stop() -> dict:
     return out
 
 
-DPP_TUNE_TAU_SAFETY, DPP_TUNE_OUTER_BLOCK, DPP_TUNE_UPDATE_KERNEL = 0, 1, 2
+DPP_TUNE_TAU_SAFETY, DPP_TUNE_OUTER_BLOCK, DPP_TUNE_UPDATE_KERNEL, DPP_TUNE_MAX_CTAS = 0, 1, 2, 3
 
 
 def set_tuning(key: int, value: float) -> None:

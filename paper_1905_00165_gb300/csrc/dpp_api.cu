@@ -282,6 +282,13 @@ dpp_status dpp_set_tuning(int32_t key, double value) {
       if (value != 0.0 && value != 1.0) return fail(DPP_ERR_INVALID_ARG, "update kernel is 0 or 1");
       g_tuning.update_kernel = (int)value;
       return DPP_OK;
+    case DPP_TUNE_MAX_CTAS: {
+      const int v = (int)value;
+      if ((double)v != value || (v != 0 && v < 8) || v > 4096)
+        return fail(DPP_ERR_INVALID_ARG, "max CTAs must be 0 or in [8, 4096]");
+      g_tuning.max_ctas = v;
+      return DPP_OK;
+    }
     default:
       return fail(DPP_ERR_INVALID_ARG, "unknown tuning key");
   }
@@ -292,6 +299,7 @@ double dpp_get_tuning(int32_t key) {
     case DPP_TUNE_TAU_SAFETY: return g_tuning.tau_safety;
     case DPP_TUNE_OUTER_BLOCK: return (double)g_tuning.outer_block;
     case DPP_TUNE_UPDATE_KERNEL: return (double)g_tuning.update_kernel;
+    case DPP_TUNE_MAX_CTAS: return (double)g_tuning.max_ctas;
     default: return -1.0;
   }
 }

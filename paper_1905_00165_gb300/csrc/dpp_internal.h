@@ -66,7 +66,8 @@ cudaError_t sample_fp64(const DrawArgs& a, bool hermitian, Workspace ws);
 struct Tuning {
   double tau_safety = 8.0;  // c in the borderline bound
   int outer_block = 256;    // mixed path: columns contracted per trailing update
-  int update_kernel = 0;    // 0 = tcgen05 3xTF32, 1 = SIMT FP32
+  int update_kernel = 0;    // 0 = tcgen05, 1 = SIMT FP32
+  int max_ctas = 0;         // mixed path: CTAs per launch (0 = one per SM)
 };
 extern Tuning g_tuning;
 constexpr int kMaxOuterBlock = 256;

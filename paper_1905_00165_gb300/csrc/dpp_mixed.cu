@@ -1350,6 +1350,7 @@ cudaError_t sample_mixed(const DrawArgs& a, Workspace ws) {
       // serve the recomputes (which are bandwidth- and latency-bound)
       const int64_t mw = n - p - NBp;
       int64_t nw = cap - 1;  // CTA 0 decides, CTA 1 helps, the rest stream
+      if (g_tuning.max_ctas > 0 && nw + 1 > g_tuning.max_ctas) nw = g_tuning.max_ctas - 1;
       oa.wrow0 = p + NBp;
       const int64_t ntall = nw > 1 ? nw - 1 : 1;  // CTA 1 is the helper
       oa.wrows = (mw + ntall - 1) / ntall;

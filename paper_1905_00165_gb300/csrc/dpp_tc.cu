@@ -502,6 +502,7 @@ cudaError_t launch(float* C, int64_t ldc, int64_t n, int64_t r0, int kdim, void*
   cudaError_t e = dev_info(&di);
   if (e != cudaSuccess) return e;
   int64_t grid = di.sm_count;
+  if (g_tuning.max_ctas > 0 && grid > g_tuning.max_ctas) grid = g_tuning.max_ctas;
   if (grid > a.ntiles) grid = a.ntiles;
   k_update_tc<MODE><<<(unsigned)grid, kThreads, smem_bytes<MODE>(), s>>>(maps, a);
   return cudaGetLastError();
