@@ -52,7 +52,7 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-fp64-ref", action="store_true")
     p.add_argument("--no-batched", action="store_true")
-    p.add_argument("--streams", type=int, default=3,
+    p.add_argument("--streams", type=int, default=4,
                    help="draws in flight on this many streams, each launch capped at "
                         "SMs / streams CTAs")
     p.add_argument("--suite", action="store_true",
@@ -404,7 +404,7 @@ def main():
         prec_name = "bf16x6" if dpp.workspace_size(0, n, 0, 2, 1) > 0 else "fp64"
     prec = dpp.PRECISIONS[prec_name]
     _lib.set_tuning(_lib.DPP_TUNE_UPDATE_KERNEL, 0 if args.update == "tc" else 1)
-    steps = args.steps if args.steps is not None else (20 if prec_name != "fp64" else 4)
+    steps = args.steps if args.steps is not None else (40 if prec_name != "fp64" else 4)
     warmup = max(args.warmup, 3)
 
     # ---- inputs (resident before timing) --------------------------------
