@@ -64,6 +64,26 @@ def parse():
     return p.parse_args()
 
 
+def tc_traffic_per_launch():
+    """DRAM bytes per k_update_tc launch at n = 16384, from the ncu capture
+    summarised in profiles/ (None once dpp_tc.cu has changed since then)."""
+    import hashlib
+    try:
+        src = os.path.join(ROOT, "paper_1905_00165_gb300", "csrc", "dpp_tc.cu")
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        vals = {}
+        with open(os.path.join(ROOT, "profiles", "k_update_tc_traffic_n16384.txt")) as f:
+            for ln in f:
+                if ":" in ln:
+                    k, v = ln.split(":", 1)
+                    vals[k.strip()] = v.strip()
+        if vals.get("dpp_tc.cu sha256[:16]") != h:
+            return None
+        return float(vals["dram bytes per launch (mean)"])
+    except Exception:
+        return None
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -505,7 +525,8 @@ def main():
             bf16 = peaks.get("bf16_tflops", 1888.3)
             ach = per_launch_flops / (avg_ms / 1e3) / 1e12
             roof = {"kernel": dom, "bound": "tensor", "achieved": ach, "peak": bf16 / 6.0,
-                    "unit": "TFLOP/s", "frac": ach / (bf16 / 6.0), "traffic": None,
+                    "unit": "TFLOP/s", "frac": ach / (bf16 / 6.0),
+                    "traffic": tc_traffic_per_launch() if n == 16384 else None,
                     "executed_tensor_frac": 6.0 * ach / bf16,
                     "peak_source": "MEASURED_PEAKS bf16_tflops (burst), / 6 products"}
         else:

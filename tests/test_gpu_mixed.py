@@ -209,3 +209,40 @@ def test_borderline_band_has_margin(dpp):
     worst = max(worst, float(_pivot_error_ratios(dpp, K, 3).max()))
     print(f"max pivot error / (2^-22 sqrt(j+1)(K_jj+s_j)) = {worst:.3e}, c = {c}")
     assert worst < c / 8.0
+
+
+def test_capped_ctas_and_concurrent_streams(dpp):
+    """The mixed path with each launch capped at 40 CTAs still matches the
+    oracle, and four draws issued on four streams at once give the same
+    samples, pivots and log P as the same draws one after another."""
+    import torch
+    from paper_1905_00165_gb300 import _lib
+    n = 1100
+    K = W.hermitian_kernel(n, seed=17, kind="beta")
+    Kd = torch.from_numpy(K).cuda()
+    old = _lib.get_tuning(_lib.DPP_TUNE_MAX_CTAS)
+    _lib.set_tuning(_lib.DPP_TUNE_MAX_CTAS, 40)
+    try:
+        for seed in range(2):
+            u = O.uniforms(seed, 0, n)
+            ref = O.sample_ldl(K, u)
+            s = _run(dpp, K, seed, precision="bf16x6")
+            compare_draw(s.keep.cpu().numpy(), s.logp, s.pivots.cpu().numpy(), ref, u,
+                         logp_rtol=MIXED_LOGP_RTOL, piv_atol=1e-4)
+        seq = []
+        for seed in range(4):
+            s = dpp.sample_hermitian(Kd, seed=seed, precision="bf16x6")
+            torch.cuda.synchronize()
+            seq.append((s.keep.clone(), s.pivots.clone(), s.logp))
+        streams = [torch.cuda.Stream() for _ in range(4)]
+        conc = []
+        for seed, st in enumerate(streams):
+            with torch.cuda.stream(st):
+                conc.append(dpp.sample_hermitian(Kd, seed=seed, precision="bf16x6"))
+        torch.cuda.synchronize()
+        for (k0, p0, l0), s in zip(seq, conc):
+            assert torch.equal(k0, s.keep)
+            assert torch.equal(p0, s.pivots)
+            assert s.logp == l0
+    finally:
+        _lib.set_tuning(_lib.DPP_TUNE_MAX_CTAS, old)
