@@ -1171,8 +1171,8 @@ __global__ void __launch_bounds__(256) k_f32_update(F32Args u) {
   int64_t tr, tc;
   const int64_t x = blockIdx.x;
   if (TRI) {
-    tr = (int64_t)((sqrt(8.0 * (double)x + 1.0) - 1.0) * 0.5);
-    while (tr * (tr + 1) / 2 > x) --tr;
+    tr = (int64_t)((sqrtf(8.f * (float)x + 1.f) - 1.f) * 0.5f);  // FP32 estimate, exact below
+    while (tr > 0 && tr * (tr + 1) / 2 > x) --tr;
     while ((tr + 1) * (tr + 2) / 2 <= x) ++tr;
     tc = x - tr * (tr + 1) / 2;
   } else {

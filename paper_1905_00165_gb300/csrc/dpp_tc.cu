@@ -228,9 +228,12 @@ struct TcArgs {
   int* err;
 };
 
+// Row and column of lower-triangle tile x (row-major order). The estimate is
+// FP32 (the FP64 pipe is the GPU's slowest and every epilogue thread calls
+// this per tile) and the integer loops make it exact.
 __device__ inline void tile_coords(int64_t x, int64_t* tr, int64_t* tc) {
-  int64_t r = (int64_t)((sqrt(8.0 * (double)x + 1.0) - 1.0) * 0.5);
-  while (r * (r + 1) / 2 > x) --r;
+  int64_t r = (int64_t)((sqrtf(8.f * (float)x + 1.f) - 1.f) * 0.5f);
+  while (r > 0 && r * (r + 1) / 2 > x) --r;
   while ((r + 1) * (r + 2) / 2 <= x) ++r;
   *tr = r;
   *tc = x - r * (r + 1) / 2;
