@@ -5,8 +5,8 @@
 //     (double-float inside the sequential loop) and formed from the FP32
 //     factor entries (w = l d), so a pivot carries no FP32 accumulation error
 //     of its own; final pivots and log P(Y) are FP64;
-//   * panel solves in FP32 SIMT, trailing updates on tensor cores (3xTF32,
-//     FP32 accumulate) or FP32 SIMT;
+//   * panel solves in FP32 SIMT, trailing updates on tensor cores (BF16x6 or
+//     3xTF32 operand splits, FP32 accumulation) or FP32 SIMT;
 //   * a decision is exact outside the borderline band and made in FP64 on a
 //     recomputed pivot inside it.
 // Borderline test: a pivot whose uniform lies within
@@ -14,12 +14,11 @@
 // of its threshold is recomputed in FP64 from the original K (the exact
 // conditional probability, Props. 3-5) before its decision.
 //
-// Blocking (two levels): a 32-wide inner panel carries the sequential
-// decisions (one warp) and the panel solve (all CTAs, one cooperative launch);
-// the inner panels of one outer block of width NB (<= 256) are updated
-// left-looking from the previous inner panels of the same outer block; after
-// each outer block one rank-NB trailing update is applied to the whole
-// remaining lower triangle, which makes the dominant contraction NB deep.
+// Blocking (two levels): the inner panels (32 wide) of one outer block of
+// width NB (<= 256) are decided and solved inside one cooperative launch (see
+// the pipeline described at cta0_block); after each outer block one rank-NB
+// trailing update is applied to the whole remaining lower triangle, which
+// makes the dominant contraction NB deep.
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -63,15 +62,12 @@ __global__ void __launch_bounds__(256) k_export(const float* A, int64_t lda, con
   }
 }
 
-// One cooperative launch per outer block [p, p + NBp) of the mixed path.
-//
-// CTA 0 owns the rows of the outer block's diagonal block and runs ahead
-// through its 32-wide inner panels: left-looking update of the panel from the
-// block's earlier panels, the sequential decisions (warp 0), and the panel
-// solve of its remaining rows; after each panel it releases two flags (the
-// panel's L11 and pivots; the rows the next panel needs). CTAs 1..G-1 own the
-// rows below the outer block and stream behind CTA 0 (update, wait, solve),
-// serving FP64 recompute requests while they wait.
+// One cooperative launch per outer block [p, p + NBp) of the mixed path:
+// CTA 0 decides the block's inner panels (warp 0) with its support warps
+// preparing each next diagonal block, CTA 1 (the helper) streams the block's
+// own rows below that, and CTAs 2.. stream the rows below the block
+// (left-looking update, wait, solve), serving FP64 recompute requests while
+// they wait. Every CTA from 1 on is a recompute worker.
 struct OuterArgs {
   const double* K;
   int64_t ldk;
