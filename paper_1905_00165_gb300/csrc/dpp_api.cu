@@ -92,6 +92,8 @@ size_t dpp_workspace_size(int32_t op, int64_t n, int32_t dtype, int32_t precisio
       return 0;
     case DPP_OP_SAMPLE_LU:
       if (precision == DPP_PREC_FP64) return ws_fp64(n, dtype, false, true);
+      if ((precision == DPP_PREC_3XTF32 || precision == DPP_PREC_BF16X6) && dtype == DPP_R64)
+        return ws_mixed_lu(n);
       return 0;
     case DPP_OP_LOGPROB_BACKWARD:
       if (precision == DPP_PREC_FP64) return ws_backward(n, dtype, hermitian != 0);
@@ -136,7 +138,7 @@ static dpp_status sample_common(bool hermitian, const void* K, int64_t n, int64_
       // the mixed path reads K in FP64 for recomputes: it must stay intact
       return fail(DPP_ERR_INVALID_ARG, "mixed precision cannot factor in place (factor_out == K)");
     }
-    e = sample_mixed(a, ws);
+    e = hermitian ? sample_mixed(a, ws) : sample_mixed_lu(a, ws);
   }
   if (e != cudaSuccess) return fail_cuda(e, hermitian ? "dpp_sample_hermitian" : "dpp_sample_lu");
   return DPP_OK;

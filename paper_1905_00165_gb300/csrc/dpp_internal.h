@@ -76,18 +76,23 @@ constexpr int kMaxOuterBlock = 256;
 size_t ws_mixed(int64_t n);
 cudaError_t sample_mixed(const DrawArgs& a, Workspace ws);
 
+// Mixed-precision general (LU) sampler (dpp_mixed_lu.cu).
+size_t ws_mixed_lu(int64_t n);
+cudaError_t sample_mixed_lu(const DrawArgs& a, Workspace ws);
+
 // Operand splits of the tensor-core trailing update.
 enum { kSplit3xTf32 = 0, kSplitBf16x6 = 1 };
 
-// Trailing update C -= W L^T on the lower triangle of rows/cols [r0, n) of the
-// FP32 column-major C (ldc), on tcgen05 tensor cores (dpp_tc.cu). The W and L
+// Trailing update C -= W L^T on the lower triangle (full = false) or the whole
+// square (full = true) of rows/cols [r0, n) of the FP32 column-major C (ldc),
+// on tcgen05 tensor cores (dpp_tc.cu). The W and L
 // operands are given as splits in row-major [n x ldk] buffers (first kdim
 // columns used): two TF32 pieces (fp32 storage) for kSplit3xTf32, three BF16
 // pieces for kSplitBf16x6. kdim must be a multiple of the k-block (32 / 64);
 // ldk * element size must be a multiple of 16; buffers 16-byte aligned.
 cudaError_t outer_update_tc(int mode, float* C, int64_t ldc, int64_t n, int64_t r0, int kdim,
-                            void* const* Wops, void* const* Lops, int ldk, int* err_flag,
-                            cudaStream_t s);
+                            void* const* Wops, void* const* Lops, int ldk, bool full,
+                            int* err_flag, cudaStream_t s);
 
 // Batched sampler (dpp_batched.cu).
 struct BatchedArgs {

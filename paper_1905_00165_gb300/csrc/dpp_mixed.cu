@@ -1368,7 +1368,7 @@ cudaError_t sample_mixed(const DrawArgs& a, Workspace ws) {
       const double fl = (double)m * (double)m * (double)NBp;  // lower half of 2 m^2 NB
       if (use_tc && NBp % kb_tc == 0) {
         ProfScope ps(kProfUpdateTc, a.stream, fl, 8.0 * (double)m * (double)m / 2.0);
-        e = outer_update_tc(split, L.A32, L.ld32, n, r0, NBp, L.Wop, L.Lop, NB, L.err, a.stream);
+        e = outer_update_tc(split, L.A32, L.ld32, n, r0, NBp, L.Wop, L.Lop, NB, false, L.err, a.stream);
         if (e != cudaSuccess) return e;
       } else {
         F32Args u;

@@ -1,0 +1,1046 @@
+// Mixed-precision DPP sampler for a general (non-Hermitian) kernel: the LU
+// form of Algorithm 1, blocked as in Algorithm 4.
+//
+// Factorization kept in an FP32 copy A32 of K (full square, column-major):
+//   K_P - 1_G = L D U~,  U~ = D^{-1} U unit upper,  M = U~^T unit lower,
+// stored as L strictly below the diagonal, the FP32 pivot on it and U~ (that
+// is M^T) strictly above. With W = L D the Schur update of one block of
+// columns is  A22 -= L21 U12 = W21 M21^T,  the same C -= W L^T contraction as
+// the Hermitian path, over the whole square instead of one triangle.
+//
+// Arithmetic: as the Hermitian mixed path. A running diagonal
+// kd_i = K_ii - sum_k w_ik m_ik in FP64 (double-float inside the decision
+// loop) formed from the FP32 factor entries gives each pivot; a pivot whose
+// uniform lies within
+//   tau_j = c * 2^-22 * sqrt(j + 1) * (|K_jj| + s_j),  s_j = sum_k |w_jk m_jk|,
+// of it is recomputed in FP64 from the original K (below) before its
+// decision, so every decision is that of the exact chain (Theorem 1).
+//
+// FP64 recompute of pivot g (Props. 3-5): d_g = K_gg - b^T A^{-1} a with
+// A = K_P - 1_G, a = K[P, g], b = K[g, P]^T. For any x0, y0, with
+// r = a - A x0 and s = b - A^T y0,
+//     b^T A^{-1} a = b^T x0 + y0^T r + s^T A^{-1} r.
+// The mixed factors give x0 = M_P^{-T} m (m = row g of M, so x0 ~ A^{-1} a),
+// y0 = L_P^{-T} l (l = row g of L), and the last term as
+// sum_c (L_P^{-1} r)_c (M_P^{-1} s)_c / d_c, which is second order in the
+// factorization's error; residuals and dot products are FP64. The two
+// triangular sweeps of each side run as wavefronts over 32-index blocks on
+// the worker CTAs, with the protocol and helpers of the Hermitian recompute.
+//
+// One cooperative launch per outer block [q, q + kb) of at most 256 columns:
+//   CTA 0      : for each 32-wide inner panel, forms the diagonal block
+//                (left-looking over the outer block's earlier panels),
+//                makes its decisions in order (warp 0) and publishes it;
+//   CTA 1      : the helper; solves the outer block's own later rows and
+//                columns against each published panel, the next panel's
+//                first, and signals that one;
+//   CTAs 2..   : workers; 32-index chunks of the rows and columns beyond the
+//                outer block, left-looking update + both triangular solves
+//                against each panel, writing W and M (and their tensor-core
+//                splits). All CTAs from 1 on serve recompute requests while
+//                they wait for the next panel.
+// After each outer block one rank-kb update of the trailing square runs on
+// the tensor cores (full-square mode of the Hermitian path's kernel).
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include "dpp_device.cuh"
+#include "dpp_internal.h"
+#include "dpp_profile.h"
+#include "dpp_recompute.cuh"
+
+namespace dpp {
+namespace {
+
+constexpr unsigned kLuFull = 0xffffffffu;
+constexpr int kLuThreads = 256;
+constexpr int kNB = kMaxOuterBlock;  // row length of the W / M operand buffers
+
+// control word: the helper has solved, against the panel with this epoch,
+// the chunk that forms the next panel
+enum { kCtlHelp = 10 };
+
+// Recompute state of the LU form: the Hermitian set (x0 words, v1 words,
+// inverses of the L blocks, residual r) plus the second side's.
+struct LuRc {
+  RecomputeArgs rc;
+  unsigned long long* yw;   // y0 words
+  unsigned long long* v2w;  // v2 words
+  float* inv2;              // inverse of each 32 x 32 unit lower diagonal block of M
+  double* s2;               // residual s = b - A^T y0
+};
+
+struct LuArgs {
+  const double* K;
+  int64_t ldk;
+  float* A;
+  int64_t lda, n, q;
+  int kb;
+  const double* uniforms;
+  uint64_t seed, inst;
+  uint8_t* keep;
+  double* piv;
+  double* kd;
+  double* s;
+  float* Wk;  // row-major [n x kNB]: W = L D of the outer block's columns
+  float* Mk;  // row-major [n x kNB]: M
+  void* Wop[3];
+  void* Mop[3];
+  int split;
+  dpp_result* res;
+  unsigned epoch0;
+  double tol;
+  float tau0;
+  LuRc lr;
+};
+
+// ---------------------------------------------------------------------------
+// FP64 recompute, LU form
+// ---------------------------------------------------------------------------
+__device__ inline float word_at(const RecomputeArgs& a, const unsigned long long* words,
+                                int64_t c, unsigned id, bool* live) {
+  const unsigned long long w = ld_relaxed_u64(words + c);
+  if (word_has(w, id)) return __uint_as_float((unsigned)w);
+  return word_value_slow(a, words + c, id, live);
+}
+
+// F(i, c) is L(i, c) = A[i + c lda] (TRANS false) or M(i, c) = A[c + i lda]
+// (TRANS true). Warp 0: column `lane` of the inverse of the unit lower block
+// F_tt into z, and the inverse row-major into inv.
+template <bool TRANS>
+__device__ __forceinline__ void lu_diag_inverse(const RecomputeArgs& a, float* inv, int64_t t,
+                                                int nr, float (*sD)[33], float (&z)[32]) {
+  const int lane = threadIdx.x & 31;
+  const float* A = a.A;
+  const int64_t r0 = 32 * t;
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    const float* src = TRANS ? &A[(r0 + k) + (r0 + lane) * a.lda] : &A[(r0 + lane) + (r0 + k) * a.lda];
+    sD[lane][k] = (lane < nr && k < lane) ? __ldcg(src) : 0.f;
+  }
+  __syncwarp();
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < i; ++k) s = fmaf(sD[i][k], z[k], s);
+    z[i] = (i == lane) ? 1.f : (i < lane ? 0.f : -s);
+  }
+  float* dst = inv + (size_t)t * 1024;
+#pragma unroll
+  for (int i = 0; i < 32; ++i) dst[i * 32 + lane] = z[i];
+  __syncwarp();
+}
+
+// Backward sweep, block t:  x_t = F_tt^{-T} (f_t - sum_{s > t} F_st^T x_s),
+// f = row g of F; x published as words. Sources are split over the 8 warps
+// (s = t + 1 + wp + 8 m); each loads its tiles in the coalesced orientation.
+template <bool TRANS>
+__device__ __forceinline__ void lu_r1_block(const RecomputeArgs& a, float* inv,
+                                            unsigned long long* words, int64_t g, int64_t nblk,
+                                            int64_t t, unsigned id, Handoff& hf, int seqh,
+                                            float (*sD)[33], bool* live) {
+  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+  const float* A = a.A;
+  const int64_t lda = a.lda;
+  const int nr = (int)((g - 32 * t) < 32 ? (g - 32 * t) : 32);
+  float z[32];
+  float f = 0.f;
+  if (wp == 0) {
+    lu_diag_inverse<TRANS>(a, inv, t, nr, sD, z);
+    const int64_t c = 32 * t + lane;
+    if (lane < nr) f = __ldcg(TRANS ? &A[c + g * lda] : &A[g + c * lda]);
+  }
+  float red;
+  if (TRANS) {
+    // lane = column of block t: F(32 s + k, 32 t + lane) = A[(32 t + lane) + (32 s + k) lda]
+    float acc = 0.f;
+    for (int64_t s = t + 1 + wp; s < nblk; s += 8) {
+      const int ns = (int)((g - 32 * s) < 32 ? (g - 32 * s) : 32);
+      const float* cp = A + (32 * t + lane) + 32 * s * lda;
+      float v[32];
+#pragma unroll
+      for (int k = 0; k < 32; ++k) v[k] = (k < ns && lane < nr) ? __ldcg(cp + k * lda) : 0.f;
+      float xs = 0.f;
+      if (*live && !warp_wait_words(a, words + 32 * s, ns, id, &xs)) *live = false;
+#pragma unroll
+      for (int k = 0; k < 32; ++k) acc = fmaf(v[k], __shfl_sync(kLuFull, xs, k), acc);
+    }
+    red = acc;
+  } else {
+    // lane = row of block s: F(32 s + lane, 32 t + c) = A[(32 s + lane) + (32 t + c) lda]
+    float acc[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) acc[c] = 0.f;
+    for (int64_t s = t + 1 + wp; s < nblk; s += 8) {
+      const int ns = (int)((g - 32 * s) < 32 ? (g - 32 * s) : 32);
+      const float* tp = A + (32 * s + lane) + 32 * t * lda;
+      float tile[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) tile[c] = (lane < ns && c < nr) ? __ldcg(tp + c * lda) : 0.f;
+      float xs = 0.f;
+      if (*live && !warp_wait_words(a, words + 32 * s, ns, id, &xs)) *live = false;
+#pragma unroll
+      for (int c = 0; c < 32; ++c) acc[c] = fmaf(tile[c], xs, acc[c]);
+    }
+    red = transpose_reduce(acc, lane);
+  }
+  if (wp != 0) {
+    handoff_put(a, hf, seqh, wp, red, live);
+  } else {
+    const float y = f - handoff_take(a, hf, seqh, red, live);
+    float x = 0.f;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) x = fmaf(z[k], __shfl_sync(kLuFull, y, k), x);
+    if (lane < nr) st_relaxed_u64(words + 32 * t + lane, make_word(id, x));
+  }
+}
+
+// Forward sweep, block t:  v_t = F_tt^{-1} (rhs_t - sum_{s < t} F_ts v_s).
+// Returns v for lane i of warp 0 (0 elsewhere).
+template <bool TRANS>
+__device__ __forceinline__ float lu_r3_block(const RecomputeArgs& a, const float* inv,
+                                             unsigned long long* words, const double* rhs,
+                                             int64_t g, int64_t t, unsigned id, Handoff& hf,
+                                             int seqh, bool* live) {
+  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+  const float* A = a.A;
+  const int64_t lda = a.lda;
+  const int nr = (int)((g - 32 * t) < 32 ? (g - 32 * t) : 32);
+  float invrow[32];
+  if (wp == 0) {
+    const float* src = inv + (size_t)t * 1024 + lane * 32;
+#pragma unroll
+    for (int c = 0; c < 32; ++c) invrow[c] = src[c];
+  }
+  const int64_t slast = t - 1 - wp;
+  float red;
+  if (!TRANS) {
+    // lane = row of block t: F(32 t + lane, 32 s + c) = A[(32 t + lane) + (32 s + c) lda]
+    float acc = 0.f;
+    if (slast >= 0) {
+      for (int64_t s = slast % 8; s <= slast; s += 8) {
+        const float* tp = A + (32 * t + lane) + 32 * s * lda;
+        float tile[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) tile[c] = lane < nr ? __ldcg(tp + c * lda) : 0.f;
+        float vs = 0.f;
+        if (*live && !warp_wait_words(a, words + 32 * s, 32, id, &vs)) *live = false;
+#pragma unroll
+        for (int c = 0; c < 32; ++c) acc = fmaf(tile[c], __shfl_sync(kLuFull, vs, c), acc);
+      }
+    }
+    red = acc;
+  } else {
+    // lane = column of block s: F(32 t + i, 32 s + lane) = A[(32 s + lane) + (32 t + i) lda]
+    float acc[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) acc[i] = 0.f;
+    if (slast >= 0) {
+      for (int64_t s = slast % 8; s <= slast; s += 8) {
+        const float* tp = A + (32 * s + lane) + 32 * t * lda;
+        float tile[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) tile[i] = i < nr ? __ldcg(tp + i * lda) : 0.f;
+        float vs = 0.f;
+        if (*live && !warp_wait_words(a, words + 32 * s, 32, id, &vs)) *live = false;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) acc[i] = fmaf(tile[i], vs, acc[i]);
+      }
+    }
+    red = transpose_reduce(acc, lane);
+  }
+  float v = 0.f;
+  if (wp != 0) {
+    handoff_put(a, hf, seqh, wp, red, live);
+  } else {
+    const float sum = handoff_take(a, hf, seqh, red, live);
+    const double yd = (lane < nr ? rhs[32 * t + lane] : 0.0) - (double)sum;
+    const float y = (float)yd;
+#pragma unroll
+    for (int c = 0; c < 32; ++c) v = fmaf(invrow[c], __shfl_sync(kLuFull, y, c), v);
+    if (lane < nr) st_relaxed_u64(words + 32 * t + lane, make_word(id, v));
+  }
+  return v;
+}
+
+// Both residuals of the owner's block t (indices i in [32 t, 32 t + nr)):
+//   r_i = K[i, g] - sum_{c < g} K[i, c] x0_c  (+ x0_i if i was rejected),
+//   s_i = K[g, i] - sum_{c < g} K[c, i] y0_c  (+ y0_i if i was rejected),
+// FP64 from the original K; warp 0 lane i accumulates K[g, i] x0_i into bx
+// and y0_i r_i into yr. Part r reads rows of K (lane = i), part s columns
+// (lane = c, reduced over the lanes at the end); both coalesced.
+__device__ __noinline__ void lu_residual(const LuRc& L, unsigned id, int64_t g, int64_t t, int nr,
+                                         double (*sRedA)[32], double (*sRedB)[32], bool* live,
+                                         double* bx, double* yr) {
+  const RecomputeArgs& a = L.rc;
+  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+  const double* K = a.K;
+  const int64_t ldk = a.ldk;
+  const int64_t i = 32 * t + lane;
+  const bool vi = lane < nr;
+  const int64_t nblk = (g + 31) / 32;
+  double accA = 0.0;
+  double accB[32];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) accB[k] = 0.0;
+  for (int64_t m = wp; m < nblk; m += 8) {
+    const int64_t c0 = 32 * m;
+    const int nc = (int)((g - c0) < 32 ? (g - c0) : 32);
+    const bool vc = lane < nc;
+    const float xl = vc ? word_at(a, a.xw, c0 + lane, id, live) : 0.f;
+    const float yl = vc ? word_at(a, L.yw, c0 + lane, id, live) : 0.f;
+    double kv[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) kv[k] = (vi && k < nc) ? K[i + (c0 + k) * ldk] : 0.0;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) accA = fma(kv[k], (double)__shfl_sync(kLuFull, xl, k), accA);
+#pragma unroll
+    for (int k = 0; k < 32; ++k) kv[k] = (vc && k < nr) ? K[(c0 + lane) + (32 * t + k) * ldk] : 0.0;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) accB[k] = fma(kv[k], (double)yl, accB[k]);
+  }
+  sRedA[wp][lane] = accA;
+  sRedB[wp][lane] = transpose_reduce_d(accB, lane);
+  __syncthreads();
+  if (wp == 0 && vi) {
+    double tr = 0.0, ts = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      tr += sRedA[k][lane];
+      ts += sRedB[k][lane];
+    }
+    const double xi = (double)word_at(a, a.xw, i, id, live);
+    const double yi = (double)word_at(a, L.yw, i, id, live);
+    const double kgi = K[g + i * ldk];
+    double ri = K[i + g * ldk] - tr;
+    double si = kgi - ts;
+    if (a.keep[i] == 0) {  // (K_P - 1_G) has -1 on the rejected diagonal
+      ri += xi;
+      si += yi;
+    }
+    a.r[i] = ri;
+    L.s2[i] = si;
+    *bx = fma(kgi, xi, *bx);
+    *yr = fma(yi, ri, *yr);
+  }
+  __syncthreads();
+}
+
+// Worker side of one request (all threads of a worker CTA).
+__device__ __noinline__ bool lu_serve(const LuRc& L, unsigned id) {
+  const RecomputeArgs& a = L.rc;
+  __shared__ float sD[32][33];
+  __shared__ Handoff hf;
+  __shared__ double sRedA[8][32];
+  __shared__ double sRedB[8][32];
+  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+  const int64_t w = blockIdx.x - 1, nw = a.grid - 1;
+  const int64_t g = (int64_t)ld_acquire(&a.ctrl[kCtlG]);
+  const int64_t nblk = (g + 31) / 32;
+  bool live = true;
+  if (tid < 8) hf.ready[tid] = 0;
+  if (tid == 0) hf.cons = 0;
+  __syncthreads();
+  {
+    // x0 = M_P^{-T} m and y0 = L_P^{-T} l, owned blocks from the last one down
+    int seqh = 0;
+    const int64_t tfirst = (w < nblk) ? w + ((nblk - 1 - w) / nw) * nw : -1;
+    for (int64_t t = tfirst; t >= 0; t -= nw) {
+      lu_r1_block<true>(a, L.inv2, a.xw, g, nblk, t, id, hf, seqh++, sD, &live);
+      lu_r1_block<false>(a, a.inv, L.yw, g, nblk, t, id, hf, seqh++, sD, &live);
+    }
+  }
+  __syncthreads();
+  if (tid < 8) hf.ready[tid] = 0;
+  if (tid == 0) hf.cons = 0;
+  __syncthreads();
+  double bx = 0.0, yr = 0.0, es = 0.0;
+  {
+    // residuals, then v1 = L_P^{-1} r and v2 = M_P^{-1} s, owned blocks upwards
+    int seqh = 0;
+    for (int64_t t = w; t < nblk; t += nw) {
+      const int nr = (int)((g - 32 * t) < 32 ? (g - 32 * t) : 32);
+      lu_residual(L, id, g, t, nr, sRedA, sRedB, &live, &bx, &yr);
+      const float v1 = lu_r3_block<false>(a, a.inv, a.vw, a.r, g, t, id, hf, seqh++, &live);
+      const float v2 = lu_r3_block<true>(a, L.inv2, L.v2w, L.s2, g, t, id, hf, seqh++, &live);
+      if (wp == 0 && lane < nr) es += (double)v1 * (double)v2 / a.piv[32 * t + lane];
+    }
+  }
+  if (wp == 0) {
+    bx = warp_sum(bx);
+    yr = warp_sum(yr);
+    es = warp_sum(es);
+    if (lane == 0) {
+      a.part[4 * w + 0] = bx;
+      a.part[4 * w + 1] = yr;
+      a.part[4 * w + 2] = es;
+      __threadfence();
+      const unsigned done = atomicAdd(&a.ctrl[kCtlCount], 1u) + 1u;
+      if (done == (unsigned)nw) {
+        atomicExch(&a.ctrl[kCtlCount], 0u);
+        __threadfence();
+        st_release(&a.ctrl[kCtlAck], id);
+      }
+    }
+  }
+  __syncthreads();
+  return live && ld_acquire(&a.ctrl[kCtlAbort]) == 0;
+}
+
+// CTAs 1..G-1: serve requests until the panel with this epoch is published.
+__device__ inline bool lu_follower(const LuRc& L, unsigned epoch, int* s_ok) {
+  const RecomputeArgs& a = L.rc;
+  __shared__ unsigned s_cmd, s_id;
+  unsigned served = 0;
+  while (true) {
+    if (threadIdx.x == 0) {
+      unsigned cmd = 0, id = 0;
+      const unsigned long long t0 = global_ns();
+      unsigned sleep = 64;
+      for (unsigned it = 1;; ++it) {
+        if (ld_acquire(&a.ctrl[kCtlDone]) >= epoch) { cmd = 2; break; }
+        const unsigned req = ld_acquire(&a.ctrl[kCtlReq]);
+        if (req >= ((epoch << 8) | (served + 1u))) { cmd = 1; id = req; break; }
+        if ((it & 7) == 0 && rc_give_up(a, t0)) { cmd = 0; break; }
+        __nanosleep(sleep);
+        if (sleep < 1024) sleep <<= 1;
+      }
+      __threadfence();
+      s_cmd = cmd;
+      s_id = id;
+    }
+    __syncthreads();
+    const unsigned cmd = s_cmd, id = s_id;
+    __syncthreads();
+    if (cmd == 0) {
+      *s_ok = 0;
+      return false;
+    }
+    if (cmd == 1) {
+      if (!lu_serve(L, id)) {
+        *s_ok = 0;
+        return false;
+      }
+      served = id & 0xffu;
+      continue;
+    }
+    *s_ok = 1;
+    return true;
+  }
+}
+
+// Leader (warp 0 of CTA 0): pivot g recomputed in FP64. The factor entries of
+// indices < g must be in global memory. Lane-uniform results.
+__device__ inline bool lu_leader(const LuRc& L, int64_t g, unsigned epoch, int* seq, double* pe,
+                                 double* est) {
+  const RecomputeArgs& a = L.rc;
+  const int lane = threadIdx.x & 31;
+  __threadfence();
+  __syncwarp();
+  *seq += 1;
+  const unsigned id = (epoch << 8) | (unsigned)(*seq);
+  bool ok = a.grid >= 2;
+  if (ok && lane == 0) {
+    atomicExch(&a.ctrl[kCtlG], (unsigned)g);
+    __threadfence();
+    st_release(&a.ctrl[kCtlReq], id);
+    ok = rc_wait_geq(a, &a.ctrl[kCtlAck], id);
+  }
+  ok = __shfl_sync(kLuFull, ok, 0);
+  double bx = 0.0, yr = 0.0, e = 0.0;
+  if (ok && lane == 0) {
+    for (int w = 0; w < a.grid - 1; ++w) {
+      bx += __ldcg(&a.part[4 * w + 0]);
+      yr += __ldcg(&a.part[4 * w + 1]);
+      e += __ldcg(&a.part[4 * w + 2]);
+    }
+  }
+  const double kgg = a.K[g + g * a.ldk];
+  double d2 = kgg - bx - yr - e;
+  double er = fabs(e) * 1e-2 + 1e-12 * (1.0 + fabs(kgg) + fabs(bx) + fabs(yr));
+  d2 = __shfl_sync(kLuFull, d2, 0);
+  er = __shfl_sync(kLuFull, er, 0);
+  if (ok) {
+    *pe = d2;
+    *est = er;
+  }
+  return ok;
+}
+
+// ---------------------------------------------------------------------------
+// Panel kernel
+// ---------------------------------------------------------------------------
+struct LuSmem {
+  float L11[32][33];  // L of the current panel's diagonal block (strictly lower)
+  float M11[32][33];  // M of the same block (strictly lower)
+  float X[32][33];    // chunk rows x panel columns (then W)
+  float Z[32][33];    // chunk columns x panel rows, transposed (then M)
+  float WA[32][33];   // staged 32-deep slices of the left-looking products
+  float MB[32][33];
+  float WB[32][33];
+  float MA[32][33];
+  float d[32];
+  float rd[32];
+};
+constexpr size_t kLuDynSmem = sizeof(LuSmem);
+extern __shared__ __align__(16) unsigned char g_lu_dyn[];
+__device__ __forceinline__ LuSmem& lus() { return *reinterpret_cast<LuSmem*>(g_lu_dyn); }
+
+// Per-outer-block bookkeeping of CTA 0.
+struct LuLog {
+  double d[kMaxOuterBlock];
+  unsigned char kp[kMaxOuterBlock];
+  int border;
+  float max_ratio;
+  int rc_failed;
+};
+__shared__ LuLog g_lulog;
+__shared__ int g_lu_ok;
+
+__device__ inline float tf32_rna_lu(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// Tensor-core operand pieces of v at element off of the split buffers.
+__device__ inline void write_split(int split, void* const* ops, int64_t off, float v) {
+  if (split == kSplitBf16x6) {
+    // three BF16 pieces: v = b0 + b1 + b2 exactly (8 + 8 + 8 bits)
+    const __nv_bfloat16 b0 = __float2bfloat16_rn(v);
+    const float r1 = v - __bfloat162float(b0);
+    const __nv_bfloat16 b1 = __float2bfloat16_rn(r1);
+    const float r2 = r1 - __bfloat162float(b1);
+    static_cast<__nv_bfloat16*>(ops[0])[off] = b0;
+    static_cast<__nv_bfloat16*>(ops[1])[off] = b1;
+    static_cast<__nv_bfloat16*>(ops[2])[off] = __float2bfloat16_rn(r2);
+  } else {
+    const float h = tf32_rna_lu(v);
+    static_cast<float*>(ops[0])[off] = h;
+    static_cast<float*>(ops[1])[off] = tf32_rna_lu(v - h);
+  }
+}
+
+// The published panel [p, p + b): L11, M11 and the FP32 pivots into shared
+// memory (identity beyond b).
+__device__ void load_panel(const LuArgs& a, int64_t p, int b) {
+  LuSmem& S = lus();
+  const float* A = a.A;
+  for (int idx = threadIdx.x; idx < 1024; idx += kLuThreads) {
+    const int r = idx & 31, c = idx >> 5;
+    const float v = (r < b && c < b && r != c) ? __ldcg(&A[(p + r) + (p + c) * a.lda]) : 0.f;
+    S.L11[r][c] = r > c ? v : 0.f;  // L(p + r, p + c)
+    S.M11[c][r] = c > r ? v : 0.f;  // M(p + c, p + r) = A[p + r, p + c]
+  }
+  if (threadIdx.x < 32) {
+    const int c = threadIdx.x;
+    const float d = c < b ? (float)__ldcg(&a.piv[p + c]) : 1.f;
+    S.d[c] = d;
+    S.rd[c] = c < b ? 1.f / d : 0.f;
+  }
+}
+
+// Chunk [c0, c0 + 32) against panel [p, p + b), left-looking over the outer
+// block's earlier columns [q, p):
+//   X[r][c] = A[c0 + r, p + c] - sum_t W[c0 + r, t] M[p + c, t]
+//   Z[r][c] = A[p + c, c0 + r] - sum_t W[p + c, t] M[c0 + r, t]   (if want_z)
+// into shared memory. Thread (r = lane, c = warp + 8 j) owns 4 + 4 outputs.
+__device__ void chunk_left(const LuArgs& a, int64_t p, int b, int64_t c0, bool want_z) {
+  LuSmem& S = lus();
+  const int tid = threadIdx.x, r = tid & 31, cg = tid >> 5;
+  const float* A = a.A;
+  const int64_t lda = a.lda;
+  const int nc = (int)((a.n - c0) < 32 ? (a.n - c0) : 32);
+  const int D = (int)(p - a.q);
+  float x[4], z[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int c = cg + 8 * j;
+    x[j] = (r < nc && c < b) ? __ldcg(&A[(c0 + r) + (p + c) * lda]) : 0.f;
+    // Z loaded with lanes along the panel rows (contiguous), read back below
+    if (want_z)
+      S.Z[c][r] = (c < nc && r < b) ? __ldcg(&A[(p + r) + (c0 + c) * lda]) : 0.f;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < 4; ++j) z[j] = want_z ? S.Z[r][cg + 8 * j] : 0.f;
+  for (int t0 = 0; t0 < D; t0 += 32) {
+    for (int idx = tid; idx < 1024; idx += kLuThreads) {
+      const int rr = idx >> 5, tt = idx & 31;
+      S.WA[rr][tt] = rr < nc ? __ldcg(&a.Wk[(c0 + rr) * kNB + t0 + tt]) : 0.f;
+      S.MB[rr][tt] = rr < b ? __ldcg(&a.Mk[(p + rr) * kNB + t0 + tt]) : 0.f;
+      if (want_z) {
+        S.WB[rr][tt] = rr < b ? __ldcg(&a.Wk[(p + rr) * kNB + t0 + tt]) : 0.f;
+        S.MA[rr][tt] = rr < nc ? __ldcg(&a.Mk[(c0 + rr) * kNB + t0 + tt]) : 0.f;
+      }
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int tt = 0; tt < 32; ++tt) {
+      const float wa = S.WA[r][tt];
+      const float ma = want_z ? S.MA[r][tt] : 0.f;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = cg + 8 * j;
+        x[j] = fmaf(-wa, S.MB[c][tt], x[j]);
+        if (want_z) z[j] = fmaf(-ma, S.WB[c][tt], z[j]);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    S.X[r][cg + 8 * j] = x[j];
+    if (want_z) S.Z[r][cg + 8 * j] = z[j];
+  }
+  __syncthreads();
+}
+
+// Both triangular solves of a chunk against the published panel, then its
+// running-diagonal terms and the stores (L and M into A32, W and M rows into
+// the operand buffers, tensor-core splits if `splits`).
+__device__ void chunk_solve(const LuArgs& a, int64_t p, int b, int64_t c0, bool splits) {
+  LuSmem& S = lus();
+  chunk_left(a, p, b, c0, true);
+  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+  const int nc = (int)((a.n - c0) < 32 ? (a.n - c0) : 32);
+  const int D = (int)(p - a.q);
+  if (wp == 0) {
+    // row c0 + lane:  W M11^T = X  (forward over the panel columns)
+    float y[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) y[c] = S.X[lane][c];
+#pragma unroll
+    for (int c = 1; c < 32; ++c) {
+#pragma unroll
+      for (int k = 0; k < c; ++k) y[c] = fmaf(-y[k], S.M11[c][k], y[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < 32; ++c) S.X[lane][c] = y[c];
+  } else if (wp == 1) {
+    // column c0 + lane:  L11 u = Z,  M = u / d
+    float u[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) u[c] = S.Z[lane][c];
+#pragma unroll
+    for (int c = 1; c < 32; ++c) {
+#pragma unroll
+      for (int k = 0; k < c; ++k) u[c] = fmaf(-S.L11[c][k], u[k], u[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < 32; ++c) S.Z[lane][c] = u[c] * S.rd[c];
+  }
+  __syncthreads();
+  if (wp == 0 && lane < nc) {
+    f2 dsum = {0.f, 0.f};
+    float ssum = 0.f;
+    for (int c = 0; c < b; ++c) {
+      const float w = S.X[lane][c], m = S.Z[lane][c];
+      dsum = f2_add_prod(dsum, w, m);
+      ssum += fabsf(w * m);
+    }
+    a.kd[c0 + lane] -= f2_to_double(dsum);
+    a.s[c0 + lane] += (double)ssum;
+  }
+  float* A = a.A;
+  const int64_t lda = a.lda;
+  for (int idx = tid; idx < 1024; idx += kLuThreads) {
+    {
+      // L = W / d, lanes along the chunk rows
+      const int r = idx & 31, c = idx >> 5;
+      if (r < nc && c < b) A[(c0 + r) + (p + c) * lda] = S.X[r][c] * S.rd[c];
+    }
+    {
+      // M^T above the diagonal and the operand rows, lanes along the panel
+      const int c = idx & 31, r = idx >> 5;
+      if (r < nc && c < b) {
+        const float m = S.Z[r][c], w = S.X[r][c];
+        A[(p + c) + (c0 + r) * lda] = m;
+        const int64_t off = (c0 + r) * kNB + D + c;
+        a.Wk[off] = w;
+        a.Mk[off] = m;
+        if (splits) {
+          write_split(a.split, a.Wop, off, w);
+          write_split(a.split, a.Mop, off, m);
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Warp 0 of CTA 0: the decisions of panel [p, p + b) on the block in S.X
+// (lane i holds row i), pivots from the running diagonal in double-float.
+__device__ __noinline__ void lu_decide(const LuArgs& a, int64_t p, int b, unsigned epoch) {
+  LuSmem& S = lus();
+  LuLog& lg = g_lulog;
+  float (*X)[33] = S.X;
+  const int lane = threadIdx.x & 31;
+  const int64_t i = p + lane;
+  const bool vi = lane < b;
+  float* A = a.A;
+  const int64_t lda = a.lda;
+  f2 dd = vi ? f2_from_double(__ldcg(&a.kd[i])) : make_f2(0.f, 0.f);
+  float si = vi ? (float)__ldcg(&a.s[i]) : 0.f;
+  const float kf = vi ? (float)a.K[i + i * a.ldk] : 0.f;
+  const float sq = sqrtf((float)(i + 1));
+  const double u = vi ? (a.uniforms ? a.uniforms[i] : philox_uniform(a.seed, a.inst, (uint64_t)i))
+                      : 0.5;
+  int seq = 0;
+  for (int J = 0; J < b; ++J) {
+    const double ph = (double)__shfl_sync(kLuFull, dd.hi, J) + (double)__shfl_sync(kLuFull, dd.lo, J);
+    const double uj = __shfl_sync(kLuFull, u, J);
+    const float tau = a.tau0 * __shfl_sync(kLuFull, sq, J) *
+                          (fabsf(__shfl_sync(kLuFull, kf, J)) + __shfl_sync(kLuFull, si, J)) +
+                      0x1.0p-22f;
+    double pe = ph;
+    if (fabs(uj - ph) <= (double)tau) {
+      // the factor entries of [p, p + J] so far, out to global memory
+      if (lane <= J) {
+        for (int c = 0; c <= J; ++c) A[(p + lane) + (p + c) * lda] = X[lane][c];
+      }
+      double est = 0.0;
+      const bool ok = lu_leader(a.lr, p + J, epoch, &seq, &pe, &est);
+      if (lane == 0) {
+        lg.border += 1;
+        const float ratio = (float)(fabs(pe - ph) / (double)tau);
+        if (ratio > lg.max_ratio) lg.max_ratio = ratio;
+        if (!ok || est > fabs(uj - pe)) lg.rc_failed = 1;
+      }
+      if (!ok) pe = ph;
+    }
+    const bool kp = uj < pe;
+    const double d = kp ? pe : pe - 1.0;
+    if (lane == J) {
+      a.piv[p + J] = d;
+      a.keep[p + J] = kp ? 1 : 0;
+    }
+    if (lane == 0) {
+      lg.d[p - a.q + J] = d;
+      lg.kp[p - a.q + J] = kp ? 1 : 0;
+    }
+    const float df = (float)d;
+    const float rdf = 1.f / df;
+    if (lane > J && vi) {
+      const float l = X[lane][J] * rdf;
+      for (int c = J + 1; c < b; ++c) X[lane][c] = fmaf(-l, X[J][c], X[lane][c]);
+      const float uji = X[J][lane];  // U(p + J, p + lane), not yet scaled
+      dd = f2_sub_prod(dd, l, uji);
+      si += fabsf(l * uji);
+      X[lane][J] = l;
+    }
+    __syncwarp();
+    if (lane == J) {
+      for (int c = J + 1; c < b; ++c) X[J][c] *= rdf;
+      X[J][J] = df;
+    }
+    __syncwarp();
+  }
+  if (vi) {
+    for (int c = 0; c < b; ++c) A[i + (p + c) * lda] = X[lane][c];
+  }
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(kLuThreads, 1) k_lu_outer(LuArgs a) {
+  int& s_ok = g_lu_ok;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int np = (a.kb + 31) / 32;
+  const int64_t qe = a.q + a.kb;
+  const RecomputeArgs& rc = a.lr.rc;
+
+  if (blockIdx.x == 0) {
+    LuLog& lg = g_lulog;
+    if (tid == 0) {
+      lg.border = 0;
+      lg.max_ratio = 0.f;
+      lg.rc_failed = 0;
+    }
+    __syncthreads();
+    bool alive = true;
+    for (int k = 0; k < np && alive; ++k) {
+      const int64_t p = a.q + 32 * k;
+      const int b = (int)((qe - p) < 32 ? (qe - p) : 32);
+      const unsigned epoch = a.epoch0 + (unsigned)k;
+      if (k > 0) {
+        if (tid == 0) s_ok = rc_wait_geq(rc, &rc.ctrl[kCtlHelp], epoch - 1) ? 1 : 0;
+        __syncthreads();
+        if (!s_ok) {
+          alive = false;
+          break;
+        }
+      }
+      chunk_left(a, p, b, p, false);
+      if (warp == 0) lu_decide(a, p, b, epoch);
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        st_release(&rc.ctrl[kCtlDone], epoch);
+      }
+    }
+    __syncthreads();
+    // likelihood and bookkeeping of the block (FP64)
+    double lp = 0.0;
+    int kept = 0, oor = 0, bad = 0;
+    for (int i = tid; i < a.kb; i += kLuThreads) {
+      const double d = lg.d[i];
+      const double pre = lg.kp[i] ? d : d + 1.0;
+      lp += log(fabs(d));
+      kept += lg.kp[i];
+      oor += (pre < -a.tol || pre > 1.0 + a.tol) ? 1 : 0;
+      bad |= isfinite(d) ? 0 : 1;
+    }
+    lp = warp_sum(lp);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      kept += __shfl_xor_sync(kLuFull, kept, o);
+      oor += __shfl_xor_sync(kLuFull, oor, o);
+      bad |= __shfl_xor_sync(kLuFull, bad, o);
+    }
+    __shared__ double s_lp[kLuThreads / 32];
+    __shared__ int s_cnt[3][kLuThreads / 32];
+    if (lane == 0) {
+      s_lp[warp] = lp;
+      s_cnt[0][warp] = kept;
+      s_cnt[1][warp] = oor;
+      s_cnt[2][warp] = bad;
+    }
+    __syncthreads();
+    if (tid == 0 && alive) {
+      double Ls = 0.0;
+      int Kc = 0, O = 0, B = 0;
+      for (int w = 0; w < kLuThreads / 32; ++w) {
+        Ls += s_lp[w];
+        Kc += s_cnt[0][w];
+        O += s_cnt[1][w];
+        B |= s_cnt[2][w];
+      }
+      dpp_result* r = a.res;
+      r->logp += Ls;
+      if (Kc) atomicAdd(&r->n_kept, Kc);
+      if (O) {
+        atomicAdd(&r->n_out_of_range, O);
+        atomicOr(&r->status, DPP_RES_INADMISSIBLE);
+      }
+      if (B) atomicOr(&r->status, DPP_RES_NONFINITE);
+      if (lg.border) {
+        atomicAdd(&r->n_borderline, lg.border);
+        if ((double)lg.max_ratio > r->max_err_ratio) r->max_err_ratio = (double)lg.max_ratio;
+      }
+      if (lg.rc_failed) atomicOr(&r->status, DPP_RES_RECOMPUTE);
+    }
+    return;
+  }
+
+  const bool helper = blockIdx.x == 1;
+  const int64_t nwk = (int64_t)gridDim.x - 2, w = (int64_t)blockIdx.x - 2;
+  for (int k = 0; k < np; ++k) {
+    const int64_t p = a.q + 32 * k;
+    const int b = (int)((qe - p) < 32 ? (qe - p) : 32);
+    const unsigned epoch = a.epoch0 + (unsigned)k;
+    if (!lu_follower(a.lr, epoch, &s_ok)) return;
+    load_panel(a, p, b);
+    __syncthreads();
+    if (helper) {
+      for (int64_t c0 = p + b; c0 < qe; c0 += 32) {
+        chunk_solve(a, p, b, c0, false);
+        if (c0 == p + b && tid == 0) {
+          __threadfence();
+          st_release(&rc.ctrl[kCtlHelp], epoch);
+        }
+      }
+      if (p + b >= qe && tid == 0) st_release(&rc.ctrl[kCtlHelp], epoch);
+    } else {
+      for (int64_t c0 = qe + 32 * w; c0 < a.n; c0 += 32 * nwk) chunk_solve(a, p, b, c0, true);
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(256) k_convert_full(const double* K, int64_t ldk, float* A,
+                                                      int64_t lda, int64_t n, double* kd,
+                                                      double* s) {
+  for (int64_t j = blockIdx.x; j < n; j += gridDim.x) {
+    const double* col = K + j * ldk;
+    float* dst = A + j * lda;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) dst[i] = (float)col[i];
+    if (threadIdx.x == 0) {
+      kd[j] = col[j];
+      s[j] = 0.0;
+    }
+  }
+}
+
+// In-place LU of K - 1_{Y^c} in FP64: L strictly below the diagonal, the
+// pivots on it, U = D U~ above it.
+__global__ void __launch_bounds__(256) k_export_lu(const float* A, int64_t lda, const double* piv,
+                                                   double* F, int64_t ldf, int64_t n) {
+  for (int64_t j = blockIdx.x; j < n; j += gridDim.x) {
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const double v = (double)A[i + j * lda];
+      F[i + j * ldf] = i > j ? v : (i == j ? piv[j] : piv[i] * v);
+    }
+  }
+}
+
+struct LuLayout {
+  int64_t ld32;
+  float* A32;
+  float *Wk, *Mk;
+  void* Wop[3];
+  void* Mop[3];
+  double *kd, *s, *piv;
+  unsigned* flag;
+  int* err;
+  RecomputeScratch rs;
+  unsigned long long *yw, *v2w;
+  float* inv2;
+  double* s2;
+};
+
+bool carve_lu(Workspace& ws, int64_t n, LuLayout* L) {
+  L->ld32 = ((n + 31) / 32) * 32;
+  if (L->ld32 < 32) L->ld32 = 32;
+  const size_t nn = (size_t)(n > 0 ? n : 1);
+  L->A32 = static_cast<float*>(ws.take(sizeof(float) * (size_t)L->ld32 * nn));
+  const size_t ob = sizeof(float) * nn * (size_t)kNB;
+  L->Wk = static_cast<float*>(ws.take(ob));
+  L->Mk = static_cast<float*>(ws.take(ob));
+  bool ops_ok = true;
+  for (int o = 0; o < 3; ++o) {
+    L->Wop[o] = ws.take(ob);
+    L->Mop[o] = ws.take(ob);
+    ops_ok = ops_ok && L->Wop[o] && L->Mop[o];
+  }
+  L->kd = static_cast<double*>(ws.take(sizeof(double) * nn));
+  L->s = static_cast<double*>(ws.take(sizeof(double) * nn));
+  L->piv = static_cast<double*>(ws.take(sizeof(double) * nn));
+  L->flag = static_cast<unsigned*>(ws.take(256));
+  L->err = reinterpret_cast<int*>(L->flag) + 16;
+  if (!recompute_carve(ws, n, &L->rs)) return false;
+  L->yw = static_cast<unsigned long long*>(ws.take(sizeof(unsigned long long) * nn));
+  L->v2w = static_cast<unsigned long long*>(ws.take(sizeof(unsigned long long) * nn));
+  L->inv2 = static_cast<float*>(ws.take(sizeof(float) * 1024 * (size_t)L->rs.nblk));
+  L->s2 = static_cast<double*>(ws.take(sizeof(double) * nn));
+  return L->A32 && L->Wk && L->Mk && ops_ok && L->kd && L->s && L->piv && L->flag && L->yw &&
+         L->v2w && L->inv2 && L->s2;
+}
+
+}  // namespace
+
+size_t ws_mixed_lu(int64_t n) {
+  Workspace probe;
+  probe.base = reinterpret_cast<char*>(256);
+  probe.size = ~size_t(0) >> 2;
+  LuLayout L;
+  carve_lu(probe, n, &L);
+  return probe.used + 512;
+}
+
+cudaError_t sample_mixed_lu(const DrawArgs& a, Workspace ws) {
+  const int64_t n = a.n;
+  const int NB = g_tuning.outer_block;
+  LuLayout L;
+  if (!carve_lu(ws, n, &L)) return cudaErrorInvalidValue;
+  cudaError_t e = init_result(a.result, a.stream);
+  if (e != cudaSuccess || n == 0) return e;
+  if ((e = cudaMemsetAsync(L.flag, 0, 256, a.stream)) != cudaSuccess) return e;
+  if ((e = recompute_reset(L.rs, n, a.stream)) != cudaSuccess) return e;
+  const size_t words = sizeof(unsigned long long) * (size_t)n;
+  if ((e = cudaMemsetAsync(L.yw, 0, words, a.stream)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(L.v2w, 0, words, a.stream)) != cudaSuccess) return e;
+  const double* K = static_cast<const double*>(a.K);
+  {
+    ProfScope ps(kProfConvert, a.stream, 0.0, 12.0 * (double)n * (double)n);
+    k_convert_full<<<(unsigned)(n < 65535 ? n : 65535), 256, 0, a.stream>>>(K, a.ld, L.A32, L.ld32,
+                                                                             n, L.kd, L.s);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  static int cap = 0;
+  if (cap == 0) {
+    cudaError_t ea = cudaFuncSetAttribute(k_lu_outer, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)kLuDynSmem);
+    if (ea != cudaSuccess) return ea;
+    DevInfo di;
+    if ((ea = dev_info(&di)) != cudaSuccess) return ea;
+    int per_sm = 0;
+    ea = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lu_outer, kLuThreads,
+                                                       kLuDynSmem);
+    if (ea != cudaSuccess) return ea;
+    cap = per_sm * di.sm_count;
+    if (cap > kMaxCoopCtas) cap = kMaxCoopCtas;
+    if (cap < 3) return cudaErrorLaunchOutOfResources;
+  }
+  int grid = cap;
+  if (g_tuning.max_ctas > 0 && grid > g_tuning.max_ctas) grid = g_tuning.max_ctas;
+  if (grid < 3) grid = 3;
+  const int split = a.precision == DPP_PREC_BF16X6 ? kSplitBf16x6 : kSplit3xTf32;
+  unsigned epoch = 1;
+  for (int64_t q = 0; q < n; q += NB) {
+    const int kb = (int)((n - q) < NB ? (n - q) : NB);
+    LuArgs la;
+    la.K = K;
+    la.ldk = a.ld;
+    la.A = L.A32;
+    la.lda = L.ld32;
+    la.n = n;
+    la.q = q;
+    la.kb = kb;
+    la.uniforms = a.uniforms;
+    la.seed = a.seed;
+    la.inst = a.instance;
+    la.keep = a.keep;
+    la.piv = L.piv;
+    la.kd = L.kd;
+    la.s = L.s;
+    la.Wk = L.Wk;
+    la.Mk = L.Mk;
+    for (int o = 0; o < 3; ++o) {
+      la.Wop[o] = L.Wop[o];
+      la.Mop[o] = L.Mop[o];
+    }
+    la.split = split;
+    la.res = a.result;
+    la.epoch0 = epoch;
+    la.tol = 1e-3;
+    la.tau0 = (float)(g_tuning.tau_safety * 0x1.0p-22);
+    la.lr.rc = recompute_args(L.rs, K, a.ld, L.A32, L.ld32, L.piv, a.keep, n, q, a.result);
+    la.lr.rc.grid = grid;
+    la.lr.yw = L.yw;
+    la.lr.v2w = L.v2w;
+    la.lr.inv2 = L.inv2;
+    la.lr.s2 = L.s2;
+    void* args[] = {&la};
+    {
+      ProfScope ps(kProfPanel, a.stream);
+      e = cudaLaunchCooperativeKernel((const void*)k_lu_outer, dim3((unsigned)grid),
+                                      dim3(kLuThreads), args, kLuDynSmem, a.stream);
+    }
+    if (e != cudaSuccess) return e;
+    epoch += (unsigned)((kb + 31) / 32);
+    const int64_t r0 = q + kb;
+    if (r0 < n) {
+      const int64_t m = n - r0;
+      const double fl = 2.0 * (double)m * (double)m * (double)kb;
+      ProfScope ps(kProfUpdateTc, a.stream, fl, 8.0 * (double)m * (double)m);
+      e = outer_update_tc(split, L.A32, L.ld32, n, r0, kb, L.Wop, L.Mop, kNB, true, L.err,
+                          a.stream);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  if (a.pivots_user) {
+    e = cudaMemcpyAsync(a.pivots_user, L.piv, sizeof(double) * n, cudaMemcpyDeviceToDevice,
+                        a.stream);
+    if (e != cudaSuccess) return e;
+  }
+  if (a.factor_out) {
+    ProfScope ps(kProfOther, a.stream);
+    k_export_lu<<<(unsigned)(n < 65535 ? n : 65535), 256, 0, a.stream>>>(
+        L.A32, L.ld32, L.piv, static_cast<double*>(a.factor_out), a.ld, n);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace dpp

@@ -337,7 +337,7 @@ __device__ __forceinline__ float x0_at(const RecomputeArgs& a, int64_t c, unsign
 //           rows (K[i, c], c <= i; in the diagonal tile K[c, i] for c > i);
 //   part B: tiles below the diagonal block, K[c, i] for c >= 32 t + 32, lanes
 //           = c (coalesced down column i), reduced over the lanes at the end.
-__device__ __noinline__ void residual_block(const RecomputeArgs& a, unsigned id, int64_t g,
+static __device__ __noinline__ void residual_block(const RecomputeArgs& a, unsigned id, int64_t g,
                                             int64_t t, int nr, double (*sRedA)[32],
                                             double (*sRedB)[32], bool* live, double* kx,
                                             double* xr) {
@@ -400,7 +400,7 @@ __device__ __noinline__ void residual_block(const RecomputeArgs& a, unsigned id,
 
 // Worker side of one request (all threads of a worker CTA). Returns false on
 // abort or timeout (the CTA must then leave the launch).
-__device__ __noinline__ bool recompute_serve(const RecomputeArgs& a, unsigned id) {
+static __device__ __noinline__ bool recompute_serve(const RecomputeArgs& a, unsigned id) {
   __shared__ float sD[32][33];
   __shared__ Handoff hf;
   __shared__ double sRedA[8][32];

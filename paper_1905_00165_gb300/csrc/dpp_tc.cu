@@ -5,7 +5,10 @@
 //
 // which is the rank-NB update A22 -= W L21^T = L21 D1 L21^T of the blocked
 // LDL^T sampler (Algorithm 3's Schur complement, Hermitian form), i.e. the
-// contraction that carries asymptotically all of the work (Section 4).
+// contraction that carries asymptotically all of the work (Section 4). In
+// full mode every tile of the square trailing block is updated: the LU form
+// A22 -= L21 U12 = (L21 D1) (D1^{-1} U12), with L the rows of D1^{-1} U12
+// transposed.
 //
 // Precision (chosen per call):
 //   3xTF32 : W = Wh + Wl, L = Lh + Ll (TF32 pairs); per 8-deep k-step
@@ -224,7 +227,8 @@ struct TcArgs {
   int64_t ldc, n, r0;
   int kblocks;
   int64_t tiles;   // tiles along one side of the trailing block
-  int64_t ntiles;  // lower-triangle tiles
+  int64_t ntiles;  // tiles updated: the lower triangle's, or tiles^2 if full
+  int full;        // 1: every tile of the square block (LU), 0: lower triangle
   int* err;
 };
 
@@ -237,6 +241,16 @@ __device__ inline void tile_coords(int64_t x, int64_t* tr, int64_t* tc) {
   while ((r + 1) * (r + 2) / 2 <= x) ++r;
   *tr = r;
   *tc = x - r * (r + 1) / 2;
+}
+
+// Row and column of tile x of this launch (row-major order in either mode).
+__device__ inline void tile_of(const TcArgs& a, int64_t x, int64_t* tr, int64_t* tc) {
+  if (a.full) {
+    *tr = x / a.tiles;
+    *tc = x - *tr * a.tiles;
+  } else {
+    tile_coords(x, tr, tc);
+  }
 }
 
 __device__ inline void mbar_arrive(uint32_t bar) {
@@ -295,7 +309,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = true;
       for (int64_t x = blockIdx.x; x < a.ntiles && ok; x += gridDim.x) {
         int64_t tr, tc;
-        tile_coords(x, &tr, &tc);
+        tile_of(a, x, &tr, &tc);
         const int i0 = (int)(a.r0 + tr * kBM), c0 = (int)(a.r0 + tc * kBN);
         for (int kb = 0; kb < KB; ++kb, ++g) {
           const int s = (int)(g % kStages);
@@ -379,12 +393,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int drains = KB * kDrainsPerKB;
     for (int64_t x = blockIdx.x; x < a.ntiles && ok; x += gridDim.x) {
       int64_t tr, tc;
-      tile_coords(x, &tr, &tc);
+      tile_of(a, x, &tr, &tc);
       const int64_t row = a.r0 + tr * kBM + rloc;
       const int64_t c0 = a.r0 + tc * kBN + half * kEpiCols;
       int64_t cend = c0 + kEpiCols;
       if (cend > a.n) cend = a.n;
-      if (tr == tc && cend > row + 1) cend = row + 1;
+      if (!a.full && tr == tc && cend > row + 1) cend = row + 1;
       const int ncol = (row < a.n && cend > c0) ? (int)(cend - c0) : 0;
       // the tile's C values are fetched now and land while the MMAs run, so
       // the read-modify-write at the end of the tile waits on no load
@@ -470,7 +484,7 @@ bool make_map(CUtensorMap* m, const void* ptr, int64_t rows, int ldk, int esz, i
 
 template <int MODE>
 cudaError_t launch(float* C, int64_t ldc, int64_t n, int64_t r0, int kdim, void* const* Wops,
-                   void* const* Lops, int ldk, int* err_flag, cudaStream_t s) {
+                   void* const* Lops, int ldk, bool full, int* err_flag, cudaStream_t s) {
   using Cfg = TcCfg<MODE>;
   const int esz = MODE == kSplit3xTf32 ? 4 : 2;
   if (kdim % Cfg::kBK != 0 || kdim <= 0 || kdim > ldk) return cudaErrorInvalidValue;
@@ -499,7 +513,8 @@ cudaError_t launch(float* C, int64_t ldc, int64_t n, int64_t r0, int kdim, void*
   a.r0 = r0;
   a.kblocks = kdim / Cfg::kBK;
   a.tiles = (m + kBM - 1) / kBM;
-  a.ntiles = a.tiles * (a.tiles + 1) / 2;
+  a.ntiles = full ? a.tiles * a.tiles : a.tiles * (a.tiles + 1) / 2;
+  a.full = full ? 1 : 0;
   a.err = err_flag;
   DevInfo di;
   cudaError_t e = dev_info(&di);
@@ -514,12 +529,12 @@ cudaError_t launch(float* C, int64_t ldc, int64_t n, int64_t r0, int kdim, void*
 }  // namespace
 
 cudaError_t outer_update_tc(int mode, float* C, int64_t ldc, int64_t n, int64_t r0, int kdim,
-                            void* const* Wops, void* const* Lops, int ldk, int* err_flag,
-                            cudaStream_t s) {
+                            void* const* Wops, void* const* Lops, int ldk, bool full,
+                            int* err_flag, cudaStream_t s) {
   if (mode == kSplit3xTf32)
-    return launch<kSplit3xTf32>(C, ldc, n, r0, kdim, Wops, Lops, ldk, err_flag, s);
+    return launch<kSplit3xTf32>(C, ldc, n, r0, kdim, Wops, Lops, ldk, full, err_flag, s);
   if (mode == kSplitBf16x6)
-    return launch<kSplitBf16x6>(C, ldc, n, r0, kdim, Wops, Lops, ldk, err_flag, s);
+    return launch<kSplitBf16x6>(C, ldc, n, r0, kdim, Wops, Lops, ldk, full, err_flag, s);
   return cudaErrorInvalidValue;
 }
 

@@ -49,7 +49,10 @@ def test_workspace_sizes(L):
     assert dpp.workspace_size(0, 0, 0, 0, 1) > 0
     assert dpp.workspace_size(0, 100, 7, 0, 1) == 0  # unknown dtype
     assert dpp.workspace_size(9, 100, 0, 0, 1) == 0  # unknown op
-    assert dpp.workspace_size(1, 100, 0, 1, 0) == 0  # LU has no mixed path
+    # mixed LU: real only; its FP32 copy of K is full square
+    assert dpp.workspace_size(1, 100, 0, 1, 0) > 100 * 100 * 4
+    assert dpp.workspace_size(1, 100, 0, 2, 0) == dpp.workspace_size(1, 100, 0, 1, 0)
+    assert dpp.workspace_size(1, 100, 1, 1, 0) == 0  # no complex mixed LU
 
 
 def _call(L, K=None, n=4, ld=4, dtype=0, prec=0, keep=None, res=None, ws=None, wsb=0):
