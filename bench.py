@@ -55,6 +55,8 @@ def parse():
     p.add_argument("--streams", type=int, default=4,
                    help="draws in flight on this many streams, each launch capped at "
                         "SMs / streams CTAs")
+    p.add_argument("--suite-only", default="",
+                   help="with --suite: comma-separated subset of C1,C2,C3,C4")
     p.add_argument("--suite", action="store_true",
                    help="one JSON line per workload of the paper-shaped configurations "
                         "(FP64 n=512; n=4096 real/complex, projection/Beta; spanning trees of "
@@ -262,71 +264,120 @@ def run_suite(args):
                                               ws.data_ptr(), need, stream.cuda_stream))
         return fn, keep, raw
 
+    only = {c.strip() for c in args.suite_only.split(",") if c.strip()}
+
+    def want(c):
+        return not only or c in only
+
     # C1: FP64, n = 512, 256 draws with seeds 0..255
-    n = 512
-    Kd = torch.from_numpy(W.hermitian_kernel(n, seed=0, kind="uniform")).to(dev).contiguous()
-    fn, keep, raw = hermitian(Kd, n, "fp64")
-    ms, prof = timed(fn, 256)
-    line("C1", {"n": n, "kernel": "Haar, lam~U(0,1)", "draws": 256}, "fp64", ms, n ** 3 / 3, prof)
-    b = dpp.BatchedSampler([Kd] * 256, instance=list(range(256)))
-    ms_b, prof_b = timed(lambda s: b.draw(s), 5)
-    print(json.dumps({"suite": "C1-batched", "config": {"n": n, "instances": 256},
-                      "precision": "fp32+f64 pivots", "samples_per_s": 256e3 / ms_b,
-                      "ms_per_launch": ms_b}), flush=True)
-    del b, Kd
+    def suite_c1():
+        n = 512
+        Kd = torch.from_numpy(W.hermitian_kernel(n, seed=0, kind="uniform")).to(dev).contiguous()
+        fn, keep, raw = hermitian(Kd, n, "fp64")
+        ms, prof = timed(fn, 256)
+        line("C1", {"n": n, "kernel": "Haar, lam~U(0,1)", "draws": 256}, "fp64", ms, n ** 3 / 3, prof)
+        b = dpp.BatchedSampler([Kd] * 256, instance=list(range(256)))
+        ms_b, prof_b = timed(lambda s: b.draw(s), 5)
+        print(json.dumps({"suite": "C1-batched", "config": {"n": n, "instances": 256},
+                          "precision": "fp32+f64 pivots", "samples_per_s": 256e3 / ms_b,
+                          "ms_per_launch": ms_b}), flush=True)
+        del b, Kd
 
     # C2: n = 4096, real projection / Beta, FP64 and mixed; complex Beta FP64
-    n = 4096
-    for kind in ("projection", "beta"):
-        Kd = W.hermitian_kernel(n, seed=0, kind=kind, device=str(dev), return_torch=True).contiguous()
-        for prec_name, draws in (("fp64", 4), ("bf16x6", 16)):
-            fn, keep, raw = hermitian(Kd, n, prec_name)
-            ms, prof = timed(fn, draws)
-            res = _lib.decode_result(bytes(raw.cpu().numpy().tobytes()))
-            line("C2", {"n": n, "kind": kind, "dtype": "f64"}, prec_name, ms, n ** 3 / 3, prof,
-                 {"last_draw_kept": res["n_kept"], "last_draw_borderline": res["n_borderline"]})
-        del Kd
-    Kc = W.hermitian_kernel(n, seed=0, kind="beta", complex_=True, device=str(dev),
-                            return_torch=True).contiguous()
-    fn, keep, raw = hermitian(Kc, n, "fp64", dt=1)
-    ms, prof = timed(fn, 2, warm=1)
-    line("C2", {"n": n, "kind": "beta", "dtype": "c128"}, "fp64", ms, 4 * n ** 3 / 3, prof)
-    del Kc
+    def suite_c2():
+        n = 4096
+        for kind in ("projection", "beta"):
+            Kd = W.hermitian_kernel(n, seed=0, kind=kind, device=str(dev), return_torch=True).contiguous()
+            for prec_name, draws in (("fp64", 4), ("bf16x6", 16)):
+                fn, keep, raw = hermitian(Kd, n, prec_name)
+                ms, prof = timed(fn, draws)
+                res = _lib.decode_result(bytes(raw.cpu().numpy().tobytes()))
+                line("C2", {"n": n, "kind": kind, "dtype": "f64"}, prec_name, ms, n ** 3 / 3, prof,
+                     {"last_draw_kept": res["n_kept"], "last_draw_borderline": res["n_borderline"]})
+            del Kd
+        Kc = W.hermitian_kernel(n, seed=0, kind="beta", complex_=True, device=str(dev),
+                                return_torch=True).contiguous()
+        fn, keep, raw = hermitian(Kc, n, "fp64", dt=1)
+        ms, prof = timed(fn, 2, warm=1)
+        line("C2", {"n": n, "kind": "beta", "dtype": "c128"}, "fp64", ms, 4 * n ** 3 / 3, prof)
+        del Kc
 
     # C3: uniform spanning trees of the 64 x 64 grid (n = 8064, rank 4095)
-    d = 64
-    from oracle import oracle as O
-    K, edges, V = W.ust_grid_kernel(d, device=str(dev))
-    n = K.shape[0]
-    Kd = torch.from_numpy(K).to(dev).contiguous()
-    ref = -W.grid_spanning_tree_log_count(d)
-    for prec_name, draws in (("bf16x6", 64), ("fp64", 2)):
-        fn, keep, raw = hermitian(Kd, n, prec_name)
-        ms, prof = timed(fn, draws, warm=1)
-        k = keep.cpu().numpy().astype(bool)
-        res = _lib.decode_result(bytes(raw.cpu().numpy().tobytes()))
-        line("C3", {"grid": d, "n": n, "rank": V - 1}, prec_name, ms, n ** 3 / 3, prof,
-             {"last_draw_spanning_tree": bool(O.is_spanning_tree(edges[k], V)),
-              "last_draw_logp": res["logp"], "logp_expected": ref})
-    del Kd
+    def suite_c3():
+        d = 64
+        from oracle import oracle as O
+        K, edges, V = W.ust_grid_kernel(d, device=str(dev))
+        n = K.shape[0]
+        Kd = torch.from_numpy(K).to(dev).contiguous()
+        ref = -W.grid_spanning_tree_log_count(d)
+        for prec_name, draws in (("bf16x6", 64), ("fp64", 2)):
+            fn, keep, raw = hermitian(Kd, n, prec_name)
+            ms, prof = timed(fn, draws, warm=1)
+            k = keep.cpu().numpy().astype(bool)
+            res = _lib.decode_result(bytes(raw.cpu().numpy().tobytes()))
+            line("C3", {"grid": d, "n": n, "rank": V - 1}, prec_name, ms, n ** 3 / 3, prof,
+                 {"last_draw_spanning_tree": bool(O.is_spanning_tree(edges[k], V)),
+                  "last_draw_logp": res["logp"], "logp_expected": ref})
+        del Kd
 
-    # C4: real LU n = 8192, K = D^{-1} S D (FP64; the mixed path is Hermitian only)
-    n = 8192
-    K, S = W.lu_similarity_kernel(n, seed=0, device=str(dev))
-    Kd = torch.from_numpy(np.ascontiguousarray(K.T)).to(dev)  # column-major storage
-    need = dpp.workspace_size(1, n, 0, 0, 0)
-    ws = torch.empty(need, dtype=torch.uint8, device=dev)
-    keep = torch.empty(n, dtype=torch.uint8, device=dev)
-    raw = torch.zeros(_lib.RESULT_BYTES, dtype=torch.uint8, device=dev)
-    L = dpp.load()
+    # C4: real LU n = 8192, K = D^{-1} S D: FP64 and mixed (BF16x6 / 3xTF32)
+    def suite_c4():
+        n = 8192
+        K, S = W.lu_similarity_kernel(n, seed=0, device=str(dev))
+        Kd = torch.from_numpy(np.ascontiguousarray(K.T)).to(dev)  # column-major storage
+        L = dpp.load()
+        cfg4 = {"n": n, "kind": "D^-1 S D, lam~U(0,1), D lognormal(0,0.5)"}
 
-    def lu(seed):
-        _lib.check(L.dpp_sample_lu(Kd.data_ptr(), n, n, 0, 0, seed, 0, None, keep.data_ptr(),
-                                   None, None, raw.data_ptr(), ws.data_ptr(), need,
-                                   stream.cuda_stream))
-    ms, prof = timed(lu, 2, warm=1)
-    line("C4", {"n": n, "kind": "D^-1 S D, lam~U(0,1), D lognormal(0,0.5)"}, "fp64", ms,
-         2 * n ** 3 / 3, prof)
+        def lu_fn(prec_name, st):
+            prec = dpp.PRECISIONS[prec_name]
+            need = dpp.workspace_size(1, n, 0, prec, 0)
+            ws = torch.empty(need, dtype=torch.uint8, device=dev)
+            keep = torch.empty(n, dtype=torch.uint8, device=dev)
+            raw = torch.zeros(_lib.RESULT_BYTES, dtype=torch.uint8, device=dev)
+
+            def fn(seed):
+                _lib.check(L.dpp_sample_lu(Kd.data_ptr(), n, n, 0, prec, seed, 0, None,
+                                           keep.data_ptr(), None, None, raw.data_ptr(),
+                                           ws.data_ptr(), need, st.cuda_stream))
+            return fn, raw
+
+        for prec_name, draws in (("fp64", 2), ("bf16x6", 32), ("3xtf32", 16)):
+            fn, raw = lu_fn(prec_name, stream)
+            ms, prof = timed(fn, draws, warm=1)
+            res = _lib.decode_result(bytes(raw.cpu().numpy().tobytes()))
+            line("C4", cfg4, prec_name, ms, 2 * n ** 3 / 3, prof,
+                 {"last_draw_kept": res["n_kept"], "last_draw_borderline": res["n_borderline"],
+                  "last_draw_status": res["status"]})
+        # several mixed draws in flight, each launch on a quarter of the SMs
+        nst = 4
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        old_cap = _lib.get_tuning(_lib.DPP_TUNE_MAX_CTAS)
+        _lib.set_tuning(_lib.DPP_TUNE_MAX_CTAS, max(8, sms // nst))
+        try:
+            streams = [torch.cuda.Stream(dev) for _ in range(nst)]
+            fns = [lu_fn("bf16x6", st)[0] for st in streams]
+            draws = 32
+            for i, f in enumerate(fns):
+                f(10**6 + i)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for d in range(draws):
+                fns[d % nst](d)
+            torch.cuda.synchronize()
+            ms = (time.perf_counter() - t0) * 1e3 / draws
+        finally:
+            _lib.set_tuning(_lib.DPP_TUNE_MAX_CTAS, old_cap)
+        line("C4", dict(cfg4, streams=nst), "bf16x6", ms, 2 * n ** 3 / 3, {},
+             {"timing": "wall clock over all streams, after a device synchronize"})
+
+    if want("C1"):
+        suite_c1()
+    if want("C2"):
+        suite_c2()
+    if want("C3"):
+        suite_c3()
+    if want("C4"):
+        suite_c4()
     return 0
 
 

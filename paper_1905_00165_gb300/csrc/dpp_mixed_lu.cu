@@ -56,9 +56,12 @@ constexpr unsigned kLuFull = 0xffffffffu;
 constexpr int kLuThreads = 256;
 constexpr int kNB = kMaxOuterBlock;  // row length of the W / M operand buffers
 
-// control word: the helper has solved, against the panel with this epoch,
-// the chunk that forms the next panel
-enum { kCtlHelp = 10 };
+// control words: kCtlChunk + j holds the epoch of the last panel that the
+// outer block's chunk j (indices [q + 32 j, q + 32 j + 32)) was solved
+// against; once it reaches the epoch of panel j - 1, the chunk's rows are
+// final and the buffer Bbuf holds its diagonal block, ready for decisions.
+enum { kCtlChunk = 16 };
+constexpr int kMaxSlots = 16;  // precomputed chunks per CTA (shared memory)
 
 // Recompute state of the LU form: the Hermitian set (x0 words, v1 words,
 // inverses of the L blocks, residual r) plus the second side's.
@@ -91,6 +94,9 @@ struct LuArgs {
   unsigned epoch0;
   double tol;
   float tau0;
+  float* Bbuf;  // [32 x 32] next diagonal block, row-major
+  int nh;       // helper CTAs 1..nh (chunks of the outer block)
+  int slots;    // precomputed-chunk slots in shared memory
   LuRc lr;
 };
 
@@ -389,7 +395,7 @@ __device__ __noinline__ bool lu_serve(const LuRc& L, unsigned id) {
 }
 
 // CTAs 1..G-1: serve requests until the panel with this epoch is published.
-__device__ inline bool lu_follower(const LuRc& L, unsigned epoch, int* s_ok) {
+__device__ inline bool lu_follower(const LuRc& L, unsigned epoch, int* s_ok, unsigned max_sleep) {
   const RecomputeArgs& a = L.rc;
   __shared__ unsigned s_cmd, s_id;
   unsigned served = 0;
@@ -404,7 +410,7 @@ __device__ inline bool lu_follower(const LuRc& L, unsigned epoch, int* s_ok) {
         if (req >= ((epoch << 8) | (served + 1u))) { cmd = 1; id = req; break; }
         if ((it & 7) == 0 && rc_give_up(a, t0)) { cmd = 0; break; }
         __nanosleep(sleep);
-        if (sleep < 1024) sleep <<= 1;
+        if (sleep < max_sleep) sleep <<= 1;
       }
       __threadfence();
       s_cmd = cmd;
@@ -427,6 +433,19 @@ __device__ inline bool lu_follower(const LuRc& L, unsigned epoch, int* s_ok) {
     }
     *s_ok = 1;
     return true;
+  }
+}
+
+// Bounded wait of one thread with a short poll interval, for the waits on the
+// chain of panels (only a few CTAs poll these words).
+__device__ inline bool wait_geq_short(const RecomputeArgs& a, const unsigned* flag,
+                                      unsigned target) {
+  if (ld_acquire(flag) >= target) return true;
+  const unsigned long long t0 = global_ns();
+  for (unsigned it = 1;; ++it) {
+    if (ld_acquire(flag) >= target) return true;
+    if ((it & 15) == 0 && rc_give_up(a, t0)) return false;
+    __nanosleep(64);
   }
 }
 
@@ -480,12 +499,23 @@ struct LuSmem {
   float MB[32][33];
   float WB[32][33];
   float MA[32][33];
+  float Bp[32][33];   // next diagonal block, left-looking part
   float d[32];
   float rd[32];
 };
-constexpr size_t kLuDynSmem = sizeof(LuSmem);
+// Dynamic shared memory: LuSmem, then `slots` pairs of 32 x 33 tiles (X, Z)
+// of chunks whose left-looking part was computed before their panel.
+constexpr size_t kTileBytes = sizeof(float) * 32 * 33;
+constexpr size_t kLuBaseSmem = (sizeof(LuSmem) + 15) & ~size_t(15);
+inline size_t lu_dyn_smem(int slots) { return kLuBaseSmem + (size_t)slots * 2 * kTileBytes; }
 extern __shared__ __align__(16) unsigned char g_lu_dyn[];
 __device__ __forceinline__ LuSmem& lus() { return *reinterpret_cast<LuSmem*>(g_lu_dyn); }
+__device__ __forceinline__ float (*slot_x(int i))[33] {
+  return reinterpret_cast<float (*)[33]>(g_lu_dyn + kLuBaseSmem + (size_t)(2 * i) * kTileBytes);
+}
+__device__ __forceinline__ float (*slot_z(int i))[33] {
+  return reinterpret_cast<float (*)[33]>(g_lu_dyn + kLuBaseSmem + (size_t)(2 * i + 1) * kTileBytes);
+}
 
 // Per-outer-block bookkeeping of CTA 0.
 struct LuLog {
@@ -541,30 +571,31 @@ __device__ void load_panel(const LuArgs& a, int64_t p, int b) {
   }
 }
 
-// Chunk [c0, c0 + 32) against panel [p, p + b), left-looking over the outer
-// block's earlier columns [q, p):
-//   X[r][c] = A[c0 + r, p + c] - sum_t W[c0 + r, t] M[p + c, t]
-//   Z[r][c] = A[p + c, c0 + r] - sum_t W[p + c, t] M[c0 + r, t]   (if want_z)
-// into shared memory. Thread (r = lane, c = warp + 8 j) owns 4 + 4 outputs.
-__device__ void chunk_left(const LuArgs& a, int64_t p, int b, int64_t c0, bool want_z) {
+// Chunk [c0, c0 + 32) against panel [p, p + b), left-looking over the first
+// D columns of the outer block (the panels already solved):
+//   X[r][c] = A[c0 + r, p + c] - sum_{t < D} W[c0 + r, t] M[p + c, t]
+//   Z[r][c] = A[p + c, c0 + r] - sum_{t < D} W[p + c, t] M[c0 + r, t]   (Z given)
+// Thread (r = lane, c = warp + 8 j) owns 4 + 4 outputs; the W and M rows are
+// staged 32 deep in shared memory.
+__device__ void chunk_left(const LuArgs& a, int64_t p, int b, int64_t c0, int D, float (*X)[33],
+                           float (*Z)[33]) {
   LuSmem& S = lus();
   const int tid = threadIdx.x, r = tid & 31, cg = tid >> 5;
+  const bool want_z = Z != nullptr;
   const float* A = a.A;
   const int64_t lda = a.lda;
   const int nc = (int)((a.n - c0) < 32 ? (a.n - c0) : 32);
-  const int D = (int)(p - a.q);
   float x[4], z[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const int c = cg + 8 * j;
     x[j] = (r < nc && c < b) ? __ldcg(&A[(c0 + r) + (p + c) * lda]) : 0.f;
     // Z loaded with lanes along the panel rows (contiguous), read back below
-    if (want_z)
-      S.Z[c][r] = (c < nc && r < b) ? __ldcg(&A[(p + r) + (c0 + c) * lda]) : 0.f;
+    if (want_z) Z[c][r] = (c < nc && r < b) ? __ldcg(&A[(p + r) + (c0 + c) * lda]) : 0.f;
   }
   __syncthreads();
 #pragma unroll
-  for (int j = 0; j < 4; ++j) z[j] = want_z ? S.Z[r][cg + 8 * j] : 0.f;
+  for (int j = 0; j < 4; ++j) z[j] = want_z ? Z[r][cg + 8 * j] : 0.f;
   for (int t0 = 0; t0 < D; t0 += 32) {
     for (int idx = tid; idx < 1024; idx += kLuThreads) {
       const int rr = idx >> 5, tt = idx & 31;
@@ -591,18 +622,19 @@ __device__ void chunk_left(const LuArgs& a, int64_t p, int b, int64_t c0, bool w
   }
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    S.X[r][cg + 8 * j] = x[j];
-    if (want_z) S.Z[r][cg + 8 * j] = z[j];
+    X[r][cg + 8 * j] = x[j];
+    if (want_z) Z[r][cg + 8 * j] = z[j];
   }
   __syncthreads();
 }
 
-// Both triangular solves of a chunk against the published panel, then its
-// running-diagonal terms and the stores (L and M into A32, W and M rows into
-// the operand buffers, tensor-core splits if `splits`).
-__device__ void chunk_solve(const LuArgs& a, int64_t p, int b, int64_t c0, bool splits) {
+// Both triangular solves of a left-looked chunk (X, Z) against the published
+// panel, leaving W in X and M in Z; then its running-diagonal terms and the
+// stores (L and M into A32, W and M rows into the operand buffers, and the
+// tensor-core splits if `splits`).
+__device__ void chunk_solve(const LuArgs& a, int64_t p, int b, int64_t c0, float (*X)[33],
+                            float (*Z)[33], bool splits) {
   LuSmem& S = lus();
-  chunk_left(a, p, b, c0, true);
   const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
   const int nc = (int)((a.n - c0) < 32 ? (a.n - c0) : 32);
   const int D = (int)(p - a.q);
@@ -610,33 +642,33 @@ __device__ void chunk_solve(const LuArgs& a, int64_t p, int b, int64_t c0, bool 
     // row c0 + lane:  W M11^T = X  (forward over the panel columns)
     float y[32];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) y[c] = S.X[lane][c];
+    for (int c = 0; c < 32; ++c) y[c] = X[lane][c];
 #pragma unroll
     for (int c = 1; c < 32; ++c) {
 #pragma unroll
       for (int k = 0; k < c; ++k) y[c] = fmaf(-y[k], S.M11[c][k], y[c]);
     }
 #pragma unroll
-    for (int c = 0; c < 32; ++c) S.X[lane][c] = y[c];
+    for (int c = 0; c < 32; ++c) X[lane][c] = y[c];
   } else if (wp == 1) {
     // column c0 + lane:  L11 u = Z,  M = u / d
     float u[32];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) u[c] = S.Z[lane][c];
+    for (int c = 0; c < 32; ++c) u[c] = Z[lane][c];
 #pragma unroll
     for (int c = 1; c < 32; ++c) {
 #pragma unroll
       for (int k = 0; k < c; ++k) u[c] = fmaf(-S.L11[c][k], u[k], u[c]);
     }
 #pragma unroll
-    for (int c = 0; c < 32; ++c) S.Z[lane][c] = u[c] * S.rd[c];
+    for (int c = 0; c < 32; ++c) Z[lane][c] = u[c] * S.rd[c];
   }
   __syncthreads();
   if (wp == 0 && lane < nc) {
     f2 dsum = {0.f, 0.f};
     float ssum = 0.f;
     for (int c = 0; c < b; ++c) {
-      const float w = S.X[lane][c], m = S.Z[lane][c];
+      const float w = X[lane][c], m = Z[lane][c];
       dsum = f2_add_prod(dsum, w, m);
       ssum += fabsf(w * m);
     }
@@ -649,13 +681,13 @@ __device__ void chunk_solve(const LuArgs& a, int64_t p, int b, int64_t c0, bool 
     {
       // L = W / d, lanes along the chunk rows
       const int r = idx & 31, c = idx >> 5;
-      if (r < nc && c < b) A[(c0 + r) + (p + c) * lda] = S.X[r][c] * S.rd[c];
+      if (r < nc && c < b) A[(c0 + r) + (p + c) * lda] = X[r][c] * S.rd[c];
     }
     {
       // M^T above the diagonal and the operand rows, lanes along the panel
       const int c = idx & 31, r = idx >> 5;
       if (r < nc && c < b) {
-        const float m = S.Z[r][c], w = S.X[r][c];
+        const float m = Z[r][c], w = X[r][c];
         A[(p + c) + (c0 + r) * lda] = m;
         const int64_t off = (c0 + r) * kNB + D + c;
         a.Wk[off] = w;
@@ -670,13 +702,43 @@ __device__ void chunk_solve(const LuArgs& a, int64_t p, int b, int64_t c0, bool 
   __syncthreads();
 }
 
-// Warp 0 of CTA 0: the decisions of panel [p, p + b) on the block in S.X
-// (lane i holds row i), pivots from the running diagonal in double-float.
+// The next diagonal block from its left-looking part (S.Bp) and the chunk's
+// just-solved W (in X) and M (in Z) against the current panel, into Bbuf.
+__device__ void next_block(const LuArgs& a, float (*X)[33], float (*Z)[33], int b) {
+  LuSmem& S = lus();
+  const int tid = threadIdx.x, r = tid & 31, cg = tid >> 5;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int c = cg + 8 * j;
+    float v = S.Bp[r][c];
+    for (int t = 0; t < b; ++t) v = fmaf(-X[r][t], Z[c][t], v);
+    a.Bbuf[r * 32 + c] = v;
+  }
+  __syncthreads();
+}
+
+// Decisions of panel [p, p + b) on the block in S.X, by all 8 warps of CTA 0.
+//
+// Fast chain: warp w holds columns 4w..4w+3 of every row (lane = row) in
+// registers, so the pivot row reaches every warp by shuffles inside the warp;
+// row i's running pivot dd (double-float) and the other per-row state live in
+// lane i of the warp that owns column i. Step J: the owner of column J
+// decides on pivot J in FP32 (exact outside the borderline band, whose floor
+// exceeds the rounding of u and of the pivot) and publishes the multipliers
+// l_i = A[i][J] / d_J in shared memory (double-buffered); after one barrier
+// every warp applies the rank-1 update to its columns. At the first pivot
+// inside the band the chain stops, and warp 0 finishes the panel with the
+// rolled shared-memory loop, recomputing every band pivot in FP64.
 __device__ __noinline__ void lu_decide(const LuArgs& a, int64_t p, int b, unsigned epoch) {
   LuSmem& S = lus();
   LuLog& lg = g_lulog;
   float (*X)[33] = S.X;
-  const int lane = threadIdx.x & 31;
+  __shared__ float s_l[2][32];
+  __shared__ float s_rd[2], s_df[2];
+  __shared__ int s_stop[2];
+  __shared__ float s_ddh[32], s_ddl[32], s_si[32];
+  __shared__ unsigned char s_kp[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t i = p + lane;
   const bool vi = lane < b;
   float* A = a.A;
@@ -686,71 +748,159 @@ __device__ __noinline__ void lu_decide(const LuArgs& a, int64_t p, int b, unsign
   const float kf = vi ? (float)a.K[i + i * a.ldk] : 0.f;
   const float sq = sqrtf((float)(i + 1));
   const double u = vi ? (a.uniforms ? a.uniforms[i] : philox_uniform(a.seed, a.inst, (uint64_t)i))
-                      : 0.5;
-  int seq = 0;
+                      : 2.0;
+  const float uf = (float)u;
+  const float tau0 = a.tau0;
+  bool mykeep = false;
+  int stop = -1;
+  float v[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) v[j] = (vi && 4 * warp + j < b) ? X[lane][4 * warp + j] : 0.f;
   for (int J = 0; J < b; ++J) {
-    const double ph = (double)__shfl_sync(kLuFull, dd.hi, J) + (double)__shfl_sync(kLuFull, dd.lo, J);
-    const double uj = __shfl_sync(kLuFull, u, J);
-    const float tau = a.tau0 * __shfl_sync(kLuFull, sq, J) *
-                          (fabsf(__shfl_sync(kLuFull, kf, J)) + __shfl_sync(kLuFull, si, J)) +
-                      0x1.0p-22f;
-    double pe = ph;
-    if (fabs(uj - ph) <= (double)tau) {
-      // the factor entries of [p, p + J] so far, out to global memory
-      if (lane <= J) {
-        for (int c = 0; c <= J; ++c) A[(p + lane) + (p + c) * lda] = X[lane][c];
+    const int buf = J & 1;
+    if (warp == (J >> 2)) {
+      const float ph = __shfl_sync(kLuFull, dd.hi, J);
+      const float uj = __shfl_sync(kLuFull, uf, J);
+      const float tau = tau0 * __shfl_sync(kLuFull, sq, J) *
+                            (fabsf(__shfl_sync(kLuFull, kf, J)) + __shfl_sync(kLuFull, si, J)) +
+                        0x1.0p-22f;
+      const bool border = fabsf(uj - ph) <= tau;
+      if (!border) {
+        const bool kp = uj < ph;
+        const float df = kp ? ph : ph - 1.0f;
+        const float rd = 1.0f / df;
+        if (lane == J) {
+          if (!kp) dd = f2_add_f(dd, -1.0f);
+          mykeep = kp;
+        }
+        const int jj = J & 3;
+        const float colJ = jj == 0 ? v[0] : (jj == 1 ? v[1] : (jj == 2 ? v[2] : v[3]));
+        s_l[buf][lane] = colJ * rd;
+        if (lane == 0) {
+          s_rd[buf] = rd;
+          s_df[buf] = df;
+        }
       }
-      double est = 0.0;
-      const bool ok = lu_leader(a.lr, p + J, epoch, &seq, &pe, &est);
-      if (lane == 0) {
-        lg.border += 1;
-        const float ratio = (float)(fabs(pe - ph) / (double)tau);
-        if (ratio > lg.max_ratio) lg.max_ratio = ratio;
-        if (!ok || est > fabs(uj - pe)) lg.rc_failed = 1;
+      if (lane == 0) s_stop[buf] = border ? 1 : 0;
+    }
+    __syncthreads();
+    if (s_stop[buf]) {
+      stop = J;
+      break;
+    }
+    const float l = s_l[buf][lane];
+    const float rd = s_rd[buf], df = s_df[buf];
+    const bool act = (lane > J) && vi;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = 4 * warp + j;
+      const float pk = __shfl_sync(kLuFull, v[j], J);  // row J's entry in column c
+      float x = v[j];
+      if (act && c > J) x = fmaf(-l, pk, x);
+      if (act && c == J) x = l;
+      if (lane == J && c > J) x = pk * rd;  // M^T entries of row J
+      if (lane == J && c == J) x = df;
+      v[j] = x;
+      if (lane == c && act) {  // row c's running pivot
+        dd = f2_sub_prod(dd, l, pk);
+        si += fabsf(l * pk);
       }
-      if (!ok) pe = ph;
     }
-    const bool kp = uj < pe;
-    const double d = kp ? pe : pe - 1.0;
-    if (lane == J) {
-      a.piv[p + J] = d;
-      a.keep[p + J] = kp ? 1 : 0;
+  }
+  // hand the block and the per-row state to warp 0
+#pragma unroll
+  for (int j = 0; j < 4; ++j) X[lane][4 * warp + j] = v[j];
+  if ((lane >> 2) == warp) {
+    s_ddh[lane] = dd.hi;
+    s_ddl[lane] = dd.lo;
+    s_si[lane] = si;
+    s_kp[lane] = mykeep ? 1 : 0;
+  }
+  __syncthreads();
+  if (warp != 0) return;
+  dd = make_f2(s_ddh[lane], s_ddl[lane]);
+  si = s_si[lane];
+  mykeep = s_kp[lane] != 0;
+  if (stop >= 0) {
+    // the pivots decided so far, out to global memory for the recomputes
+    if (lane < stop) {
+      a.piv[i] = f2_to_double(dd);
+      a.keep[i] = mykeep ? 1 : 0;
     }
-    if (lane == 0) {
-      lg.d[p - a.q + J] = d;
-      lg.kp[p - a.q + J] = kp ? 1 : 0;
+    int seq = 0;
+    for (int J = stop; J < b; ++J) {
+      const double ph =
+          (double)__shfl_sync(kLuFull, dd.hi, J) + (double)__shfl_sync(kLuFull, dd.lo, J);
+      const double uj = __shfl_sync(kLuFull, u, J);
+      const float tau = a.tau0 * __shfl_sync(kLuFull, sq, J) *
+                            (fabsf(__shfl_sync(kLuFull, kf, J)) + __shfl_sync(kLuFull, si, J)) +
+                        0x1.0p-22f;
+      double pe = ph;
+      if (fabs(uj - ph) <= (double)tau) {
+        // the factor entries of [p, p + J] so far, out to global memory
+        if (lane <= J) {
+          for (int c = 0; c <= J; ++c) A[(p + lane) + (p + c) * lda] = X[lane][c];
+        }
+        double est = 0.0;
+        const bool ok = lu_leader(a.lr, p + J, epoch, &seq, &pe, &est);
+        if (lane == 0) {
+          lg.border += 1;
+          const float ratio = (float)(fabs(pe - ph) / (double)tau);
+          if (ratio > lg.max_ratio) lg.max_ratio = ratio;
+          if (!ok || est > fabs(uj - pe)) lg.rc_failed = 1;
+        }
+        if (!ok) pe = ph;
+      }
+      const bool kp = uj < pe;
+      const double d = kp ? pe : pe - 1.0;
+      if (lane == J) {
+        dd = f2_from_double(d);
+        mykeep = kp;
+        a.piv[p + J] = d;
+        a.keep[p + J] = kp ? 1 : 0;
+      }
+      const float df = (float)d;
+      const float rdf = 1.f / df;
+      if (lane > J && vi) {
+        const float l = X[lane][J] * rdf;
+        for (int c = J + 1; c < b; ++c) X[lane][c] = fmaf(-l, X[J][c], X[lane][c]);
+        const float uji = X[J][lane];  // U(p + J, p + lane), not yet scaled
+        dd = f2_sub_prod(dd, l, uji);
+        si += fabsf(l * uji);
+        X[lane][J] = l;
+      }
+      __syncwarp();
+      if (lane == J) {
+        for (int c = J + 1; c < b; ++c) X[J][c] *= rdf;
+        X[J][J] = df;
+      }
+      __syncwarp();
     }
-    const float df = (float)d;
-    const float rdf = 1.f / df;
-    if (lane > J && vi) {
-      const float l = X[lane][J] * rdf;
-      for (int c = J + 1; c < b; ++c) X[lane][c] = fmaf(-l, X[J][c], X[lane][c]);
-      const float uji = X[J][lane];  // U(p + J, p + lane), not yet scaled
-      dd = f2_sub_prod(dd, l, uji);
-      si += fabsf(l * uji);
-      X[lane][J] = l;
-    }
-    __syncwarp();
-    if (lane == J) {
-      for (int c = J + 1; c < b; ++c) X[J][c] *= rdf;
-      X[J][J] = df;
-    }
-    __syncwarp();
   }
   if (vi) {
+    const double d = f2_to_double(dd);
+    a.piv[i] = d;
+    a.keep[i] = mykeep ? 1 : 0;
+    lg.d[p - a.q + lane] = d;
+    lg.kp[p - a.q + lane] = mykeep ? 1 : 0;
     for (int c = 0; c < b; ++c) A[i + (p + c) * lda] = X[lane][c];
   }
   __syncwarp();
 }
 
+__device__ __forceinline__ int chunk_owner(int j, int nh) { return 1 + (j - 1) % nh; }
+
 __global__ void __launch_bounds__(kLuThreads, 1) k_lu_outer(LuArgs a) {
+  LuSmem& S = lus();
   int& s_ok = g_lu_ok;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int np = (a.kb + 31) / 32;
-  const int64_t qe = a.q + a.kb;
+  const int64_t q = a.q, qe = q + a.kb;
   const RecomputeArgs& rc = a.lr.rc;
+  const int nh = a.nh;
 
   if (blockIdx.x == 0) {
+    // ---- decisions, panel by panel ----
     LuLog& lg = g_lulog;
     if (tid == 0) {
       lg.border = 0;
@@ -759,20 +909,24 @@ __global__ void __launch_bounds__(kLuThreads, 1) k_lu_outer(LuArgs a) {
     }
     __syncthreads();
     bool alive = true;
-    for (int k = 0; k < np && alive; ++k) {
-      const int64_t p = a.q + 32 * k;
+    for (int k = 0; k < np; ++k) {
+      const int64_t p = q + 32 * k;
       const int b = (int)((qe - p) < 32 ? (qe - p) : 32);
       const unsigned epoch = a.epoch0 + (unsigned)k;
-      if (k > 0) {
-        if (tid == 0) s_ok = rc_wait_geq(rc, &rc.ctrl[kCtlHelp], epoch - 1) ? 1 : 0;
+      if (k == 0) {
+        chunk_left(a, p, b, p, 0, S.X, nullptr);
+      } else {
+        // the chunk's owner has solved it against panel k - 1 and formed the block
+        if (tid == 0) s_ok = wait_geq_short(rc, &rc.ctrl[kCtlChunk + k], epoch - 1) ? 1 : 0;
         __syncthreads();
         if (!s_ok) {
           alive = false;
           break;
         }
+        for (int idx = tid; idx < 1024; idx += kLuThreads) S.X[idx >> 5][idx & 31] = __ldcg(&a.Bbuf[idx]);
+        __syncthreads();
       }
-      chunk_left(a, p, b, p, false);
-      if (warp == 0) lu_decide(a, p, b, epoch);
+      lu_decide(a, p, b, epoch);
       __syncthreads();
       if (tid == 0) {
         __threadfence();
@@ -833,26 +987,76 @@ __global__ void __launch_bounds__(kLuThreads, 1) k_lu_outer(LuArgs a) {
     return;
   }
 
-  const bool helper = blockIdx.x == 1;
-  const int64_t nwk = (int64_t)gridDim.x - 2, w = (int64_t)blockIdx.x - 2;
+  if (blockIdx.x <= nh) {
+    // ---- helper h: the outer block's chunks j with owner h, in order ----
+    const int h = blockIdx.x;
+    for (int k = 0; k < np; ++k) {
+      const int64_t p = q + 32 * k;
+      const int b = (int)((qe - p) < 32 ? (qe - p) : 32);
+      const unsigned epoch = a.epoch0 + (unsigned)k;
+      const int D = 32 * k;
+      if (k > 0) {
+        // the panel's own rows are final through panel k - 1
+        if (tid == 0) s_ok = wait_geq_short(rc, &rc.ctrl[kCtlChunk + k], epoch - 1) ? 1 : 0;
+        __syncthreads();
+        if (!s_ok) return;
+      }
+      // before the panel is published: the left-looking parts
+      int ns = 0;
+      for (int j = k + 1; j < np; ++j) {
+        if (chunk_owner(j, nh) != h) continue;
+        chunk_left(a, p, b, q + 32 * j, D, slot_x(ns), slot_z(ns));
+        if (j == k + 1) {
+          const int bj = (int)((qe - (q + 32 * j)) < 32 ? (qe - (q + 32 * j)) : 32);
+          chunk_left(a, q + 32 * j, bj, q + 32 * j, D, S.Bp, nullptr);
+        }
+        ++ns;
+      }
+      if (!lu_follower(a.lr, epoch, &s_ok, 128)) return;
+      load_panel(a, p, b);
+      __syncthreads();
+      ns = 0;
+      for (int j = k + 1; j < np; ++j) {
+        if (chunk_owner(j, nh) != h) continue;
+        chunk_solve(a, p, b, q + 32 * j, slot_x(ns), slot_z(ns), false);
+        if (j == k + 1) next_block(a, slot_x(ns), slot_z(ns), b);
+        if (tid == 0) {
+          __threadfence();
+          st_release(&rc.ctrl[kCtlChunk + j], epoch);
+        }
+        ++ns;
+      }
+      __syncthreads();
+    }
+    return;
+  }
+
+  // ---- workers: chunks beyond the outer block ----
+  const int64_t nwk = (int64_t)gridDim.x - nh - 1, w = (int64_t)blockIdx.x - nh - 1;
   for (int k = 0; k < np; ++k) {
-    const int64_t p = a.q + 32 * k;
+    const int64_t p = q + 32 * k;
     const int b = (int)((qe - p) < 32 ? (qe - p) : 32);
     const unsigned epoch = a.epoch0 + (unsigned)k;
-    if (!lu_follower(a.lr, epoch, &s_ok)) return;
+    const int D = 32 * k;
+    if (k > 0) {
+      if (tid == 0) s_ok = rc_wait_geq(rc, &rc.ctrl[kCtlChunk + k], epoch - 1) ? 1 : 0;
+      __syncthreads();
+      if (!s_ok) return;
+    }
+    int m = 0;
+    for (int64_t c0 = qe + 32 * w; c0 < a.n && m < a.slots; c0 += 32 * nwk, ++m)
+      chunk_left(a, p, b, c0, D, slot_x(m), slot_z(m));
+    if (!lu_follower(a.lr, epoch, &s_ok, 1024)) return;
     load_panel(a, p, b);
     __syncthreads();
-    if (helper) {
-      for (int64_t c0 = p + b; c0 < qe; c0 += 32) {
-        chunk_solve(a, p, b, c0, false);
-        if (c0 == p + b && tid == 0) {
-          __threadfence();
-          st_release(&rc.ctrl[kCtlHelp], epoch);
-        }
+    m = 0;
+    for (int64_t c0 = qe + 32 * w; c0 < a.n; c0 += 32 * nwk, ++m) {
+      if (m < a.slots) {
+        chunk_solve(a, p, b, c0, slot_x(m), slot_z(m), true);
+      } else {
+        chunk_left(a, p, b, c0, D, S.X, S.Z);
+        chunk_solve(a, p, b, c0, S.X, S.Z, true);
       }
-      if (p + b >= qe && tid == 0) st_release(&rc.ctrl[kCtlHelp], epoch);
-    } else {
-      for (int64_t c0 = qe + 32 * w; c0 < a.n; c0 += 32 * nwk) chunk_solve(a, p, b, c0, true);
     }
     __syncthreads();
   }
@@ -893,6 +1097,7 @@ struct LuLayout {
   double *kd, *s, *piv;
   unsigned* flag;
   int* err;
+  float* Bbuf;
   RecomputeScratch rs;
   unsigned long long *yw, *v2w;
   float* inv2;
@@ -918,12 +1123,14 @@ bool carve_lu(Workspace& ws, int64_t n, LuLayout* L) {
   L->piv = static_cast<double*>(ws.take(sizeof(double) * nn));
   L->flag = static_cast<unsigned*>(ws.take(256));
   L->err = reinterpret_cast<int*>(L->flag) + 16;
+  L->Bbuf = static_cast<float*>(ws.take(sizeof(float) * 1024));
   if (!recompute_carve(ws, n, &L->rs)) return false;
   L->yw = static_cast<unsigned long long*>(ws.take(sizeof(unsigned long long) * nn));
   L->v2w = static_cast<unsigned long long*>(ws.take(sizeof(unsigned long long) * nn));
   L->inv2 = static_cast<float*>(ws.take(sizeof(float) * 1024 * (size_t)L->rs.nblk));
   L->s2 = static_cast<double*>(ws.take(sizeof(double) * nn));
-  return L->A32 && L->Wk && L->Mk && ops_ok && L->kd && L->s && L->piv && L->flag && L->yw &&
+  return L->A32 && L->Wk && L->Mk && ops_ok && L->kd && L->s && L->piv && L->flag && L->Bbuf &&
+         L->yw &&
          L->v2w && L->inv2 && L->s2;
 }
 
@@ -960,13 +1167,13 @@ cudaError_t sample_mixed_lu(const DrawArgs& a, Workspace ws) {
   static int cap = 0;
   if (cap == 0) {
     cudaError_t ea = cudaFuncSetAttribute(k_lu_outer, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)kLuDynSmem);
+                                          (int)lu_dyn_smem(kMaxSlots));
     if (ea != cudaSuccess) return ea;
     DevInfo di;
     if ((ea = dev_info(&di)) != cudaSuccess) return ea;
     int per_sm = 0;
     ea = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lu_outer, kLuThreads,
-                                                       kLuDynSmem);
+                                                       lu_dyn_smem(kMaxSlots));
     if (ea != cudaSuccess) return ea;
     cap = per_sm * di.sm_count;
     if (cap > kMaxCoopCtas) cap = kMaxCoopCtas;
@@ -975,6 +1182,16 @@ cudaError_t sample_mixed_lu(const DrawArgs& a, Workspace ws) {
   int grid = cap;
   if (g_tuning.max_ctas > 0 && grid > g_tuning.max_ctas) grid = g_tuning.max_ctas;
   if (grid < 3) grid = 3;
+  // CTA 0 decides, CTAs 1..nh own the outer block's chunks, the rest the
+  // chunks beyond it; slots hold the chunks a CTA precomputes per panel
+  const int nh = grid - 2 < kMaxOuterBlock / 32 - 1 ? grid - 2 : kMaxOuterBlock / 32 - 1;
+  const int64_t nwk = grid - 1 - nh;
+  const int64_t trail = ((n > NB ? n - NB : 0) + 31) / 32;
+  int slots = (int)((trail + nwk - 1) / nwk);
+  const int hslots = (kMaxOuterBlock / 32 - 1 + nh - 1) / nh;
+  if (slots < hslots) slots = hslots;
+  if (slots > kMaxSlots) slots = kMaxSlots;
+  const size_t dyn = lu_dyn_smem(slots);
   const int split = a.precision == DPP_PREC_BF16X6 ? kSplitBf16x6 : kSplit3xTf32;
   unsigned epoch = 1;
   for (int64_t q = 0; q < n; q += NB) {
@@ -1005,6 +1222,9 @@ cudaError_t sample_mixed_lu(const DrawArgs& a, Workspace ws) {
     la.epoch0 = epoch;
     la.tol = 1e-3;
     la.tau0 = (float)(g_tuning.tau_safety * 0x1.0p-22);
+    la.Bbuf = L.Bbuf;
+    la.nh = nh;
+    la.slots = slots;
     la.lr.rc = recompute_args(L.rs, K, a.ld, L.A32, L.ld32, L.piv, a.keep, n, q, a.result);
     la.lr.rc.grid = grid;
     la.lr.yw = L.yw;
@@ -1015,7 +1235,7 @@ cudaError_t sample_mixed_lu(const DrawArgs& a, Workspace ws) {
     {
       ProfScope ps(kProfPanel, a.stream);
       e = cudaLaunchCooperativeKernel((const void*)k_lu_outer, dim3((unsigned)grid),
-                                      dim3(kLuThreads), args, kLuDynSmem, a.stream);
+                                      dim3(kLuThreads), args, dyn, a.stream);
     }
     if (e != cudaSuccess) return e;
     epoch += (unsigned)((kb + 31) / 32);
