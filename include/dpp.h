@@ -286,12 +286,23 @@ dpp_status dpp_logprob_backward_batched(int32_t batch, const int64_t* n,
  *                         else 8..4096, at most one per SM). With half the SMs,
  *                         two draws on two streams can overlap one draw's
  *                         latency-bound panels with the other's update.
+ *   DPP_TUNE_PANEL_PIPELINE  mixed Hermitian path, panel kernel: 1 = single
+ *                         helper (CTA 0 decides with one warp while its other
+ *                         warps prepare the next block, CTA 1 streams the outer
+ *                         block's rows), 2 = chunked (CTA 0 decides with all
+ *                         its warps, helper CTAs own the outer block's 32-row
+ *                         chunks, left-looking products are computed before
+ *                         each panel is published; the LU path's kernel),
+ *                         0 = automatic (the default): chunked when a launch
+ *                         gets at least 96 CTAs, else single helper. The SIMT
+ *                         trailing update always runs with pipeline 1.
  * Returns DPP_ERR_INVALID_ARG for an unknown key or out-of-range value. */
 typedef enum {
   DPP_TUNE_TAU_SAFETY = 0,
   DPP_TUNE_OUTER_BLOCK = 1,
   DPP_TUNE_UPDATE_KERNEL = 2,
-  DPP_TUNE_MAX_CTAS = 3
+  DPP_TUNE_MAX_CTAS = 3,
+  DPP_TUNE_PANEL_PIPELINE = 4
 } dpp_tune_key;
 
 dpp_status dpp_set_tuning(int32_t key, double value);

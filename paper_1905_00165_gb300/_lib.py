@@ -134,6 +134,7 @@ def profile_stop() -> dict:
 
 
 DPP_TUNE_TAU_SAFETY, DPP_TUNE_OUTER_BLOCK, DPP_TUNE_UPDATE_KERNEL, DPP_TUNE_MAX_CTAS = 0, 1, 2, 3
+DPP_TUNE_PANEL_PIPELINE = 4
 
 
 def set_tuning(key: int, value: float) -> None:

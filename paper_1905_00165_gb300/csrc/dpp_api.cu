@@ -87,8 +87,11 @@ size_t dpp_workspace_size(int32_t op, int64_t n, int32_t dtype, int32_t precisio
   switch (op) {
     case DPP_OP_SAMPLE_HERMITIAN:
       if (precision == DPP_PREC_FP64) return ws_fp64(n, dtype, true, true);
-      if ((precision == DPP_PREC_3XTF32 || precision == DPP_PREC_BF16X6) && dtype == DPP_R64)
-        return ws_mixed(n);
+      if ((precision == DPP_PREC_3XTF32 || precision == DPP_PREC_BF16X6) && dtype == DPP_R64) {
+        // either panel pipeline may run
+        const size_t a = ws_mixed(n), b = ws_mixed_lu(n);
+        return a > b ? a : b;
+      }
       return 0;
     case DPP_OP_SAMPLE_LU:
       if (precision == DPP_PREC_FP64) return ws_fp64(n, dtype, false, true);
@@ -138,7 +141,14 @@ static dpp_status sample_common(bool hermitian, const void* K, int64_t n, int64_
       // the mixed path reads K in FP64 for recomputes: it must stay intact
       return fail(DPP_ERR_INVALID_ARG, "mixed precision cannot factor in place (factor_out == K)");
     }
-    e = hermitian ? sample_mixed(a, ws) : sample_mixed_lu(a, ws);
+    if (!hermitian)
+      e = sample_mixed_lu(a, ws);
+    else if (g_tuning.update_kernel == 0 &&
+             (g_tuning.panel_pipeline == 2 ||
+              (g_tuning.panel_pipeline == 0 && (g_tuning.max_ctas == 0 || g_tuning.max_ctas >= 96))))
+      e = sample_mixed_chunked(a, ws);
+    else
+      e = sample_mixed(a, ws);
   }
   if (e != cudaSuccess) return fail_cuda(e, hermitian ? "dpp_sample_hermitian" : "dpp_sample_lu");
   return DPP_OK;
@@ -291,6 +301,11 @@ dpp_status dpp_set_tuning(int32_t key, double value) {
       g_tuning.max_ctas = v;
       return DPP_OK;
     }
+    case DPP_TUNE_PANEL_PIPELINE:
+      if (value != 0.0 && value != 1.0 && value != 2.0)
+        return fail(DPP_ERR_INVALID_ARG, "panel pipeline is 0, 1 or 2");
+      g_tuning.panel_pipeline = (int)value;
+      return DPP_OK;
     default:
       return fail(DPP_ERR_INVALID_ARG, "unknown tuning key");
   }
@@ -302,6 +317,7 @@ double dpp_get_tuning(int32_t key) {
     case DPP_TUNE_OUTER_BLOCK: return (double)g_tuning.outer_block;
     case DPP_TUNE_UPDATE_KERNEL: return (double)g_tuning.update_kernel;
     case DPP_TUNE_MAX_CTAS: return (double)g_tuning.max_ctas;
+    case DPP_TUNE_PANEL_PIPELINE: return (double)g_tuning.panel_pipeline;
     default: return -1.0;
   }
 }

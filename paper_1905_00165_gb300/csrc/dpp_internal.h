@@ -68,6 +68,7 @@ struct Tuning {
   int outer_block = 256;    // mixed path: columns contracted per trailing update
   int update_kernel = 0;    // 0 = tcgen05, 1 = SIMT FP32
   int max_ctas = 0;         // mixed path: CTAs per launch (0 = one per SM)
+  int panel_pipeline = 0;   // mixed Hermitian path: 0 = auto, 1 = single helper, 2 = chunked
 };
 extern Tuning g_tuning;
 constexpr int kMaxOuterBlock = 256;
@@ -76,9 +77,11 @@ constexpr int kMaxOuterBlock = 256;
 size_t ws_mixed(int64_t n);
 cudaError_t sample_mixed(const DrawArgs& a, Workspace ws);
 
-// Mixed-precision general (LU) sampler (dpp_mixed_lu.cu).
+// Mixed-precision general (LU) sampler, and the Hermitian sampler on the same
+// chunked panel pipeline (dpp_mixed_lu.cu).
 size_t ws_mixed_lu(int64_t n);
 cudaError_t sample_mixed_lu(const DrawArgs& a, Workspace ws);
+cudaError_t sample_mixed_chunked(const DrawArgs& a, Workspace ws);
 
 // Operand splits of the tensor-core trailing update.
 enum { kSplit3xTf32 = 0, kSplitBf16x6 = 1 };

@@ -394,7 +394,9 @@ __device__ __noinline__ bool lu_serve(const LuRc& L, unsigned id) {
   return live && ld_acquire(&a.ctrl[kCtlAbort]) == 0;
 }
 
-// CTAs 1..G-1: serve requests until the panel with this epoch is published.
+// CTAs 1..G-1: serve requests until the panel with this epoch is published
+// (SYM: the one-sided recompute of the Hermitian form).
+template <bool SYM>
 __device__ inline bool lu_follower(const LuRc& L, unsigned epoch, int* s_ok, unsigned max_sleep) {
   const RecomputeArgs& a = L.rc;
   __shared__ unsigned s_cmd, s_id;
@@ -424,7 +426,7 @@ __device__ inline bool lu_follower(const LuRc& L, unsigned epoch, int* s_ok, uns
       return false;
     }
     if (cmd == 1) {
-      if (!lu_serve(L, id)) {
+      if (!(SYM ? recompute_serve(a, id) : lu_serve(L, id))) {
         *s_ok = 0;
         return false;
       }
@@ -491,8 +493,12 @@ __device__ inline bool lu_leader(const LuRc& L, int64_t g, unsigned epoch, int* 
 // Panel kernel
 // ---------------------------------------------------------------------------
 struct LuSmem {
+  float d[32];
+  float rd[32];
   float L11[32][33];  // L of the current panel's diagonal block (strictly lower)
   float M11[32][33];  // M of the same block (strictly lower)
+  // from here on, ten contiguous 32 x 33 tiles; the worker CTAs use them as
+  // one staging area (wstage) instead
   float X[32][33];    // chunk rows x panel columns (then W)
   float Z[32][33];    // chunk columns x panel rows, transposed (then M)
   float WA[32][33];   // staged 32-deep slices of the left-looking products
@@ -500,8 +506,7 @@ struct LuSmem {
   float WB[32][33];
   float MA[32][33];
   float Bp[32][33];   // next diagonal block, left-looking part
-  float d[32];
-  float rd[32];
+  float E[3][32][33];
 };
 // Dynamic shared memory: LuSmem, then `slots` pairs of 32 x 33 tiles (X, Z)
 // of chunks whose left-looking part was computed before their panel.
@@ -516,6 +521,8 @@ __device__ __forceinline__ float (*slot_x(int i))[33] {
 __device__ __forceinline__ float (*slot_z(int i))[33] {
   return reinterpret_cast<float (*)[33]>(g_lu_dyn + kLuBaseSmem + (size_t)(2 * i + 1) * kTileBytes);
 }
+// Worker staging: 128 chunk rows of W and of M, 32 panel rows of M and of W.
+__device__ __forceinline__ float (*wstage(int row))[33] { return &lus().X[0] + row; }
 
 // Per-outer-block bookkeeping of CTA 0.
 struct LuLog {
@@ -554,14 +561,19 @@ __device__ inline void write_split(int split, void* const* ops, int64_t off, flo
 
 // The published panel [p, p + b): L11, M11 and the FP32 pivots into shared
 // memory (identity beyond b).
+template <bool SYM>
 __device__ void load_panel(const LuArgs& a, int64_t p, int b) {
   LuSmem& S = lus();
   const float* A = a.A;
   for (int idx = threadIdx.x; idx < 1024; idx += kLuThreads) {
     const int r = idx & 31, c = idx >> 5;
-    const float v = (r < b && c < b && r != c) ? __ldcg(&A[(p + r) + (p + c) * a.lda]) : 0.f;
+    const float v = (r < b && c < b && r != c && (!SYM || r > c))
+                        ? __ldcg(&A[(p + r) + (p + c) * a.lda]) : 0.f;
     S.L11[r][c] = r > c ? v : 0.f;  // L(p + r, p + c)
-    S.M11[c][r] = c > r ? v : 0.f;  // M(p + c, p + r) = A[p + r, p + c]
+    if (SYM)
+      S.M11[r][c] = r > c ? v : 0.f;  // M = L
+    else
+      S.M11[c][r] = c > r ? v : 0.f;  // M(p + c, p + r) = A[p + r, p + c]
   }
   if (threadIdx.x < 32) {
     const int c = threadIdx.x;
@@ -577,6 +589,7 @@ __device__ void load_panel(const LuArgs& a, int64_t p, int b) {
 //   Z[r][c] = A[p + c, c0 + r] - sum_{t < D} W[p + c, t] M[c0 + r, t]   (Z given)
 // Thread (r = lane, c = warp + 8 j) owns 4 + 4 outputs; the W and M rows are
 // staged 32 deep in shared memory.
+template <bool SYM>
 __device__ void chunk_left(const LuArgs& a, int64_t p, int b, int64_t c0, int D, float (*X)[33],
                            float (*Z)[33]) {
   LuSmem& S = lus();
@@ -589,7 +602,13 @@ __device__ void chunk_left(const LuArgs& a, int64_t p, int b, int64_t c0, int D,
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const int c = cg + 8 * j;
-    x[j] = (r < nc && c < b) ? __ldcg(&A[(c0 + r) + (p + c) * lda]) : 0.f;
+    if (SYM && c0 == p) {
+      // diagonal block: only its lower triangle is stored
+      const int hi = r > c ? r : c, lo = r > c ? c : r;
+      x[j] = (r < nc && c < b) ? __ldcg(&A[(p + hi) + (p + lo) * lda]) : 0.f;
+    } else {
+      x[j] = (r < nc && c < b) ? __ldcg(&A[(c0 + r) + (p + c) * lda]) : 0.f;
+    }
     // Z loaded with lanes along the panel rows (contiguous), read back below
     if (want_z) Z[c][r] = (c < nc && r < b) ? __ldcg(&A[(p + r) + (c0 + c) * lda]) : 0.f;
   }
@@ -632,6 +651,7 @@ __device__ void chunk_left(const LuArgs& a, int64_t p, int b, int64_t c0, int D,
 // panel, leaving W in X and M in Z; then its running-diagonal terms and the
 // stores (L and M into A32, W and M rows into the operand buffers, and the
 // tensor-core splits if `splits`).
+template <bool SYM>
 __device__ void chunk_solve(const LuArgs& a, int64_t p, int b, int64_t c0, float (*X)[33],
                             float (*Z)[33], bool splits) {
   LuSmem& S = lus();
@@ -650,7 +670,7 @@ __device__ void chunk_solve(const LuArgs& a, int64_t p, int b, int64_t c0, float
     }
 #pragma unroll
     for (int c = 0; c < 32; ++c) X[lane][c] = y[c];
-  } else if (wp == 1) {
+  } else if (!SYM && wp == 1) {
     // column c0 + lane:  L11 u = Z,  M = u / d
     float u[32];
 #pragma unroll
@@ -664,6 +684,14 @@ __device__ void chunk_solve(const LuArgs& a, int64_t p, int b, int64_t c0, float
     for (int c = 0; c < 32; ++c) Z[lane][c] = u[c] * S.rd[c];
   }
   __syncthreads();
+  if (SYM) {
+    // M = L = W / d
+    for (int idx = tid; idx < 1024; idx += kLuThreads) {
+      const int c = idx & 31, r = idx >> 5;
+      Z[r][c] = X[r][c] * S.rd[c];
+    }
+    __syncthreads();
+  }
   if (wp == 0 && lane < nc) {
     f2 dsum = {0.f, 0.f};
     float ssum = 0.f;
@@ -688,7 +716,7 @@ __device__ void chunk_solve(const LuArgs& a, int64_t p, int b, int64_t c0, float
       const int c = idx & 31, r = idx >> 5;
       if (r < nc && c < b) {
         const float m = Z[r][c], w = X[r][c];
-        A[(p + c) + (c0 + r) * lda] = m;
+        if (!SYM) A[(p + c) + (c0 + r) * lda] = m;
         const int64_t off = (c0 + r) * kNB + D + c;
         a.Wk[off] = w;
         a.Mk[off] = m;
@@ -717,6 +745,183 @@ __device__ void next_block(const LuArgs& a, float (*X)[33], float (*Z)[33], int 
   __syncthreads();
 }
 
+// Left-looking parts of the cnt chunks c_m = c_first + m c_stride (m < cnt)
+// against panel [p, p + b) over the first D columns of the outer block, into
+// slots 0..cnt-1 (same definitions as chunk_left). The chunks' rows form one
+// tall operand: per 32-deep step the panel rows are staged once, then 128
+// chunk rows at a time, and each thread accumulates a 4 x 4 block.
+template <bool SYM>
+__device__ void chunks_left(const LuArgs& a, int64_t p, int b, int D, int64_t c_first,
+                            int64_t c_stride, int cnt) {
+  const int tid = threadIdx.x;
+  const float* A = a.A;
+  const int64_t lda = a.lda, n = a.n;
+  for (int m = 0; m < cnt; ++m) {
+    const int64_t c0 = c_first + m * c_stride;
+    const int nc = (int)((n - c0) < 32 ? (n - c0) : 32);
+    float (*X)[33] = slot_x(m);
+    float (*Z)[33] = slot_z(m);
+    for (int idx = tid; idx < 1024; idx += kLuThreads) {
+      const int lo = idx & 31, hi = idx >> 5;
+      X[lo][hi] = (lo < nc && hi < b) ? __ldcg(&A[(c0 + lo) + (p + hi) * lda]) : 0.f;
+      if (!SYM) Z[hi][lo] = (hi < nc && lo < b) ? __ldcg(&A[(p + lo) + (c0 + hi) * lda]) : 0.f;
+    }
+  }
+  __syncthreads();
+  float (*WA4)[33] = wstage(0);
+  float (*MA4)[33] = wstage(128);
+  float (*MB)[33] = wstage(256);
+  float (*WB)[33] = wstage(288);
+  const int ty = tid >> 3, tx = tid & 7;
+  for (int t0 = 0; t0 < D; t0 += 32) {
+    for (int idx = tid; idx < 1024; idx += kLuThreads) {
+      const int rr = idx >> 5, tt = idx & 31;
+      MB[rr][tt] = rr < b ? __ldcg(&a.Mk[(p + rr) * kNB + t0 + tt]) : 0.f;
+      if (!SYM) WB[rr][tt] = rr < b ? __ldcg(&a.Wk[(p + rr) * kNB + t0 + tt]) : 0.f;
+    }
+    for (int m0 = 0; m0 < cnt; m0 += 4) {
+      for (int idx = tid; idx < 4096; idx += kLuThreads) {
+        const int rr = idx >> 5, tt = idx & 31;
+        const int m = m0 + (rr >> 5);
+        const int64_t row = c_first + m * c_stride + (rr & 31);
+        const bool ok = m < cnt && row < n;
+        WA4[rr][tt] = ok ? __ldcg(&a.Wk[row * kNB + t0 + tt]) : 0.f;
+        if (!SYM) MA4[rr][tt] = ok ? __ldcg(&a.Mk[row * kNB + t0 + tt]) : 0.f;
+      }
+      __syncthreads();
+      float ax[4][4], az[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ax[i][j] = az[i][j] = 0.f;
+#pragma unroll 4
+      for (int tt = 0; tt < 32; ++tt) {
+        float wa[4], mb[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) wa[i] = WA4[4 * ty + i][tt];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) mb[j] = MB[4 * tx + j][tt];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) ax[i][j] = fmaf(wa[i], mb[j], ax[i][j]);
+        if (!SYM) {
+          float ma[4], wb[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) ma[i] = MA4[4 * ty + i][tt];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) wb[j] = WB[4 * tx + j][tt];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) az[i][j] = fmaf(ma[i], wb[j], az[i][j]);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int rr = 4 * ty + i, m = m0 + (rr >> 5), r = rr & 31;
+        if (m < cnt) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            slot_x(m)[r][4 * tx + j] -= ax[i][j];
+            if (!SYM) slot_z(m)[r][4 * tx + j] -= az[i][j];
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Solves and stores of the cnt left-looked chunks in slots 0..cnt-1 against
+// the published panel (as chunk_solve, one warp per chunk side).
+template <bool SYM>
+__device__ void chunks_solve(const LuArgs& a, int64_t p, int b, int64_t c_first, int64_t c_stride,
+                             int cnt) {
+  LuSmem& S = lus();
+  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+  const int64_t n = a.n;
+  const int D = (int)(p - a.q);
+  const int ntask = SYM ? cnt : 2 * cnt;
+  for (int task = wp; task < ntask; task += kLuThreads / 32) {
+    const int m = SYM ? task : task >> 1;
+    if (SYM || (task & 1) == 0) {
+      float (*X)[33] = slot_x(m);
+      float y[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) y[c] = X[lane][c];
+#pragma unroll
+      for (int c = 1; c < 32; ++c) {
+#pragma unroll
+        for (int k = 0; k < c; ++k) y[c] = fmaf(-y[k], S.M11[c][k], y[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < 32; ++c) X[lane][c] = y[c];
+      if (SYM) {
+        float (*Z)[33] = slot_z(m);
+#pragma unroll
+        for (int c = 0; c < 32; ++c) Z[lane][c] = y[c] * S.rd[c];
+      }
+    } else {
+      float (*Z)[33] = slot_z(m);
+      float u[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) u[c] = Z[lane][c];
+#pragma unroll
+      for (int c = 1; c < 32; ++c) {
+#pragma unroll
+        for (int k = 0; k < c; ++k) u[c] = fmaf(-S.L11[c][k], u[k], u[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < 32; ++c) Z[lane][c] = u[c] * S.rd[c];
+    }
+  }
+  __syncthreads();
+  // running diagonal: one thread per chunk row
+  for (int e = tid; e < 32 * cnt; e += kLuThreads) {
+    const int m = e >> 5, r = e & 31;
+    const int64_t row = c_first + m * c_stride + r;
+    if (row < n) {
+      f2 dsum = {0.f, 0.f};
+      float ssum = 0.f;
+      for (int c = 0; c < b; ++c) {
+        const float w = slot_x(m)[r][c], mm = slot_z(m)[r][c];
+        dsum = f2_add_prod(dsum, w, mm);
+        ssum += fabsf(w * mm);
+      }
+      a.kd[row] -= f2_to_double(dsum);
+      a.s[row] += (double)ssum;
+    }
+  }
+  float* A = a.A;
+  const int64_t lda = a.lda;
+  for (int m = 0; m < cnt; ++m) {
+    const int64_t c0 = c_first + m * c_stride;
+    const int nc = (int)((n - c0) < 32 ? (n - c0) : 32);
+    float (*X)[33] = slot_x(m);
+    float (*Z)[33] = slot_z(m);
+    for (int idx = tid; idx < 1024; idx += kLuThreads) {
+      {
+        const int r = idx & 31, c = idx >> 5;
+        if (r < nc && c < b) A[(c0 + r) + (p + c) * lda] = X[r][c] * S.rd[c];
+      }
+      {
+        const int c = idx & 31, r = idx >> 5;
+        if (r < nc && c < b) {
+          const float mm = Z[r][c], w = X[r][c];
+          if (!SYM) A[(p + c) + (c0 + r) * lda] = mm;
+          const int64_t off = (c0 + r) * kNB + D + c;
+          a.Wk[off] = w;
+          a.Mk[off] = mm;
+          write_split(a.split, a.Wop, off, w);
+          write_split(a.split, a.Mop, off, mm);
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
 // Decisions of panel [p, p + b) on the block in S.X, by all 8 warps of CTA 0.
 //
 // Fast chain: warp w holds columns 4w..4w+3 of every row (lane = row) in
@@ -729,6 +934,7 @@ __device__ void next_block(const LuArgs& a, float (*X)[33], float (*Z)[33], int 
 // every warp applies the rank-1 update to its columns. At the first pivot
 // inside the band the chain stops, and warp 0 finishes the panel with the
 // rolled shared-memory loop, recomputing every band pivot in FP64.
+template <bool SYM>
 __device__ __noinline__ void lu_decide(const LuArgs& a, int64_t p, int b, unsigned epoch) {
   LuSmem& S = lus();
   LuLog& lg = g_lulog;
@@ -837,12 +1043,18 @@ __device__ __noinline__ void lu_decide(const LuArgs& a, int64_t p, int b, unsign
                         0x1.0p-22f;
       double pe = ph;
       if (fabs(uj - ph) <= (double)tau) {
-        // the factor entries of [p, p + J] so far, out to global memory
-        if (lane <= J) {
-          for (int c = 0; c <= J; ++c) A[(p + lane) + (p + c) * lda] = X[lane][c];
-        }
         double est = 0.0;
-        const bool ok = lu_leader(a.lr, p + J, epoch, &seq, &pe, &est);
+        bool ok;
+        if (SYM) {
+          // the Hermitian recompute writes the block's rows itself
+          ok = recompute_leader(a.lr.rc, X, b, p, J, epoch, &seq, &pe, &est);
+        } else {
+          // the factor entries of [p, p + J] so far, out to global memory
+          if (lane <= J) {
+            for (int c = 0; c <= J; ++c) A[(p + lane) + (p + c) * lda] = X[lane][c];
+          }
+          ok = lu_leader(a.lr, p + J, epoch, &seq, &pe, &est);
+        }
         if (lane == 0) {
           lg.border += 1;
           const float ratio = (float)(fabs(pe - ph) / (double)tau);
@@ -883,13 +1095,15 @@ __device__ __noinline__ void lu_decide(const LuArgs& a, int64_t p, int b, unsign
     a.keep[i] = mykeep ? 1 : 0;
     lg.d[p - a.q + lane] = d;
     lg.kp[p - a.q + lane] = mykeep ? 1 : 0;
-    for (int c = 0; c < b; ++c) A[i + (p + c) * lda] = X[lane][c];
+    const int cend = SYM ? lane + 1 : b;
+    for (int c = 0; c < cend; ++c) A[i + (p + c) * lda] = X[lane][c];
   }
   __syncwarp();
 }
 
 __device__ __forceinline__ int chunk_owner(int j, int nh) { return 1 + (j - 1) % nh; }
 
+template <bool SYM>
 __global__ void __launch_bounds__(kLuThreads, 1) k_lu_outer(LuArgs a) {
   LuSmem& S = lus();
   int& s_ok = g_lu_ok;
@@ -914,7 +1128,7 @@ __global__ void __launch_bounds__(kLuThreads, 1) k_lu_outer(LuArgs a) {
       const int b = (int)((qe - p) < 32 ? (qe - p) : 32);
       const unsigned epoch = a.epoch0 + (unsigned)k;
       if (k == 0) {
-        chunk_left(a, p, b, p, 0, S.X, nullptr);
+        chunk_left<SYM>(a, p, b, p, 0, S.X, nullptr);
       } else {
         // the chunk's owner has solved it against panel k - 1 and formed the block
         if (tid == 0) s_ok = wait_geq_short(rc, &rc.ctrl[kCtlChunk + k], epoch - 1) ? 1 : 0;
@@ -926,7 +1140,7 @@ __global__ void __launch_bounds__(kLuThreads, 1) k_lu_outer(LuArgs a) {
         for (int idx = tid; idx < 1024; idx += kLuThreads) S.X[idx >> 5][idx & 31] = __ldcg(&a.Bbuf[idx]);
         __syncthreads();
       }
-      lu_decide(a, p, b, epoch);
+      lu_decide<SYM>(a, p, b, epoch);
       __syncthreads();
       if (tid == 0) {
         __threadfence();
@@ -1005,20 +1219,20 @@ __global__ void __launch_bounds__(kLuThreads, 1) k_lu_outer(LuArgs a) {
       int ns = 0;
       for (int j = k + 1; j < np; ++j) {
         if (chunk_owner(j, nh) != h) continue;
-        chunk_left(a, p, b, q + 32 * j, D, slot_x(ns), slot_z(ns));
+        chunk_left<SYM>(a, p, b, q + 32 * j, D, slot_x(ns), SYM ? nullptr : slot_z(ns));
         if (j == k + 1) {
           const int bj = (int)((qe - (q + 32 * j)) < 32 ? (qe - (q + 32 * j)) : 32);
-          chunk_left(a, q + 32 * j, bj, q + 32 * j, D, S.Bp, nullptr);
+          chunk_left<SYM>(a, q + 32 * j, bj, q + 32 * j, D, S.Bp, nullptr);
         }
         ++ns;
       }
-      if (!lu_follower(a.lr, epoch, &s_ok, 128)) return;
-      load_panel(a, p, b);
+      if (!lu_follower<SYM>(a.lr, epoch, &s_ok, 128)) return;
+      load_panel<SYM>(a, p, b);
       __syncthreads();
       ns = 0;
       for (int j = k + 1; j < np; ++j) {
         if (chunk_owner(j, nh) != h) continue;
-        chunk_solve(a, p, b, q + 32 * j, slot_x(ns), slot_z(ns), false);
+        chunk_solve<SYM>(a, p, b, q + 32 * j, slot_x(ns), slot_z(ns), false);
         if (j == k + 1) next_block(a, slot_x(ns), slot_z(ns), b);
         if (tid == 0) {
           __threadfence();
@@ -1033,6 +1247,9 @@ __global__ void __launch_bounds__(kLuThreads, 1) k_lu_outer(LuArgs a) {
 
   // ---- workers: chunks beyond the outer block ----
   const int64_t nwk = (int64_t)gridDim.x - nh - 1, w = (int64_t)blockIdx.x - nh - 1;
+  const int64_t c_first = qe + 32 * w, c_stride = 32 * nwk;
+  const int total = c_first < a.n ? (int)((a.n - 1 - c_first) / c_stride + 1) : 0;
+  const int first = total < a.slots ? total : a.slots;
   for (int k = 0; k < np; ++k) {
     const int64_t p = q + 32 * k;
     const int b = (int)((qe - p) < 32 ? (qe - p) : 32);
@@ -1043,32 +1260,27 @@ __global__ void __launch_bounds__(kLuThreads, 1) k_lu_outer(LuArgs a) {
       __syncthreads();
       if (!s_ok) return;
     }
-    int m = 0;
-    for (int64_t c0 = qe + 32 * w; c0 < a.n && m < a.slots; c0 += 32 * nwk, ++m)
-      chunk_left(a, p, b, c0, D, slot_x(m), slot_z(m));
-    if (!lu_follower(a.lr, epoch, &s_ok, 1024)) return;
-    load_panel(a, p, b);
+    chunks_left<SYM>(a, p, b, D, c_first, c_stride, first);
+    if (!lu_follower<SYM>(a.lr, epoch, &s_ok, 1024)) return;
+    load_panel<SYM>(a, p, b);
     __syncthreads();
-    m = 0;
-    for (int64_t c0 = qe + 32 * w; c0 < a.n; c0 += 32 * nwk, ++m) {
-      if (m < a.slots) {
-        chunk_solve(a, p, b, c0, slot_x(m), slot_z(m), true);
-      } else {
-        chunk_left(a, p, b, c0, D, S.X, S.Z);
-        chunk_solve(a, p, b, c0, S.X, S.Z, true);
-      }
+    chunks_solve<SYM>(a, p, b, c_first, c_stride, first);
+    for (int m0 = first; m0 < total; m0 += a.slots) {
+      const int cnt = (total - m0) < a.slots ? (total - m0) : a.slots;
+      chunks_left<SYM>(a, p, b, D, c_first + m0 * c_stride, c_stride, cnt);
+      chunks_solve<SYM>(a, p, b, c_first + m0 * c_stride, c_stride, cnt);
     }
-    __syncthreads();
   }
 }
 
+// FP32 copy of K (lower: its lower triangle only) and the running diagonal.
 __global__ void __launch_bounds__(256) k_convert_full(const double* K, int64_t ldk, float* A,
                                                       int64_t lda, int64_t n, double* kd,
-                                                      double* s) {
+                                                      double* s, int lower) {
   for (int64_t j = blockIdx.x; j < n; j += gridDim.x) {
     const double* col = K + j * ldk;
     float* dst = A + j * lda;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) dst[i] = (float)col[i];
+    for (int64_t i = (lower ? j : 0) + threadIdx.x; i < n; i += blockDim.x) dst[i] = (float)col[i];
     if (threadIdx.x == 0) {
       kd[j] = col[j];
       s[j] = 0.0;
@@ -1077,11 +1289,11 @@ __global__ void __launch_bounds__(256) k_convert_full(const double* K, int64_t l
 }
 
 // In-place LU of K - 1_{Y^c} in FP64: L strictly below the diagonal, the
-// pivots on it, U = D U~ above it.
+// pivots on it, U = D U~ above it (lower: L and the pivots only, LDL^T).
 __global__ void __launch_bounds__(256) k_export_lu(const float* A, int64_t lda, const double* piv,
-                                                   double* F, int64_t ldf, int64_t n) {
+                                                   double* F, int64_t ldf, int64_t n, int lower) {
   for (int64_t j = blockIdx.x; j < n; j += gridDim.x) {
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int64_t i = (lower ? j : 0) + threadIdx.x; i < n; i += blockDim.x) {
       const double v = (double)A[i + j * lda];
       F[i + j * ldf] = i > j ? v : (i == j ? piv[j] : piv[i] * v);
     }
@@ -1145,7 +1357,10 @@ size_t ws_mixed_lu(int64_t n) {
   return probe.used + 512;
 }
 
-cudaError_t sample_mixed_lu(const DrawArgs& a, Workspace ws) {
+namespace {
+
+template <bool SYM>
+cudaError_t sample_chunked(const DrawArgs& a, Workspace ws) {
   const int64_t n = a.n;
   const int NB = g_tuning.outer_block;
   LuLayout L;
@@ -1159,20 +1374,21 @@ cudaError_t sample_mixed_lu(const DrawArgs& a, Workspace ws) {
   if ((e = cudaMemsetAsync(L.v2w, 0, words, a.stream)) != cudaSuccess) return e;
   const double* K = static_cast<const double*>(a.K);
   {
-    ProfScope ps(kProfConvert, a.stream, 0.0, 12.0 * (double)n * (double)n);
-    k_convert_full<<<(unsigned)(n < 65535 ? n : 65535), 256, 0, a.stream>>>(K, a.ld, L.A32, L.ld32,
-                                                                             n, L.kd, L.s);
+    ProfScope ps(kProfConvert, a.stream, 0.0, (SYM ? 6.0 : 12.0) * (double)n * (double)n);
+    k_convert_full<<<(unsigned)(n < 65535 ? n : 65535), 256, 0, a.stream>>>(
+        K, a.ld, L.A32, L.ld32, n, L.kd, L.s, SYM ? 1 : 0);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   static int cap = 0;
   if (cap == 0) {
-    cudaError_t ea = cudaFuncSetAttribute(k_lu_outer, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t ea = cudaFuncSetAttribute(k_lu_outer<SYM>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)lu_dyn_smem(kMaxSlots));
     if (ea != cudaSuccess) return ea;
     DevInfo di;
     if ((ea = dev_info(&di)) != cudaSuccess) return ea;
     int per_sm = 0;
-    ea = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lu_outer, kLuThreads,
+    ea = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lu_outer<SYM>, kLuThreads,
                                                        lu_dyn_smem(kMaxSlots));
     if (ea != cudaSuccess) return ea;
     cap = per_sm * di.sm_count;
@@ -1184,7 +1400,11 @@ cudaError_t sample_mixed_lu(const DrawArgs& a, Workspace ws) {
   if (grid < 3) grid = 3;
   // CTA 0 decides, CTAs 1..nh own the outer block's chunks, the rest the
   // chunks beyond it; slots hold the chunks a CTA precomputes per panel
-  const int nh = grid - 2 < kMaxOuterBlock / 32 - 1 ? grid - 2 : kMaxOuterBlock / 32 - 1;
+  // (one CTA per chunk on a full grid; on a small grid a helper owns
+  // several chunks, so that most CTAs stay workers)
+  int nh = (grid - 2) / 8;
+  if (nh > kMaxOuterBlock / 32 - 1) nh = kMaxOuterBlock / 32 - 1;
+  if (nh < 1) nh = 1;
   const int64_t nwk = grid - 1 - nh;
   const int64_t trail = ((n > NB ? n - NB : 0) + 31) / 32;
   int slots = (int)((trail + nwk - 1) / nwk);
@@ -1234,7 +1454,7 @@ cudaError_t sample_mixed_lu(const DrawArgs& a, Workspace ws) {
     void* args[] = {&la};
     {
       ProfScope ps(kProfPanel, a.stream);
-      e = cudaLaunchCooperativeKernel((const void*)k_lu_outer, dim3((unsigned)grid),
+      e = cudaLaunchCooperativeKernel((const void*)k_lu_outer<SYM>, dim3((unsigned)grid),
                                       dim3(kLuThreads), args, dyn, a.stream);
     }
     if (e != cudaSuccess) return e;
@@ -1242,9 +1462,10 @@ cudaError_t sample_mixed_lu(const DrawArgs& a, Workspace ws) {
     const int64_t r0 = q + kb;
     if (r0 < n) {
       const int64_t m = n - r0;
-      const double fl = 2.0 * (double)m * (double)m * (double)kb;
-      ProfScope ps(kProfUpdateTc, a.stream, fl, 8.0 * (double)m * (double)m);
-      e = outer_update_tc(split, L.A32, L.ld32, n, r0, kb, L.Wop, L.Mop, kNB, true, L.err,
+      // lower triangle (SYM) or whole square of 2 m^2 kb flops
+      const double fl = (SYM ? 1.0 : 2.0) * (double)m * (double)m * (double)kb;
+      ProfScope ps(kProfUpdateTc, a.stream, fl, (SYM ? 4.0 : 8.0) * (double)m * (double)m);
+      e = outer_update_tc(split, L.A32, L.ld32, n, r0, kb, L.Wop, L.Mop, kNB, !SYM, L.err,
                           a.stream);
       if (e != cudaSuccess) return e;
     }
@@ -1257,10 +1478,18 @@ cudaError_t sample_mixed_lu(const DrawArgs& a, Workspace ws) {
   if (a.factor_out) {
     ProfScope ps(kProfOther, a.stream);
     k_export_lu<<<(unsigned)(n < 65535 ? n : 65535), 256, 0, a.stream>>>(
-        L.A32, L.ld32, L.piv, static_cast<double*>(a.factor_out), a.ld, n);
+        L.A32, L.ld32, L.piv, static_cast<double*>(a.factor_out), a.ld, n, SYM ? 1 : 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t sample_mixed_lu(const DrawArgs& a, Workspace ws) { return sample_chunked<false>(a, ws); }
+
+cudaError_t sample_mixed_chunked(const DrawArgs& a, Workspace ws) {
+  return sample_chunked<true>(a, ws);
 }
 
 }  // namespace dpp

@@ -29,18 +29,23 @@ def dpp():
 _PREC = {"p": "3xtf32"}
 
 
-@pytest.fixture(params=[(1, "3xtf32"), (0, "3xtf32"), (0, "bf16x6")],
-                ids=["simt", "tcgen05-3xtf32", "tcgen05-bf16x6"])
+@pytest.fixture(params=[(1, "3xtf32", 0), (0, "3xtf32", 0), (0, "bf16x6", 0), (0, "bf16x6", 1)],
+                ids=["simt", "tcgen05-3xtf32", "tcgen05-bf16x6", "tcgen05-bf16x6-single-helper"])
 def update_kernel(request, dpp):
-    """Trailing-update kernel (SIMT FP32 or tensor cores) and operand split."""
+    """Trailing-update kernel (SIMT FP32 or tensor cores), operand split and
+    panel pipeline (0: automatic, the chunked one on a full grid; 1: single
+    helper)."""
     from paper_1905_00165_gb300 import _lib
-    kern, prec = request.param
+    kern, prec, pipe = request.param
     old = _lib.get_tuning(_lib.DPP_TUNE_UPDATE_KERNEL)
+    oldp = _lib.get_tuning(_lib.DPP_TUNE_PANEL_PIPELINE)
     _lib.set_tuning(_lib.DPP_TUNE_UPDATE_KERNEL, kern)
+    _lib.set_tuning(_lib.DPP_TUNE_PANEL_PIPELINE, pipe)
     _PREC["p"] = prec
     yield request.param
     _PREC["p"] = "3xtf32"
     _lib.set_tuning(_lib.DPP_TUNE_UPDATE_KERNEL, old)
+    _lib.set_tuning(_lib.DPP_TUNE_PANEL_PIPELINE, oldp)
 
 
 def _run(dpp, K, seed=0, uniforms=None, factor=False, precision=None):
@@ -211,7 +216,8 @@ def test_borderline_band_has_margin(dpp):
     assert worst < c / 8.0
 
 
-def test_capped_ctas_and_concurrent_streams(dpp):
+@pytest.mark.parametrize("pipeline", [1, 2], ids=["single-helper", "chunked"])
+def test_capped_ctas_and_concurrent_streams(dpp, pipeline):
     """The mixed path with each launch capped at 40 CTAs still matches the
     oracle, and four draws issued on four streams at once give the same
     samples, pivots and log P as the same draws one after another."""
@@ -221,7 +227,9 @@ def test_capped_ctas_and_concurrent_streams(dpp):
     K = W.hermitian_kernel(n, seed=17, kind="beta")
     Kd = torch.from_numpy(K).cuda()
     old = _lib.get_tuning(_lib.DPP_TUNE_MAX_CTAS)
+    oldp = _lib.get_tuning(_lib.DPP_TUNE_PANEL_PIPELINE)
     _lib.set_tuning(_lib.DPP_TUNE_MAX_CTAS, 40)
+    _lib.set_tuning(_lib.DPP_TUNE_PANEL_PIPELINE, pipeline)
     try:
         for seed in range(2):
             u = O.uniforms(seed, 0, n)
@@ -246,3 +254,29 @@ def test_capped_ctas_and_concurrent_streams(dpp):
             assert s.logp == l0
     finally:
         _lib.set_tuning(_lib.DPP_TUNE_MAX_CTAS, old)
+        _lib.set_tuning(_lib.DPP_TUNE_PANEL_PIPELINE, oldp)
+
+
+def test_chunked_pipeline_small_grid(dpp):
+    """The chunked panel pipeline on 8 CTAs: one helper owns every chunk of
+    the outer block and each worker has more chunks than shared-memory slots
+    (the rest are solved after the panel is published); still the oracle's
+    draw."""
+    from paper_1905_00165_gb300 import _lib
+    n = 3600
+    K = W.hermitian_kernel(n, seed=23, kind="beta")
+    old = _lib.get_tuning(_lib.DPP_TUNE_MAX_CTAS)
+    oldp = _lib.get_tuning(_lib.DPP_TUNE_PANEL_PIPELINE)
+    _lib.set_tuning(_lib.DPP_TUNE_MAX_CTAS, 8)
+    _lib.set_tuning(_lib.DPP_TUNE_PANEL_PIPELINE, 2)
+    try:
+        u = O.uniforms(2, 0, n)
+        ref = O.sample_ldl(K, u)
+        s = _run(dpp, K, 2, precision="bf16x6")
+        r = s.result()
+        assert r["status"] & (_lib.DPP_RES_TIMEOUT | _lib.DPP_RES_NONFINITE) == 0, r
+        compare_draw(s.keep.cpu().numpy(), r["logp"], s.pivots.cpu().numpy(), ref, u,
+                     logp_rtol=MIXED_LOGP_RTOL, piv_atol=1e-4)
+    finally:
+        _lib.set_tuning(_lib.DPP_TUNE_MAX_CTAS, old)
+        _lib.set_tuning(_lib.DPP_TUNE_PANEL_PIPELINE, oldp)

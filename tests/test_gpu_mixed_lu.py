@@ -164,3 +164,23 @@ def test_mixed_lu_matches_fp64_path_n8192(dpp):
         assert np.array_equal(km[:j0], kr[:j0]), int(np.flatnonzero(km[:j0] != kr[:j0])[0])
         if j0 == n:
             assert abs(rm["logp"] - rr["logp"]) <= MIXED_LOGP_RTOL * abs(rr["logp"])
+
+
+def test_mixed_lu_small_grid(dpp):
+    """8 CTAs per launch: one helper owns all of the outer block's chunks and
+    each worker has more chunks than shared-memory slots."""
+    from paper_1905_00165_gb300 import _lib
+    n = 3600
+    K, _ = W.lu_similarity_kernel(n, seed=29)
+    old = _lib.get_tuning(_lib.DPP_TUNE_MAX_CTAS)
+    _lib.set_tuning(_lib.DPP_TUNE_MAX_CTAS, 8)
+    try:
+        u = O.uniforms(5, 0, n)
+        ref = O.sample_lu(K, u)
+        s = _run(dpp, K, 5)
+        r = s.result()
+        assert r["status"] & _bad(_lib) == 0, r
+        compare_draw(s.keep.cpu().numpy(), r["logp"], s.pivots.cpu().numpy(), ref, u,
+                     logp_rtol=MIXED_LOGP_RTOL, piv_atol=1e-4)
+    finally:
+        _lib.set_tuning(_lib.DPP_TUNE_MAX_CTAS, old)
