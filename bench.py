@@ -300,6 +300,13 @@ def run_suite(args):
         fn, keep, raw = hermitian(Kc, n, "fp64", dt=1)
         ms, prof = timed(fn, 2, warm=1)
         line("C2", {"n": n, "kind": "beta", "dtype": "c128"}, "fp64", ms, 4 * n ** 3 / 3, prof)
+        for prec_name in ("bf16x6", "3xtf32"):
+            fn, keep, raw = hermitian(Kc, n, prec_name, dt=1)
+            ms, prof = timed(fn, 16)
+            res = _lib.decode_result(bytes(raw.cpu().numpy().tobytes()))
+            line("C2", {"n": n, "kind": "beta", "dtype": "c128"}, prec_name, ms, 4 * n ** 3 / 3,
+                 prof, {"last_draw_kept": res["n_kept"], "last_draw_borderline": res["n_borderline"],
+                        "last_draw_status": res["status"]})
         del Kc
 
     # C3: uniform spanning trees of the 64 x 64 grid (n = 8064, rank 4095)

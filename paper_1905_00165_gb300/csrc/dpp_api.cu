@@ -92,6 +92,8 @@ size_t dpp_workspace_size(int32_t op, int64_t n, int32_t dtype, int32_t precisio
         const size_t a = ws_mixed(n), b = ws_mixed_lu(n);
         return a > b ? a : b;
       }
+      if ((precision == DPP_PREC_3XTF32 || precision == DPP_PREC_BF16X6) && dtype == DPP_C128)
+        return ws_mixed_cx(n);
       return 0;
     case DPP_OP_SAMPLE_LU:
       if (precision == DPP_PREC_FP64) return ws_fp64(n, dtype, false, true);
@@ -143,6 +145,8 @@ static dpp_status sample_common(bool hermitian, const void* K, int64_t n, int64_
     }
     if (!hermitian)
       e = sample_mixed_lu(a, ws);
+    else if (dtype == DPP_C128)
+      e = sample_mixed_cx(a, ws);
     else if (g_tuning.update_kernel == 0 &&
              (g_tuning.panel_pipeline == 2 ||
               (g_tuning.panel_pipeline == 0 && (g_tuning.max_ctas == 0 || g_tuning.max_ctas >= 96))))

@@ -83,6 +83,10 @@ size_t ws_mixed_lu(int64_t n);
 cudaError_t sample_mixed_lu(const DrawArgs& a, Workspace ws);
 cudaError_t sample_mixed_chunked(const DrawArgs& a, Workspace ws);
 
+// Mixed-precision Hermitian sampler for complex K (dpp_mixed_cplx.cu).
+size_t ws_mixed_cx(int64_t n);
+cudaError_t sample_mixed_cx(const DrawArgs& a, Workspace ws);
+
 // Operand splits of the tensor-core trailing update.
 enum { kSplit3xTf32 = 0, kSplitBf16x6 = 1 };
 

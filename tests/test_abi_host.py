@@ -53,6 +53,8 @@ def test_workspace_sizes(L):
     assert dpp.workspace_size(1, 100, 0, 1, 0) > 100 * 100 * 4
     assert dpp.workspace_size(1, 100, 0, 2, 0) == dpp.workspace_size(1, 100, 0, 1, 0)
     assert dpp.workspace_size(1, 100, 1, 1, 0) == 0  # no complex mixed LU
+    # complex mixed Hermitian: planar FP32 copy (8 B per element)
+    assert dpp.workspace_size(0, 100, 1, 2, 1) > 100 * 100 * 8
 
 
 def _call(L, K=None, n=4, ld=4, dtype=0, prec=0, keep=None, res=None, ws=None, wsb=0):
@@ -72,8 +74,8 @@ def test_invalid_arguments_rejected_on_host(L):
     assert _call(L, K=fake, n=4, keep=fake, res=fake) == _lib.DPP_ERR_WORKSPACE
     assert _call(L, K=fake, n=4, keep=fake, res=fake, ws=fake + 8, wsb=1 << 20) == _lib.DPP_ERR_WORKSPACE
     assert _call(L, K=fake, n=4, keep=fake, res=fake, ws=fake, wsb=16) == _lib.DPP_ERR_WORKSPACE
-    # unsupported precision for complex input
-    assert _call(L, K=fake, n=4, dtype=1, prec=1, keep=fake, res=fake, ws=fake, wsb=1 << 30) == \
+    # unsupported precision (FP32 is the batched entry's only)
+    assert _call(L, K=fake, n=4, dtype=1, prec=3, keep=fake, res=fake, ws=fake, wsb=1 << 30) == \
         _lib.DPP_ERR_UNSUPPORTED
     assert L.dpp_uniforms(0, 0, -1, None, None) == _lib.DPP_ERR_INVALID_ARG
 
