@@ -120,8 +120,9 @@ size_t dpp_workspace_size(int32_t op, int64_t n, int32_t dtype,
 /* Sample DPP(K) for Hermitian K (LDL^H form of Algorithms 1 and 4).
  *   K          device, n x n column-major (ld >= n), lower triangle read.
  *   dtype      DPP_R64 or DPP_C128.
- *   precision  DPP_PREC_FP64 (R64, C128), DPP_PREC_3XTF32 or DPP_PREC_BF16X6
- *              (R64).
+ *   precision  DPP_PREC_FP64, DPP_PREC_3XTF32 or DPP_PREC_BF16X6 (R64 and
+ *              C128; a complex mixed draw keeps planar FP32 copies of K and
+ *              runs each trailing update as two real tensor-core contractions).
  *   seed, instance  Philox stream (ignored if uniforms != NULL).
  *   uniforms   device, n doubles, or NULL for Philox.
  *   keep       device, n bytes: keep[j] = 1 iff j is in the sample.
