@@ -260,11 +260,25 @@ dpp_status dpp_logprob_backward(const void* K, int64_t n, int64_t ld,
  *   K, keep, grad_logp, dK  HOST arrays of batch DEVICE pointers: K_i
  *              (column-major, lower triangle read), keep_i (n_i bytes),
  *              g_i (one double), dK_i (n_i x ld_dk_i doubles, written).
- *   workspace  device, >= dpp_workspace_size(DPP_OP_LOGPROB_BACKWARD, n_max,
- *              DPP_R64, DPP_PREC_FP64, 1) with n_max = max_i n_i.
+ *   workspace  device. With at least
+ *              dpp_logprob_backward_batched_workspace(batch, n_max) bytes (or
+ *              any size from the one-CTA value of that layout up, which runs
+ *              on fewer CTAs) all instances run in ONE persistent launch:
+ *              each CTA takes the next instance, largest n first, and does its
+ *              LDL^T, the triangular inverse and Z^T D^{-1} Z in FP64 in
+ *              32 x 32 tiles. Otherwise, with at least
+ *              dpp_workspace_size(DPP_OP_LOGPROB_BACKWARD, n_max, DPP_R64,
+ *              DPP_PREC_FP64, 1) bytes (n_max = max_i n_i), the instances are
+ *              enqueued one after another, each a chain of launches.
  * Errors: DPP_ERR_INVALID_ARG / DPP_ERR_WORKSPACE found on the host before
  * anything is enqueued; DPP_ERR_CUDA if a launch fails (earlier instances
  * may then already be enqueued). */
+/* Workspace bytes for the one-launch form of dpp_logprob_backward_batched on
+ * the current device (one CTA per SM, or DPP_TUNE_MAX_CTAS): a descriptor per
+ * instance plus, per CTA, n_max^2 + 33 n_max + 32 n_max doubles (rounded up to
+ * multiples of 32). Returns 0 for negative arguments. */
+size_t dpp_logprob_backward_batched_workspace(int32_t batch, int64_t n_max);
+
 dpp_status dpp_logprob_backward_batched(int32_t batch, const int64_t* n,
                                         const void* const* K, const int64_t* ld,
                                         const uint8_t* const* keep,

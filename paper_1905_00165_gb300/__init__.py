@@ -207,8 +207,8 @@ class BatchedSampler:
 
     def logprob_backward(self, grad_logp=None, count=None):
         """dK_i = g_i (K_i - 1_{Y_i^c})^{-T} for the first ``count`` instances
-        (default: all) and their last draw (FP64, one library call that
-        enqueues every instance)."""
+        (default: all) and their last draw (FP64, one persistent launch over
+        every instance)."""
         import ctypes
         import numpy as np
         torch = _torch()
@@ -228,7 +228,8 @@ class BatchedSampler:
         kk = P(*[k.data_ptr() for k in self.keep[:B]])
         gp = P(*[g.data_ptr() + 8 * i for i in range(B)])
         dp = P(*[d.data_ptr() for d in dKs])
-        need = workspace_size(DPP_OP_LOGPROB_BACKWARD, max(ns) if ns else 0, DPP_R64, DPP_PREC_FP64, 1)
+        # the one-launch form: a descriptor per instance and n_max^2 scratch per CTA
+        need = self.L.dpp_logprob_backward_batched_workspace(B, max(ns) if ns else 0)
         ws = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
         st = self.L.dpp_logprob_backward_batched(
             B, n_h.ctypes.data, ctypes.cast(kp, ctypes.c_void_p), ld_h.ctypes.data,

@@ -72,6 +72,8 @@ def load(path: Optional[str] = None):
     L.dpp_logprob_backward.restype = i32
     L.dpp_logprob_backward_batched.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
     L.dpp_logprob_backward_batched.restype = i32
+    L.dpp_logprob_backward_batched_workspace.argtypes = [i32, i64]
+    L.dpp_logprob_backward_batched_workspace.restype = sz
     L.dpp_uniforms.argtypes = [u64, u64, i64, vp, vp]
     L.dpp_uniforms.restype = i32
     L.dpp_profile_start.argtypes = []

@@ -1,0 +1,332 @@
+// Adjoint of log P(Y_i) for a batch of real symmetric kernels in ONE
+// persistent launch:
+//
+//   log P(Y) = log|det(K - 1_{Y^c})|  (Theorem 1)   =>   dK = g (K - 1_{Y^c})^{-1}
+//
+// Each CTA takes the next instance from a device counter over the instances
+// sorted by decreasing n (longest first), and does the whole instance in
+// FP64 with 32 x 32 tiles staged in shared memory:
+//   1. A = K - 1_{Y^c} (lower triangle) in the instance's dK buffer, and its
+//      blocked LDL^T in place (the decisions are the given sample, so no
+//      uniforms: each pivot is taken as it comes);
+//   2. the inverses of the 32 x 32 unit lower diagonal blocks of L;
+//   3. Z = L^{-1}, block row by block row:  Z_IJ = L_II^{-1} (delta_IJ - sum_K L_IK Z_KJ);
+//   4. A^{-1} = Z^T D^{-1} Z on the lower tiles (k >= max(i, j)), times g,
+//      written to both triangles of dK.
+// GB300's FP64 rate is a small fraction of its FP32 rate, so the work is
+// FP64-compute-bound; one instance per CTA keeps every SM busy without any
+// inter-CTA synchronisation.
+#include <algorithm>
+#include <vector>
+
+#include "dpp_device.cuh"
+#include "dpp_internal.h"
+#include "dpp_profile.h"
+
+namespace dpp {
+namespace {
+
+constexpr int kAT = 256;  // threads per CTA
+
+struct AdjDesc {
+  const double* K;
+  const uint8_t* keep;
+  const double* g;
+  double* dK;
+  int64_t n, ld, ldd;
+};
+
+struct AdjArgs {
+  const AdjDesc* desc;  // sorted by decreasing n
+  int32_t batch;
+  unsigned* counter;
+  double* scratch;      // per CTA: Z [ldz x ldz], W [ldz x 32], Linv [nt x 1024], d [ldz]
+  int64_t per_cta;      // doubles per CTA
+  int64_t ldz;          // n_max rounded up to 32
+};
+
+__shared__ double s_a[32][33];
+__shared__ double s_b[32][33];
+__shared__ double s_c[32][33];
+__shared__ unsigned s_inst;
+
+// acc[j] (thread: row r = lane, column cg + 8 j) += sum_t s_a[r][t] s_b[cg + 8 j][t]
+__device__ __forceinline__ void tile_abT(double (&acc)[4]) {
+  const int r = threadIdx.x & 31, cg = threadIdx.x >> 5;
+#pragma unroll 8
+  for (int t = 0; t < 32; ++t) {
+    const double a = s_a[r][t];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[j] = fma(a, s_b[cg + 8 * j][t], acc[j]);
+  }
+}
+
+__device__ void adjoint_one(const AdjArgs& a, const AdjDesc& d, double* scr) {
+  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+  const int r = lane, cg = wp;
+  const int64_t n = d.n, ldd = d.ldd, ldz = a.ldz;
+  const int nt = (int)((n + 31) / 32);
+  double* A = d.dK;
+  double* Z = scr;
+  double* Wb = Z + ldz * ldz;
+  double* Linv = Wb + ldz * 32;
+  double* dv = Linv + (int64_t)nt * 1024;
+
+  // ---- 1. A = K - 1_{Y^c}, lower triangle ----
+  for (int64_t j = 0; j < n; ++j) {
+    for (int64_t i = j + tid; i < n; i += kAT) {
+      double v = d.K[i + j * d.ld];
+      if (i == j && d.keep[i] == 0) v -= 1.0;
+      A[i + j * ldd] = v;
+    }
+  }
+  __syncthreads();
+
+  // ---- blocked LDL^T, right-looking ----
+  for (int P = 0; P < nt; ++P) {
+    const int64_t p = 32 * (int64_t)P;
+    const int b = (int)((n - p) < 32 ? (n - p) : 32);
+    // (a) diagonal block, one row per lane of warp 0, mirrored to full
+    for (int idx = tid; idx < 1024; idx += kAT) {
+      const int i = idx & 31, c = idx >> 5;
+      double v = 0.0;
+      if (i < b && c < b) v = i >= c ? A[(p + i) + (p + c) * ldd] : A[(p + c) + (p + i) * ldd];
+      s_a[i][c] = v;
+    }
+    __syncthreads();
+    if (wp == 0) {
+      for (int J = 0; J < b; ++J) {
+        const double dj = s_a[J][J];
+        if (lane > J && lane < b) {
+          const double l = s_a[lane][J] / dj;
+          for (int c = J + 1; c < b; ++c) s_a[lane][c] = fma(-l, s_a[J][c], s_a[lane][c]);
+          s_a[lane][J] = l;
+        }
+        __syncwarp();
+      }
+      if (lane < b) {
+        dv[p + lane] = s_a[lane][lane];
+        for (int c = 0; c <= lane; ++c) A[(p + lane) + (p + c) * ldd] = s_a[lane][c];
+      }
+    }
+    __syncthreads();
+    // (b) rows below: W L11^T = A[i, p:p+b], L = W / d
+    for (int64_t i = p + b + tid; i < n; i += kAT) {
+      double w[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) w[c] = c < b ? A[i + (p + c) * ldd] : 0.0;
+#pragma unroll
+      for (int c = 1; c < 32; ++c) {
+#pragma unroll
+        for (int k = 0; k < c; ++k) w[c] = fma(-w[k], s_a[c][k], w[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        if (c < b) {
+          Wb[i * 32 + c] = w[c];
+          A[i + (p + c) * ldd] = w[c] / dv[p + c];
+        }
+      }
+    }
+    __syncthreads();
+    // (c) trailing update of the lower tiles: A_IJ -= W_I L_J^T
+    for (int I = P + 1; I < nt; ++I) {
+      for (int J = P + 1; J <= I; ++J) {
+        for (int idx = tid; idx < 1024; idx += kAT) {
+          const int rr = idx >> 5, t = idx & 31;
+          const int64_t ri = 32 * (int64_t)I + rr, rj = 32 * (int64_t)J + rr;
+          s_a[rr][t] = (ri < n && t < b) ? Wb[ri * 32 + t] : 0.0;
+          s_b[rr][t] = (rj < n && t < b) ? A[rj + (p + t) * ldd] : 0.0;
+        }
+        __syncthreads();
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        tile_abT(acc);
+        const int64_t i = 32 * (int64_t)I + r;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int64_t c = 32 * (int64_t)J + cg + 8 * j;
+          if (i < n && c <= i) A[i + c * ldd] -= acc[j];
+        }
+        __syncthreads();
+      }
+    }
+  }
+
+  // ---- 2. inverses of the unit lower diagonal blocks (one warp each) ----
+  for (int I = wp; I < nt; I += kAT / 32) {
+    const int64_t p = 32 * (int64_t)I;
+    const int b = (int)((n - p) < 32 ? (n - p) : 32);
+    double z[32];  // column `lane` of the inverse
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      double s = 0.0;
+      if (i > lane && i < b) {
+#pragma unroll
+        for (int k = 0; k < i; ++k)
+          if (k >= lane) s = fma(A[(p + i) + (p + k) * ldd], z[k], s);
+      }
+      z[i] = (i == lane) ? 1.0 : (i < lane || i >= b ? 0.0 : -s);
+    }
+#pragma unroll
+    for (int i = 0; i < 32; ++i) Linv[(int64_t)I * 1024 + i * 32 + lane] = z[i];
+  }
+  __syncthreads();
+
+  // ---- 3. Z = L^{-1}, block rows in order ----
+  for (int I = 0; I < nt; ++I) {
+    for (int J = 0; J <= I; ++J) {
+      double acc[4] = {0.0, 0.0, 0.0, 0.0};
+      // T = sum_{K=J}^{I-1} L_IK Z_KJ   (acc holds T[r][c] with c = cg + 8 j)
+      for (int K = J; K < I; ++K) {
+        for (int idx = tid; idx < 1024; idx += kAT) {
+          const int rr = idx >> 5, t = idx & 31;
+          const int64_t ri = 32 * (int64_t)I + rr, ck = 32 * (int64_t)K + t;
+          s_a[rr][t] = (ri < n && ck < n) ? A[ri + ck * ldd] : 0.0;
+          // s_b[c][t] = Z[K*32 + t][J*32 + c]
+          const int64_t zr = 32 * (int64_t)K + t, zc = 32 * (int64_t)J + rr;
+          s_b[rr][t] = (zr < n && zc < n) ? Z[zr + zc * ldz] : 0.0;
+        }
+        __syncthreads();
+        tile_abT(acc);
+        __syncthreads();
+      }
+      // Z_IJ = Linv_I (delta_IJ - T)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = cg + 8 * j;
+        s_c[c][r] = (I == J ? (r == c ? 1.0 : 0.0) : 0.0) - acc[j];  // transposed: s_c[c][t]
+      }
+      for (int idx = tid; idx < 1024; idx += kAT) {
+        const int rr = idx >> 5, t = idx & 31;
+        s_a[rr][t] = Linv[(int64_t)I * 1024 + rr * 32 + t];
+      }
+      __syncthreads();
+      double z[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 8
+      for (int t = 0; t < 32; ++t) {
+        const double la = s_a[r][t];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) z[j] = fma(la, s_c[cg + 8 * j][t], z[j]);
+      }
+      const int64_t i = 32 * (int64_t)I + r;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int64_t c = 32 * (int64_t)J + cg + 8 * j;
+        if (i < n && c < n) Z[i + c * ldz] = z[j];
+      }
+      __syncthreads();
+    }
+  }
+
+  // ---- 4. dK = g Z^T D^{-1} Z, lower tiles mirrored ----
+  const double g = *d.g;
+  for (int I = 0; I < nt; ++I) {
+    for (int J = 0; J <= I; ++J) {
+      double acc[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int K = I; K < nt; ++K) {
+        for (int idx = tid; idx < 1024; idx += kAT) {
+          const int rr = idx >> 5, t = idx & 31;
+          const int64_t k = 32 * (int64_t)K + t;
+          const int64_t ci = 32 * (int64_t)I + rr, cj = 32 * (int64_t)J + rr;
+          // s_a[r][t] = Z[k][I*32 + r] / d_k ; s_b[c][t] = Z[k][J*32 + c]
+          s_a[rr][t] = (k < n && ci < n) ? Z[k + ci * ldz] / dv[k] : 0.0;
+          s_b[rr][t] = (k < n && cj < n) ? Z[k + cj * ldz] : 0.0;
+        }
+        __syncthreads();
+        tile_abT(acc);
+        __syncthreads();
+      }
+      const int64_t i = 32 * (int64_t)I + r;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int64_t c = 32 * (int64_t)J + cg + 8 * j;
+        if (i < n && c <= i) {
+          const double v = g * acc[j];
+          A[i + c * ldd] = v;
+          A[c + i * ldd] = v;
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kAT, 1) k_adjoint_batched(AdjArgs a) {
+  double* scr = a.scratch + (int64_t)blockIdx.x * a.per_cta;
+  while (true) {
+    if (threadIdx.x == 0) s_inst = atomicAdd(a.counter, 1u);
+    __syncthreads();
+    const unsigned inst = s_inst;
+    __syncthreads();
+    if (inst >= (unsigned)a.batch) return;
+    const AdjDesc d = a.desc[inst];
+    if (d.n > 0) adjoint_one(a, d, scr);
+  }
+}
+
+inline int64_t adj_ldz(int64_t n_max) { return ((n_max + 31) / 32) * 32; }
+
+inline int64_t adj_per_cta(int64_t n_max) {
+  const int64_t ldz = adj_ldz(n_max > 0 ? n_max : 1);
+  return ldz * ldz + ldz * 32 + (ldz / 32) * 1024 + ldz + 32;
+}
+
+inline size_t adj_header(int32_t batch) {
+  return align256(sizeof(AdjDesc) * (size_t)(batch > 0 ? batch : 1)) + 256;
+}
+
+}  // namespace
+
+size_t ws_adjoint_batched(int32_t batch, int64_t n_max, int ctas) {
+  return adj_header(batch) + sizeof(double) * (size_t)adj_per_cta(n_max) * (size_t)ctas + 256;
+}
+
+int adjoint_batched_ctas() {
+  DevInfo di;
+  if (dev_info(&di) != cudaSuccess || di.sm_count <= 0) return 1;
+  int c = di.sm_count;
+  if (g_tuning.max_ctas > 0 && c > g_tuning.max_ctas) c = g_tuning.max_ctas;
+  return c;
+}
+
+cudaError_t adjoint_batched(int32_t batch, const int64_t* n, const double* const* K,
+                            const int64_t* ld, const uint8_t* const* keep,
+                            const double* const* g, double* const* dK, const int64_t* ld_dk,
+                            int64_t n_max, Workspace ws, cudaStream_t s) {
+  // descriptors, longest instance first
+  std::vector<AdjDesc> h((size_t)batch);
+  std::vector<int32_t> order((size_t)batch);
+  for (int32_t i = 0; i < batch; ++i) order[(size_t)i] = i;
+  std::sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return n[x] > n[y]; });
+  for (int32_t k = 0; k < batch; ++k) {
+    const int32_t i = order[(size_t)k];
+    h[(size_t)k] = AdjDesc{K[i], keep[i], g[i], dK[i], n[i], ld[i], ld_dk[i]};
+  }
+  char* base = ws.base;
+  AdjDesc* desc = reinterpret_cast<AdjDesc*>(base);
+  unsigned* counter = reinterpret_cast<unsigned*>(base + adj_header(batch) - 256);
+  const size_t used = adj_header(batch);
+  const int64_t per = adj_per_cta(n_max);
+  int ctas = adjoint_batched_ctas();
+  const int64_t room = (int64_t)((ws.size - used) / (sizeof(double) * (size_t)per));
+  if (room < ctas) ctas = (int)room;
+  if (ctas < 1) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemcpyAsync(desc, h.data(), sizeof(AdjDesc) * (size_t)batch,
+                                  cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
+  AdjArgs a;
+  a.desc = desc;
+  a.batch = batch;
+  a.counter = counter;
+  a.scratch = reinterpret_cast<double*>(base + used);
+  a.per_cta = per;
+  a.ldz = adj_ldz(n_max > 0 ? n_max : 1);
+  {
+    ProfScope ps(kProfOther, s);
+    k_adjoint_batched<<<(unsigned)ctas, kAT, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace dpp

@@ -264,9 +264,20 @@ dpp_status dpp_logprob_backward_batched(int32_t batch, const int64_t* n, const v
       return fail(DPP_ERR_INVALID_ARG, "NULL pointer of a non-empty instance");
     if (n[i] > n_max) n_max = n[i];
   }
-  const size_t need = ws_backward(n_max, DPP_R64, true);
   if (!workspace || !aligned(workspace, 256))
     return fail(DPP_ERR_WORKSPACE, "workspace must be non-NULL and 256-byte aligned");
+  if (workspace_bytes >= ws_adjoint_batched(batch, n_max, 1)) {
+    // one persistent launch over all instances
+    Workspace ws;
+    ws.base = static_cast<char*>(workspace);
+    ws.size = workspace_bytes;
+    cudaError_t e = adjoint_batched(batch, n, reinterpret_cast<const double* const*>(K), ld, keep,
+                                    grad_logp, reinterpret_cast<double* const*>(dK), ld_dk, n_max,
+                                    ws, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail_cuda(e, "dpp_logprob_backward_batched");
+    return DPP_OK;
+  }
+  const size_t need = ws_backward(n_max, DPP_R64, true);
   if (workspace_bytes < need) return fail(DPP_ERR_WORKSPACE, "workspace too small for n_max");
   for (int32_t i = 0; i < batch; ++i) {
     if (n[i] == 0) continue;
@@ -278,6 +289,11 @@ dpp_status dpp_logprob_backward_batched(int32_t batch, const int64_t* n, const v
     if (e != cudaSuccess) return fail_cuda(e, "dpp_logprob_backward_batched");
   }
   return DPP_OK;
+}
+
+size_t dpp_logprob_backward_batched_workspace(int32_t batch, int64_t n_max) {
+  if (batch < 0 || n_max < 0) return 0;
+  return ws_adjoint_batched(batch, n_max, adjoint_batched_ctas());
 }
 
 dpp_status dpp_set_tuning(int32_t key, double value) {

@@ -129,6 +129,14 @@ cudaError_t logprob_backward(const void* K, int64_t n, int64_t ld, int32_t dtype
                              const double* grad, void* dK, int64_t ld_dk,
                              Workspace ws, cudaStream_t stream);
 
+// Batched adjoint in one persistent launch (dpp_adjoint_batched.cu).
+size_t ws_adjoint_batched(int32_t batch, int64_t n_max, int ctas);
+int adjoint_batched_ctas();
+cudaError_t adjoint_batched(int32_t batch, const int64_t* n, const double* const* K,
+                            const int64_t* ld, const uint8_t* const* keep,
+                            const double* const* g, double* const* dK, const int64_t* ld_dk,
+                            int64_t n_max, Workspace ws, cudaStream_t s);
+
 // Result initialisation and uniform generation (dpp_fp64.cu).
 cudaError_t init_result(dpp_result* r, cudaStream_t s);
 cudaError_t fill_uniforms(uint64_t seed, uint64_t instance, int64_t n, double* out,

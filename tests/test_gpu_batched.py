@@ -114,3 +114,62 @@ def test_batched_adjoint_matches_closed_form(dpp):
         got = dKs[i].cpu().numpy()
         err = np.abs(got - ref).max() / max(1.0, np.abs(ref).max())
         assert err < 1e-9, (i, err)
+
+
+def _adjoint_call(dpp, Ks, keeps, g, ws_bytes):
+    """dpp_logprob_backward_batched with an explicit workspace size."""
+    import ctypes
+    import torch
+    from paper_1905_00165_gb300 import _lib
+    L = dpp.load()
+    B = len(Ks)
+    ns = [int(K.shape[0]) for K in Ks]
+    dKs = [dpp.empty_colmajor(m, torch.float64, "cuda") for m in ns]
+    n_h = np.asarray(ns, dtype=np.int64)
+    ld_h = np.asarray([K.stride(1) if m else 1 for K, m in zip(Ks, ns)], dtype=np.int64)
+    ldd_h = np.asarray([d.stride(1) if m else 1 for d, m in zip(dKs, ns)], dtype=np.int64)
+    P = ctypes.c_void_p * B
+    kp = P(*[K.data_ptr() for K in Ks])
+    kk = P(*[k.data_ptr() for k in keeps])
+    gp = P(*[g.data_ptr() + 8 * i for i in range(B)])
+    dp = P(*[d.data_ptr() for d in dKs])
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+    st = L.dpp_logprob_backward_batched(
+        B, n_h.ctypes.data, ctypes.cast(kp, ctypes.c_void_p), ld_h.ctypes.data,
+        ctypes.cast(kk, ctypes.c_void_p), ctypes.cast(gp, ctypes.c_void_p),
+        ctypes.cast(dp, ctypes.c_void_p), ldd_h.ctypes.data, ws.data_ptr(), ws_bytes,
+        torch.cuda.current_stream().cuda_stream)
+    _lib.check(st)
+    torch.cuda.synchronize()
+    return [d.cpu().numpy() for d in dKs]
+
+
+def test_batched_adjoint_one_launch_ragged_and_small_grid(dpp):
+    """The one-launch adjoint on ragged orders (n = 1, 31, 33, 64, 65, 257, ...)
+    against the closed form, with the full workspace and with one that fits
+    two CTAs (more instances than CTAs), and against the per-instance path."""
+    import torch
+    from paper_1905_00165_gb300 import _lib
+    sizes = [1, 31, 33, 64, 65, 100, 257, 300, 5, 129]
+    Ks = [W.hermitian_kernel(m, seed=50 + i, kind="uniform") for i, m in enumerate(sizes)]
+    Kd = [torch.from_numpy(np.ascontiguousarray(K)).cuda() for K in Ks]
+    keeps_h = [O.sample_ldl(K, O.uniforms(2, i, K.shape[0])).keep for i, K in enumerate(Ks)]
+    keeps = [torch.from_numpy(k).cuda() for k in keeps_h]
+    g = torch.tensor([1.0, -0.5, 2.0, 0.25, 1.5, -1.0, 0.75, 3.0, -2.0, 0.5],
+                     dtype=torch.float64, device="cuda")
+    L = dpp.load()
+    n_max = max(sizes)
+    full = L.dpp_logprob_backward_batched_workspace(len(Ks), n_max)
+    ldz = ((n_max + 31) // 32) * 32
+    per_cta = 8 * (ldz * ldz + ldz * 32 + (ldz // 32) * 1024 + ldz + 32)
+    two = full - (full // per_cta - 2) * per_cta  # room for exactly two CTAs
+    legacy = dpp.workspace_size(_lib.DPP_OP_LOGPROB_BACKWARD, n_max, _lib.DPP_R64,
+                                _lib.DPP_PREC_FP64, 1)
+    assert legacy < two <= full
+    outs = [_adjoint_call(dpp, Kd, keeps, g, w) for w in (full, two, legacy)]
+    for i, K in enumerate(Ks):
+        ref = O.logprob_grad(K, keeps_h[i], float(g[i]))
+        scale = max(1.0, np.abs(ref).max())
+        for out in outs:
+            err = np.abs(out[i] - ref).max() / scale
+            assert err < 1e-9, (i, sizes[i], err)
