@@ -252,24 +252,19 @@ dpp_status dpp_logprob_backward(const void* K, int64_t n, int64_t ld,
 /* Adjoint of log P(Y_i) for each instance of a batch of real symmetric
  * kernels (for instance the draws of dpp_sample_batched), Y_i fixed:
  * dK_i = g_i (K_i - 1_{Y_i^c})^{-T}, in FP64, exactly as dpp_logprob_backward
- * with hermitian = 1. The instances are enqueued one after another on
- * `stream` and share the workspace (stream order makes that safe).
+ * with hermitian = 1.
  *   batch      number of instances (>= 0).
  *   n, ld, ld_dk  HOST arrays of batch entries: order, leading dimension of
  *              K_i (>= max(1, n_i)) and of dK_i.
  *   K, keep, grad_logp, dK  HOST arrays of batch DEVICE pointers: K_i
  *              (column-major, lower triangle read), keep_i (n_i bytes),
  *              g_i (one double), dK_i (n_i x ld_dk_i doubles, written).
- *   workspace  device. With at least
- *              dpp_logprob_backward_batched_workspace(batch, n_max) bytes (or
- *              any size from the one-CTA value of that layout up, which runs
- *              on fewer CTAs) all instances run in ONE persistent launch:
- *              each CTA takes the next instance, largest n first, and does its
- *              LDL^T, the triangular inverse and Z^T D^{-1} Z in FP64 in
- *              32 x 32 tiles. Otherwise, with at least
- *              dpp_workspace_size(DPP_OP_LOGPROB_BACKWARD, n_max, DPP_R64,
- *              DPP_PREC_FP64, 1) bytes (n_max = max_i n_i), the instances are
- *              enqueued one after another, each a chain of launches.
+ *   workspace  device, dpp_logprob_backward_batched_workspace(batch, n_max)
+ *              bytes (n_max = max_i n_i) for one CTA per SM; a smaller one runs
+ *              on as many CTAs as it holds (at least one). All instances run in
+ *              ONE persistent launch: each CTA takes the next instance, largest
+ *              n first, and does its LDL^T, the triangular inverse and
+ *              Z^T D^{-1} Z in FP64 in 32 x 32 tiles.
  * Errors: DPP_ERR_INVALID_ARG / DPP_ERR_WORKSPACE found on the host before
  * anything is enqueued; DPP_ERR_CUDA if a launch fails (earlier instances
  * may then already be enqueued). */

@@ -266,28 +266,16 @@ dpp_status dpp_logprob_backward_batched(int32_t batch, const int64_t* n, const v
   }
   if (!workspace || !aligned(workspace, 256))
     return fail(DPP_ERR_WORKSPACE, "workspace must be non-NULL and 256-byte aligned");
-  if (workspace_bytes >= ws_adjoint_batched(batch, n_max, 1)) {
-    // one persistent launch over all instances
-    Workspace ws;
-    ws.base = static_cast<char*>(workspace);
-    ws.size = workspace_bytes;
-    cudaError_t e = adjoint_batched(batch, n, reinterpret_cast<const double* const*>(K), ld, keep,
-                                    grad_logp, reinterpret_cast<double* const*>(dK), ld_dk, n_max,
-                                    ws, static_cast<cudaStream_t>(stream));
-    if (e != cudaSuccess) return fail_cuda(e, "dpp_logprob_backward_batched");
-    return DPP_OK;
-  }
-  const size_t need = ws_backward(n_max, DPP_R64, true);
-  if (workspace_bytes < need) return fail(DPP_ERR_WORKSPACE, "workspace too small for n_max");
-  for (int32_t i = 0; i < batch; ++i) {
-    if (n[i] == 0) continue;
-    Workspace ws;
-    ws.base = static_cast<char*>(workspace);
-    ws.size = workspace_bytes;
-    cudaError_t e = logprob_backward(K[i], n[i], ld[i], DPP_R64, true, keep[i], grad_logp[i],
-                                     dK[i], ld_dk[i], ws, static_cast<cudaStream_t>(stream));
-    if (e != cudaSuccess) return fail_cuda(e, "dpp_logprob_backward_batched");
-  }
+  if (workspace_bytes < ws_adjoint_batched(batch, n_max, 1))
+    return fail(DPP_ERR_WORKSPACE, "workspace too small for one CTA of the batched adjoint");
+  // one persistent launch over all instances, on as many CTAs as the workspace holds
+  Workspace ws;
+  ws.base = static_cast<char*>(workspace);
+  ws.size = workspace_bytes;
+  cudaError_t e = adjoint_batched(batch, n, reinterpret_cast<const double* const*>(K), ld, keep,
+                                  grad_logp, reinterpret_cast<double* const*>(dK), ld_dk, n_max,
+                                  ws, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return fail_cuda(e, "dpp_logprob_backward_batched");
   return DPP_OK;
 }
 

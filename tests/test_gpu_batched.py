@@ -126,7 +126,8 @@ def _adjoint_call(dpp, Ks, keeps, g, ws_bytes):
     ns = [int(K.shape[0]) for K in Ks]
     dKs = [dpp.empty_colmajor(m, torch.float64, "cuda") for m in ns]
     n_h = np.asarray(ns, dtype=np.int64)
-    ld_h = np.asarray([K.stride(1) if m else 1 for K, m in zip(Ks, ns)], dtype=np.int64)
+    # symmetric K stored row-major: the same as column-major with ld = n
+    ld_h = np.asarray([K.stride(0) if m else 1 for K, m in zip(Ks, ns)], dtype=np.int64)
     ldd_h = np.asarray([d.stride(1) if m else 1 for d, m in zip(dKs, ns)], dtype=np.int64)
     P = ctypes.c_void_p * B
     kp = P(*[K.data_ptr() for K in Ks])
@@ -147,7 +148,8 @@ def _adjoint_call(dpp, Ks, keeps, g, ws_bytes):
 def test_batched_adjoint_one_launch_ragged_and_small_grid(dpp):
     """The one-launch adjoint on ragged orders (n = 1, 31, 33, 64, 65, 257, ...)
     against the closed form, with the full workspace and with one that fits
-    two CTAs (more instances than CTAs), and against the per-instance path."""
+    two CTAs (more instances than CTAs); the single-instance entry point
+    against the same closed form."""
     import torch
     from paper_1905_00165_gb300 import _lib
     sizes = [1, 31, 33, 64, 65, 100, 257, 300, 5, 129]
@@ -163,10 +165,11 @@ def test_batched_adjoint_one_launch_ragged_and_small_grid(dpp):
     ldz = ((n_max + 31) // 32) * 32
     per_cta = 8 * (ldz * ldz + ldz * 32 + (ldz // 32) * 1024 + ldz + 32)
     two = full - (full // per_cta - 2) * per_cta  # room for exactly two CTAs
-    legacy = dpp.workspace_size(_lib.DPP_OP_LOGPROB_BACKWARD, n_max, _lib.DPP_R64,
-                                _lib.DPP_PREC_FP64, 1)
-    assert legacy < two <= full
-    outs = [_adjoint_call(dpp, Kd, keeps, g, w) for w in (full, two, legacy)]
+    assert two <= full
+    outs = [_adjoint_call(dpp, Kd, keeps, g, w) for w in (full, two)]
+    # and the single-instance entry point (a chain of launches per instance)
+    outs.append([dpp.logprob_backward(K, k, grad_logp=g[i:i + 1]).cpu().numpy()
+                 for i, (K, k) in enumerate(zip(Kd, keeps))])
     for i, K in enumerate(Ks):
         ref = O.logprob_grad(K, keeps_h[i], float(g[i]))
         scale = max(1.0, np.abs(ref).max())
