@@ -27,20 +27,21 @@
 // triangular sweeps of each side run as wavefronts over 32-index blocks on
 // the worker CTAs, with the protocol and helpers of the Hermitian recompute.
 //
-// One cooperative launch per outer block [q, q + kb) of at most 256 columns:
-//   CTA 0      : for each 32-wide inner panel, forms the diagonal block
-//                (left-looking over the outer block's earlier panels),
-//                makes its decisions in order (warp 0) and publishes it;
-//   CTA 1      : the helper; solves the outer block's own later rows and
-//                columns against each published panel, the next panel's
-//                first, and signals that one;
-//   CTAs 2..   : workers; 32-index chunks of the rows and columns beyond the
-//                outer block, left-looking update + both triangular solves
-//                against each panel, writing W and M (and their tensor-core
-//                splits). All CTAs from 1 on serve recompute requests while
-//                they wait for the next panel.
-// After each outer block one rank-kb update of the trailing square runs on
-// the tensor cores (full-square mode of the Hermitian path's kernel).
+// One cooperative launch per outer block [q, q + kb) of at most 256 columns,
+// cut into 32-index chunks (32 rows and, for LU, the same 32 columns):
+//   CTA 0       : decides each 32-wide panel with all eight warps and
+//                 publishes it;
+//   CTAs 1..nh  : helpers; own the outer block's later chunks (one each on a
+//                 full grid). Before a panel is published they compute their
+//                 chunks' left-looking products; after it, they solve them, and
+//                 the owner of the next chunk forms the next diagonal block;
+//   the rest    : workers; own the chunks beyond the outer block (left-looking
+//                 products before the publish as one tall product, solves and
+//                 the tensor-core operand splits after it).
+// All CTAs from 1 on serve recompute requests while they wait for a panel.
+// After each outer block one rank-kb update of the trailing square (LU) or
+// triangle (the symmetric instantiation, used by the Hermitian sampler) runs
+// on the tensor cores.
 #include <cuda_bf16.h>
 #include <math.h>
 
