@@ -79,8 +79,8 @@ def tc_traffic_per_launch(split="bf16x6"):
                 else "k_update_tc_3xtf32_traffic_n16384.txt")
         with open(os.path.join(ROOT, "profiles", name)) as f:
             for ln in f:
-                if ":" in ln:
-                    k, v = ln.split(":", 1)
+                if ": " in ln:  # keys may hold a colon themselves ("sha256[:16]")
+                    k, v = ln.split(": ", 1)
                     vals[k.strip()] = v.strip()
         if vals.get("dpp_tc.cu sha256[:16]") != h:
             return None
