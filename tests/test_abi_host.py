@@ -105,3 +105,15 @@ def test_static_entry_limits_checked_on_host(L):
         _lib.DPP_ERR_INVALID_ARG
     assert f(fake, 4, 3, _lib.DPP_R64, 0, 0, None, fake, fake, None, fake, None) == \
         _lib.DPP_ERR_INVALID_ARG
+
+
+def test_batched_adjoint_workspace_query(L):
+    """The one-launch batched adjoint's workspace: descriptors per instance plus
+    at least one CTA's n_max^2 scratch; grows with the batch and n_max."""
+    L.dpp_logprob_backward_batched_workspace.argtypes = [ctypes.c_int32, ctypes.c_int64]
+    L.dpp_logprob_backward_batched_workspace.restype = ctypes.c_size_t
+    a = L.dpp_logprob_backward_batched_workspace(10, 300)
+    assert a >= 8 * 320 * 320
+    assert L.dpp_logprob_backward_batched_workspace(1000, 300) > a
+    assert L.dpp_logprob_backward_batched_workspace(10, 600) > a
+    assert L.dpp_logprob_backward_batched_workspace(-1, 300) == 0
