@@ -169,6 +169,7 @@ __device__ __forceinline__ void lu_r1_block(const RecomputeArgs& a, float* inv,
 #pragma unroll
       for (int k = 0; k < 32; ++k) v[k] = (k < ns && lane < nr) ? __ldcg(cp + k * lda) : 0.f;
       float xs = 0.f;
+      *live = __all_sync(kLuFull, *live);  // warp-uniform before the collective wait
       if (*live && !warp_wait_words(a, words + 32 * s, ns, id, &xs)) *live = false;
 #pragma unroll
       for (int k = 0; k < 32; ++k) acc = fmaf(v[k], __shfl_sync(kLuFull, xs, k), acc);
@@ -186,6 +187,7 @@ __device__ __forceinline__ void lu_r1_block(const RecomputeArgs& a, float* inv,
 #pragma unroll
       for (int c = 0; c < 32; ++c) tile[c] = (lane < ns && c < nr) ? __ldcg(tp + c * lda) : 0.f;
       float xs = 0.f;
+      *live = __all_sync(kLuFull, *live);  // warp-uniform before the collective wait
       if (*live && !warp_wait_words(a, words + 32 * s, ns, id, &xs)) *live = false;
 #pragma unroll
       for (int c = 0; c < 32; ++c) acc[c] = fmaf(tile[c], xs, acc[c]);
@@ -232,6 +234,7 @@ __device__ __forceinline__ float lu_r3_block(const RecomputeArgs& a, const float
 #pragma unroll
         for (int c = 0; c < 32; ++c) tile[c] = lane < nr ? __ldcg(tp + c * lda) : 0.f;
         float vs = 0.f;
+        *live = __all_sync(kLuFull, *live);  // warp-uniform before the collective wait
         if (*live && !warp_wait_words(a, words + 32 * s, 32, id, &vs)) *live = false;
 #pragma unroll
         for (int c = 0; c < 32; ++c) acc = fmaf(tile[c], __shfl_sync(kLuFull, vs, c), acc);
@@ -250,6 +253,7 @@ __device__ __forceinline__ float lu_r3_block(const RecomputeArgs& a, const float
 #pragma unroll
         for (int i = 0; i < 32; ++i) tile[i] = i < nr ? __ldcg(tp + i * lda) : 0.f;
         float vs = 0.f;
+        *live = __all_sync(kLuFull, *live);  // warp-uniform before the collective wait
         if (*live && !warp_wait_words(a, words + 32 * s, 32, id, &vs)) *live = false;
 #pragma unroll
         for (int i = 0; i < 32; ++i) acc[i] = fmaf(tile[i], vs, acc[i]);

@@ -451,6 +451,7 @@ static __device__ __noinline__ bool recompute_serve(const RecomputeArgs& a, unsi
 #pragma unroll
         for (int c = 0; c < 32; ++c) tile[c] = (lane < ns && c < nr) ? __ldcg(tp + c * lda) : 0.f;
         float xs = 0.f;
+        live = __all_sync(kRcFull, live);  // warp-uniform before the collective wait
         if (live && !warp_wait_words(a, a.xw + 32 * s, ns, id, &xs)) live = false;
 #pragma unroll
         for (int c = 0; c < 32; ++c) acc[c] = fmaf(tile[c], xs, acc[c]);
@@ -461,6 +462,7 @@ static __device__ __noinline__ bool recompute_serve(const RecomputeArgs& a, unsi
       } else {
         if (ncrit > 0) {
           float xs = 0.f;
+          live = __all_sync(kRcFull, live);  // warp-uniform before the collective wait
           if (live && !warp_wait_words(a, a.xw + 32 * (t + 1), ncrit, id, &xs)) live = false;
 #pragma unroll
           for (int k = 0; k < 32; ++k) red = fmaf(crit[k], __shfl_sync(kRcFull, xs, k), red);
@@ -503,6 +505,7 @@ static __device__ __noinline__ bool recompute_serve(const RecomputeArgs& a, unsi
 #pragma unroll
           for (int c = 0; c < 32; ++c) tile[c] = lane < nr ? __ldcg(tp + c * lda) : 0.f;
           float vs = 0.f;
+          live = __all_sync(kRcFull, live);  // warp-uniform before the collective wait
           if (live && !warp_wait_words(a, a.vw + 32 * s, 32, id, &vs)) live = false;
 #pragma unroll
           for (int c = 0; c < 32; ++c) acc = fmaf(tile[c], __shfl_sync(kRcFull, vs, c), acc);
