@@ -290,7 +290,9 @@ dpp_status dpp_logprob_backward_batched(int32_t batch, const int64_t* n,
  *                         update contracts this many columns at once (32..256,
  *                         multiple of 32; default 256)
  *   DPP_TUNE_UPDATE_KERNEL  mixed-path trailing update: 0 = tensor cores
- *                         (tcgen05), 1 = SIMT FP32 (default 0)
+ *                         (tcgen05), 1 = SIMT FP32 (default 0; real Hermitian
+ *                         K only: the mixed LU and complex paths always use
+ *                         the tensor cores)
  *   DPP_TUNE_MAX_CTAS     mixed path: CTAs per launch of the outer-block and
  *                         tensor-core kernels (0 = one per SM, the default;
  *                         else 8..4096, at most one per SM). With half the SMs,
