@@ -117,3 +117,39 @@ def test_batched_adjoint_workspace_query(L):
     assert L.dpp_logprob_backward_batched_workspace(1000, 300) > a
     assert L.dpp_logprob_backward_batched_workspace(10, 600) > a
     assert L.dpp_logprob_backward_batched_workspace(-1, 300) == 0
+
+
+def test_tuning_keys_validated_on_host(L):
+    """Every tuning key round-trips through set/get and rejects out-of-range
+    values (no CUDA call involved)."""
+    cases = [
+        (_lib.DPP_TUNE_TAU_SAFETY, [8.0, 4.0], [0.0, -1.0]),
+        (_lib.DPP_TUNE_OUTER_BLOCK, [256, 64], [48, 512, 0]),
+        (_lib.DPP_TUNE_UPDATE_KERNEL, [0, 1], [2]),
+        (_lib.DPP_TUNE_MAX_CTAS, [0, 8, 38], [4, 5000]),
+        (_lib.DPP_TUNE_PANEL_PIPELINE, [0, 1, 2], [3, -1]),
+    ]
+    for key, good, bad in cases:
+        old = _lib.get_tuning(key)
+        try:
+            for v in good:
+                _lib.set_tuning(key, v)
+                assert _lib.get_tuning(key) == v
+            for v in bad:
+                assert L.dpp_set_tuning(key, float(v)) == _lib.DPP_ERR_INVALID_ARG
+                assert _lib.get_tuning(key) == good[-1]
+        finally:
+            _lib.set_tuning(key, old)
+    assert L.dpp_set_tuning(99, 1.0) == _lib.DPP_ERR_INVALID_ARG
+
+
+def test_mixed_workspace_sizes_per_form():
+    """Mixed precision: real Hermitian (either panel pipeline), complex
+    Hermitian (planar copy, 8 B per element) and real LU (full square) have
+    workspaces; complex LU has none."""
+    n = 1000
+    herm = dpp.workspace_size(0, n, _lib.DPP_R64, _lib.DPP_PREC_3XTF32, 1)
+    cplx = dpp.workspace_size(0, n, _lib.DPP_C128, _lib.DPP_PREC_3XTF32, 1)
+    lu = dpp.workspace_size(1, n, _lib.DPP_R64, _lib.DPP_PREC_BF16X6, 0)
+    assert herm >= 4 * n * n and lu >= 4 * n * n and cplx >= 8 * n * n
+    assert dpp.workspace_size(1, n, _lib.DPP_C128, _lib.DPP_PREC_BF16X6, 0) == 0
