@@ -714,7 +714,7 @@ def main():
 
     if rank == 0:
         line = {
-            "metric": f"DPP samples/s, dense Hermitian n={n} ({prec_name})",
+            "metric": f"DPP samples/s, dense Hermitian n={n}",
             "value": value, "unit": "samples/s", "n_gpus": ws_n, "steps": steps,
             "warmup": warmup, "ms_per_step": ms / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
