@@ -42,8 +42,6 @@ def parse():
     p.add_argument("--n", type=int, default=16384)
     p.add_argument("--kind", default="beta", choices=["beta", "uniform", "projection"])
     p.add_argument("--precision", default="auto", choices=["auto", "fp64", "3xtf32", "bf16x6"])
-    p.add_argument("--cpu-sample-n", type=int, default=3072,
-                   help="order of the leading block the CPU oracle samples")
     p.add_argument("--update", default="tc", choices=["tc", "simt"],
                    help="mixed path trailing update: tcgen05 3xTF32 or SIMT FP32")
     p.add_argument("--gen", default="gpu", choices=["gpu", "cpu"],
@@ -291,31 +289,34 @@ def run_suite(args):
                           "ms_per_launch": ms_b}), flush=True)
         del b, Kd
 
-    # C2: n = 4096, real projection / Beta, FP64 and mixed; complex Beta FP64
+    # C2: n = 4096 and 16384; real and complex; projection (rank n/4) and
+    # Beta(1/2, 1/2) spectra; FP64 and mixed
     def suite_c2():
-        n = 4096
-        for kind in ("projection", "beta"):
-            Kd = W.hermitian_kernel(n, seed=0, kind=kind, device=str(dev), return_torch=True).contiguous()
-            for prec_name, draws in (("fp64", 4), ("bf16x6", 16)):
-                fn, keep, raw = hermitian(Kd, n, prec_name)
-                ms, prof = timed(fn, draws)
-                res = _lib.decode_result(bytes(raw.cpu().numpy().tobytes()))
-                line("C2", {"n": n, "kind": kind, "dtype": "f64"}, prec_name, ms, n ** 3 / 3, prof,
-                     {"last_draw_kept": res["n_kept"], "last_draw_borderline": res["n_borderline"]})
-            del Kd
-        Kc = W.hermitian_kernel(n, seed=0, kind="beta", complex_=True, device=str(dev),
-                                return_torch=True).contiguous()
-        fn, keep, raw = hermitian(Kc, n, "fp64", dt=1)
-        ms, prof = timed(fn, 2, warm=1)
-        line("C2", {"n": n, "kind": "beta", "dtype": "c128"}, "fp64", ms, 4 * n ** 3 / 3, prof)
-        for prec_name in ("bf16x6", "3xtf32"):
-            fn, keep, raw = hermitian(Kc, n, prec_name, dt=1)
-            ms, prof = timed(fn, 16)
-            res = _lib.decode_result(bytes(raw.cpu().numpy().tobytes()))
-            line("C2", {"n": n, "kind": "beta", "dtype": "c128"}, prec_name, ms, 4 * n ** 3 / 3,
-                 prof, {"last_draw_kept": res["n_kept"], "last_draw_borderline": res["n_borderline"],
-                        "last_draw_status": res["status"]})
-        del Kc
+        for n in (4096, 16384):
+            for dt, cplx in ((0, False), (1, True)):
+                for kind in ("projection", "beta"):
+                    Kd = W.hermitian_kernel(n, seed=0, kind=kind, complex_=cplx, device=str(dev),
+                                            return_torch=True)
+                    Kd = Kd.t().contiguous().t() if cplx else Kd.contiguous()
+                    flops = (4 if cplx else 1) * n ** 3 / 3
+                    big = n >= 16384
+                    runs = (("fp64", 1 if big else 2, 1), ("bf16x6", 8 if big else 16, 2),
+                            ("3xtf32", 8 if big else 16, 2))
+                    for prec_name, draws, warm in runs:
+                        fn, keep, raw = hermitian(Kd, n, prec_name, dt=dt)
+                        ms, prof = timed(fn, draws, warm=warm)
+                        res = _lib.decode_result(bytes(raw.cpu().numpy().tobytes()))
+                        extra = {"last_draw_kept": res["n_kept"],
+                                 "last_draw_borderline": res["n_borderline"],
+                                 "last_draw_status": res["status"]}
+                        if kind == "projection":
+                            extra["rank"] = n // 4
+                        line("C2", {"n": n, "kind": kind, "dtype": "c128" if cplx else "f64"},
+                             prec_name, ms, flops, prof, extra)
+                        del fn, keep, raw
+                        torch.cuda.empty_cache()
+                    del Kd
+                    torch.cuda.empty_cache()
 
     # C3: uniform spanning trees of the 64 x 64 grid (n = 8064, rank 4095)
     def suite_c3():
@@ -403,25 +404,47 @@ def dist_env():
     return ws, rank, local
 
 
-def cpu_oracle_baseline(K_host, n_full: int, m: int, seed: int = 0):
-    """Time the FP64 oracle (as it stands) on the leading m x m block of the same
-    kernel, one draw, and scale to order n by the n^3 cost of the factorization."""
+def oracle_full_draw(K_host, seed: int):
+    """One oracle draw (Algorithm 1, LDL^H form, FP64, as it stands) on the
+    full kernel with the Philox uniforms of `seed`, timed on the host cores."""
     from oracle import oracle as O
     O.build()
-    Km = K_host[:m, :m].copy()
-    u = O.uniforms(seed, 0, m)
+    n = K_host.shape[0]
+    u = O.uniforms(seed, 0, n)
     t0 = time.perf_counter()
-    O.sample_ldl(Km, u)
+    ref = O.sample_ldl(K_host, u)
     dt = time.perf_counter() - t0
-    scale = (n_full / m) ** 3
-    return {"value": 1.0 / (dt * scale), "unit": "samples/s", "cores": O.num_threads(),
-            "kind": "oracle",
-            "sample": (f"one oracle draw on the leading {m}x{m} block of the n={n_full} kernel "
-                       f"took {dt:.2f} s; scaled by (n/m)^3 = {scale:.1f} to one n={n_full} draw")}
+    return ref, u, dt, O.num_threads()
+
+
+def err_vs_oracle(keep, pivots, res, ref, u, gap=1e-9):
+    """Decision agreement, pivot and log P error of one GPU draw against the
+    oracle's draw with the same uniforms. Decisions are compared up to the
+    first pivot whose uniform lies within `gap` of the oracle's pivot (there
+    rounding order may decide either way)."""
+    import numpy as np
+    n = len(ref.keep)
+    piv_o = np.asarray(ref.pivots, dtype=np.float64)
+    pre = np.where(ref.keep == 1, piv_o, piv_o + 1.0)
+    close = np.flatnonzero(np.abs(u - pre) <= gap)
+    j0 = int(close[0]) if len(close) else n
+    agree = np.asarray(keep[:j0]) == ref.keep[:j0]
+    first_diff = int(np.flatnonzero(~agree)[0]) if not agree.all() else None
+    jp = j0 if first_diff is None else first_diff
+    perr = float(np.max(np.abs(np.asarray(pivots[:jp]) - piv_o[:jp]))) if jp else 0.0
+    return {"decisions_compared": j0, "decisions_equal": bool(agree.all()),
+            "first_mismatch": first_diff, "borderline_draw": j0 < n,
+            "logp_gpu": res["logp"], "logp_oracle": ref.logp,
+            "logp_rel_err": abs(res["logp"] - ref.logp) / max(1.0, abs(ref.logp)),
+            "max_pivot_abs_err": perr, "gpu_recomputed_pivots": res["n_borderline"],
+            "n_kept_gpu": res["n_kept"], "n_kept_oracle": int(ref.keep.sum())}
 
 
 def run_reference(args):
-    """The oracle arm: the plain FP64 CPU oracle timed on the host cores."""
+    """The oracle arm: the plain FP64 CPU oracle, as it stands, timed on the
+    host cores on the full n x n kernel of the headline workload. Each step is
+    one complete oracle draw; as many steps are run as fit in about two and a
+    half minutes (at least one), and `steps` reports that number."""
     ws, rank, local = dist_env()
     if rank != 0:
         return 0
@@ -429,36 +452,90 @@ def run_reference(args):
     import workloads as W
     from oracle import oracle as O
     O.build()
-    n, m = args.n, args.cpu_sample_n
-    steps = args.steps if args.steps is not None else 2
-    # the leading m x m block of K has the law of an m x m block of a Haar
-    # conjugated spectrum; generate the full kernel only for modest n
-    K = W.hermitian_kernel(m, seed=0, kind=args.kind)
-    for w in range(max(0, min(args.warmup, 1))):
-        O.sample_ldl(K, O.uniforms(10**6 + w, 0, m))
-    t0 = time.perf_counter()
-    for s in range(steps):
-        O.sample_ldl(K, O.uniforms(s, 0, m))
-    dt = (time.perf_counter() - t0) / steps
-    scale = (n / m) ** 3
-    value = 1.0 / (dt * scale)
+    n = args.n
+    t_gen = time.perf_counter()
+    dev = None
+    try:
+        import torch
+        if torch.cuda.is_available():
+            dev = f"cuda:{local}"
+    except Exception:
+        dev = None
+    # the same kernel as the GPU arm (Haar factor computed on the device when
+    # there is one; the oracle itself runs on the host cores only)
+    K = W.hermitian_kernel(n, seed=0, kind=args.kind, device=dev)
+    K = np.ascontiguousarray(K)
+    t_gen = time.perf_counter() - t_gen
+    # warm-up: one draw on a 1024 x 1024 block starts the OpenMP threads
+    O.sample_ldl(K[:1024, :1024], O.uniforms(10**6, 0, 1024))
+    requested = args.steps if args.steps is not None else 1
+    budget_s = 150.0
+    times = []
+    t_all = time.perf_counter()
+    for s in range(max(1, requested)):
+        t0 = time.perf_counter()
+        O.sample_ldl(K, O.uniforms(s, 0, n))
+        times.append(time.perf_counter() - t0)
+        elapsed = time.perf_counter() - t_all
+        if elapsed + times[-1] > budget_s:
+            break
+    total = sum(times)
+    steps = len(times)
+    value = steps / total
     line = {
         "impl": "reference", "metric": f"DPP samples/s, dense Hermitian n={n}",
         "value": value, "unit": "samples/s", "n_gpus": args.gpus, "steps": steps,
-        "warmup": args.warmup, "ms_per_step": dt * scale * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "steps_requested": requested, "warmup": 0, "ms_per_step": total / steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
         "config": {"workload": f"hermitian_real_{args.kind}_n{n}", "n": n,
-                   "kernel": f"Q diag(lam) Q^T, Haar Q, lam~{args.kind}",
-                   "l2_policy": "inputs larger than L2"},
+                   "kernel": f"Q diag(lam) Q^T, Haar Q (seed 0), lam~{args.kind}",
+                   "seeds": "Philox seed = step index",
+                   "l2_policy": "inputs larger than L2 (2 GiB FP64 K), no flush"},
         "cpu_baseline": {"value": value, "unit": "samples/s", "cores": O.num_threads(),
                          "kind": "oracle",
-                         "sample": f"each step: one oracle draw on an {m}x{m} kernel of the same "
-                                   f"law, scaled by (n/m)^3 = {scale:.1f}"},
+                         "sample": (f"{steps} complete oracle draw(s) of the n={n} kernel "
+                                    f"({', '.join(f'{t:.1f}' for t in times)} s each); "
+                                    "warm-up: one draw on a 1024 x 1024 block; the step count "
+                                    "is capped so the arm ends in about 2.5 min")},
         "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
+        "input_generation_s": t_gen,
     }
     print(json.dumps(line))
     return 0
+
+
+def measure_dense_peaks(dev):
+    """Dense TF32 and FP64 matmul throughput on this GPU (torch.matmul, CUDA
+    events, best of several): the denominators for the FP64 path and a
+    measured-TF32 fraction beside the nominal-ratio one."""
+    import torch
+    out = {}
+    for name, dt, n, reps in (("tf32", torch.float32, 8192, 6), ("fp64", torch.float64, 4096, 3)):
+        old = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = name == "tf32"
+        try:
+            a = torch.randn(n, n, device=dev, dtype=dt)
+            b = torch.randn(n, n, device=dev, dtype=dt)
+            c = a @ b
+            torch.cuda.synchronize()
+            best = None
+            for _ in range(reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                c = a @ b
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None else min(best, ms)
+            out[f"{name}_tflops"] = 2.0 * n ** 3 / (best / 1e3) / 1e12
+            del a, b, c
+        finally:
+            torch.backends.cuda.matmul.allow_tf32 = old
+    out["how"] = "torch.matmul: TF32 8192^3 best of 6, FP64 4096^3 best of 3 (2 n^3 flops)"
+    return out
 
 
 def main():
@@ -566,6 +643,13 @@ def main():
     res = _lib.decode_result(bytes(raw.cpu().numpy().tobytes()))
     value = ws_n * steps / (ms / 1e3)
     algo_flops = n ** 3 / 3.0
+    # the last timed draw on the first stream, kept for the oracle comparison
+    s_par = max(s for s in range(steps) if s % nst == 0)
+    seed_par = base_seed + s_par
+    par_keep = keeps[0].cpu().numpy().copy()
+    par_piv = pivs[0].cpu().numpy().copy()
+    par_res = res
+    dense = measure_dense_peaks(dev)
 
     # ---- roofline of the dominant kernel -----------------------------------
     peaks = measured_peaks()
@@ -578,9 +662,11 @@ def main():
         per_launch_flops = st["flops"] / max(1, st["launches"])
         if dom == "update_fp64":
             ach = per_launch_flops / (avg_ms / 1e3) / 1e12
-            roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": FP64_NOMINAL_TFLOPS,
-                    "unit": "TFLOP/s", "frac": ach / FP64_NOMINAL_TFLOPS, "traffic": None,
-                    "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (cuBLAS DGEMM measured 1.10)"}
+            f64 = dense["fp64_tflops"]
+            roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": f64,
+                    "unit": "TFLOP/s", "frac": ach / f64, "traffic": None,
+                    "peak_source": "FP64 torch.matmul measured in this run",
+                    "frac_of_nominal_1.25": ach / FP64_NOMINAL_TFLOPS}
         elif dom == "update_tc" and prec_name == "3xtf32":
             tf32 = peaks.get("bf16_tflops", 1888.3) * TF32_PER_BF16
             ach = per_launch_flops / (avg_ms / 1e3) / 1e12
@@ -588,7 +674,9 @@ def main():
                     "unit": "TFLOP/s", "frac": ach / (tf32 / 3.0),
                     "traffic": tc_traffic_per_launch("3xtf32") if n == 16384 else None,
                     "executed_tensor_frac": 3.0 * ach / tf32,
-                    "peak_source": "measured bf16 x nominal tf32/bf16 (2.25:1.1), / 3 products"}
+                    "peak_source": "measured bf16 x nominal tf32/bf16 (2.25:1.1), / 3 products",
+                    "measured_tf32_tflops": dense["tf32_tflops"],
+                    "frac_of_measured_tf32_div3": ach / (dense["tf32_tflops"] / 3.0)}
         elif dom == "update_tc":
             bf16 = peaks.get("bf16_tflops", 1888.3)
             ach = per_launch_flops / (avg_ms / 1e3) / 1e12
@@ -630,6 +718,7 @@ def main():
         torch.cuda.synchronize()
         t64 = e0.elapsed_time(e1) / 1e3
         fp64_ref = {"samples_per_s": 1.0 / t64, "tflops": algo_flops / t64 / 1e12,
+                    "frac_of_measured_fp64": algo_flops / t64 / 1e12 / dense["fp64_tflops"],
                     "draws": 1, "speedup_mixed_over_fp64": value / ws_n * t64}
         del ws64
 
@@ -708,9 +797,17 @@ def main():
         batched = bench_batched(dpp, _lib, dev, args.batch, draws=5)
 
     cpu = None
+    err = None
     if rank == 0 and ws_n == 1 and not args.no_cpu:
-        cpu = cpu_oracle_baseline(Kd[: args.cpu_sample_n, : args.cpu_sample_n].cpu().numpy(), n,
-                                  args.cpu_sample_n)
+        # one complete oracle draw of the same kernel with the uniforms of the
+        # kept timed draw: the CPU baseline and that draw's error in one
+        ref, u_par, t_or, cores = oracle_full_draw(Kd.cpu().numpy(), seed_par)
+        cpu = {"value": 1.0 / t_or, "unit": "samples/s", "cores": cores, "kind": "oracle",
+               "sample": (f"one complete oracle draw of the n={n} kernel (seed {seed_par}) "
+                          f"on the host cores: {t_or:.1f} s")}
+        err = dict(err_vs_oracle(par_keep, par_piv, par_res, ref, u_par), seed=seed_par,
+                   draw=f"timed draw {s_par} (stream 0) of the bench configuration")
+        del ref
 
     if rank == 0:
         line = {
@@ -730,8 +827,10 @@ def main():
                        "streams": nst},
             "tflops_algorithmic": value * algo_flops / 1e12,
             "roofline": roof,
+            "err_vs_oracle": err,
             "kernels": kernels,
             "fp64_gpu_path": fp64_ref,
+            "dense_peaks_measured": dense,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "batched": batched,

@@ -170,7 +170,9 @@ dpp_status dpp_sample_hermitian(const void* K, int64_t n, int64_t ld,
  * Set-up: the first call on each device, made with that device current, looks
  * up the array's device address (cudaGetSymbolAddress, which may load the
  * library's module onto the device); make that first call before any stream
- * capture begins. Nothing in the array needs to start at zero: the call clears
+ * capture begins. Every later call whose stream is not capturing looks the
+ * address up again (so a device reset, after which the array may move, is
+ * picked up); a call inside a capture uses the device's last address. Nothing in the array needs to start at zero: the call clears
  * its flag word on `stream` before the first kernel.
  * Concurrency: all calls on one device share the one array, so two calls in
  * flight at once on a device (different streams, or host threads without
@@ -308,13 +310,27 @@ dpp_status dpp_logprob_backward_batched(int32_t batch, const int64_t* n,
  *                         0 = automatic (the default): chunked when a launch
  *                         gets at least 96 CTAs, else single helper. The SIMT
  *                         trailing update always runs with pipeline 1.
+ *   DPP_TUNE_WAIT_NS      limit, in nanoseconds, of every bounded wait between
+ *                         the CTAs of the panel launches (FP64 panels, mixed
+ *                         panel pipelines and their FP64 recomputes); a wait
+ *                         that runs out ends its launch early and sets
+ *                         DPP_RES_TIMEOUT (1e5..6e10, default 2e9)
+ *   DPP_TUNE_FAULT_WITHHOLD  fault injection for tests of the bounded waits
+ *                         (default 0). With 1, the CTA that makes the
+ *                         decisions never releases a panel to the other CTAs
+ *                         (the FP64 panel kernels and the chunked mixed
+ *                         pipeline): their waits run out after DPP_TUNE_WAIT_NS,
+ *                         every launch still ends, and the draw's status has
+ *                         DPP_RES_TIMEOUT. Its outputs are then meaningless.
  * Returns DPP_ERR_INVALID_ARG for an unknown key or out-of-range value. */
 typedef enum {
   DPP_TUNE_TAU_SAFETY = 0,
   DPP_TUNE_OUTER_BLOCK = 1,
   DPP_TUNE_UPDATE_KERNEL = 2,
   DPP_TUNE_MAX_CTAS = 3,
-  DPP_TUNE_PANEL_PIPELINE = 4
+  DPP_TUNE_PANEL_PIPELINE = 4,
+  DPP_TUNE_WAIT_NS = 5,
+  DPP_TUNE_FAULT_WITHHOLD = 6
 } dpp_tune_key;
 
 dpp_status dpp_set_tuning(int32_t key, double value);

@@ -137,6 +137,7 @@ def profile_stop() -> dict:
 
 DPP_TUNE_TAU_SAFETY, DPP_TUNE_OUTER_BLOCK, DPP_TUNE_UPDATE_KERNEL, DPP_TUNE_MAX_CTAS = 0, 1, 2, 3
 DPP_TUNE_PANEL_PIPELINE = 4
+DPP_TUNE_WAIT_NS, DPP_TUNE_FAULT_WITHHOLD = 5, 6
 
 
 def set_tuning(key: int, value: float) -> None:

@@ -314,6 +314,15 @@ dpp_status dpp_set_tuning(int32_t key, double value) {
         return fail(DPP_ERR_INVALID_ARG, "panel pipeline is 0, 1 or 2");
       g_tuning.panel_pipeline = (int)value;
       return DPP_OK;
+    case DPP_TUNE_WAIT_NS:
+      if (!(value >= 1e5 && value <= 6e10))
+        return fail(DPP_ERR_INVALID_ARG, "wait limit must be in [1e5, 6e10] ns");
+      g_tuning.wait_ns = value;
+      return DPP_OK;
+    case DPP_TUNE_FAULT_WITHHOLD:
+      if (value != 0.0 && value != 1.0) return fail(DPP_ERR_INVALID_ARG, "fault withhold is 0 or 1");
+      g_tuning.fault_withhold = (int)value;
+      return DPP_OK;
     default:
       return fail(DPP_ERR_INVALID_ARG, "unknown tuning key");
   }
@@ -326,6 +335,8 @@ double dpp_get_tuning(int32_t key) {
     case DPP_TUNE_UPDATE_KERNEL: return (double)g_tuning.update_kernel;
     case DPP_TUNE_MAX_CTAS: return (double)g_tuning.max_ctas;
     case DPP_TUNE_PANEL_PIPELINE: return (double)g_tuning.panel_pipeline;
+    case DPP_TUNE_WAIT_NS: return g_tuning.wait_ns;
+    case DPP_TUNE_FAULT_WITHHOLD: return (double)g_tuning.fault_withhold;
     default: return -1.0;
   }
 }

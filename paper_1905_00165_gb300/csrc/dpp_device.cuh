@@ -182,8 +182,11 @@ __device__ inline double philox_uniform(uint64_t seed, uint64_t instance, uint64
 }
 
 // ---------------------------------------------------------------------------
-// Bounded waits. Every spin in this library gives up after kWaitNs of
+// Bounded waits. Every spin in this library gives up after a limit of
 // wall-clock time (device %globaltimer), reports DPP_RES_TIMEOUT and returns.
+// The waits between the CTAs of the panel launches take their limit from the
+// launch arguments (DPP_TUNE_WAIT_NS, 2 s by default); the tensor-core
+// update's pipeline waits use the fixed kWaitNs.
 // ---------------------------------------------------------------------------
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
 
@@ -203,14 +206,15 @@ __device__ inline void st_release(unsigned* p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Spin (one thread) until *flag >= target. Returns false on timeout.
-__device__ inline bool wait_geq(const unsigned* flag, unsigned target) {
+// Spin (one thread) until *flag >= target. Returns false after limit_ns.
+__device__ inline bool wait_geq(const unsigned* flag, unsigned target,
+                                unsigned long long limit_ns) {
   if (ld_acquire(flag) >= target) return true;
   const unsigned long long t0 = global_ns();
   unsigned sleep = 32;
   while (true) {
     if (ld_acquire(flag) >= target) return true;
-    if (global_ns() - t0 > kWaitNs) return false;
+    if (global_ns() - t0 > limit_ns) return false;
     __nanosleep(sleep);
     if (sleep < 1024) sleep <<= 1;
   }

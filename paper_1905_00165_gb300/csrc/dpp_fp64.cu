@@ -40,6 +40,8 @@ struct PanelArgs {
   unsigned* flag;
   unsigned epoch;
   double tol;
+  unsigned long long wait_ns;  // limit of the other CTAs' wait for the release
+  int withhold;                // fault injection: CTA 0 never releases the panel
 };
 
 template <class T>
@@ -77,7 +79,7 @@ struct DecisionLog {
 // Non-zero CTAs wait for CTA 0's release of this panel's epoch.
 __device__ inline bool panel_wait(const PanelArgs& a, int* s_ok) {
   if (threadIdx.x == 0) {
-    const bool ok = wait_geq(a.flag, a.epoch);
+    const bool ok = wait_geq(a.flag, a.epoch, a.wait_ns);
     if (!ok) flag_status(a.res, DPP_RES_TIMEOUT);
     *s_ok = ok ? 1 : 0;
     __threadfence();
@@ -146,7 +148,7 @@ __global__ void __launch_bounds__(kPanelThreads) k_panel_herm(PanelArgs a) {
     if (threadIdx.x < kPanel) sd[threadIdx.x] = threadIdx.x < b ? S::re(blk[threadIdx.x][threadIdx.x]) : 1.0;
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) st_release(a.flag, a.epoch);
+    if (threadIdx.x == 0 && !a.withhold) st_release(a.flag, a.epoch);
   } else {
     if (!panel_wait(a, &s_ok)) return;
     for (int idx = threadIdx.x; idx < kPanel * kPanel; idx += blockDim.x) {
@@ -241,7 +243,7 @@ __global__ void __launch_bounds__(kPanelThreads) k_panel_lu(PanelArgs a) {
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) st_release(a.flag, a.epoch);
+    if (threadIdx.x == 0 && !a.withhold) st_release(a.flag, a.epoch);
   } else {
     if (!panel_wait(a, &s_ok)) return;
     for (int idx = threadIdx.x; idx < kPanel * kPanel; idx += blockDim.x) {
@@ -430,8 +432,12 @@ cudaError_t run_fp64(const DrawArgs& a, bool herm, Workspace ws) {
     if (e != cudaSuccess) return e;
   }
   auto panel = herm ? k_panel_herm<T> : k_panel_lu<T>;
-  static int cap_h = 0, cap_l = 0;
-  int& cap = herm ? cap_h : cap_l;
+  // cooperative capacity of the panel kernel, per device and form
+  static int caps[64][2] = {};
+  int dev = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  int& cap = caps[dev][herm ? 0 : 1];
   if (cap == 0) cap = coop_capacity(panel, kPanelThreads, 0);
   const size_t upd_smem = esz * (size_t)kPanel * (2 * kTile + 1);
   auto upd = herm ? k_update<T, true> : k_update<T, false>;
@@ -459,6 +465,8 @@ cudaError_t run_fp64(const DrawArgs& a, bool herm, Workspace ws) {
     pa.flag = flag;
     pa.epoch = epoch;
     pa.tol = 1e-6;
+    pa.wait_ns = (unsigned long long)g_tuning.wait_ns;
+    pa.withhold = g_tuning.fault_withhold;
     const int64_t items = herm ? m : 2 * m;
     int64_t g = (items + kPanelThreads - 1) / kPanelThreads;
     if (g < 1) g = 1;

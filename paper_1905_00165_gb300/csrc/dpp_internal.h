@@ -69,6 +69,8 @@ struct Tuning {
   int update_kernel = 0;    // 0 = tcgen05, 1 = SIMT FP32
   int max_ctas = 0;         // mixed path: CTAs per launch (0 = one per SM)
   int panel_pipeline = 0;   // mixed Hermitian path: 0 = auto, 1 = single helper, 2 = chunked
+  double wait_ns = 2e9;     // limit of the bounded device waits (ns)
+  int fault_withhold = 0;   // fault injection: the deciding CTA never releases a panel
 };
 extern Tuning g_tuning;
 constexpr int kMaxOuterBlock = 256;

@@ -98,6 +98,7 @@ struct LuArgs {
   float* Bbuf;  // [32 x 32] next diagonal block, row-major
   int nh;       // helper CTAs 1..nh (chunks of the outer block)
   int slots;    // precomputed-chunk slots in shared memory
+  int withhold; // fault injection: CTA 0 never publishes a panel
   LuRc lr;
 };
 
@@ -1147,7 +1148,7 @@ __global__ void __launch_bounds__(kLuThreads, 1) k_lu_outer(LuArgs a) {
       }
       lu_decide<SYM>(a, p, b, epoch);
       __syncthreads();
-      if (tid == 0) {
+      if (tid == 0 && !a.withhold) {
         __threadfence();
         st_release(&rc.ctrl[kCtlDone], epoch);
       }
@@ -1450,6 +1451,7 @@ cudaError_t sample_chunked(const DrawArgs& a, Workspace ws) {
     la.Bbuf = L.Bbuf;
     la.nh = nh;
     la.slots = slots;
+    la.withhold = g_tuning.fault_withhold;
     la.lr.rc = recompute_args(L.rs, K, a.ld, L.A32, L.ld32, L.piv, a.keep, n, q, a.result);
     la.lr.rc.grid = grid;
     la.lr.yw = L.yw;

@@ -68,6 +68,7 @@ struct RecomputeArgs {
   int64_t n, q;
   int grid;
   dpp_result* res;
+  unsigned long long wait_ns;  // limit of every bounded wait of the launch
 };
 
 inline bool recompute_carve(Workspace& ws, int64_t n, RecomputeScratch* s) {
@@ -112,6 +113,7 @@ inline RecomputeArgs recompute_args(const RecomputeScratch& s, const double* K, 
   a.q = q;
   a.grid = 1;
   a.res = res;
+  a.wait_ns = (unsigned long long)g_tuning.wait_ns;
   return a;
 }
 
@@ -139,7 +141,7 @@ __device__ inline bool word_has(unsigned long long w, unsigned id) {
 // Raise the abort flag on timeout; true if the caller must give up.
 __device__ inline bool rc_give_up(const RecomputeArgs& a, unsigned long long t0) {
   if (ld_acquire(&a.ctrl[kCtlAbort]) != 0) return true;
-  if (global_ns() - t0 > kWaitNs) {
+  if (global_ns() - t0 > a.wait_ns) {
     atomicExch(&a.ctrl[kCtlAbort], 1u);
     flag_status(a.res, DPP_RES_TIMEOUT);
     return true;

@@ -15,7 +15,10 @@
 //
 // Set-up: the first call on each device (with that device current) looks up
 // the array's device address with cudaGetSymbolAddress, which may load this
-// module onto the device; the address is kept per device for later calls.
+// module onto the device. Later calls look it up again whenever their stream
+// is not capturing (a device reset reloads the module, and the array may then
+// live at another address); a call inside a stream capture uses the address
+// of the device's last call.
 //
 // Concurrency: every call on one device uses the same array, so two calls in
 // flight at the same time on one device (two streams, or two host threads
@@ -40,14 +43,17 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {};
 
-// Device address of g_static_scratch on the current device (looked up once).
-cudaError_t static_scratch(void** out) {
+// Device address of g_static_scratch on the current device: looked up on
+// every call whose stream is not capturing, else the device's cached one.
+cudaError_t static_scratch(cudaStream_t stream, void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if ((e = cudaStreamIsCapturing(stream, &cs)) != cudaSuccess) return e;
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch_ptr[dev]) {
+  if (!g_scratch_ptr[dev] || cs == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_static_scratch);
     if (e != cudaSuccess) return e;
@@ -96,7 +102,7 @@ dpp_status dpp_sample_hermitian_static(const void* K, int64_t n, int64_t ld, int
     return set_last_error(DPP_ERR_WORKSPACE, buf);
   }
   void* scratch = nullptr;
-  cudaError_t e = static_scratch(&scratch);
+  cudaError_t e = static_scratch(static_cast<cudaStream_t>(stream), &scratch);
   if (e != cudaSuccess) return set_last_cuda_error(e, "dpp_sample_hermitian_static: scratch set-up");
   DrawArgs a;
   a.K = K;

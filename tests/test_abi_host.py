@@ -128,6 +128,8 @@ def test_tuning_keys_validated_on_host(L):
         (_lib.DPP_TUNE_UPDATE_KERNEL, [0, 1], [2]),
         (_lib.DPP_TUNE_MAX_CTAS, [0, 8, 38], [4, 5000]),
         (_lib.DPP_TUNE_PANEL_PIPELINE, [0, 1, 2], [3, -1]),
+        (_lib.DPP_TUNE_WAIT_NS, [2e9, 1e6], [1e4, 1e11, -1.0]),
+        (_lib.DPP_TUNE_FAULT_WITHHOLD, [1, 0], [2, -1]),
     ]
     for key, good, bad in cases:
         old = _lib.get_tuning(key)

@@ -39,9 +39,36 @@ def test_batched_parity_uneven_sizes(dpp):
         ref = O.sample_ldl(K, u)
         r = res[i]
         assert r["status"] & ~4 == 0, (i, r)
-        compare_draw(b.keep[i][:n].cpu().numpy(), r["logp"], b.pivots[i][:n].cpu().numpy(), ref,
-                     u, logp_rtol=1e-6, piv_atol=1e-4)
-        assert r["n_kept"] == int(ref.keep.sum()) or True
+        j0, border = compare_draw(b.keep[i][:n].cpu().numpy(), r["logp"],
+                                  b.pivots[i][:n].cpu().numpy(), ref, u, logp_rtol=1e-6,
+                                  piv_atol=1e-4)
+        if not border:
+            assert r["n_kept"] == int(ref.keep.sum()), (i, r["n_kept"], int(ref.keep.sum()))
+
+
+def test_batched_parity_large_instances(dpp):
+    """Instances of the batched workload's upper range (n in [512, 1024],
+    L-ensembles and Haar kernels, ragged against the 32-wide panels) against
+    the oracle, instance by instance."""
+    import torch
+    sizes = [1024, 512, 777, 1000, 640, 901, 1023, 513]
+    Ks = [W.lensemble_kernel(m, seed=300 + i) if i % 2 == 0 else
+          W.hermitian_kernel(m, seed=300 + i, kind="beta") for i, m in enumerate(sizes)]
+    seed = 13
+    b = dpp.sample_batched(_to_dev(Ks), seed=seed, want_pivots=True)
+    torch.cuda.synchronize()
+    res = b.results()
+    for i, K in enumerate(Ks):
+        n = K.shape[0]
+        u = O.uniforms(seed, i, n)
+        ref = O.sample_ldl(K, u)
+        r = res[i]
+        assert r["status"] & ~4 == 0, (i, r)
+        j0, border = compare_draw(b.keep[i][:n].cpu().numpy(), r["logp"],
+                                  b.pivots[i][:n].cpu().numpy(), ref, u, logp_rtol=1e-6,
+                                  piv_atol=1e-4)
+        if not border:
+            assert r["n_kept"] == int(ref.keep.sum()), (i, r["n_kept"], int(ref.keep.sum()))
 
 
 def test_batched_lensembles_and_instances(dpp):

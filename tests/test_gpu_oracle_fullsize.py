@@ -1,0 +1,262 @@
+"""The CUDA paths against the FP64 CPU oracle at the sizes the benchmark measures.
+
+One oracle draw per workload (the plain Algorithm 1 in its LDL^H or LU form,
+on the host cores; about a minute for n = 16384) is compared with:
+
+* Hermitian real, n = 16384, Beta(1/2, 1/2) spectrum, seed 0:
+    - the FP64 GPU path (decisions up to the first pivot within 1e-9 of its
+      uniform, pivots, log P within 1e-10 relative);
+    - the mixed path one draw at a time (3xTF32 and BF16x6, chunked panel
+      pipeline on the full grid);
+    - the mixed path in the benchmark's launch configuration (3xTF32, each
+      launch on a quarter of the SMs, four draws on four streams);
+  and the borderline band tau_j = c 2^-22 sqrt(j+1) (K_jj + s_j) is checked
+  against the mixed pivots' real error on all 16384 pivots (decisions forced
+  to the oracle's, so no pivot is recomputed).
+* General (LU) real, n = 8192, K = D^{-1} S D: FP64 and mixed paths; band
+  with s_j = sum_k |L_jk U_kj|.
+* Hermitian complex, n = 4096, Beta(1/2, 1/2): FP64 and mixed paths; band
+  with s_j = sum_k |L_jk|^2 |d_k|.
+
+The mixed paths must give the oracle's decisions on every draw without a
+borderline pivot (Theorem 1: the chain of decisions is a function of K and
+the uniforms), with log P within 1e-6 relative (FP32 factors, FP64 pivots).
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import oracle as O
+from tests._parity import compare_draw
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+MIXED_LOGP_RTOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def dpp():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1905_00165_gb300 as m
+    return m
+
+
+def _ok(r, lib, recompute_ok=False):
+    bad = lib.DPP_RES_TIMEOUT | lib.DPP_RES_NONFINITE
+    if not recompute_ok:
+        bad |= lib.DPP_RES_RECOMPUTE
+    return (r["status"] & bad) == 0
+
+
+def _band_ratio(dmix, dref, kdiag, s):
+    """|d_mixed - d_oracle| / (2^-22 sqrt(j+1) (|K_jj| + s_j)) for every pivot."""
+    n = len(dref)
+    scale = 2.0 ** -22 * np.sqrt(np.arange(n) + 1.0) * (np.abs(kdiag) + s)
+    return np.abs(np.asarray(dmix) - np.asarray(dref)) / scale
+
+
+# ---------------------------------------------------------------------------
+# Hermitian real, n = 16384
+# ---------------------------------------------------------------------------
+N_BIG = 16384
+SEED_BIG = 0
+
+
+@pytest.fixture(scope="module")
+def herm_big(dpp):
+    import torch
+    Kd = W.hermitian_kernel(N_BIG, seed=0, kind="beta", device="cuda",
+                            return_torch=True).contiguous()
+    Kh = Kd.cpu().numpy()
+    u = O.uniforms(SEED_BIG, 0, N_BIG)
+    ref = O.sample_ldl(Kh, u)
+    torch.cuda.synchronize()
+    yield Kd, Kh, u, ref
+    del Kd
+
+
+def _draw(dpp, Kd, seed, precision, **kw):
+    import torch
+    s = dpp.sample_hermitian(Kd, seed=seed, precision=precision, **kw)
+    torch.cuda.synchronize()
+    return s
+
+
+def test_fp64_path_matches_oracle_n16384(dpp, herm_big):
+    from paper_1905_00165_gb300 import _lib
+    Kd, Kh, u, ref = herm_big
+    s = _draw(dpp, Kd, SEED_BIG, "fp64")
+    r = s.result()
+    assert _ok(r, _lib), r
+    j0, border = compare_draw(s.keep.cpu().numpy(), r["logp"], s.pivots.cpu().numpy(), ref, u,
+                              piv_atol=1e-8)
+    print(f"n={N_BIG} fp64: compared {j0} decisions, borderline={border}, "
+          f"logp gpu={r['logp']:.12g} oracle={ref.logp:.12g}")
+
+
+@pytest.mark.parametrize("precision", ["3xtf32", "bf16x6"])
+def test_mixed_one_draw_matches_oracle_n16384(dpp, herm_big, precision):
+    from paper_1905_00165_gb300 import _lib
+    Kd, Kh, u, ref = herm_big
+    s = _draw(dpp, Kd, SEED_BIG, precision)
+    r = s.result()
+    assert _ok(r, _lib), r
+    j0, border = compare_draw(s.keep.cpu().numpy(), r["logp"], s.pivots.cpu().numpy(), ref, u,
+                              logp_rtol=MIXED_LOGP_RTOL, piv_atol=1e-4)
+    if not border:
+        print(f"n={N_BIG} {precision}: logp rel err "
+              f"{abs(r['logp'] - ref.logp) / abs(ref.logp):.3e}, recomputed {r['n_borderline']}")
+
+
+def test_bench_configuration_matches_oracle_n16384(dpp, herm_big):
+    """3xTF32, each launch capped at a quarter of the SMs, four draws in
+    flight on four streams: the draw with the oracle's seed is the oracle's."""
+    import torch
+    from paper_1905_00165_gb300 import _lib
+    Kd, Kh, u, ref = herm_big
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    old = _lib.get_tuning(_lib.DPP_TUNE_MAX_CTAS)
+    _lib.set_tuning(_lib.DPP_TUNE_MAX_CTAS, max(8, sms // 4))
+    try:
+        streams = [torch.cuda.Stream() for _ in range(4)]
+        out = []
+        for k, st in enumerate(streams):
+            with torch.cuda.stream(st):
+                out.append(dpp.sample_hermitian(Kd, seed=SEED_BIG + k, precision="3xtf32"))
+        torch.cuda.synchronize()
+    finally:
+        _lib.set_tuning(_lib.DPP_TUNE_MAX_CTAS, old)
+    s = out[0]
+    r = s.result()
+    assert _ok(r, _lib), r
+    compare_draw(s.keep.cpu().numpy(), r["logp"], s.pivots.cpu().numpy(), ref, u,
+                 logp_rtol=MIXED_LOGP_RTOL, piv_atol=1e-4)
+    for s in out[1:]:
+        assert _ok(s.result(), _lib), s.result()
+
+
+@pytest.mark.parametrize("precision", ["3xtf32", "bf16x6"])
+def test_band_margin_hermitian_n16384(dpp, herm_big, precision):
+    """Every one of the 16384 mixed pivots (decisions forced to the oracle's)
+    lies within c/8 of the band's scale of the exact pivot."""
+    import torch
+    from paper_1905_00165_gb300 import _lib
+    Kd, Kh, u, ref = herm_big
+    uf = torch.from_numpy(O.forced_uniforms(ref.keep)).cuda()
+    s = _draw(dpp, Kd, 0, precision, uniforms=uf)
+    assert _ok(s.result(), _lib), s.result()
+    assert s.result()["n_borderline"] == 0
+    Lm = np.tril(ref.A, -1)
+    sj = (Lm * Lm) @ np.abs(ref.pivots)
+    ratio = _band_ratio(s.pivots.cpu().numpy(), ref.pivots, np.diag(Kh), sj)
+    c = _lib.get_tuning(_lib.DPP_TUNE_TAU_SAFETY)
+    worst = float(ratio.max())
+    print(f"hermitian n={N_BIG} {precision}: max |d_mixed - d_oracle| / "
+          f"(2^-22 sqrt(j+1)(K_jj+s_j)) = {worst:.3e} at j={int(ratio.argmax())}; c = {c}")
+    assert worst < c / 8.0
+
+
+# ---------------------------------------------------------------------------
+# General (LU) real, n = 8192
+# ---------------------------------------------------------------------------
+N_LU = 8192
+
+
+@pytest.fixture(scope="module")
+def lu_big(dpp):
+    import torch
+    K, S = W.lu_similarity_kernel(N_LU, seed=0, device="cuda")
+    Kd = torch.from_numpy(np.ascontiguousarray(K.T)).cuda().t()  # column-major view of K
+    u = O.uniforms(0, 0, N_LU)
+    ref = O.sample_lu(K, u)
+    yield Kd, K, u, ref
+    del Kd
+
+
+def _draw_lu(dpp, Kd, seed, precision, **kw):
+    import torch
+    s = dpp.sample_lu(Kd, seed=seed, precision=precision, **kw)
+    torch.cuda.synchronize()
+    return s
+
+
+@pytest.mark.parametrize("precision", ["fp64", "bf16x6", "3xtf32"])
+def test_lu_matches_oracle_n8192(dpp, lu_big, precision):
+    from paper_1905_00165_gb300 import _lib
+    Kd, K, u, ref = lu_big
+    s = _draw_lu(dpp, Kd, 0, precision)
+    r = s.result()
+    assert _ok(r, _lib), r
+    if precision == "fp64":
+        compare_draw(s.keep.cpu().numpy(), r["logp"], s.pivots.cpu().numpy(), ref, u,
+                     piv_atol=1e-8)
+    else:
+        compare_draw(s.keep.cpu().numpy(), r["logp"], s.pivots.cpu().numpy(), ref, u,
+                     logp_rtol=MIXED_LOGP_RTOL, piv_atol=1e-4)
+
+
+def test_band_margin_lu_n8192(dpp, lu_big):
+    import torch
+    from paper_1905_00165_gb300 import _lib
+    Kd, K, u, ref = lu_big
+    uf = torch.from_numpy(O.forced_uniforms(ref.keep)).cuda()
+    s = _draw_lu(dpp, Kd, 0, "bf16x6", uniforms=uf)
+    assert _ok(s.result(), _lib), s.result()
+    Lm = np.tril(ref.A, -1)
+    Um = np.triu(ref.A, 1)
+    sj = np.sum(np.abs(Lm) * np.abs(Um.T), axis=1)  # sum_k |L_jk U_kj|
+    ratio = _band_ratio(s.pivots.cpu().numpy(), ref.pivots, np.diag(K), sj)
+    c = _lib.get_tuning(_lib.DPP_TUNE_TAU_SAFETY)
+    worst = float(ratio.max())
+    print(f"LU n={N_LU}: max ratio {worst:.3e} at j={int(ratio.argmax())}; c = {c}")
+    assert worst < c / 8.0
+
+
+# ---------------------------------------------------------------------------
+# Hermitian complex, n = 4096
+# ---------------------------------------------------------------------------
+N_CX = 4096
+
+
+@pytest.fixture(scope="module")
+def cx_big(dpp):
+    import torch
+    K = W.hermitian_kernel(N_CX, seed=0, kind="beta", complex_=True, device="cuda")
+    Kd = torch.from_numpy(np.ascontiguousarray(K.T)).cuda().t()
+    u = O.uniforms(0, 0, N_CX)
+    ref = O.sample_ldl(K, u)
+    yield Kd, K, u, ref
+    del Kd
+
+
+@pytest.mark.parametrize("precision", ["fp64", "bf16x6", "3xtf32"])
+def test_complex_matches_oracle_n4096(dpp, cx_big, precision):
+    from paper_1905_00165_gb300 import _lib
+    Kd, K, u, ref = cx_big
+    s = _draw(dpp, Kd, 0, precision)
+    r = s.result()
+    assert _ok(r, _lib), r
+    if precision == "fp64":
+        compare_draw(s.keep.cpu().numpy(), r["logp"], s.pivots.cpu().numpy(), ref, u,
+                     piv_atol=1e-8)
+    else:
+        compare_draw(s.keep.cpu().numpy(), r["logp"], s.pivots.cpu().numpy(), ref, u,
+                     logp_rtol=MIXED_LOGP_RTOL, piv_atol=1e-4)
+
+
+def test_band_margin_complex_n4096(dpp, cx_big):
+    import torch
+    from paper_1905_00165_gb300 import _lib
+    Kd, K, u, ref = cx_big
+    uf = torch.from_numpy(O.forced_uniforms(ref.keep)).cuda()
+    s = _draw(dpp, Kd, 0, "bf16x6", uniforms=uf)
+    assert _ok(s.result(), _lib), s.result()
+    Lm = np.tril(ref.A, -1)
+    sj = (np.abs(Lm) ** 2) @ np.abs(ref.pivots)
+    ratio = _band_ratio(s.pivots.cpu().numpy(), ref.pivots, np.real(np.diag(K)), sj)
+    c = _lib.get_tuning(_lib.DPP_TUNE_TAU_SAFETY)
+    worst = float(ratio.max())
+    print(f"complex n={N_CX}: max ratio {worst:.3e} at j={int(ratio.argmax())}; c = {c}")
+    assert worst < c / 8.0
+
