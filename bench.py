@@ -50,9 +50,9 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-fp64-ref", action="store_true")
     p.add_argument("--no-batched", action="store_true")
-    p.add_argument("--streams", type=int, default=4,
+    p.add_argument("--streams", type=int, default=0,
                    help="draws in flight on this many streams, each launch capped at "
-                        "SMs / streams CTAs")
+                        "SMs / streams CTAs (0: the autotuner's choice)")
     p.add_argument("--suite-only", default="",
                    help="with --suite: comma-separated subset of C1,C2,C3,C4")
     p.add_argument("--suite", action="store_true",
@@ -581,10 +581,28 @@ def main():
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
     need = dpp.workspace_size(0, n, 0, prec, 1)
-    nst = max(1, args.streams)
-    if nst > 1:
-        sms = torch.cuda.get_device_properties(dev).multi_processor_count
-        _lib.set_tuning(_lib.DPP_TUNE_MAX_CTAS, max(8, sms // nst))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    tuning = None
+    if args.streams > 0:
+        # an explicit stream count: the knobs decide, not the tuning table
+        nst = args.streams
+        _lib.set_tuning(_lib.DPP_TUNE_USE_CACHE, 0)
+        if nst > 1:
+            _lib.set_tuning(_lib.DPP_TUNE_MAX_CTAS, max(8, sms // nst))
+    else:
+        # the autotuner's entry for this GPU and key (the committed table, or a
+        # tuning run on this kernel now); the library applies its outer block,
+        # panel pipeline and CTA cap to every draw below
+        cache = os.path.join(ROOT, "paper_1905_00165_gb300", "tune_gb300.json")
+        if os.path.exists(cache):
+            _lib.tune_load(cache)
+        tuning = _lib.tune_lookup(0, n, 0, prec)
+        source = "tuning table"
+        if tuning is None:
+            tuning = dpp.autotune(Kd, hermitian=True, precision=prec_name, max_streams=4, draws=12)
+            source = "autotuned in this run"
+        tuning["source"] = source
+        nst = int(tuning["streams"])
     wsbs = [torch.empty(need, dtype=torch.uint8, device=dev) for _ in range(nst)]
     keeps = [torch.empty(n, dtype=torch.uint8, device=dev) for _ in range(nst)]
     pivs = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(nst)]
@@ -692,10 +710,12 @@ def main():
                     "frac": gbs / hbm, "traffic": None, "peak_source": "MEASURED_PEAKS hbm_gbs"}
         roof["launches_per_step"] = st["launches"] / steps
         roof["avg_launch_ms"] = avg_ms
-        if nst > 1:
-            # each launch holds at most SMs / streams CTAs (one per SM), and
-            # the streams' launches overlap: the fraction of that SM share
-            share = min(1.0, max(8, sms // nst) / sms)
+        cap = (int(tuning["max_ctas"]) if tuning is not None
+               else (max(8, sms // nst) if nst > 1 else 0))
+        if cap and cap < sms:
+            # each launch holds at most `cap` CTAs (one per SM), and the
+            # streams' launches overlap: the fraction of that SM share
+            share = cap / sms
             roof["ctas_per_launch_share"] = share
             roof["frac_of_sm_share"] = roof["frac"] / share
     kernels = {k: {"launches": v["launches"], "total_ms": round(v["total_ms"], 3),
@@ -824,7 +844,7 @@ def main():
                        "seeds": f"Philox seed = step index (+ rank offset)",
                        "l2_policy": "inputs larger than L2 (2 GiB FP64 K), no flush",
                        "parallelism": f"replicas x{ws_n}",
-                       "streams": nst},
+                       "streams": nst, "tuning": tuning},
             "tflops_algorithmic": value * algo_flops / 1e12,
             "roofline": roof,
             "err_vs_oracle": err,

@@ -108,7 +108,9 @@ typedef struct {
 typedef enum {
   DPP_OP_SAMPLE_HERMITIAN = 0,
   DPP_OP_SAMPLE_LU = 1,
-  DPP_OP_LOGPROB_BACKWARD = 2
+  DPP_OP_LOGPROB_BACKWARD = 2,
+  DPP_OP_GREEDY_HERMITIAN = 3,
+  DPP_OP_GREEDY_LU = 4
 } dpp_op;
 
 /* Bytes of device workspace needed by one call of `op` at order n.
@@ -201,6 +203,28 @@ dpp_status dpp_sample_lu(const void* K, int64_t n, int64_t ld, int32_t dtype,
                          void* factor_out, double* pivots, dpp_result* result,
                          void* workspace, size_t workspace_bytes,
                          void* stream);
+
+/* Greedy maximum-likelihood variant (Section 2, the remark after Prop. 1):
+ * every Bernoulli draw of Algorithm 1 is replaced by its more likely outcome,
+ * so index j is kept iff Re(d_j) > 1/2 (a tie, Re d_j = 1/2, rejects), with
+ * d_j the conditional inclusion probability given the decisions on [0, j).
+ * The result is deterministic: no seed. It equals the sampler's decision rule
+ * "keep iff u_j < Re d_j" with every u_j = 1/2, and runs the same kernels:
+ * on the mixed precisions a pivot within the borderline band of 1/2 is
+ * recomputed in FP64 from K before its decision, so every decision is that
+ * of the exact FP64 chain.
+ *   Arguments as dpp_sample_hermitian / dpp_sample_lu without seed, instance
+ *   and uniforms; workspace >= dpp_workspace_size(DPP_OP_GREEDY_HERMITIAN or
+ *   DPP_OP_GREEDY_LU, n, dtype, precision, hermitian), whose first
+ *   ceil(8 n / 256) * 256 bytes hold the thresholds.
+ *   result->logp is log of the greedy set's probability, sum_j log|d_j|. */
+dpp_status dpp_greedy_hermitian(const void* K, int64_t n, int64_t ld, int32_t dtype,
+                                int32_t precision, uint8_t* keep, void* factor_out,
+                                double* pivots, dpp_result* result, void* workspace,
+                                size_t workspace_bytes, void* stream);
+dpp_status dpp_greedy_lu(const void* K, int64_t n, int64_t ld, int32_t dtype, int32_t precision,
+                         uint8_t* keep, void* factor_out, double* pivots, dpp_result* result,
+                         void* workspace, size_t workspace_bytes, void* stream);
 
 /* Many independent draws, one per Hermitian (real symmetric) kernel of its own
  * order, in ONE persistent launch (no host synchronisation). Each CTA takes
@@ -322,6 +346,10 @@ dpp_status dpp_logprob_backward_batched(int32_t batch, const int64_t* n,
  *                         pipeline): their waits run out after DPP_TUNE_WAIT_NS,
  *                         every launch still ends, and the draw's status has
  *                         DPP_RES_TIMEOUT. Its outputs are then meaningless.
+ *   DPP_TUNE_USE_CACHE    1 (default): when the autotuner's table (below) has
+ *                         an entry for a call's key, that entry's outer block,
+ *                         panel pipeline and CTA cap replace the three knobs
+ *                         above for the call; 0: the knobs alone decide.
  * Returns DPP_ERR_INVALID_ARG for an unknown key or out-of-range value. */
 typedef enum {
   DPP_TUNE_TAU_SAFETY = 0,
@@ -330,11 +358,75 @@ typedef enum {
   DPP_TUNE_MAX_CTAS = 3,
   DPP_TUNE_PANEL_PIPELINE = 4,
   DPP_TUNE_WAIT_NS = 5,
-  DPP_TUNE_FAULT_WITHHOLD = 6
+  DPP_TUNE_FAULT_WITHHOLD = 6,
+  DPP_TUNE_USE_CACHE = 7
 } dpp_tune_key;
 
 dpp_status dpp_set_tuning(int32_t key, double value);
 double dpp_get_tuning(int32_t key);
+
+/* Autotuner. The paper's only knobs are its tile and block sizes (Section 4,
+ * chosen by hand per machine); here the launch configuration of a draw is
+ * measured on the GPU at hand and kept in a table keyed by (GPU name, SM
+ * count, op, dtype, precision, n bucket = floor(log2 n)).
+ *
+ * One entry: the configuration and the throughput it reached. `streams` is
+ * the number of draws the caller should keep in flight (on that many
+ * streams); `max_ctas` is the per-launch CTA cap that goes with it (0 = one
+ * CTA per SM). The library applies outer_block, panel_pipeline and max_ctas
+ * to every later call with the entry's key (unless DPP_TUNE_USE_CACHE is 0);
+ * keeping `streams` draws in flight is the caller's part. */
+typedef struct {
+  int32_t op;              /* DPP_OP_SAMPLE_HERMITIAN or DPP_OP_SAMPLE_LU      */
+  int32_t dtype;
+  int32_t precision;
+  int32_t n_bucket;        /* floor(log2 n) of the order it was tuned at       */
+  int64_t n;               /* the order it was tuned at                        */
+  int32_t outer_block;     /* as DPP_TUNE_OUTER_BLOCK                          */
+  int32_t panel_pipeline;  /* as DPP_TUNE_PANEL_PIPELINE (1 or 2; 0 if n/a)    */
+  int32_t max_ctas;        /* as DPP_TUNE_MAX_CTAS                             */
+  int32_t streams;         /* draws in flight                                  */
+  double samples_per_s;    /* measured with this configuration                 */
+  int32_t candidates;      /* configurations timed to choose it                */
+  int32_t reserved;
+} dpp_tune_entry;
+
+/* Device workspace for dpp_autotune: max_streams draws' workspaces, keep
+ * masks and results (0 for an unsupported combination). */
+size_t dpp_autotune_workspace_size(int32_t op, int64_t n, int32_t dtype, int32_t precision,
+                                   int32_t max_streams);
+
+/* Time every candidate configuration on the caller's kernel K (device,
+ * column-major as for dpp_sample_hermitian / dpp_sample_lu; op selects which)
+ * and keep the fastest in the table. Candidates: draws in flight 1, 2 and 4
+ * (up to max_streams, 1..4), each launch then capped at SMs / streams CTAs;
+ * outer block 128 and 256 (mixed precisions); for real Hermitian mixed draws,
+ * both panel pipelines. Each candidate runs one warm-up draw per stream and
+ * then `draws` timed draws (Philox seeds 0, 1, ...) dealt round-robin to its
+ * streams, timed with CUDA events between a start event on `stream` and the
+ * last draw's end. Blocks the host until done; allocates only its own CUDA
+ * streams and events (destroyed before returning). `best` (host, nullable)
+ * receives the chosen entry.
+ * Errors: DPP_ERR_INVALID_ARG / DPP_ERR_WORKSPACE / DPP_ERR_UNSUPPORTED on
+ * the host before any work; DPP_ERR_CUDA if a draw or the timing fails. */
+dpp_status dpp_autotune(int32_t op, const void* K, int64_t n, int64_t ld, int32_t dtype,
+                        int32_t precision, int32_t max_streams, int32_t draws,
+                        void* workspace, size_t workspace_bytes, dpp_tune_entry* best,
+                        void* stream);
+
+/* The table's entry for (op, n, dtype, precision) on the current device:
+ * DPP_OK and *out filled, or DPP_ERR_UNSUPPORTED if there is none. */
+dpp_status dpp_tune_lookup(int32_t op, int64_t n, int32_t dtype, int32_t precision,
+                           dpp_tune_entry* out);
+
+/* Write the whole table (entries of every GPU) to `path` as JSON, or merge
+ * the entries of a JSON file written by dpp_tune_save into it (an entry with
+ * the same key is replaced). The library loads the file named by the
+ * environment variable DPP_TUNE_CACHE, if set, when it is loaded.
+ * dpp_tune_clear empties the table. */
+dpp_status dpp_tune_save(const char* path);
+dpp_status dpp_tune_load(const char* path);
+void dpp_tune_clear(void);
 
 /* Fill `out` (device, n doubles) with the Philox uniforms u_0..u_{n-1} that
  * the samplers use for (seed, instance). */

@@ -14,7 +14,8 @@ from ._lib import (DPP_C128, DPP_OP_LOGPROB_BACKWARD, DPP_OP_SAMPLE_HERMITIAN,
                    DPP_OP_SAMPLE_LU, DPP_PREC_3XTF32, DPP_PREC_BF16X6, DPP_PREC_FP64, DPP_R64,
                    DPPError, PRECISIONS, decode_result, load, workspace_size)
 
-__all__ = ["sample_hermitian", "sample_hermitian_static", "sample_lu", "sample_batched", "BatchedSampler",
+__all__ = ["sample_hermitian", "sample_hermitian_static", "sample_lu", "greedy_hermitian",
+           "greedy_lu", "sample_batched", "BatchedSampler", "autotune",
            "logprob_backward", "uniforms", "Sample", "DPPLogProb", "DPPError", "load",
            "workspace_size"]
 
@@ -116,6 +117,48 @@ def _sample(hermitian: bool, K, seed: int, instance: int, precision: str, unifor
            ws.data_ptr(), ws.numel(), _stream(dev))
     _lib.check(st)
     return Sample(keep, piv[:npiv], fac, raw)
+
+
+def _greedy(hermitian: bool, K, precision: str, factor: bool, workspace):
+    torch = _torch()
+    L = load()
+    if not K.is_cuda:
+        raise ValueError("K must be a CUDA tensor")
+    prec = PRECISIONS[precision]
+    dt = _dtype_code(K)
+    Kc, ld = colmajor(K)
+    n = K.shape[0]
+    dev = K.device
+    keep = torch.empty(max(n, 1), dtype=torch.uint8, device=dev)
+    npiv = 2 * n if (not hermitian and dt == DPP_C128) else n
+    piv = torch.empty(max(npiv, 1), dtype=torch.float64, device=dev)
+    fac = None
+    if factor:
+        if ld != n and n:
+            Kc, ld = Kc.t().contiguous().t(), n
+        fac = empty_colmajor(n, K.dtype, dev)
+    raw = torch.zeros(_lib.RESULT_BYTES, dtype=torch.uint8, device=dev)
+    op = _lib.DPP_OP_GREEDY_HERMITIAN if hermitian else _lib.DPP_OP_GREEDY_LU
+    need = workspace_size(op, n, dt, prec, 1 if hermitian else 0)
+    if need == 0:
+        raise DPPError(_lib.DPP_ERR_UNSUPPORTED, f"unsupported: dtype={K.dtype} precision={precision}")
+    ws = workspace if workspace is not None else torch.empty(need, dtype=torch.uint8, device=dev)
+    f = L.dpp_greedy_hermitian if hermitian else L.dpp_greedy_lu
+    st = f(Kc.data_ptr() if n else None, n, ld, dt, prec, keep.data_ptr() if n else None,
+           None if fac is None else fac.data_ptr(), piv.data_ptr(), raw.data_ptr(),
+           ws.data_ptr(), ws.numel(), _stream(dev))
+    _lib.check(st)
+    return Sample(keep[:n], piv[:npiv], fac, raw)
+
+
+def greedy_hermitian(K, precision: str = "fp64", factor: bool = False, workspace=None) -> Sample:
+    """Greedy maximum-likelihood set for Hermitian K: keep j iff d_j > 1/2."""
+    return _greedy(True, K, precision, factor, workspace)
+
+
+def greedy_lu(K, precision: str = "fp64", factor: bool = False, workspace=None) -> Sample:
+    """Greedy maximum-likelihood set for general K (LU form)."""
+    return _greedy(False, K, precision, factor, workspace)
 
 
 def sample_hermitian(K, seed: int = 0, instance: int = 0, precision: str = "fp64",
@@ -251,6 +294,29 @@ def sample_batched(Ks, seed: int = 0, instance=None, want_pivots: bool = False, 
     b = BatchedSampler(Ks, instance=instance, want_pivots=want_pivots, uniforms=uniforms)
     b.draw(seed)
     return b
+
+
+def autotune(K, hermitian: bool = True, precision: str = "3xtf32", max_streams: int = 4,
+             draws: int = 8) -> dict:
+    """Time the candidate launch configurations of a draw on K (see
+    dpp_autotune) and keep the fastest in the library's tuning table, which
+    every later call with the same key uses. Returns the chosen entry."""
+    import ctypes
+    torch = _torch()
+    L = load()
+    dt = _dtype_code(K)
+    Kc, ld = colmajor(K)
+    n = K.shape[0]
+    op = DPP_OP_SAMPLE_HERMITIAN if hermitian else DPP_OP_SAMPLE_LU
+    prec = PRECISIONS[precision]
+    need = int(L.dpp_autotune_workspace_size(op, n, dt, prec, max_streams))
+    if need == 0:
+        raise DPPError(_lib.DPP_ERR_UNSUPPORTED, "autotune: unsupported configuration")
+    ws = torch.empty(need, dtype=torch.uint8, device=K.device)
+    e = _lib.TuneEntry()
+    _lib.check(L.dpp_autotune(op, Kc.data_ptr(), n, ld, dt, prec, max_streams, draws,
+                              ws.data_ptr(), need, ctypes.byref(e), _stream(K.device)))
+    return e.as_dict()
 
 
 def uniforms(seed: int, instance: int, n: int, device="cuda"):

@@ -18,6 +18,7 @@ DPP_OK, DPP_ERR_INVALID_ARG, DPP_ERR_CUDA, DPP_ERR_WORKSPACE, DPP_ERR_UNSUPPORTE
 DPP_R64, DPP_C128 = 0, 1
 DPP_PREC_FP64, DPP_PREC_3XTF32, DPP_PREC_BF16X6, DPP_PREC_FP32 = 0, 1, 2, 3
 DPP_OP_SAMPLE_HERMITIAN, DPP_OP_SAMPLE_LU, DPP_OP_LOGPROB_BACKWARD = 0, 1, 2
+DPP_OP_GREEDY_HERMITIAN, DPP_OP_GREEDY_LU = 3, 4
 DPP_STATIC_SCRATCH_BYTES = 4 << 20
 DPP_STATIC_MAX_N_R64, DPP_STATIC_MAX_N_C128 = 15418, 7942
 DPP_RES_NONFINITE, DPP_RES_TIMEOUT, DPP_RES_INADMISSIBLE, DPP_RES_RECOMPUTE = 1, 2, 4, 8
@@ -62,6 +63,10 @@ def load(path: Optional[str] = None):
         f = getattr(L, name)
         f.argtypes = [vp, i64, i64, i32, i32, u64, u64, vp, vp, vp, vp, vp, vp, sz, vp]
         f.restype = i32
+    for name in ("dpp_greedy_hermitian", "dpp_greedy_lu"):
+        f = getattr(L, name)
+        f.argtypes = [vp, i64, i64, i32, i32, vp, vp, vp, vp, vp, sz, vp]
+        f.restype = i32
     L.dpp_sample_hermitian_static.argtypes = [vp, i64, i64, i32, u64, u64, vp, vp, vp, vp, vp, vp]
     L.dpp_sample_hermitian_static.restype = i32
     L.dpp_batched_workspace_size.argtypes = [i32, i64, i32]
@@ -86,6 +91,18 @@ def load(path: Optional[str] = None):
     L.dpp_get_tuning.restype = ctypes.c_double
     L.dpp_launch_count.argtypes = []
     L.dpp_launch_count.restype = ctypes.c_uint64
+    L.dpp_autotune_workspace_size.argtypes = [i32, i64, i32, i32, i32]
+    L.dpp_autotune_workspace_size.restype = sz
+    L.dpp_autotune.argtypes = [i32, vp, i64, i64, i32, i32, i32, i32, vp, sz, vp, vp]
+    L.dpp_autotune.restype = i32
+    L.dpp_tune_lookup.argtypes = [i32, i64, i32, i32, vp]
+    L.dpp_tune_lookup.restype = i32
+    L.dpp_tune_save.argtypes = [ctypes.c_char_p]
+    L.dpp_tune_save.restype = i32
+    L.dpp_tune_load.argtypes = [ctypes.c_char_p]
+    L.dpp_tune_load.restype = i32
+    L.dpp_tune_clear.argtypes = []
+    L.dpp_tune_clear.restype = None
     _lib = L
     return L
 
@@ -137,7 +154,42 @@ def profile_stop() -> dict:
 
 DPP_TUNE_TAU_SAFETY, DPP_TUNE_OUTER_BLOCK, DPP_TUNE_UPDATE_KERNEL, DPP_TUNE_MAX_CTAS = 0, 1, 2, 3
 DPP_TUNE_PANEL_PIPELINE = 4
-DPP_TUNE_WAIT_NS, DPP_TUNE_FAULT_WITHHOLD = 5, 6
+DPP_TUNE_WAIT_NS, DPP_TUNE_FAULT_WITHHOLD, DPP_TUNE_USE_CACHE = 5, 6, 7
+
+
+class TuneEntry(ctypes.Structure):
+    """dpp_tune_entry (include/dpp.h)."""
+    _fields_ = [("op", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("n_bucket", ctypes.c_int32),
+                ("n", ctypes.c_int64), ("outer_block", ctypes.c_int32),
+                ("panel_pipeline", ctypes.c_int32), ("max_ctas", ctypes.c_int32),
+                ("streams", ctypes.c_int32), ("samples_per_s", ctypes.c_double),
+                ("candidates", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+def tune_lookup(op: int, n: int, dtype: int, precision: int):
+    """The tuning table's entry for this key on the current device, or None."""
+    e = TuneEntry()
+    st = load().dpp_tune_lookup(op, n, dtype, precision, ctypes.byref(e))
+    if st == DPP_ERR_UNSUPPORTED:
+        return None
+    check(st)
+    return e.as_dict()
+
+
+def tune_save(path: str) -> None:
+    check(load().dpp_tune_save(os.fsencode(path)))
+
+
+def tune_load(path: str) -> None:
+    check(load().dpp_tune_load(os.fsencode(path)))
+
+
+def tune_clear() -> None:
+    load().dpp_tune_clear()
 
 
 def set_tuning(key: int, value: float) -> None:

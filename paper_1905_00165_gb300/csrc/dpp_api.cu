@@ -103,6 +103,14 @@ size_t dpp_workspace_size(int32_t op, int64_t n, int32_t dtype, int32_t precisio
     case DPP_OP_LOGPROB_BACKWARD:
       if (precision == DPP_PREC_FP64) return ws_backward(n, dtype, hermitian != 0);
       return 0;
+    case DPP_OP_GREEDY_HERMITIAN:
+    case DPP_OP_GREEDY_LU: {
+      // the sampler's workspace behind n doubles of decision thresholds
+      const size_t w = dpp_workspace_size(op == DPP_OP_GREEDY_HERMITIAN ? DPP_OP_SAMPLE_HERMITIAN
+                                                                        : DPP_OP_SAMPLE_LU,
+                                          n, dtype, precision, hermitian);
+      return w ? w + align256(sizeof(double) * (size_t)(n > 0 ? n : 1)) : 0;
+    }
     default:
       return 0;
   }
@@ -118,6 +126,7 @@ static dpp_status sample_common(bool hermitian, const void* K, int64_t n, int64_
                                          n, dtype, precision, hermitian);
   dpp_status st = check_draw(K, n, ld, dtype, keep, factor_out, result, workspace, ws_bytes, need);
   if (st != DPP_OK) return st;
+  begin_call(hermitian ? DPP_OP_SAMPLE_HERMITIAN : DPP_OP_SAMPLE_LU, n, dtype, precision);
   DrawArgs a;
   a.K = K;
   a.n = n;
@@ -175,6 +184,43 @@ dpp_status dpp_sample_lu(const void* K, int64_t n, int64_t ld, int32_t dtype, in
                        factor_out, pivots, result, workspace, workspace_bytes, stream);
 }
 
+// Greedy maximum-likelihood draw: the sampler's decision "keep j iff
+// u_j < Re d_j" with every threshold u_j = 1/2 is "keep j iff Re d_j > 1/2, a
+// tie rejects". The thresholds live in the first bytes of the workspace.
+static dpp_status greedy_common(bool hermitian, const void* K, int64_t n, int64_t ld,
+                                int32_t dtype, int32_t precision, uint8_t* keep,
+                                void* factor_out, double* pivots, dpp_result* result,
+                                void* workspace, size_t ws_bytes, void* stream) {
+  g_last_error.clear();
+  const size_t need = dpp_workspace_size(hermitian ? DPP_OP_GREEDY_HERMITIAN : DPP_OP_GREEDY_LU,
+                                         n, dtype, precision, hermitian);
+  dpp_status st = check_draw(K, n, ld, dtype, keep, factor_out, result, workspace, ws_bytes, need);
+  if (st != DPP_OK) return st;
+  if (precision != DPP_PREC_FP64 && factor_out && factor_out == K)
+    return fail(DPP_ERR_INVALID_ARG, "mixed precision cannot factor in place (factor_out == K)");
+  const size_t ub = align256(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double* half = static_cast<double*>(workspace);
+  cudaError_t e = fill_constant(0.5, n, half, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return fail_cuda(e, "dpp_greedy: thresholds");
+  return sample_common(hermitian, K, n, ld, dtype, precision, 0, 0, half, keep, factor_out,
+                       pivots, result, static_cast<char*>(workspace) + ub, ws_bytes - ub, stream);
+}
+
+dpp_status dpp_greedy_hermitian(const void* K, int64_t n, int64_t ld, int32_t dtype,
+                                int32_t precision, uint8_t* keep, void* factor_out,
+                                double* pivots, dpp_result* result, void* workspace,
+                                size_t workspace_bytes, void* stream) {
+  return greedy_common(true, K, n, ld, dtype, precision, keep, factor_out, pivots, result,
+                       workspace, workspace_bytes, stream);
+}
+
+dpp_status dpp_greedy_lu(const void* K, int64_t n, int64_t ld, int32_t dtype, int32_t precision,
+                         uint8_t* keep, void* factor_out, double* pivots, dpp_result* result,
+                         void* workspace, size_t workspace_bytes, void* stream) {
+  return greedy_common(false, K, n, ld, dtype, precision, keep, factor_out, pivots, result,
+                       workspace, workspace_bytes, stream);
+}
+
 size_t dpp_batched_workspace_size(int32_t batch, int64_t n_max, int32_t precision) {
   if (batch < 0 || n_max < 0 || precision != DPP_PREC_FP32) return 0;
   return ws_batched(batch, n_max, batched_default_ctas());
@@ -198,6 +244,7 @@ dpp_status dpp_sample_batched(int32_t batch, const int64_t* n, const double* con
     return fail(DPP_ERR_WORKSPACE, "workspace must be non-NULL and 256-byte aligned");
   const size_t minimal = ws_batched(batch, n_max, 1);
   if (workspace_bytes < minimal) return fail(DPP_ERR_WORKSPACE, "workspace too small");
+  begin_call(kOpBatched, n_max, DPP_R64, precision);
   BatchedArgs b;
   b.batch = batch;
   b.n = n;
@@ -237,6 +284,7 @@ dpp_status dpp_logprob_backward(const void* K, int64_t n, int64_t ld, int32_t dt
     return fail(DPP_ERR_WORKSPACE, "workspace must be non-NULL and 256-byte aligned");
   if (workspace_bytes < need) return fail(DPP_ERR_WORKSPACE, "workspace too small");
   if (n == 0) return DPP_OK;
+  begin_call(DPP_OP_LOGPROB_BACKWARD, n, dtype, precision);
   Workspace ws;
   ws.base = static_cast<char*>(workspace);
   ws.size = workspace_bytes;
@@ -269,6 +317,7 @@ dpp_status dpp_logprob_backward_batched(int32_t batch, const int64_t* n, const v
   if (workspace_bytes < ws_adjoint_batched(batch, n_max, 1))
     return fail(DPP_ERR_WORKSPACE, "workspace too small for one CTA of the batched adjoint");
   // one persistent launch over all instances, on as many CTAs as the workspace holds
+  begin_call(DPP_OP_LOGPROB_BACKWARD, n_max, DPP_R64, DPP_PREC_FP64);
   Workspace ws;
   ws.base = static_cast<char*>(workspace);
   ws.size = workspace_bytes;
@@ -281,6 +330,7 @@ dpp_status dpp_logprob_backward_batched(int32_t batch, const int64_t* n, const v
 
 size_t dpp_logprob_backward_batched_workspace(int32_t batch, int64_t n_max) {
   if (batch < 0 || n_max < 0) return 0;
+  begin_call(DPP_OP_LOGPROB_BACKWARD, n_max, DPP_R64, DPP_PREC_FP64);
   return ws_adjoint_batched(batch, n_max, adjoint_batched_ctas());
 }
 
@@ -289,39 +339,43 @@ dpp_status dpp_set_tuning(int32_t key, double value) {
   switch (key) {
     case DPP_TUNE_TAU_SAFETY:
       if (!(value > 0.0 && value < 1e6)) return fail(DPP_ERR_INVALID_ARG, "tau safety out of range");
-      g_tuning.tau_safety = value;
+      g_settings.tau_safety = value;
       return DPP_OK;
     case DPP_TUNE_OUTER_BLOCK: {
       const int v = (int)value;
       if ((double)v != value || v < 32 || v > kMaxOuterBlock || v % 32 != 0)
         return fail(DPP_ERR_INVALID_ARG, "outer block must be a multiple of 32 in [32, 256]");
-      g_tuning.outer_block = v;
+      g_settings.outer_block = v;
       return DPP_OK;
     }
     case DPP_TUNE_UPDATE_KERNEL:
       if (value != 0.0 && value != 1.0) return fail(DPP_ERR_INVALID_ARG, "update kernel is 0 or 1");
-      g_tuning.update_kernel = (int)value;
+      g_settings.update_kernel = (int)value;
       return DPP_OK;
     case DPP_TUNE_MAX_CTAS: {
       const int v = (int)value;
       if ((double)v != value || (v != 0 && v < 8) || v > 4096)
         return fail(DPP_ERR_INVALID_ARG, "max CTAs must be 0 or in [8, 4096]");
-      g_tuning.max_ctas = v;
+      g_settings.max_ctas = v;
       return DPP_OK;
     }
     case DPP_TUNE_PANEL_PIPELINE:
       if (value != 0.0 && value != 1.0 && value != 2.0)
         return fail(DPP_ERR_INVALID_ARG, "panel pipeline is 0, 1 or 2");
-      g_tuning.panel_pipeline = (int)value;
+      g_settings.panel_pipeline = (int)value;
       return DPP_OK;
     case DPP_TUNE_WAIT_NS:
       if (!(value >= 1e5 && value <= 6e10))
         return fail(DPP_ERR_INVALID_ARG, "wait limit must be in [1e5, 6e10] ns");
-      g_tuning.wait_ns = value;
+      g_settings.wait_ns = value;
       return DPP_OK;
     case DPP_TUNE_FAULT_WITHHOLD:
       if (value != 0.0 && value != 1.0) return fail(DPP_ERR_INVALID_ARG, "fault withhold is 0 or 1");
-      g_tuning.fault_withhold = (int)value;
+      g_settings.fault_withhold = (int)value;
+      return DPP_OK;
+    case DPP_TUNE_USE_CACHE:
+      if (value != 0.0 && value != 1.0) return fail(DPP_ERR_INVALID_ARG, "use cache is 0 or 1");
+      g_settings.use_cache = (int)value;
       return DPP_OK;
     default:
       return fail(DPP_ERR_INVALID_ARG, "unknown tuning key");
@@ -330,13 +384,14 @@ dpp_status dpp_set_tuning(int32_t key, double value) {
 
 double dpp_get_tuning(int32_t key) {
   switch (key) {
-    case DPP_TUNE_TAU_SAFETY: return g_tuning.tau_safety;
-    case DPP_TUNE_OUTER_BLOCK: return (double)g_tuning.outer_block;
-    case DPP_TUNE_UPDATE_KERNEL: return (double)g_tuning.update_kernel;
-    case DPP_TUNE_MAX_CTAS: return (double)g_tuning.max_ctas;
-    case DPP_TUNE_PANEL_PIPELINE: return (double)g_tuning.panel_pipeline;
-    case DPP_TUNE_WAIT_NS: return g_tuning.wait_ns;
-    case DPP_TUNE_FAULT_WITHHOLD: return (double)g_tuning.fault_withhold;
+    case DPP_TUNE_TAU_SAFETY: return g_settings.tau_safety;
+    case DPP_TUNE_OUTER_BLOCK: return (double)g_settings.outer_block;
+    case DPP_TUNE_UPDATE_KERNEL: return (double)g_settings.update_kernel;
+    case DPP_TUNE_MAX_CTAS: return (double)g_settings.max_ctas;
+    case DPP_TUNE_PANEL_PIPELINE: return (double)g_settings.panel_pipeline;
+    case DPP_TUNE_WAIT_NS: return g_settings.wait_ns;
+    case DPP_TUNE_FAULT_WITHHOLD: return (double)g_settings.fault_withhold;
+    case DPP_TUNE_USE_CACHE: return (double)g_settings.use_cache;
     default: return -1.0;
   }
 }

@@ -396,6 +396,12 @@ __global__ void k_uniforms(uint64_t seed, uint64_t inst, int64_t n, double* out)
     out[j] = philox_uniform(seed, inst, (uint64_t)j);
 }
 
+__global__ void k_fill(double value, int64_t n, double* out) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x)
+    out[j] = value;
+}
+
 template <class K>
 int coop_capacity(K kernel, int threads, size_t smem) {
   DevInfo di;
@@ -523,6 +529,15 @@ cudaError_t run_fp64(const DrawArgs& a, bool herm, Workspace ws) {
 cudaError_t init_result(dpp_result* r, cudaStream_t s) {
   ProfScope ps(kProfOther, s);
   k_init_result<<<1, 1, 0, s>>>(r);
+  return cudaGetLastError();
+}
+
+cudaError_t fill_constant(double value, int64_t n, double* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  int64_t g = (n + 255) / 256;
+  if (g > 4096) g = 4096;
+  ProfScope ps(kProfOther, s);
+  k_fill<<<(unsigned)g, 256, 0, s>>>(value, n, out);
   return cudaGetLastError();
 }
 

@@ -71,8 +71,16 @@ struct Tuning {
   int panel_pipeline = 0;   // mixed Hermitian path: 0 = auto, 1 = single helper, 2 = chunked
   double wait_ns = 2e9;     // limit of the bounded device waits (ns)
   int fault_withhold = 0;   // fault injection: the deciding CTA never releases a panel
+  int use_cache = 1;        // apply the autotuner's entry for a call's key
 };
-extern Tuning g_tuning;
+// The process-wide settings (dpp_set_tuning), and the settings of the call in
+// progress on this host thread: every entry point starts with begin_call,
+// which copies the former into the latter and applies the autotuner's cached
+// entry for the call's key (dpp_tune.cu).
+extern Tuning g_settings;
+extern thread_local Tuning g_tuning;
+void begin_call(int32_t op, int64_t n, int32_t dtype, int32_t precision);
+constexpr int32_t kOpBatched = 5;  // key of dpp_sample_batched in the tuning cache
 constexpr int kMaxOuterBlock = 256;
 
 // Mixed-precision Hermitian sampler (dpp_mixed.cu).
@@ -143,5 +151,6 @@ cudaError_t adjoint_batched(int32_t batch, const int64_t* n, const double* const
 cudaError_t init_result(dpp_result* r, cudaStream_t s);
 cudaError_t fill_uniforms(uint64_t seed, uint64_t instance, int64_t n, double* out,
                           cudaStream_t s);
+cudaError_t fill_constant(double value, int64_t n, double* out, cudaStream_t s);
 
 }  // namespace dpp

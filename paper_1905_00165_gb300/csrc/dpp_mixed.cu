@@ -29,7 +29,8 @@
 
 namespace dpp {
 
-Tuning g_tuning;
+Tuning g_settings;
+thread_local Tuning g_tuning;
 
 namespace {
 
@@ -1292,7 +1293,12 @@ cudaError_t sample_mixed(const DrawArgs& a, Workspace ws) {
                                                                         L.kd, L.s);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  static int cap = 0;
+  // cooperative capacity (and the shared-memory attribute), per device
+  static int caps[64] = {};
+  int dev = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  int& cap = caps[dev];
   if (cap == 0) {
     cudaError_t ea = cudaFuncSetAttribute(k_outer_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)kOuterDynSmem);

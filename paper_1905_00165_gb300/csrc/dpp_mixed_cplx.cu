@@ -1194,7 +1194,12 @@ cudaError_t sample_mixed_cx(const DrawArgs& a, Workspace ws) {
         K, a.ld, L.Ar, L.Ai, L.ld32, n, L.kd, L.s);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  static int cap = 0;
+  // cooperative capacity (and the shared-memory attribute), per device
+  static int caps[64] = {};
+  int dev = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  int& cap = caps[dev];
   if (cap == 0) {
     cudaError_t ea = cudaFuncSetAttribute(k_cx_outer, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)kCxDyn);

@@ -1385,7 +1385,12 @@ cudaError_t sample_chunked(const DrawArgs& a, Workspace ws) {
         K, a.ld, L.A32, L.ld32, n, L.kd, L.s, SYM ? 1 : 0);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  static int cap = 0;
+  // cooperative capacity (and the shared-memory attribute), per device
+  static int caps[64] = {};
+  int dev = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  int& cap = caps[dev];
   if (cap == 0) {
     cudaError_t ea = cudaFuncSetAttribute(k_lu_outer<SYM>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -104,6 +104,7 @@ dpp_status dpp_sample_hermitian_static(const void* K, int64_t n, int64_t ld, int
   void* scratch = nullptr;
   cudaError_t e = static_scratch(static_cast<cudaStream_t>(stream), &scratch);
   if (e != cudaSuccess) return set_last_cuda_error(e, "dpp_sample_hermitian_static: scratch set-up");
+  begin_call(DPP_OP_SAMPLE_HERMITIAN, n, dtype, DPP_PREC_FP64);
   DrawArgs a;
   a.K = K;
   a.n = n;

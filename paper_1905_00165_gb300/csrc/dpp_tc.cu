@@ -498,13 +498,18 @@ cudaError_t launch(float* C, int64_t ldc, int64_t n, int64_t r0, int kdim, void*
         !make_map(&maps.L[o], Lops[o], n, ldk, esz, Cfg::kRowBytes))
       return cudaErrorInvalidValue;
   }
-  static bool attr = false;
-  if (!attr) {
+  // the shared-memory attribute is set once per device
+  static bool attr[64] = {};
+  int dev = 0;
+  cudaError_t ed = cudaGetDevice(&dev);
+  if (ed != cudaSuccess) return ed;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!attr[dev]) {
     cudaError_t e = cudaFuncSetAttribute(k_update_tc<MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          smem_bytes<MODE>());
     if (e != cudaSuccess) return e;
-    attr = true;
+    attr[dev] = true;
   }
   TcArgs a;
   a.C = C;

@@ -130,6 +130,7 @@ def test_tuning_keys_validated_on_host(L):
         (_lib.DPP_TUNE_PANEL_PIPELINE, [0, 1, 2], [3, -1]),
         (_lib.DPP_TUNE_WAIT_NS, [2e9, 1e6], [1e4, 1e11, -1.0]),
         (_lib.DPP_TUNE_FAULT_WITHHOLD, [1, 0], [2, -1]),
+        (_lib.DPP_TUNE_USE_CACHE, [0, 1], [2, -1]),
     ]
     for key, good, bad in cases:
         old = _lib.get_tuning(key)
@@ -155,3 +156,77 @@ def test_mixed_workspace_sizes_per_form():
     lu = dpp.workspace_size(1, n, _lib.DPP_R64, _lib.DPP_PREC_BF16X6, 0)
     assert herm >= 4 * n * n and lu >= 4 * n * n and cplx >= 8 * n * n
     assert dpp.workspace_size(1, n, _lib.DPP_C128, _lib.DPP_PREC_BF16X6, 0) == 0
+
+
+def test_greedy_workspace_and_arguments(L):
+    """The greedy entry points need the sampler's workspace plus n doubles of
+    thresholds, and reject bad arguments on the host."""
+    for op_s, op_g, herm in ((0, 3, 1), (1, 4, 0)):
+        for prec in (0, 1, 2):
+            ws = dpp.workspace_size(op_s, 1000, 0, prec, herm)
+            assert dpp.workspace_size(op_g, 1000, 0, prec, herm) == ws + 8000 + 192
+    assert dpp.workspace_size(4, 100, 1, 1, 0) == 0  # no complex mixed LU
+    fake = 4096
+    f = L.dpp_greedy_hermitian
+    assert f(fake, -1, 4, 0, 0, fake, None, None, fake, fake, 1 << 20, None) == _lib.DPP_ERR_INVALID_ARG
+    assert f(fake, 4, 4, 0, 0, fake, None, None, fake, fake, 16, None) == _lib.DPP_ERR_WORKSPACE
+    need = dpp.workspace_size(3, 4, 0, 1, 1)
+    # mixed in place is refused before anything is enqueued
+    assert f(fake, 4, 4, 0, 1, fake, fake, None, fake, fake, need, None) == _lib.DPP_ERR_INVALID_ARG
+
+
+def test_tune_cache_round_trip(L, tmp_path):
+    """The autotuner's table: a JSON file loads, saves back with the same
+    entries, merges by key, and malformed or out-of-range files are refused
+    (host only: no device is needed to read or write the table)."""
+    import json
+    entries = [
+        {"gpu": "NVIDIA GB300", "sms": 152, "op": 0, "dtype": 0, "precision": 1,
+         "n_bucket": 14, "n": 16384, "outer_block": 256, "panel_pipeline": 1,
+         "max_ctas": 38, "streams": 4, "samples_per_s": 47.5, "candidates": 12},
+        {"gpu": "NVIDIA GB300", "sms": 152, "op": 1, "dtype": 0, "precision": 2,
+         "n_bucket": 13, "n": 8192, "outer_block": 128, "panel_pipeline": 0,
+         "max_ctas": 0, "streams": 1, "samples_per_s": 80.25, "candidates": 6},
+    ]
+    src = tmp_path / "in.json"
+    src.write_text(json.dumps({"version": 1, "entries": entries}))
+    _lib.tune_clear()
+    try:
+        _lib.tune_load(str(src))
+        out = tmp_path / "out.json"
+        _lib.tune_save(str(out))
+        got = json.loads(out.read_text())["entries"]
+        assert got == entries
+        # an entry with the same key replaces the old one
+        upd = dict(entries[0], outer_block=128, samples_per_s=50.0)
+        src.write_text(json.dumps({"version": 1, "entries": [upd]}))
+        _lib.tune_load(str(src))
+        _lib.tune_save(str(out))
+        got = json.loads(out.read_text())["entries"]
+        assert len(got) == 2 and got[0]["outer_block"] == 128 and got[1] == entries[1]
+        # refused: malformed, out of range, missing
+        bad = tmp_path / "bad.json"
+        bad.write_text('{"entries": [{"gpu": "x", "sms": }]}')
+        assert L.dpp_tune_load(str(bad).encode()) == _lib.DPP_ERR_INVALID_ARG
+        bad.write_text(json.dumps({"entries": [dict(entries[0], outer_block=100)]}))
+        assert L.dpp_tune_load(str(bad).encode()) == _lib.DPP_ERR_INVALID_ARG
+        assert L.dpp_tune_load(str(tmp_path / "none.json").encode()) == _lib.DPP_ERR_INVALID_ARG
+        _lib.tune_save(str(out))
+        assert len(json.loads(out.read_text())["entries"]) == 2
+    finally:
+        _lib.tune_clear()
+
+
+def test_autotune_rejects_bad_arguments_on_host(L):
+    fake = 4096
+    f = L.dpp_autotune
+    need = L.dpp_autotune_workspace_size(0, 1000, 0, 1, 2)
+    assert need > 2 * dpp.workspace_size(0, 1000, 0, 1, 1)
+    assert L.dpp_autotune_workspace_size(2, 1000, 0, 1, 2) == 0  # not a sampler
+    assert L.dpp_autotune_workspace_size(0, 1000, 0, 1, 5) == 0  # too many streams
+    assert f(2, fake, 100, 100, 0, 1, 2, 4, fake, need, None, None) == _lib.DPP_ERR_INVALID_ARG
+    assert f(0, fake, 100, 50, 0, 1, 2, 4, fake, need, None, None) == _lib.DPP_ERR_INVALID_ARG
+    assert f(0, fake, 100, 100, 0, 1, 0, 4, fake, need, None, None) == _lib.DPP_ERR_INVALID_ARG
+    assert f(0, fake, 100, 100, 0, 1, 2, 0, fake, need, None, None) == _lib.DPP_ERR_INVALID_ARG
+    assert f(0, fake, 1000, 1000, 0, 1, 2, 4, fake, 1024, None, None) == _lib.DPP_ERR_WORKSPACE
+    assert f(1, fake, 100, 100, 1, 1, 2, 4, fake, need, None, None) == _lib.DPP_ERR_UNSUPPORTED
