@@ -61,28 +61,32 @@ def parse():
                         "the 64x64 grid; LU n=8192; batched L-ensembles)")
     p.add_argument("--batch", type=int, default=4096,
                    help="L-ensembles in the batched measurement (n ~ U{64..1024})")
+    p.add_argument("--case", default="", choices=["", "herm", "lu", "cplx", "batched", "adjoint"],
+                   help="run one path alone (a small loop for profiling): mixed Hermitian, "
+                        "mixed LU, mixed complex Hermitian, batched sampler or batched adjoint")
     return p.parse_args()
 
 
-def tc_traffic_per_launch(split="bf16x6"):
-    """DRAM bytes per k_update_tc launch at n = 16384 for one operand split,
-    from the ncu capture summarised in profiles/ (None once dpp_tc.cu has
-    changed since then)."""
+def tc_traffic_per_launch(n: int, kb: int = 256):
+    """Mean DRAM bytes of one 3xTF32 k_update_tc launch of an order-n draw:
+    bytes per m^2 from the one-launch ncu capture summarised in profiles/
+    (n = 8192), times the mean m^2 over the draw's launches (m = n - kb,
+    n - 2 kb, ...). None once dpp_tc.cu has changed since that capture."""
     import hashlib
     try:
         src = os.path.join(ROOT, "paper_1905_00165_gb300", "csrc", "dpp_tc.cu")
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         vals = {}
-        name = ("k_update_tc_traffic_n16384.txt" if split == "bf16x6"
-                else "k_update_tc_3xtf32_traffic_n16384.txt")
-        with open(os.path.join(ROOT, "profiles", name)) as f:
+        with open(os.path.join(ROOT, "profiles", "k_update_tc_3xtf32_traffic_n8192.txt")) as f:
             for ln in f:
                 if ": " in ln:  # keys may hold a colon themselves ("sha256[:16]")
                     k, v = ln.split(": ", 1)
                     vals[k.strip()] = v.strip()
         if vals.get("dpp_tc.cu sha256[:16]") != h:
             return None
-        return float(vals["dram bytes per launch (mean)"])
+        per_m2 = float(vals["dram bytes per m^2"])
+        ms = [n - kb * k for k in range(1, (n + kb - 1) // kb) if n - kb * k > 0]
+        return per_m2 * sum(m * m for m in ms) / max(1, len(ms))
     except Exception:
         return None
 
@@ -159,7 +163,19 @@ def bench_batched(dpp, _lib, dev, batch: int, draws: int, seed: int = 0):
     factor, FP64 pivots and recompute). samples/s = instances drawn per second."""
     import torch
     import workloads as W
-    Ks = W.lensemble_batch_torch(batch, seed=seed, device=str(dev))
+    # L-ensemble kernels L_i = Phi_i Phi_i^T, converted on the device to their
+    # marginal kernels K_i = L_i (L_i + I)^{-1} by the library (one launch)
+    Ls = W.lensemble_L_batch_torch(batch, seed=seed, device=str(dev))
+    torch.cuda.synchronize()
+    stream0 = torch.cuda.current_stream(dev)
+    c0 = torch.cuda.Event(enable_timing=True)
+    c1 = torch.cuda.Event(enable_timing=True)
+    c0.record(stream0)
+    Ks = dpp.lensemble_to_marginal(Ls)
+    c1.record(stream0)
+    torch.cuda.synchronize()
+    ms_conv = c0.elapsed_time(c1)
+    del Ls
     sizes = [int(K.shape[0]) for K in Ks]
     b = dpp.BatchedSampler(Ks)
     stream = torch.cuda.current_stream(dev)
@@ -201,6 +217,9 @@ def bench_batched(dpp, _lib, dev, batch: int, draws: int, seed: int = 0):
                 sum(v["launches"] for v in prof.values()) / draws,
             "borderline_last_draw": sum(r["n_borderline"] for r in res),
             "failed_instances": bad,
+            "conversion": {"instances_per_s": batch / (ms_conv / 1e3), "ms": ms_conv,
+                           "what": "K_i = L_i (L_i + I)^{-1} from L_i = Phi_i Phi_i^T, FP64, "
+                                   "one persistent launch (dpp_lensemble_to_marginal_batched)"},
             "adjoint": {"instances_per_s": n_adj / (ms_adj / 1e3), "ms": ms_adj,
                         "instances": n_adj, "precision": "fp64",
                         "note": "dK_i = (K_i - 1_{Y_i^c})^{-T}: forced-decision FP64 "
@@ -397,6 +416,55 @@ def run_suite(args):
     return 0
 
 
+def run_case(args):
+    """One path alone: `--warmup` then `--steps` draws of the chosen form at
+    order --n (the batched forms: --batch L-ensembles), one JSON line with the
+    mean time per draw. Used to profile one kernel family on a small case."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1905_00165_gb300 as dpp
+    from paper_1905_00165_gb300 import _lib
+    import workloads as W
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    n = args.n
+    prec = "3xtf32" if args.precision == "auto" else args.precision
+    steps = args.steps if args.steps is not None else 4
+    if args.case in ("batched", "adjoint"):
+        Ks = W.lensemble_batch_torch(args.batch, seed=0, device=str(dev))
+        b = dpp.BatchedSampler(Ks)
+        b.draw(10**6)
+        if args.case == "batched":
+            fn = b.draw
+        else:
+            fn = lambda s: b.logprob_backward()
+    else:
+        if args.case == "lu":
+            K, _ = W.lu_similarity_kernel(n, seed=0, device=str(dev))
+            Kd = torch.from_numpy(np.ascontiguousarray(K.T)).to(dev).t()
+            fn = lambda s: dpp.sample_lu(Kd, seed=s, precision=prec)
+        else:
+            Kd = W.hermitian_kernel(n, seed=0, kind=args.kind, complex_=args.case == "cplx",
+                                    device=str(dev), return_torch=True)
+            Kd = Kd.t().contiguous().t()
+            fn = lambda s: dpp.sample_hermitian(Kd, seed=s, precision=prec)
+    for w in range(args.warmup):
+        fn(10**6 + w)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for s in range(steps):
+        fn(s)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"case": args.case, "n": n, "precision": prec, "steps": steps,
+                      "ms_per_draw": e0.elapsed_time(e1) / steps}))
+    return 0
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -544,6 +612,8 @@ def main():
         return run_reference(args)
     if args.suite:
         return run_suite(args)
+    if args.case:
+        return run_case(args)
     import numpy as np
     import torch
 
@@ -690,7 +760,8 @@ def main():
             ach = per_launch_flops / (avg_ms / 1e3) / 1e12
             roof = {"kernel": dom, "bound": "tensor", "achieved": ach, "peak": tf32 / 3.0,
                     "unit": "TFLOP/s", "frac": ach / (tf32 / 3.0),
-                    "traffic": tc_traffic_per_launch("3xtf32") if n == 16384 else None,
+                    "traffic": tc_traffic_per_launch(n),
+                    "traffic_source": "ncu one launch at n = 8192, scaled by m^2 (profiles/)",
                     "executed_tensor_frac": 3.0 * ach / tf32,
                     "peak_source": "measured bf16 x nominal tf32/bf16 (2.25:1.1), / 3 products",
                     "measured_tf32_tflops": dense["tf32_tflops"],
@@ -700,7 +771,7 @@ def main():
             ach = per_launch_flops / (avg_ms / 1e3) / 1e12
             roof = {"kernel": dom, "bound": "tensor", "achieved": ach, "peak": bf16 / 6.0,
                     "unit": "TFLOP/s", "frac": ach / (bf16 / 6.0),
-                    "traffic": tc_traffic_per_launch() if n == 16384 else None,
+                    "traffic": None,
                     "executed_tensor_frac": 6.0 * ach / bf16,
                     "peak_source": "MEASURED_PEAKS bf16_tflops (burst), / 6 products"}
         else:

@@ -308,6 +308,28 @@ dpp_status dpp_logprob_backward_batched(int32_t batch, const int64_t* n,
                                         void* workspace, size_t workspace_bytes,
                                         void* stream);
 
+/* L-ensemble to marginal kernel (Section 5, stated there as future work):
+ * for each real symmetric positive semi-definite L_i of a batch,
+ *     K_i = L_i (L_i + I)^{-1} = I - (L_i + I)^{-1},
+ * the marginal kernel of the L-ensemble DPP (P(Y) proportional to
+ * det(L_Y)), ready for dpp_sample_batched. FP64, in ONE persistent launch:
+ * each CTA takes the next instance (largest n first), factors L_i + I as
+ * L D L^T (32 x 32 tiles), forms Z = L^{-1} and writes I - Z^T D^{-1} Z to both
+ * triangles of K_i.
+ *   batch      number of instances (>= 0).
+ *   n, ld, ld_k  HOST arrays: order (0..4096), leading dimension of L_i and
+ *              of K_i.
+ *   L, K       HOST arrays of DEVICE pointers (L_i lower triangle read; K_i
+ *              written in full; K_i may not alias L_i).
+ *   workspace  device, dpp_logprob_backward_batched_workspace(batch, n_max)
+ *              bytes for one CTA per SM (a smaller one runs on fewer CTAs).
+ * Errors as dpp_logprob_backward_batched. */
+dpp_status dpp_lensemble_to_marginal_batched(int32_t batch, const int64_t* n,
+                                             const double* const* L, const int64_t* ld,
+                                             double* const* K, const int64_t* ld_k,
+                                             void* workspace, size_t workspace_bytes,
+                                             void* stream);
+
 /* Process-wide tuning knobs (read at each call; not for concurrent changes).
  *   DPP_TUNE_TAU_SAFETY   c in the mixed-precision borderline bound
  *                         tau_j = c * 2^-22 * sqrt(j + 1) * (K_jj + s_j),

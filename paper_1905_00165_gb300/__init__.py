@@ -16,6 +16,7 @@ from ._lib import (DPP_C128, DPP_OP_LOGPROB_BACKWARD, DPP_OP_SAMPLE_HERMITIAN,
 
 __all__ = ["sample_hermitian", "sample_hermitian_static", "sample_lu", "greedy_hermitian",
            "greedy_lu", "sample_batched", "BatchedSampler", "autotune",
+           "lensemble_to_marginal",
            "logprob_backward", "uniforms", "Sample", "DPPLogProb", "DPPError", "load",
            "workspace_size"]
 
@@ -294,6 +295,39 @@ def sample_batched(Ks, seed: int = 0, instance=None, want_pivots: bool = False, 
     b = BatchedSampler(Ks, instance=instance, want_pivots=want_pivots, uniforms=uniforms)
     b.draw(seed)
     return b
+
+
+def lensemble_to_marginal(Ls):
+    """K_i = L_i (L_i + I)^{-1} for a list of real symmetric PSD L_i (FP64 CUDA
+    tensors, n_i <= 4096), in one persistent launch (see
+    dpp_lensemble_to_marginal_batched). Returns the K_i (column-major)."""
+    import ctypes
+    import numpy as np
+    torch = _torch()
+    L = load()
+    B = len(Ls)
+    if B == 0:
+        return []
+    Lc = [colmajor(x)[0] for x in Ls]
+    for x in Ls:
+        if x.dtype != torch.float64 or not x.is_cuda:
+            raise TypeError("L-ensemble kernels must be float64 CUDA tensors")
+    ns = [int(x.shape[0]) for x in Ls]
+    dev = Ls[0].device
+    Ks = [empty_colmajor(m, torch.float64, dev) for m in ns]
+    n_h = np.asarray(ns, dtype=np.int64)
+    ld_h = np.asarray([x.stride(1) if m else 1 for x, m in zip(Lc, ns)], dtype=np.int64)
+    ldk_h = np.asarray([k.stride(1) if m else 1 for k, m in zip(Ks, ns)], dtype=np.int64)
+    P = ctypes.c_void_p * B
+    lp = P(*[x.data_ptr() for x in Lc])
+    kp = P(*[k.data_ptr() for k in Ks])
+    need = L.dpp_logprob_backward_batched_workspace(B, max(ns))
+    ws = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+    _lib.check(L.dpp_lensemble_to_marginal_batched(
+        B, n_h.ctypes.data, ctypes.cast(lp, ctypes.c_void_p), ld_h.ctypes.data,
+        ctypes.cast(kp, ctypes.c_void_p), ldk_h.ctypes.data, ws.data_ptr(), ws.numel(),
+        _stream(dev)))
+    return Ks
 
 
 def autotune(K, hermitian: bool = True, precision: str = "3xtf32", max_streams: int = 4,

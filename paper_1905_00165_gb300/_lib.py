@@ -101,6 +101,8 @@ def load(path: Optional[str] = None):
     L.dpp_tune_save.restype = i32
     L.dpp_tune_load.argtypes = [ctypes.c_char_p]
     L.dpp_tune_load.restype = i32
+    L.dpp_lensemble_to_marginal_batched.argtypes = [i32, vp, vp, vp, vp, vp, vp, sz, vp]
+    L.dpp_lensemble_to_marginal_batched.restype = i32
     L.dpp_tune_clear.argtypes = []
     L.dpp_tune_clear.restype = None
     _lib = L

@@ -16,6 +16,10 @@
 // GB300's FP64 rate is a small fraction of its FP32 rate, so the work is
 // FP64-compute-bound; one instance per CTA keeps every SM busy without any
 // inter-CTA synchronisation.
+//
+// The same launch converts L-ensembles to marginal kernels (mode kLEnsemble):
+// with A = L + I (positive definite for positive semi-definite L) in step 1
+// and  K = I - A^{-1} = L (L + I)^{-1}  written in step 4.
 #include <algorithm>
 #include <vector>
 
@@ -28,12 +32,15 @@ namespace {
 
 constexpr int kAT = 256;  // threads per CTA
 
+enum { kAdjoint = 0, kLEnsemble = 1 };
+
 struct AdjDesc {
-  const double* K;
-  const uint8_t* keep;
-  const double* g;
-  double* dK;
+  const double* K;      // K (adjoint) or L (L-ensemble), lower triangle read
+  const uint8_t* keep;  // adjoint only
+  const double* g;      // adjoint only
+  double* dK;           // output: g A^{-1} (adjoint) or I - A^{-1} (L-ensemble)
   int64_t n, ld, ldd;
+  int mode;
 };
 
 struct AdjArgs {
@@ -72,11 +79,15 @@ __device__ void adjoint_one(const AdjArgs& a, const AdjDesc& d, double* scr) {
   double* Linv = Wb + ldz * 32;
   double* dv = Linv + (int64_t)nt * 1024;
 
-  // ---- 1. A = K - 1_{Y^c}, lower triangle ----
+  // ---- 1. A = K - 1_{Y^c} (adjoint) or L + I (L-ensemble), lower triangle ----
+  const bool lens = d.mode == kLEnsemble;
   for (int64_t j = 0; j < n; ++j) {
     for (int64_t i = j + tid; i < n; i += kAT) {
       double v = d.K[i + j * d.ld];
-      if (i == j && d.keep[i] == 0) v -= 1.0;
+      if (i == j) {
+        if (lens) v += 1.0;
+        else if (d.keep[i] == 0) v -= 1.0;
+      }
       A[i + j * ldd] = v;
     }
   }
@@ -218,8 +229,8 @@ __device__ void adjoint_one(const AdjArgs& a, const AdjDesc& d, double* scr) {
     }
   }
 
-  // ---- 4. dK = g Z^T D^{-1} Z, lower tiles mirrored ----
-  const double g = *d.g;
+  // ---- 4. dK = g Z^T D^{-1} Z (or K = I - Z^T D^{-1} Z), lower tiles mirrored ----
+  const double g = lens ? -1.0 : *d.g;
   for (int I = 0; I < nt; ++I) {
     for (int J = 0; J <= I; ++J) {
       double acc[4] = {0.0, 0.0, 0.0, 0.0};
@@ -241,7 +252,7 @@ __device__ void adjoint_one(const AdjArgs& a, const AdjDesc& d, double* scr) {
       for (int j = 0; j < 4; ++j) {
         const int64_t c = 32 * (int64_t)J + cg + 8 * j;
         if (i < n && c <= i) {
-          const double v = g * acc[j];
+          const double v = g * acc[j] + ((lens && i == c) ? 1.0 : 0.0);
           A[i + c * ldd] = v;
           A[c + i * ldd] = v;
         }
@@ -300,7 +311,8 @@ cudaError_t adjoint_batched(int32_t batch, const int64_t* n, const double* const
   std::sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return n[x] > n[y]; });
   for (int32_t k = 0; k < batch; ++k) {
     const int32_t i = order[(size_t)k];
-    h[(size_t)k] = AdjDesc{K[i], keep[i], g[i], dK[i], n[i], ld[i], ld_dk[i]};
+    h[(size_t)k] = AdjDesc{K[i], keep ? keep[i] : nullptr, g ? g[i] : nullptr, dK[i],
+                           n[i], ld[i], ld_dk[i], keep ? kAdjoint : kLEnsemble};
   }
   char* base = ws.base;
   AdjDesc* desc = reinterpret_cast<AdjDesc*>(base);
@@ -323,7 +335,7 @@ cudaError_t adjoint_batched(int32_t batch, const int64_t* n, const double* const
   a.per_cta = per;
   a.ldz = adj_ldz(n_max > 0 ? n_max : 1);
   {
-    ProfScope ps(kProfOther, s);
+    ProfScope ps(keep ? kProfAdjoint : kProfLEnsemble, s);
     k_adjoint_batched<<<(unsigned)ctas, kAT, 0, s>>>(a);
   }
   return cudaGetLastError();

@@ -328,6 +328,38 @@ dpp_status dpp_logprob_backward_batched(int32_t batch, const int64_t* n, const v
   return DPP_OK;
 }
 
+dpp_status dpp_lensemble_to_marginal_batched(int32_t batch, const int64_t* n,
+                                             const double* const* L, const int64_t* ld,
+                                             double* const* K, const int64_t* ld_k,
+                                             void* workspace, size_t workspace_bytes,
+                                             void* stream) {
+  g_last_error.clear();
+  if (batch < 0) return fail(DPP_ERR_INVALID_ARG, "batch must be >= 0");
+  if (batch == 0) return DPP_OK;
+  if (!n || !L || !ld || !K || !ld_k)
+    return fail(DPP_ERR_INVALID_ARG, "the per-instance host arrays must not be NULL");
+  int64_t n_max = 0;
+  for (int32_t i = 0; i < batch; ++i) {
+    if (n[i] < 0 || ld[i] < (n[i] > 1 ? n[i] : 1) || ld_k[i] < (n[i] > 1 ? n[i] : 1))
+      return fail(DPP_ERR_INVALID_ARG, "bad n / ld / ld_k of an instance");
+    if (n[i] > 0 && (!L[i] || !K[i])) return fail(DPP_ERR_INVALID_ARG, "NULL pointer of a non-empty instance");
+    if (n[i] > n_max) n_max = n[i];
+  }
+  if (n_max > 4096) return fail(DPP_ERR_INVALID_ARG, "n above 4096 (one CTA per instance)");
+  if (!workspace || !aligned(workspace, 256))
+    return fail(DPP_ERR_WORKSPACE, "workspace must be non-NULL and 256-byte aligned");
+  if (workspace_bytes < ws_adjoint_batched(batch, n_max, 1))
+    return fail(DPP_ERR_WORKSPACE, "workspace too small for one CTA");
+  begin_call(DPP_OP_LOGPROB_BACKWARD, n_max, DPP_R64, DPP_PREC_FP64);
+  Workspace ws;
+  ws.base = static_cast<char*>(workspace);
+  ws.size = workspace_bytes;
+  cudaError_t e = adjoint_batched(batch, n, L, ld, nullptr, nullptr, K, ld_k, n_max, ws,
+                                  static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return fail_cuda(e, "dpp_lensemble_to_marginal_batched");
+  return DPP_OK;
+}
+
 size_t dpp_logprob_backward_batched_workspace(int32_t batch, int64_t n_max) {
   if (batch < 0 || n_max < 0) return 0;
   begin_call(DPP_OP_LOGPROB_BACKWARD, n_max, DPP_R64, DPP_PREC_FP64);

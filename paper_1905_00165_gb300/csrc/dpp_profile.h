@@ -14,7 +14,9 @@ enum ProfCat {
   kProfRecompute = 5,
   kProfOther = 6,
   kProfBatched = 7,
-  kProfCategories = 8
+  kProfAdjoint = 8,
+  kProfLEnsemble = 9,
+  kProfCategories = 10
 };
 
 // Counts one launch; while profiling is on, records an event pair around the

@@ -168,14 +168,27 @@ def lensemble_sizes(batch: int, seed: int = 0, nmin: int = 64, nmax: int = 1024)
     return _rng(seed).integers(nmin, nmax + 1, size=batch)
 
 
-def lensemble_kernel(n: int, seed: int, features: int = 64,
-                     qmin: float = 0.1, qmax: float = 10.0) -> np.ndarray:
-    """K = Phi (Phi^T Phi + I)^{-1} Phi^T = L (L + I)^{-1}, L = Phi Phi^T."""
+def lensemble_features(n: int, seed: int, features: int = 64,
+                       qmin: float = 0.1, qmax: float = 10.0) -> np.ndarray:
+    """Phi (n x features): unit-norm Gaussian rows times LogUniform qualities."""
     rng = _rng(seed)
     G = rng.standard_normal((n, features))
     G /= np.linalg.norm(G, axis=1, keepdims=True)
     q = np.exp(rng.uniform(math.log(qmin), math.log(qmax), n))
-    Phi = G * q[:, None]
+    return G * q[:, None]
+
+
+def lensemble_L(n: int, seed: int, features: int = 64) -> np.ndarray:
+    """The L-ensemble kernel L = Phi Phi^T of ``lensemble_kernel``'s Phi."""
+    Phi = lensemble_features(n, seed, features)
+    L = Phi @ Phi.T
+    return 0.5 * (L + L.T)
+
+
+def lensemble_kernel(n: int, seed: int, features: int = 64,
+                     qmin: float = 0.1, qmax: float = 10.0) -> np.ndarray:
+    """K = Phi (Phi^T Phi + I)^{-1} Phi^T = L (L + I)^{-1}, L = Phi Phi^T."""
+    Phi = lensemble_features(n, seed, features, qmin, qmax)
     M = Phi.T @ Phi + np.eye(features)
     K = Phi @ np.linalg.solve(M, Phi.T)
     return 0.5 * (K + K.T)
@@ -207,4 +220,24 @@ def lensemble_batch_torch(batch: int, seed: int = 0, nmin: int = 64, nmax: int =
         Phi = G * q[:, None]
         K = Phi @ torch.linalg.solve(Phi.T @ Phi + eye, Phi.T)
         out.append(0.5 * (K + K.T))
+    return out
+
+
+def lensemble_L_batch_torch(batch: int, seed: int = 0, nmin: int = 64, nmax: int = 1024,
+                            features: int = 64, device: str = "cuda"):
+    """The L-ensemble kernels L_i = Phi_i Phi_i^T of ``lensemble_batch_torch``
+    (same sizes, same features), before conversion to marginal kernels."""
+    import torch
+    sizes = lensemble_sizes(batch, seed, nmin, nmax)
+    gen = torch.Generator(device="cpu").manual_seed(seed)
+    out = []
+    for m in sizes:
+        m = int(m)
+        G = torch.randn(m, features, generator=gen, dtype=torch.float64).to(device)
+        G = G / G.norm(dim=1, keepdim=True)
+        q = torch.exp(torch.empty(m, dtype=torch.float64).uniform_(math.log(0.1), math.log(10.0),
+                                                                   generator=gen)).to(device)
+        Phi = G * q[:, None]
+        L = Phi @ Phi.T
+        out.append(0.5 * (L + L.T))
     return out
