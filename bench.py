@@ -669,7 +669,7 @@ def main():
         tuning = _lib.tune_lookup(0, n, 0, prec)
         source = "tuning table"
         if tuning is None:
-            tuning = dpp.autotune(Kd, hermitian=True, precision=prec_name, max_streams=4, draws=12)
+            tuning = dpp.autotune(Kd, hermitian=True, precision=prec_name, max_streams=8, draws=16)
             source = "autotuned in this run"
         tuning["source"] = source
         nst = int(tuning["streams"])

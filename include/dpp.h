@@ -353,6 +353,13 @@ dpp_status dpp_lensemble_to_marginal_batched(int32_t batch, const int64_t* n,
  *                         its warps, helper CTAs own the outer block's 32-row
  *                         chunks, left-looking products are computed before
  *                         each panel is published; the LU path's kernel),
+ *                         3 = split (also for the mixed LU path): the chunked
+ *                         panel launch holds only CTA 0 and one helper CTA per
+ *                         chunk of the outer block (8 CTAs), and the rows below
+ *                         the outer block are brought through its panels
+ *                         afterwards by a separate launch on the capped grid,
+ *                         so the SMs of other draws in flight are not held
+ *                         while the decisions run,
  *                         0 = automatic (the default): chunked when a launch
  *                         gets at least 96 CTAs, else single helper. The SIMT
  *                         trailing update always runs with pipeline 1.
@@ -368,6 +375,12 @@ dpp_status dpp_lensemble_to_marginal_batched(int32_t batch, const int64_t* n,
  *                         pipeline): their waits run out after DPP_TUNE_WAIT_NS,
  *                         every launch still ends, and the draw's status has
  *                         DPP_RES_TIMEOUT. Its outputs are then meaningless.
+ *   DPP_TUNE_UPDATE_VARIANT  tensor-core trailing update (0..3, default 0):
+ *                         bit 0 = accumulate 64 deep (3xTF32) / 32 deep
+ *                         (BF16x6) in one tensor-memory accumulator before it
+ *                         is drained into FP32 registers instead of 32 / 16;
+ *                         bit 1 = 3xTF32 only: 16-deep operand stages, six of
+ *                         them, instead of three 32-deep ones
  *   DPP_TUNE_USE_CACHE    1 (default): when the autotuner's table (below) has
  *                         an entry for a call's key, that entry's outer block,
  *                         panel pipeline and CTA cap replace the three knobs
@@ -381,7 +394,8 @@ typedef enum {
   DPP_TUNE_PANEL_PIPELINE = 4,
   DPP_TUNE_WAIT_NS = 5,
   DPP_TUNE_FAULT_WITHHOLD = 6,
-  DPP_TUNE_USE_CACHE = 7
+  DPP_TUNE_USE_CACHE = 7,
+  DPP_TUNE_UPDATE_VARIANT = 8
 } dpp_tune_key;
 
 dpp_status dpp_set_tuning(int32_t key, double value);
@@ -405,12 +419,12 @@ typedef struct {
   int32_t n_bucket;        /* floor(log2 n) of the order it was tuned at       */
   int64_t n;               /* the order it was tuned at                        */
   int32_t outer_block;     /* as DPP_TUNE_OUTER_BLOCK                          */
-  int32_t panel_pipeline;  /* as DPP_TUNE_PANEL_PIPELINE (1 or 2; 0 if n/a)    */
+  int32_t panel_pipeline;  /* as DPP_TUNE_PANEL_PIPELINE (0 = automatic)      */
   int32_t max_ctas;        /* as DPP_TUNE_MAX_CTAS                             */
   int32_t streams;         /* draws in flight                                  */
   double samples_per_s;    /* measured with this configuration                 */
   int32_t candidates;      /* configurations timed to choose it                */
-  int32_t reserved;
+  int32_t update_variant;  /* as DPP_TUNE_UPDATE_VARIANT                       */
 } dpp_tune_entry;
 
 /* Device workspace for dpp_autotune: max_streams draws' workspaces, keep
@@ -420,10 +434,12 @@ size_t dpp_autotune_workspace_size(int32_t op, int64_t n, int32_t dtype, int32_t
 
 /* Time every candidate configuration on the caller's kernel K (device,
  * column-major as for dpp_sample_hermitian / dpp_sample_lu; op selects which)
- * and keep the fastest in the table. Candidates: draws in flight 1, 2 and 4
- * (up to max_streams, 1..4), each launch then capped at SMs / streams CTAs;
- * outer block 128 and 256 (mixed precisions); for real Hermitian mixed draws,
- * both panel pipelines. Each candidate runs one warm-up draw per stream and
+ * and keep the fastest in the table. Candidates: draws in flight 1, 2, 4 and
+ * 8 (up to max_streams, 1..8), each launch then capped at SMs / streams CTAs;
+ * outer block 128 and 256 (mixed precisions); panel pipelines 1, 2 and 3 for
+ * real Hermitian mixed draws, 0 and 3 for real LU mixed draws; then, with the
+ * winner's settings, the tensor-core update variants (DPP_TUNE_UPDATE_VARIANT;
+ * 1..3 for 3xTF32, 1 for BF16x6). Each candidate runs one warm-up draw per stream and
  * then `draws` timed draws (Philox seeds 0, 1, ...) dealt round-robin to its
  * streams, timed with CUDA events between a start event on `stream` and the
  * last draw's end. Blocks the host until done; allocates only its own CUDA

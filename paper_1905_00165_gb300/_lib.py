@@ -157,6 +157,7 @@ def profile_stop() -> dict:
 DPP_TUNE_TAU_SAFETY, DPP_TUNE_OUTER_BLOCK, DPP_TUNE_UPDATE_KERNEL, DPP_TUNE_MAX_CTAS = 0, 1, 2, 3
 DPP_TUNE_PANEL_PIPELINE = 4
 DPP_TUNE_WAIT_NS, DPP_TUNE_FAULT_WITHHOLD, DPP_TUNE_USE_CACHE = 5, 6, 7
+DPP_TUNE_UPDATE_VARIANT = 8
 
 
 class TuneEntry(ctypes.Structure):
@@ -166,10 +167,10 @@ class TuneEntry(ctypes.Structure):
                 ("n", ctypes.c_int64), ("outer_block", ctypes.c_int32),
                 ("panel_pipeline", ctypes.c_int32), ("max_ctas", ctypes.c_int32),
                 ("streams", ctypes.c_int32), ("samples_per_s", ctypes.c_double),
-                ("candidates", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("candidates", ctypes.c_int32), ("update_variant", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 def tune_lookup(op: int, n: int, dtype: int, precision: int):

@@ -157,7 +157,7 @@ static dpp_status sample_common(bool hermitian, const void* K, int64_t n, int64_
     else if (dtype == DPP_C128)
       e = sample_mixed_cx(a, ws);
     else if (g_tuning.update_kernel == 0 &&
-             (g_tuning.panel_pipeline == 2 ||
+             (g_tuning.panel_pipeline >= 2 ||
               (g_tuning.panel_pipeline == 0 && (g_tuning.max_ctas == 0 || g_tuning.max_ctas >= 96))))
       e = sample_mixed_chunked(a, ws);
     else
@@ -392,8 +392,8 @@ dpp_status dpp_set_tuning(int32_t key, double value) {
       return DPP_OK;
     }
     case DPP_TUNE_PANEL_PIPELINE:
-      if (value != 0.0 && value != 1.0 && value != 2.0)
-        return fail(DPP_ERR_INVALID_ARG, "panel pipeline is 0, 1 or 2");
+      if (value != 0.0 && value != 1.0 && value != 2.0 && value != 3.0)
+        return fail(DPP_ERR_INVALID_ARG, "panel pipeline is 0, 1, 2 or 3");
       g_settings.panel_pipeline = (int)value;
       return DPP_OK;
     case DPP_TUNE_WAIT_NS:
@@ -409,6 +409,13 @@ dpp_status dpp_set_tuning(int32_t key, double value) {
       if (value != 0.0 && value != 1.0) return fail(DPP_ERR_INVALID_ARG, "use cache is 0 or 1");
       g_settings.use_cache = (int)value;
       return DPP_OK;
+    case DPP_TUNE_UPDATE_VARIANT: {
+      const int v = (int)value;
+      if ((double)v != value || v < 0 || v > 3)
+        return fail(DPP_ERR_INVALID_ARG, "update variant is 0, 1, 2 or 3");
+      g_settings.update_variant = v;
+      return DPP_OK;
+    }
     default:
       return fail(DPP_ERR_INVALID_ARG, "unknown tuning key");
   }
@@ -424,6 +431,7 @@ double dpp_get_tuning(int32_t key) {
     case DPP_TUNE_WAIT_NS: return g_settings.wait_ns;
     case DPP_TUNE_FAULT_WITHHOLD: return (double)g_settings.fault_withhold;
     case DPP_TUNE_USE_CACHE: return (double)g_settings.use_cache;
+    case DPP_TUNE_UPDATE_VARIANT: return (double)g_settings.update_variant;
     default: return -1.0;
   }
 }

@@ -67,6 +67,7 @@ struct Tuning {
   double tau_safety = 8.0;  // c in the borderline bound
   int outer_block = 256;    // mixed path: columns contracted per trailing update
   int update_kernel = 0;    // 0 = tcgen05, 1 = SIMT FP32
+  int update_variant = 0;   // tcgen05 update: operand ring and drain interval (0..3)
   int max_ctas = 0;         // mixed path: CTAs per launch (0 = one per SM)
   int panel_pipeline = 0;   // mixed Hermitian path: 0 = auto, 1 = single helper, 2 = chunked
   double wait_ns = 2e9;     // limit of the bounded device waits (ns)

@@ -1279,6 +1279,35 @@ __global__ void __launch_bounds__(kLuThreads, 1) k_lu_outer(LuArgs a) {
   }
 }
 
+// Split pipeline (DPP_TUNE_PANEL_PIPELINE 3): the panel launch holds only CTA 0
+// and the helpers, which factor the outer block's own rows with the decisions;
+// afterwards this kernel, on a wide grid, brings every row below the outer
+// block through its panels: for each 32-row chunk, panel by panel, the
+// left-looking products over the earlier panels, the solve against the
+// published panel and the stores of L (M^T), W, M, the tensor-core splits and
+// the running diagonal, exactly the worker CTAs' steps of the pipelined launch.
+// Every panel is final when it starts, so there is no wait and no recompute to
+// serve; the decision chain no longer holds the SMs that stream these rows.
+template <bool SYM>
+__global__ void __launch_bounds__(kLuThreads, 1) k_below(LuArgs a) {
+  const int np = (a.kb + 31) / 32;
+  const int64_t qe = a.q + a.kb;
+  const int64_t c_first = qe + 32 * (int64_t)blockIdx.x, c_stride = 32 * (int64_t)gridDim.x;
+  const int total = c_first < a.n ? (int)((a.n - 1 - c_first) / c_stride + 1) : 0;
+  for (int m0 = 0; m0 < total; m0 += a.slots) {
+    const int cnt = (total - m0) < a.slots ? (total - m0) : a.slots;
+    const int64_t cf = c_first + (int64_t)m0 * c_stride;
+    for (int k = 0; k < np; ++k) {
+      const int64_t p = a.q + 32 * k;
+      const int b = (int)((qe - p) < 32 ? (qe - p) : 32);
+      chunks_left<SYM>(a, p, b, 32 * k, cf, c_stride, cnt);
+      load_panel<SYM>(a, p, b);
+      __syncthreads();
+      chunks_solve<SYM>(a, p, b, cf, c_stride, cnt);
+    }
+  }
+}
+
 // FP32 copy of K (lower: its lower triangle only) and the running diagonal.
 __global__ void __launch_bounds__(256) k_convert_full(const double* K, int64_t ldk, float* A,
                                                       int64_t lda, int64_t n, double* kd,
@@ -1396,6 +1425,9 @@ cudaError_t sample_chunked(const DrawArgs& a, Workspace ws) {
                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)lu_dyn_smem(kMaxSlots));
     if (ea != cudaSuccess) return ea;
+    ea = cudaFuncSetAttribute(k_below<SYM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)lu_dyn_smem(kMaxSlots));
+    if (ea != cudaSuccess) return ea;
     DevInfo di;
     if ((ea = dev_info(&di)) != cudaSuccess) return ea;
     int per_sm = 0;
@@ -1409,19 +1441,26 @@ cudaError_t sample_chunked(const DrawArgs& a, Workspace ws) {
   int grid = cap;
   if (g_tuning.max_ctas > 0 && grid > g_tuning.max_ctas) grid = g_tuning.max_ctas;
   if (grid < 3) grid = 3;
+  // split pipeline: the panel launch is CTA 0 and one helper per chunk of the
+  // outer block; the rows below go to k_below on `grid` CTAs
+  const bool split_rows = g_tuning.panel_pipeline == 3;
+  const int below_grid = grid;
+  if (split_rows) grid = kMaxOuterBlock / 32;
   // CTA 0 decides, CTAs 1..nh own the outer block's chunks, the rest the
   // chunks beyond it; slots hold the chunks a CTA precomputes per panel
   // (one CTA per chunk on a full grid; on a small grid a helper owns
   // several chunks, so that most CTAs stay workers)
-  int nh = (grid - 2) / 8;
+  int nh = split_rows ? grid - 1 : (grid - 2) / 8;
   if (nh > kMaxOuterBlock / 32 - 1) nh = kMaxOuterBlock / 32 - 1;
   if (nh < 1) nh = 1;
-  const int64_t nwk = grid - 1 - nh;
+  const int64_t nwk = split_rows ? below_grid : grid - 1 - nh;
   const int64_t trail = ((n > NB ? n - NB : 0) + 31) / 32;
   int slots = (int)((trail + nwk - 1) / nwk);
   const int hslots = (kMaxOuterBlock / 32 - 1 + nh - 1) / nh;
+  int below_slots = slots < 1 ? 1 : (slots > kMaxSlots ? kMaxSlots : slots);
   if (slots < hslots) slots = hslots;
   if (slots > kMaxSlots) slots = kMaxSlots;
+  if (split_rows) slots = hslots;
   const size_t dyn = lu_dyn_smem(slots);
   const int split = a.precision == DPP_PREC_BF16X6 ? kSplitBf16x6 : kSplit3xTf32;
   unsigned epoch = 1;
@@ -1472,6 +1511,16 @@ cudaError_t sample_chunked(const DrawArgs& a, Workspace ws) {
     if (e != cudaSuccess) return e;
     epoch += (unsigned)((kb + 31) / 32);
     const int64_t r0 = q + kb;
+    if (split_rows && r0 < n) {
+      // the rows below the outer block, through its panels ((n - r0) kb^2
+      // flops for the Hermitian form, twice that for LU)
+      LuArgs lb = la;
+      lb.slots = below_slots;
+      const double fl = (SYM ? 1.0 : 2.0) * (double)(n - r0) * (double)kb * (double)kb;
+      ProfScope ps(kProfBelow, a.stream, fl, 0.0);
+      k_below<SYM><<<(unsigned)below_grid, kLuThreads, lu_dyn_smem(below_slots), a.stream>>>(lb);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     if (r0 < n) {
       const int64_t m = n - r0;
       // lower triangle (SYM) or whole square of 2 m^2 kb flops

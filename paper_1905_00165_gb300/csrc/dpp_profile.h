@@ -16,7 +16,8 @@ enum ProfCat {
   kProfBatched = 7,
   kProfAdjoint = 8,
   kProfLEnsemble = 9,
-  kProfCategories = 10
+  kProfBelow = 10,
+  kProfCategories = 11
 };
 
 // Counts one launch; while profiling is on, records an event pair around the

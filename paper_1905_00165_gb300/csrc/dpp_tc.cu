@@ -58,18 +58,14 @@ constexpr int kAccBufs = 4;
 constexpr int kTmemCols = kAccBufs * kBN;  // all 512 columns
 
 template <int MODE>
-struct TcCfg;
+struct TcBase;
 
-// 3xTF32: 2 splits, 32 fp32 per 128-byte row, one drain per k-block of four
-// 8-deep steps (12 MMAs).
+// 3xTF32: 2 splits (TF32 hi, lo in FP32 containers), three products per
+// 8-deep k-step.
 template <>
-struct TcCfg<kSplit3xTf32> {
+struct TcBase<kSplit3xTf32> {
   static constexpr int kOps = 2;
-  static constexpr int kBK = 32;
-  static constexpr int kRowBytes = 128;  // SWIZZLE_128B rows
-  static constexpr int kStages = 3;
-  static constexpr int kSteps = 4;          // MMA k-steps per k-block
-  static constexpr int kStepsPerDrain = 4;  // drain once per k-block
+  static constexpr int kEsz = 4;
   static constexpr int kProducts = 3;
   // D = F32 (bits 4-5 = 1), A = B = TF32 (2), K-major, N >> 3, M >> 4
   static constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) |
@@ -81,18 +77,11 @@ struct TcCfg<kSplit3xTf32> {
   }
 };
 
-// BF16x6: 3 splits, 32 bf16 per 64-byte row (SWIZZLE_64B), so that a stage is
-// 48 KB and four stages fit: the MMAs of one 32-deep stage take about half a
-// microsecond, less than an L2 refill, so the ring must be deep. One drain per
-// 16-deep step.
+// BF16x6: 3 splits, the six products of combined order <= 2 per 16-deep step.
 template <>
-struct TcCfg<kSplitBf16x6> {
+struct TcBase<kSplitBf16x6> {
   static constexpr int kOps = 3;
-  static constexpr int kBK = 32;
-  static constexpr int kRowBytes = 64;
-  static constexpr int kStages = 4;
-  static constexpr int kSteps = 2;
-  static constexpr int kStepsPerDrain = 1;
+  static constexpr int kEsz = 2;
   static constexpr int kProducts = 6;
   // D = F32, A = B = BF16 (1), K-major, N >> 3, M >> 4
   static constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
@@ -104,17 +93,39 @@ struct TcCfg<kSplitBf16x6> {
   }
 };
 
-template <int MODE>
+// Operand ring and drain interval of a variant (DPP_TUNE_UPDATE_VARIANT).
+// Every MMA k-step consumes 32 bytes of each operand row (8 TF32 or 16 BF16).
+//   3xTF32 V0: 32-deep stages of 128-byte rows (SWIZZLE_128B), 3 stages,
+//              a fresh accumulator every 32 deep (12 MMAs);
+//   3xTF32 V1: the same ring, a fresh accumulator every 64 deep;
+//   3xTF32 V2: 16-deep stages of 64-byte rows (SWIZZLE_64B), 6 stages (more
+//              bytes in flight per SM), a fresh accumulator every 32 deep;
+//   3xTF32 V3: the V2 ring, every 64 deep.
+//   BF16x6 V0/V2: 32-deep stages of 64-byte rows, 4 stages, every 16 deep;
+//   BF16x6 V1/V3: the same ring, every 32 deep.
+// A drain may span stages; the last one of a tile may be shorter.
+template <int MODE, int V>
+struct TcCfg : TcBase<MODE> {
+  static constexpr bool kDeep = MODE == kSplit3xTf32 && V >= 2;
+  static constexpr int kBK = kDeep ? 16 : 32;
+  static constexpr int kRowBytes = kBK * TcBase<MODE>::kEsz;  // 128 or 64
+  static constexpr int kStages = MODE == kSplit3xTf32 ? (kDeep ? 6 : 3) : 4;
+  static constexpr int kSteps = kRowBytes / 32;  // MMA k-steps per stage
+  static constexpr int kStepsPerDrain =
+      MODE == kSplit3xTf32 ? ((V & 1) ? 8 : 4) : ((V & 1) ? 2 : 1);
+};
+
+template <class Cfg>
 __host__ __device__ constexpr int tile_bytes() {
-  return kBM * TcCfg<MODE>::kRowBytes;  // 128 rows of one split
+  return kBM * Cfg::kRowBytes;  // 128 rows of one split
 }
-template <int MODE>
+template <class Cfg>
 __host__ __device__ constexpr int stage_bytes() {
-  return 2 * TcCfg<MODE>::kOps * tile_bytes<MODE>();
+  return 2 * Cfg::kOps * tile_bytes<Cfg>();
 }
-template <int MODE>
+template <class Cfg>
 __host__ __device__ constexpr int smem_bytes() {
-  return TcCfg<MODE>::kStages * stage_bytes<MODE>() + 1024 + 256;
+  return Cfg::kStages * stage_bytes<Cfg>() + 1024 + 256;
 }
 
 __device__ inline uint32_t smem_u32(const void* p) {
@@ -205,14 +216,14 @@ __device__ inline void mma_issue(uint32_t tmem_d, uint64_t a, uint64_t b, uint32
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "l"(a), "l"(b), "r"(TcCfg<MODE>::kIdesc), "r"(accumulate)
+        "l"(a), "l"(b), "r"(TcBase<MODE>::kIdesc), "r"(accumulate)
         : "memory");
   } else {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "l"(a), "l"(b), "r"(TcCfg<MODE>::kIdesc), "r"(accumulate)
+        "l"(a), "l"(b), "r"(TcBase<MODE>::kIdesc), "r"(accumulate)
         : "memory");
   }
 }
@@ -257,14 +268,16 @@ __device__ inline void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(kThreads, 1)
+// 320 threads x at most 200 registers fill the register file of one SM (the
+// shared-memory ring allows one CTA per SM anyway); the epilogue's two 64-value
+// arrays then stay in registers.
+template <int MODE, int V>
+__global__ void __maxnreg__(200)
     k_update_tc(const __grid_constant__ TcMaps maps, TcArgs a) {
-  using Cfg = TcCfg<MODE>;
+  using Cfg = TcCfg<MODE, V>;
   constexpr int kStages = Cfg::kStages;
-  constexpr int kStageBytes = stage_bytes<MODE>();
-  constexpr int kTileBytes = tile_bytes<MODE>();
-  constexpr int kDrainsPerKB = Cfg::kSteps / Cfg::kStepsPerDrain;
+  constexpr int kStageBytes = stage_bytes<Cfg>();
+  constexpr int kTileBytes = tile_bytes<Cfg>();
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -337,10 +350,16 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // ---- MMA issuer ----
-      int64_t g = 0;   // k-blocks consumed
-      int64_t dg = 0;  // drains issued
+      // A drain group (one fresh accumulator) holds kStepsPerDrain k-steps,
+      // which may lie in one stage or span several; the last group of a tile
+      // ends with the tile's last step.
+      int64_t g = 0;   // stages consumed
+      int64_t dg = 0;  // drain groups started
       bool ok = true;
       for (int64_t x = blockIdx.x; x < a.ntiles && ok; x += gridDim.x) {
+        int in_group = 0;  // k-steps issued into the current accumulator
+        uint32_t d = 0;
+        int buf = 0;
         for (int kb = 0; kb < KB && ok; ++kb, ++g) {
           const int s = (int)(g % kStages);
           const uint32_t ph = (uint32_t)((g / kStages) & 1);
@@ -352,33 +371,36 @@ __global__ void __launch_bounds__(kThreads, 1)
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           unsigned char* st = base + s * kStageBytes;
 #pragma unroll
-          for (int dr = 0; dr < kDrainsPerKB; ++dr, ++dg) {
-            const int buf = (int)(dg % kAccBufs);
-            const uint32_t aph = (uint32_t)((dg / kAccBufs) & 1);
-            if (!mbar_wait(smem_u32(&acc_empty[buf]), aph ^ 1u)) {
-              atomicExch(&s_fail, 1);
-              ok = false;
-              break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t d = tmem + (uint32_t)(buf * kBN);
-            bool first = true;
-#pragma unroll
-            for (int ks = 0; ks < Cfg::kStepsPerDrain; ++ks) {
-              const uint32_t off = (uint32_t)((dr * Cfg::kStepsPerDrain + ks) * 32);  // 32 B per step
-#pragma unroll
-              for (int pidx = 0; pidx < Cfg::kProducts; ++pidx) {
-                int ia, ib;
-                Cfg::product(pidx, &ia, &ib);
-                const uint32_t sa = smem_u32(st + ia * kTileBytes) + off;
-                const uint32_t sb = smem_u32(st + (Cfg::kOps + ib) * kTileBytes) + off;
-                mma_issue<MODE>(d, sw_desc<Cfg::kRowBytes>(sa), sw_desc<Cfg::kRowBytes>(sb),
-                                first ? 0u : 1u);
-                first = false;
+          for (int ks = 0; ks < Cfg::kSteps; ++ks) {
+            if (in_group == 0) {
+              buf = (int)(dg % kAccBufs);
+              const uint32_t aph = (uint32_t)((dg / kAccBufs) & 1);
+              if (!mbar_wait(smem_u32(&acc_empty[buf]), aph ^ 1u)) {
+                atomicExch(&s_fail, 1);
+                ok = false;
+                break;
               }
+              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+              d = tmem + (uint32_t)(buf * kBN);
             }
-            mma_commit(smem_u32(&acc_full[buf]));
+            const uint32_t off = (uint32_t)(ks * 32);  // 32 B per k-step
+#pragma unroll
+            for (int pidx = 0; pidx < Cfg::kProducts; ++pidx) {
+              int ia, ib;
+              Cfg::product(pidx, &ia, &ib);
+              const uint32_t sa = smem_u32(st + ia * kTileBytes) + off;
+              const uint32_t sb = smem_u32(st + (Cfg::kOps + ib) * kTileBytes) + off;
+              mma_issue<MODE>(d, sw_desc<Cfg::kRowBytes>(sa), sw_desc<Cfg::kRowBytes>(sb),
+                              (in_group == 0 && pidx == 0) ? 0u : 1u);
+            }
+            ++in_group;
+            if (in_group == Cfg::kStepsPerDrain || (kb == KB - 1 && ks == Cfg::kSteps - 1)) {
+              mma_commit(smem_u32(&acc_full[buf]));
+              ++dg;
+              in_group = 0;
+            }
           }
+          if (!ok) break;
           mma_commit(smem_u32(&empty[s]));
         }
       }
@@ -390,7 +412,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int rloc = 32 * quarter + lane;
     int64_t dg = 0;
     bool ok = true;
-    const int drains = KB * kDrainsPerKB;
+    const int drains = (KB * Cfg::kSteps + Cfg::kStepsPerDrain - 1) / Cfg::kStepsPerDrain;
     for (int64_t x = blockIdx.x; x < a.ntiles && ok; x += gridDim.x) {
       int64_t tr, tc;
       tile_of(a, x, &tr, &tc);
@@ -482,10 +504,10 @@ bool make_map(CUtensorMap* m, const void* ptr, int64_t rows, int ldk, int esz, i
   return r == CUDA_SUCCESS;
 }
 
-template <int MODE>
+template <int MODE, int V>
 cudaError_t launch(float* C, int64_t ldc, int64_t n, int64_t r0, int kdim, void* const* Wops,
                    void* const* Lops, int ldk, bool full, int* err_flag, cudaStream_t s) {
-  using Cfg = TcCfg<MODE>;
+  using Cfg = TcCfg<MODE, V>;
   const int esz = MODE == kSplit3xTf32 ? 4 : 2;
   if (kdim % Cfg::kBK != 0 || kdim <= 0 || kdim > ldk) return cudaErrorInvalidValue;
   if (((int64_t)ldk * esz) % 16 != 0) return cudaErrorInvalidValue;
@@ -499,15 +521,15 @@ cudaError_t launch(float* C, int64_t ldc, int64_t n, int64_t r0, int kdim, void*
       return cudaErrorInvalidValue;
   }
   // the shared-memory attribute is set once per device
-  static bool attr[64] = {};
+  static bool attr[64] = {};  // per instantiation
   int dev = 0;
   cudaError_t ed = cudaGetDevice(&dev);
   if (ed != cudaSuccess) return ed;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (!attr[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(k_update_tc<MODE>,
+    cudaError_t e = cudaFuncSetAttribute(k_update_tc<MODE, V>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         smem_bytes<MODE>());
+                                         smem_bytes<Cfg>());
     if (e != cudaSuccess) return e;
     attr[dev] = true;
   }
@@ -527,7 +549,7 @@ cudaError_t launch(float* C, int64_t ldc, int64_t n, int64_t r0, int kdim, void*
   int64_t grid = di.sm_count;
   if (g_tuning.max_ctas > 0 && grid > g_tuning.max_ctas) grid = g_tuning.max_ctas;
   if (grid > a.ntiles) grid = a.ntiles;
-  k_update_tc<MODE><<<(unsigned)grid, kThreads, smem_bytes<MODE>(), s>>>(maps, a);
+  k_update_tc<MODE, V><<<(unsigned)grid, kThreads, smem_bytes<Cfg>(), s>>>(maps, a);
   return cudaGetLastError();
 }
 
@@ -536,10 +558,20 @@ cudaError_t launch(float* C, int64_t ldc, int64_t n, int64_t r0, int kdim, void*
 cudaError_t outer_update_tc(int mode, float* C, int64_t ldc, int64_t n, int64_t r0, int kdim,
                             void* const* Wops, void* const* Lops, int ldk, bool full,
                             int* err_flag, cudaStream_t s) {
-  if (mode == kSplit3xTf32)
-    return launch<kSplit3xTf32>(C, ldc, n, r0, kdim, Wops, Lops, ldk, full, err_flag, s);
-  if (mode == kSplitBf16x6)
-    return launch<kSplitBf16x6>(C, ldc, n, r0, kdim, Wops, Lops, ldk, full, err_flag, s);
+  const int v = g_tuning.update_variant;
+#define DPP_TC_LAUNCH(M, V) launch<M, V>(C, ldc, n, r0, kdim, Wops, Lops, ldk, full, err_flag, s)
+  if (mode == kSplit3xTf32) {
+    switch (v) {
+      case 1: return DPP_TC_LAUNCH(kSplit3xTf32, 1);
+      case 2: return DPP_TC_LAUNCH(kSplit3xTf32, 2);
+      case 3: return DPP_TC_LAUNCH(kSplit3xTf32, 3);
+      default: return DPP_TC_LAUNCH(kSplit3xTf32, 0);
+    }
+  }
+  if (mode == kSplitBf16x6) {
+    return (v & 1) ? DPP_TC_LAUNCH(kSplitBf16x6, 1) : DPP_TC_LAUNCH(kSplitBf16x6, 0);
+  }
+#undef DPP_TC_LAUNCH
   return cudaErrorInvalidValue;
 }
 

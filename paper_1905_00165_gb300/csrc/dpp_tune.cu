@@ -4,8 +4,8 @@
 // speed on a given GPU, and the paper tunes its analogues (tile and block
 // sizes) by hand per machine (Section 4). Here they are measured:
 //   - outer block width (columns contracted per tensor-core update),
-//   - panel pipeline of the mixed real Hermitian path (single helper or
-//     chunked),
+//   - panel pipeline of the mixed real paths (single helper, chunked, or
+//     split: the decisions on a few CTAs, the rows below in a wide launch),
 //   - draws in flight, and with them the per-launch CTA cap (SMs / streams):
 //     one draw leaves most SMs idle during its sequential decisions, so
 //     several draws on several streams fill them.
@@ -114,8 +114,9 @@ bool find(int32_t op, int64_t n, int32_t dtype, int32_t precision, dpp_tune_entr
 
 void apply(const dpp_tune_entry& e, Tuning* t) {
   if (e.outer_block >= 32) t->outer_block = e.outer_block;
-  if (e.panel_pipeline >= 1) t->panel_pipeline = e.panel_pipeline;
+  t->panel_pipeline = e.panel_pipeline;
   t->max_ctas = e.max_ctas;
+  t->update_variant = e.update_variant;
 }
 
 // ---------------------------------------------------------------------------
@@ -180,6 +181,7 @@ bool read_entry(const char** pp, Entry* x) {
       else if (key == "streams") e.streams = (int32_t)v;
       else if (key == "samples_per_s") e.samples_per_s = v;
       else if (key == "candidates") e.candidates = (int32_t)v;
+      else if (key == "update_variant") e.update_variant = (int32_t)v;
     }
   }
 }
@@ -190,8 +192,9 @@ bool valid(const Entry& x) {
          e.precision >= 0 && e.precision <= 2 && e.n_bucket >= 0 && e.n_bucket < 40 &&
          (e.outer_block == 0 || (e.outer_block >= 32 && e.outer_block <= kMaxOuterBlock &&
                                  e.outer_block % 32 == 0)) &&
-         e.panel_pipeline >= 0 && e.panel_pipeline <= 2 && e.max_ctas >= 0 &&
-         e.max_ctas <= 4096 && e.streams >= 1 && e.streams <= 64;
+         e.panel_pipeline >= 0 && e.panel_pipeline <= 3 && e.max_ctas >= 0 &&
+         e.max_ctas <= 4096 && e.streams >= 1 && e.streams <= 64 && e.update_variant >= 0 &&
+         e.update_variant <= 3;
 }
 
 int load_file(const char* path, std::string* err) {
@@ -323,7 +326,7 @@ extern "C" {
 size_t dpp_autotune_workspace_size(int32_t op, int64_t n, int32_t dtype, int32_t precision,
                                    int32_t max_streams) {
   if ((op != DPP_OP_SAMPLE_HERMITIAN && op != DPP_OP_SAMPLE_LU) || n < 1 || max_streams < 1 ||
-      max_streams > 4)
+      max_streams > 8)
     return 0;
   const size_t per = per_stream_bytes(op, n, dtype, precision);
   return per ? (size_t)max_streams * per + 256 : 0;
@@ -336,8 +339,8 @@ dpp_status dpp_autotune(int32_t op, const void* K, int64_t n, int64_t ld, int32_
   if (op != DPP_OP_SAMPLE_HERMITIAN && op != DPP_OP_SAMPLE_LU)
     return set_last_error(DPP_ERR_INVALID_ARG, "dpp_autotune: op must be a sampler");
   if (n < 1 || ld < n || !K) return set_last_error(DPP_ERR_INVALID_ARG, "dpp_autotune: bad K / n / ld");
-  if (max_streams < 1 || max_streams > 4)
-    return set_last_error(DPP_ERR_INVALID_ARG, "dpp_autotune: max_streams must be in [1, 4]");
+  if (max_streams < 1 || max_streams > 8)
+    return set_last_error(DPP_ERR_INVALID_ARG, "dpp_autotune: max_streams must be in [1, 8]");
   if (draws < 1 || draws > 4096)
     return set_last_error(DPP_ERR_INVALID_ARG, "dpp_autotune: draws must be in [1, 4096]");
   const size_t need = dpp_workspace_size(op, n, dtype, precision, op == DPP_OP_SAMPLE_HERMITIAN);
@@ -353,15 +356,23 @@ dpp_status dpp_autotune(int32_t op, const void* K, int64_t n, int64_t ld, int32_
   // candidates
   const bool mixed = precision != DPP_PREC_FP64;
   std::vector<dpp_tune_entry> cand;
-  const int stream_opts[3] = {1, 2, 4};
+  const int stream_opts[4] = {1, 2, 4, 8};
   for (int so : stream_opts) {
     if (so > max_streams) continue;
     const int cap = so == 1 ? 0 : (id.sms / so < 8 ? 8 : id.sms / so);
     const int nouter = mixed ? 2 : 1;
     for (int oi = 0; oi < nouter; ++oi) {
       const int outer = mixed ? (oi == 0 ? 256 : 128) : 0;
-      const bool two_pipes = mixed && op == DPP_OP_SAMPLE_HERMITIAN && dtype == DPP_R64;
-      for (int pipe = two_pipes ? 1 : 0; pipe <= (two_pipes ? 2 : 0); ++pipe) {
+      // panel pipelines: single helper, chunked and split for real Hermitian
+      // draws; chunked (0) and split for real LU draws; none to choose else
+      int pipes[3] = {0, 0, 0}, npipe = 1;
+      if (mixed && dtype == DPP_R64 && op == DPP_OP_SAMPLE_HERMITIAN) {
+        pipes[0] = 1, pipes[1] = 2, pipes[2] = 3, npipe = 3;
+      } else if (mixed && dtype == DPP_R64) {
+        pipes[0] = 0, pipes[1] = 3, npipe = 2;
+      }
+      for (int pi = 0; pi < npipe; ++pi) {
+        const int pipe = pipes[pi];
         dpp_tune_entry c{};
         c.op = op;
         c.dtype = dtype;
@@ -407,6 +418,24 @@ dpp_status dpp_autotune(int32_t op, const void* K, int64_t n, int64_t ld, int32_
       win.samples_per_s = sps;
     }
   }
+  // second pass: the tensor-core update variants with the winner's settings
+  int ncand = (int)cand.size();
+  if (rs == DPP_OK && mixed) {
+    const int nv = precision == DPP_PREC_3XTF32 ? 3 : 1;
+    for (int v = 1; v <= nv && rs == DPP_OK; ++v) {
+      dpp_tune_entry c = win;
+      c.update_variant = v;
+      double sps = 0.0;
+      rs = run_candidate(op, K, n, ld, dtype, precision, c, draws, scr, need, st,
+                         static_cast<cudaStream_t>(stream), e0, e1, done, &sps);
+      ++ncand;
+      if (rs == DPP_OK && sps > win_sps) {
+        win_sps = sps;
+        win = c;
+        win.samples_per_s = sps;
+      }
+    }
+  }
   cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
   for (int s = 0; s < max_streams; ++s) {
     if (st[s]) cudaStreamDestroy(st[s]);
@@ -415,7 +444,7 @@ dpp_status dpp_autotune(int32_t op, const void* K, int64_t n, int64_t ld, int32_
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   if (rs != DPP_OK) return rs;
-  win.candidates = (int32_t)cand.size();
+  win.candidates = (int32_t)ncand;
   put(id.name, id.sms, win);
   if (best) *best = win;
   return DPP_OK;
@@ -452,10 +481,11 @@ dpp_status dpp_tune_save(const char* path) {
     fprintf(f,
             "%s\n  {\"gpu\": \"%s\", \"sms\": %d, \"op\": %d, \"dtype\": %d, \"precision\": %d, "
             "\"n_bucket\": %d, \"n\": %lld, \"outer_block\": %d, \"panel_pipeline\": %d, "
-            "\"max_ctas\": %d, \"streams\": %d, \"samples_per_s\": %.6g, \"candidates\": %d}",
+            "\"max_ctas\": %d, \"streams\": %d, \"samples_per_s\": %.6g, \"candidates\": %d, "
+            "\"update_variant\": %d}",
             i ? "," : "", gpu.c_str(), copy[i].sms, e.op, e.dtype, e.precision, e.n_bucket,
             (long long)e.n, e.outer_block, e.panel_pipeline, e.max_ctas, e.streams,
-            e.samples_per_s, e.candidates);
+            e.samples_per_s, e.candidates, e.update_variant);
   }
   fprintf(f, "\n]}\n");
   const bool ok = fclose(f) == 0;

@@ -27,7 +27,7 @@ def main(argv=None) -> int:
     p.add_argument("--precision", default="3xtf32", choices=["fp64", "3xtf32", "bf16x6"])
     p.add_argument("--form", default="hermitian", choices=["hermitian", "lu", "complex"])
     p.add_argument("--draws", type=int, default=12)
-    p.add_argument("--max-streams", type=int, default=4)
+    p.add_argument("--max-streams", type=int, default=8)
     p.add_argument("--out", default=DEFAULT_OUT)
     args = p.parse_args(argv)
     if ROOT not in sys.path:

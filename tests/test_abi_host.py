@@ -127,10 +127,11 @@ def test_tuning_keys_validated_on_host(L):
         (_lib.DPP_TUNE_OUTER_BLOCK, [256, 64], [48, 512, 0]),
         (_lib.DPP_TUNE_UPDATE_KERNEL, [0, 1], [2]),
         (_lib.DPP_TUNE_MAX_CTAS, [0, 8, 38], [4, 5000]),
-        (_lib.DPP_TUNE_PANEL_PIPELINE, [0, 1, 2], [3, -1]),
+        (_lib.DPP_TUNE_PANEL_PIPELINE, [0, 1, 2, 3], [4, -1]),
         (_lib.DPP_TUNE_WAIT_NS, [2e9, 1e6], [1e4, 1e11, -1.0]),
         (_lib.DPP_TUNE_FAULT_WITHHOLD, [1, 0], [2, -1]),
         (_lib.DPP_TUNE_USE_CACHE, [0, 1], [2, -1]),
+        (_lib.DPP_TUNE_UPDATE_VARIANT, [0, 1, 2, 3], [4, -1, 0.5]),
     ]
     for key, good, bad in cases:
         old = _lib.get_tuning(key)
@@ -183,10 +184,12 @@ def test_tune_cache_round_trip(L, tmp_path):
     entries = [
         {"gpu": "NVIDIA GB300", "sms": 152, "op": 0, "dtype": 0, "precision": 1,
          "n_bucket": 14, "n": 16384, "outer_block": 256, "panel_pipeline": 1,
-         "max_ctas": 38, "streams": 4, "samples_per_s": 47.5, "candidates": 12},
+         "max_ctas": 38, "streams": 4, "samples_per_s": 47.5, "candidates": 12,
+         "update_variant": 2},
         {"gpu": "NVIDIA GB300", "sms": 152, "op": 1, "dtype": 0, "precision": 2,
          "n_bucket": 13, "n": 8192, "outer_block": 128, "panel_pipeline": 0,
-         "max_ctas": 0, "streams": 1, "samples_per_s": 80.25, "candidates": 6},
+         "max_ctas": 0, "streams": 1, "samples_per_s": 80.25, "candidates": 6,
+         "update_variant": 0},
     ]
     src = tmp_path / "in.json"
     src.write_text(json.dumps({"version": 1, "entries": entries}))
@@ -223,7 +226,7 @@ def test_autotune_rejects_bad_arguments_on_host(L):
     need = L.dpp_autotune_workspace_size(0, 1000, 0, 1, 2)
     assert need > 2 * dpp.workspace_size(0, 1000, 0, 1, 1)
     assert L.dpp_autotune_workspace_size(2, 1000, 0, 1, 2) == 0  # not a sampler
-    assert L.dpp_autotune_workspace_size(0, 1000, 0, 1, 5) == 0  # too many streams
+    assert L.dpp_autotune_workspace_size(0, 1000, 0, 1, 9) == 0  # too many streams
     assert f(2, fake, 100, 100, 0, 1, 2, 4, fake, need, None, None) == _lib.DPP_ERR_INVALID_ARG
     assert f(0, fake, 100, 50, 0, 1, 2, 4, fake, need, None, None) == _lib.DPP_ERR_INVALID_ARG
     assert f(0, fake, 100, 100, 0, 1, 0, 4, fake, need, None, None) == _lib.DPP_ERR_INVALID_ARG

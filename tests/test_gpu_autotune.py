@@ -21,7 +21,7 @@ def dpp():
 
 
 @pytest.mark.parametrize("hermitian,precision,n,cands",
-                         [(True, "bf16x6", 1100, 8), (False, "3xtf32", 700, 4),
+                         [(True, "bf16x6", 1100, 13), (False, "3xtf32", 700, 11),
                           (True, "fp64", 300, 2)],
                          ids=["hermitian-mixed", "lu-mixed", "hermitian-fp64"])
 def test_autotune_then_draw_matches_oracle(dpp, hermitian, precision, n, cands):

@@ -29,12 +29,14 @@ def dpp():
 _PREC = {"p": "3xtf32"}
 
 
-@pytest.fixture(params=[(1, "3xtf32", 0), (0, "3xtf32", 0), (0, "bf16x6", 0), (0, "bf16x6", 1)],
-                ids=["simt", "tcgen05-3xtf32", "tcgen05-bf16x6", "tcgen05-bf16x6-single-helper"])
+@pytest.fixture(params=[(1, "3xtf32", 0), (0, "3xtf32", 0), (0, "bf16x6", 0), (0, "bf16x6", 1),
+                        (0, "3xtf32", 3)],
+                ids=["simt", "tcgen05-3xtf32", "tcgen05-bf16x6", "tcgen05-bf16x6-single-helper",
+                     "tcgen05-3xtf32-split"])
 def update_kernel(request, dpp):
     """Trailing-update kernel (SIMT FP32 or tensor cores), operand split and
     panel pipeline (0: automatic, the chunked one on a full grid; 1: single
-    helper)."""
+    helper; 3: split, the rows below the outer block in their own launch)."""
     from paper_1905_00165_gb300 import _lib
     kern, prec, pipe = request.param
     old = _lib.get_tuning(_lib.DPP_TUNE_UPDATE_KERNEL)
@@ -216,7 +218,7 @@ def test_borderline_band_has_margin(dpp):
     assert worst < c / 8.0
 
 
-@pytest.mark.parametrize("pipeline", [1, 2], ids=["single-helper", "chunked"])
+@pytest.mark.parametrize("pipeline", [1, 2, 3], ids=["single-helper", "chunked", "split"])
 def test_capped_ctas_and_concurrent_streams(dpp, pipeline):
     """The mixed path with each launch capped at 40 CTAs still matches the
     oracle, and four draws issued on four streams at once give the same
@@ -280,3 +282,36 @@ def test_chunked_pipeline_small_grid(dpp):
     finally:
         _lib.set_tuning(_lib.DPP_TUNE_MAX_CTAS, old)
         _lib.set_tuning(_lib.DPP_TUNE_PANEL_PIPELINE, oldp)
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("precision", ["3xtf32", "bf16x6"])
+def test_update_variants_match_oracle(dpp, precision, variant):
+    """Every tensor-core update variant (operand ring depth, accumulator drain
+    interval): the factor of forced decisions agrees with the oracle's to
+    FP32-level accuracy, on every outer-block width (odd numbers of 32-deep
+    blocks end a drain group early), and a draw is the oracle's."""
+    from paper_1905_00165_gb300 import _lib
+    n = 900
+    K = W.hermitian_kernel(n, seed=5, kind="beta")
+    keep = O.sample_ldl(K, O.uniforms(1, 0, n)).keep
+    u = O.forced_uniforms(keep)
+    ref = np.tril(O.sample_ldl(K, u).A)
+    old = _lib.get_tuning(_lib.DPP_TUNE_UPDATE_VARIANT)
+    oldb = _lib.get_tuning(_lib.DPP_TUNE_OUTER_BLOCK)
+    _lib.set_tuning(_lib.DPP_TUNE_UPDATE_VARIANT, variant)
+    try:
+        for nb in (256, 96):
+            _lib.set_tuning(_lib.DPP_TUNE_OUTER_BLOCK, nb)
+            s = _run(dpp, K, uniforms=u, factor=True, precision=precision)
+            err = float(np.max(np.abs(np.tril(s.factor.cpu().numpy()) - ref)))
+            assert err < 1e-4, (nb, err)
+        _lib.set_tuning(_lib.DPP_TUNE_OUTER_BLOCK, 256)
+        uu = O.uniforms(7, 0, n)
+        r = O.sample_ldl(K, uu)
+        s = _run(dpp, K, seed=7, precision=precision)
+        compare_draw(s.keep.cpu().numpy(), s.logp, s.pivots.cpu().numpy(), r, uu,
+                     logp_rtol=MIXED_LOGP_RTOL, piv_atol=1e-4)
+    finally:
+        _lib.set_tuning(_lib.DPP_TUNE_UPDATE_VARIANT, old)
+        _lib.set_tuning(_lib.DPP_TUNE_OUTER_BLOCK, oldb)

@@ -40,9 +40,20 @@ def _bad(lib):
     return lib.DPP_RES_TIMEOUT | lib.DPP_RES_NONFINITE | lib.DPP_RES_RECOMPUTE
 
 
+@pytest.fixture(params=[0, 3], ids=["chunked", "split"])
+def pipeline(request, dpp):
+    """Panel pipeline: chunked (workers stream the rows below during the
+    decisions) or split (the rows below in a separate wide launch)."""
+    from paper_1905_00165_gb300 import _lib
+    old = _lib.get_tuning(_lib.DPP_TUNE_PANEL_PIPELINE)
+    _lib.set_tuning(_lib.DPP_TUNE_PANEL_PIPELINE, request.param)
+    yield request.param
+    _lib.set_tuning(_lib.DPP_TUNE_PANEL_PIPELINE, old)
+
+
 @pytest.mark.parametrize("precision", ["bf16x6", "3xtf32"])
 @pytest.mark.parametrize("n", [1, 31, 33, 100, 257, 300, 600, 1100])
-def test_mixed_lu_parity(dpp, n, precision):
+def test_mixed_lu_parity(dpp, pipeline, n, precision):
     from paper_1905_00165_gb300 import _lib
     K, _ = W.lu_similarity_kernel(n, seed=n + 11)
     for seed in range(3):
@@ -77,7 +88,7 @@ def test_mixed_lu_similarity_twin(dpp):
 
 
 @pytest.mark.parametrize("precision", ["bf16x6", "3xtf32"])
-def test_mixed_lu_forced_borderline(dpp, precision):
+def test_mixed_lu_forced_borderline(dpp, pipeline, precision):
     """Uniforms 1e-8 from the oracle's pivots (on the side that keeps its
     decision), at the start, middle and end of inner panels and outer blocks:
     each pivot must be recomputed in FP64 and decided exactly."""

@@ -109,17 +109,21 @@ def test_mixed_one_draw_matches_oracle_n16384(dpp, herm_big, precision):
               f"{abs(r['logp'] - ref.logp) / abs(ref.logp):.3e}, recomputed {r['n_borderline']}")
 
 
-def test_bench_configuration_matches_oracle_n16384(dpp, herm_big):
-    """3xTF32, each launch capped at a quarter of the SMs, four draws in
-    flight on four streams: the draw with the oracle's seed is the oracle's."""
+@pytest.mark.parametrize("pipeline,nst", [(1, 4), (3, 8)], ids=["single-helper-4", "split-8"])
+def test_bench_configuration_matches_oracle_n16384(dpp, herm_big, pipeline, nst):
+    """3xTF32, several draws in flight on as many streams, each launch capped
+    at SMs / streams CTAs (the configurations the autotuner chooses among):
+    the draw with the oracle's seed is the oracle's."""
     import torch
     from paper_1905_00165_gb300 import _lib
     Kd, Kh, u, ref = herm_big
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     old = _lib.get_tuning(_lib.DPP_TUNE_MAX_CTAS)
-    _lib.set_tuning(_lib.DPP_TUNE_MAX_CTAS, max(8, sms // 4))
+    oldp = _lib.get_tuning(_lib.DPP_TUNE_PANEL_PIPELINE)
+    _lib.set_tuning(_lib.DPP_TUNE_MAX_CTAS, max(8, sms // nst))
+    _lib.set_tuning(_lib.DPP_TUNE_PANEL_PIPELINE, pipeline)
     try:
-        streams = [torch.cuda.Stream() for _ in range(4)]
+        streams = [torch.cuda.Stream() for _ in range(nst)]
         out = []
         for k, st in enumerate(streams):
             with torch.cuda.stream(st):
@@ -127,6 +131,7 @@ def test_bench_configuration_matches_oracle_n16384(dpp, herm_big):
         torch.cuda.synchronize()
     finally:
         _lib.set_tuning(_lib.DPP_TUNE_MAX_CTAS, old)
+        _lib.set_tuning(_lib.DPP_TUNE_PANEL_PIPELINE, oldp)
     s = out[0]
     r = s.result()
     assert _ok(r, _lib), r
