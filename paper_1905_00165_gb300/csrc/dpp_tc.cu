@@ -268,11 +268,11 @@ __device__ inline void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// 320 threads x at most 200 registers fill the register file of one SM (the
+// 320 threads x at most 184 registers fit the register file of one SM (the
 // shared-memory ring allows one CTA per SM anyway); the epilogue's two 64-value
 // arrays then stay in registers.
 template <int MODE, int V>
-__global__ void __maxnreg__(200)
+__global__ void __maxnreg__(184)
     k_update_tc(const __grid_constant__ TcMaps maps, TcArgs a) {
   using Cfg = TcCfg<MODE, V>;
   constexpr int kStages = Cfg::kStages;
