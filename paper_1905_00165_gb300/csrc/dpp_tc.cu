@@ -192,6 +192,20 @@ __device__ inline void mma_commit(uint32_t bar) {
                : "memory");
 }
 
+__device__ inline void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 __device__ inline void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   uint32_t r[32];
   asm volatile(
@@ -268,11 +282,10 @@ __device__ inline void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// 320 threads x at most 184 registers fit the register file of one SM (the
-// shared-memory ring allows one CTA per SM anyway); the epilogue's two 64-value
-// arrays then stay in registers.
+// Ten warps are allocated registers as twelve, so a thread may hold 168; the
+// epilogue's two 64-value arrays and a 16-column TMEM slice fit in that.
 template <int MODE, int V>
-__global__ void __maxnreg__(184)
+__global__ void __launch_bounds__(kThreads, 1)
     k_update_tc(const __grid_constant__ TcMaps maps, TcArgs a) {
   using Cfg = TcCfg<MODE, V>;
   constexpr int kStages = Cfg::kStages;
@@ -445,11 +458,11 @@ __global__ void __maxnreg__(184)
         const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) +
                                (uint32_t)(buf * kBN + half * kEpiCols);
 #pragma unroll
-        for (int ch = 0; ch < kEpiCols / 32; ++ch) {
-          float v[32];
-          tmem_ld32(taddr + (uint32_t)(ch * 32), v);
+        for (int ch = 0; ch < kEpiCols / 16; ++ch) {
+          float v[16];
+          tmem_ld16(taddr + (uint32_t)(ch * 16), v);
 #pragma unroll
-          for (int c = 0; c < 32; ++c) acc[ch * 32 + c] -= v[c];
+          for (int c = 0; c < 16; ++c) acc[ch * 16 + c] -= v[c];
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         mbar_arrive(smem_u32(&acc_empty[buf]));
