@@ -1281,30 +1281,192 @@ __global__ void __launch_bounds__(kLuThreads, 1) k_lu_outer(LuArgs a) {
 
 // Split pipeline (DPP_TUNE_PANEL_PIPELINE 3): the panel launch holds only CTA 0
 // and the helpers, which factor the outer block's own rows with the decisions;
-// afterwards this kernel, on a wide grid, brings every row below the outer
-// block through its panels: for each 32-row chunk, panel by panel, the
-// left-looking products over the earlier panels, the solve against the
-// published panel and the stores of L (M^T), W, M, the tensor-core splits and
-// the running diagonal, exactly the worker CTAs' steps of the pipelined launch.
-// Every panel is final when it starts, so there is no wait and no recompute to
-// serve; the decision chain no longer holds the SMs that stream these rows.
+// afterwards this kernel, on a wide grid, brings every index below the outer
+// block through its panels. A CTA takes 64 indices i and keeps, in shared
+// memory, their row segments X[i][c] = A[i, q + c] and (LU) their column
+// segments Z[i][c] = A[q + c, i], c < kb, and runs the outer block
+// right-looking, panel by panel (p = q + 32 k):
+//   solve   W[i, p + c] = X[i][p + c] - sum_{c' < c} W[i, p + c'] M(p + c, p + c')
+//           (LU) U[i, p + c] = Z[i][p + c] - sum_{c' < c} L(p + c, p + c') U[i, p + c'],
+//           M[i, p + c] = U[i, p + c] / d_{p + c}   (Hermitian: M = L = W / d)
+//   update  X[i][j] -= sum_c W[i, p + c] M(q + j, p + c),
+//           (LU) Z[i][j] -= sum_c M[i, p + c] W(q + j, p + c),   j beyond the panel,
+// with the outer block's own W and M rows (written by the helpers). The sums
+// are those of the left-looking worker steps, accumulated panel by panel. At
+// the end it stores L (and M^T), the W and M operand rows with their
+// tensor-core splits, and subtracts sum_c W M from each running diagonal.
+constexpr int kBR = 64;  // indices per CTA of k_below
+
+inline size_t below_smem(bool sym) {
+  const size_t x = sizeof(float) * kBR * (kNB + 1);
+  const size_t ps = sizeof(float) * kNB * 33;
+  return (sym ? x : 2 * x) + (sym ? ps : 2 * ps) + sizeof(float) * (2 * 32 * 33 + 32 + kNB);
+}
+
 template <bool SYM>
-__global__ void __launch_bounds__(kLuThreads, 1) k_below(LuArgs a) {
-  const int np = (a.kb + 31) / 32;
-  const int64_t qe = a.q + a.kb;
-  const int64_t c_first = qe + 32 * (int64_t)blockIdx.x, c_stride = 32 * (int64_t)gridDim.x;
-  const int total = c_first < a.n ? (int)((a.n - 1 - c_first) / c_stride + 1) : 0;
-  for (int m0 = 0; m0 < total; m0 += a.slots) {
-    const int cnt = (total - m0) < a.slots ? (total - m0) : a.slots;
-    const int64_t cf = c_first + (int64_t)m0 * c_stride;
-    for (int k = 0; k < np; ++k) {
-      const int64_t p = a.q + 32 * k;
-      const int b = (int)((qe - p) < 32 ? (qe - p) : 32);
-      chunks_left<SYM>(a, p, b, 32 * k, cf, c_stride, cnt);
-      load_panel<SYM>(a, p, b);
-      __syncthreads();
-      chunks_solve<SYM>(a, p, b, cf, c_stride, cnt);
+__global__ void __launch_bounds__(kLuThreads) k_below(LuArgs a) {
+  constexpr int ldx = kNB + 1;
+  float* X = reinterpret_cast<float*>(g_lu_dyn);   // [kBR][ldx]: A rows, then W
+  float* Zs = SYM ? X : X + kBR * ldx;             // [kBR][ldx]: A columns, then M (LU)
+  float* Ps = (SYM ? X : Zs) + kBR * ldx;          // [kNB][33]: M rows of the outer block
+  float* Qs = SYM ? Ps : Ps + kNB * 33;            // [kNB][33]: W rows of the outer block (LU)
+  float* T11 = Qs + kNB * 33;                      // [32][33]: M of the panel's diagonal block
+  float* U11 = T11 + 32 * 33;                      // [32][33]: L of it (LU)
+  float* rdp = U11 + 32 * 33;                      // [32]: 1 / d of the panel
+  float* rda = rdp + 32;                           // [kNB]: 1 / d of the outer block
+  const int tid = threadIdx.x;
+  const int kb = a.kb, np = (kb + 31) / 32;
+  const int64_t q = a.q, qe = q + kb, n = a.n, lda = a.lda;
+  const float* A = a.A;
+  float* Aw = a.A;
+  const int ty = tid >> 4, tx = tid & 15;  // update: rows 4 ty.., columns 4 tx.. of a 64-wide chunk
+  for (int64_t i0 = qe + (int64_t)kBR * blockIdx.x; i0 < n; i0 += (int64_t)kBR * gridDim.x) {
+    const int nr = (int)((n - i0) < kBR ? (n - i0) : kBR);
+    for (int idx = tid; idx < kBR * kb; idx += kLuThreads) {
+      const int r = idx % kBR, c = idx / kBR;
+      X[r * ldx + c] = r < nr ? __ldcg(&A[(i0 + r) + (q + c) * lda]) : 0.f;
     }
+    if (!SYM) {
+      for (int idx = tid; idx < kBR * kb; idx += kLuThreads) {
+        const int c = idx % kb, r = idx / kb;
+        Zs[r * ldx + c] = r < nr ? __ldcg(&A[(q + c) + (i0 + r) * lda]) : 0.f;
+      }
+    }
+    __syncthreads();
+    for (int k = 0; k < np; ++k) {
+      const int64_t p = q + 32 * k;
+      const int b = (int)((qe - p) < 32 ? (qe - p) : 32);
+      const int D = 32 * k;
+      for (int idx = tid; idx < 1024; idx += kLuThreads) {
+        const int rr = idx >> 5, cc = idx & 31;
+        const bool in = rr < b && cc < b && rr > cc;
+        const float l = in ? __ldcg(&A[(p + rr) + (p + cc) * lda]) : 0.f;  // L(p + rr, p + cc)
+        if (SYM) {
+          T11[rr * 33 + cc] = l;
+        } else {
+          U11[rr * 33 + cc] = l;
+          T11[rr * 33 + cc] = in ? __ldcg(&A[(p + cc) + (p + rr) * lda]) : 0.f;  // M(p + rr, p + cc)
+        }
+      }
+      if (tid < 32) {
+        const float r = tid < b ? 1.f / (float)__ldcg(&a.piv[p + tid]) : 0.f;
+        rdp[tid] = r;
+        rda[D + tid] = r;
+      }
+      __syncthreads();
+      if (tid < kBR) {
+        float* xr = X + tid * ldx + D;
+        float y[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) y[c] = c < b ? xr[c] : 0.f;
+#pragma unroll
+        for (int c = 1; c < 32; ++c) {
+#pragma unroll
+          for (int kk = 0; kk < c; ++kk) y[c] = fmaf(-y[kk], T11[c * 33 + kk], y[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < 32; ++c)
+          if (c < b) xr[c] = y[c];
+      } else if (!SYM && tid < 2 * kBR) {
+        float* zr = Zs + (tid - kBR) * ldx + D;
+        float u[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) u[c] = c < b ? zr[c] : 0.f;
+#pragma unroll
+        for (int c = 1; c < 32; ++c) {
+#pragma unroll
+          for (int kk = 0; kk < c; ++kk) u[c] = fmaf(-U11[c * 33 + kk], u[kk], u[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < 32; ++c)
+          if (c < b) zr[c] = u[c] * rdp[c];
+      }
+      __syncthreads();
+      const int C0 = D + 32;
+      if (C0 < kb) {
+        for (int idx = tid; idx < (kb - C0) * 32; idx += kLuThreads) {
+          const int j = C0 + (idx >> 5), t = idx & 31;
+          const int64_t off = (q + j) * (int64_t)kNB + D + t;
+          Ps[j * 33 + t] = t < b ? __ldcg(&a.Mk[off]) : 0.f;
+          if (!SYM) Qs[j * 33 + t] = t < b ? __ldcg(&a.Wk[off]) : 0.f;
+        }
+        __syncthreads();
+        for (int j0 = C0; j0 < kb; j0 += 64) {
+          float ax[4][4], az[4][4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) ax[i][jj] = az[i][jj] = 0.f;
+          const int jb = j0 + 4 * tx;
+#pragma unroll 4
+          for (int t = 0; t < 32; ++t) {
+            float w[4], m[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) w[i] = X[(4 * ty + i) * ldx + D + t];
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) m[jj] = (jb + jj < kb) ? Ps[(jb + jj) * 33 + t] : 0.f;
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+              for (int jj = 0; jj < 4; ++jj) ax[i][jj] = fmaf(w[i], m[jj], ax[i][jj]);
+            if (!SYM) {
+              float mr[4], wq[4];
+#pragma unroll
+              for (int i = 0; i < 4; ++i) mr[i] = Zs[(4 * ty + i) * ldx + D + t];
+#pragma unroll
+              for (int jj = 0; jj < 4; ++jj) wq[jj] = (jb + jj < kb) ? Qs[(jb + jj) * 33 + t] : 0.f;
+#pragma unroll
+              for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) az[i][jj] = fmaf(mr[i], wq[jj], az[i][jj]);
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+              if (jb + jj < kb) {
+                X[(4 * ty + i) * ldx + jb + jj] -= ax[i][jj];
+                if (!SYM) Zs[(4 * ty + i) * ldx + jb + jj] -= az[i][jj];
+              }
+            }
+          __syncthreads();
+        }
+      }
+    }
+    // stores: L below the outer block (column-major, rows fastest) ...
+    for (int idx = tid; idx < kBR * kb; idx += kLuThreads) {
+      const int r = idx % kBR, c = idx / kBR;
+      if (r < nr) Aw[(i0 + r) + (q + c) * lda] = X[r * ldx + c] * rda[c];
+    }
+    // ... M^T to the right of it (LU), and the row-major operand rows
+    for (int idx = tid; idx < kBR * kb; idx += kLuThreads) {
+      const int c = idx % kb, r = idx / kb;
+      if (r < nr) {
+        const float w = X[r * ldx + c];
+        const float m = SYM ? w * rda[c] : Zs[r * ldx + c];
+        if (!SYM) Aw[(q + c) + (i0 + r) * lda] = m;
+        const int64_t off = (i0 + r) * (int64_t)kNB + c;
+        a.Wk[off] = w;
+        a.Mk[off] = m;
+        write_split(a.split, a.Wop, off, w);
+        write_split(a.split, a.Mop, off, m);
+      }
+    }
+    // running diagonal and band scale of each index
+    if (tid < nr) {
+      f2 dsum = {0.f, 0.f};
+      float ssum = 0.f;
+      for (int c = 0; c < kb; ++c) {
+        const float w = X[tid * ldx + c];
+        const float m = SYM ? w * rda[c] : Zs[tid * ldx + c];
+        dsum = f2_add_prod(dsum, w, m);
+        ssum += fabsf(w * m);
+      }
+      a.kd[i0 + tid] -= f2_to_double(dsum);
+      a.s[i0 + tid] += (double)ssum;
+    }
+    __syncthreads();
   }
 }
 
@@ -1426,7 +1588,7 @@ cudaError_t sample_chunked(const DrawArgs& a, Workspace ws) {
                                           (int)lu_dyn_smem(kMaxSlots));
     if (ea != cudaSuccess) return ea;
     ea = cudaFuncSetAttribute(k_below<SYM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)lu_dyn_smem(kMaxSlots));
+                              (int)below_smem(SYM));
     if (ea != cudaSuccess) return ea;
     DevInfo di;
     if ((ea = dev_info(&di)) != cudaSuccess) return ea;
@@ -1457,7 +1619,6 @@ cudaError_t sample_chunked(const DrawArgs& a, Workspace ws) {
   const int64_t trail = ((n > NB ? n - NB : 0) + 31) / 32;
   int slots = (int)((trail + nwk - 1) / nwk);
   const int hslots = (kMaxOuterBlock / 32 - 1 + nh - 1) / nh;
-  int below_slots = slots < 1 ? 1 : (slots > kMaxSlots ? kMaxSlots : slots);
   if (slots < hslots) slots = hslots;
   if (slots > kMaxSlots) slots = kMaxSlots;
   if (split_rows) slots = hslots;
@@ -1514,11 +1675,12 @@ cudaError_t sample_chunked(const DrawArgs& a, Workspace ws) {
     if (split_rows && r0 < n) {
       // the rows below the outer block, through its panels ((n - r0) kb^2
       // flops for the Hermitian form, twice that for LU)
-      LuArgs lb = la;
-      lb.slots = below_slots;
       const double fl = (SYM ? 1.0 : 2.0) * (double)(n - r0) * (double)kb * (double)kb;
+      int64_t bg = (n - r0 + kBR - 1) / kBR;
+      const int64_t bcap = (int64_t)below_grid * (SYM ? 2 : 1);  // CTAs resident per SM
+      if (bg > bcap) bg = bcap;
       ProfScope ps(kProfBelow, a.stream, fl, 0.0);
-      k_below<SYM><<<(unsigned)below_grid, kLuThreads, lu_dyn_smem(below_slots), a.stream>>>(lb);
+      k_below<SYM><<<(unsigned)bg, kLuThreads, below_smem(SYM), a.stream>>>(la);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (r0 < n) {
