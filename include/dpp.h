@@ -333,7 +333,7 @@ dpp_status dpp_lensemble_to_marginal_batched(int32_t batch, const int64_t* n,
 /* Process-wide tuning knobs (read at each call; not for concurrent changes).
  *   DPP_TUNE_TAU_SAFETY   c in the mixed-precision borderline bound
  *                         tau_j = c * 2^-22 * sqrt(j + 1) * (K_jj + s_j),
- *                         s_j = sum_{k<j} |L_jk|^2 |d_k|            (default 1)
+ *                         s_j = sum_{k<j} |L_jk|^2 |d_k|            (default 8)
  *   DPP_TUNE_OUTER_BLOCK  outer block width of the mixed path: the trailing
  *                         update contracts this many columns at once (32..256,
  *                         multiple of 32; default 256)

@@ -64,7 +64,7 @@ cudaError_t sample_fp64(const DrawArgs& a, bool hermitian, Workspace ws);
 
 // Process-wide tuning knobs (dpp_set_tuning).
 struct Tuning {
-  double tau_safety = 1.0;  // c in the borderline bound
+  double tau_safety = 8.0;  // c in the borderline bound
   int outer_block = 256;    // mixed path: columns contracted per trailing update
   int update_kernel = 0;    // 0 = tcgen05, 1 = SIMT FP32
   int update_variant = 0;   // tcgen05 update: operand ring and drain interval (0..3)
