@@ -99,6 +99,7 @@ struct LuArgs {
   int nh;       // helper CTAs 1..nh (chunks of the outer block)
   int slots;    // precomputed-chunk slots in shared memory
   int withhold; // fault injection: CTA 0 never publishes a panel
+  int no_rows;  // split pipeline: the CTAs beyond the helpers only serve recomputes
   LuRc lr;
 };
 
@@ -1251,6 +1252,13 @@ __global__ void __launch_bounds__(kLuThreads, 1) k_lu_outer(LuArgs a) {
     return;
   }
 
+  if (a.no_rows) {
+    // split pipeline: the rows below are k_below's; serve each panel's
+    // recompute requests until the panel is published
+    for (int k = 0; k < np; ++k)
+      if (!lu_follower<SYM>(a.lr, a.epoch0 + (unsigned)k, &s_ok, 1024)) return;
+    return;
+  }
   // ---- workers: chunks beyond the outer block ----
   const int64_t nwk = (int64_t)gridDim.x - nh - 1, w = (int64_t)blockIdx.x - nh - 1;
   const int64_t c_first = qe + 32 * w, c_stride = 32 * nwk;
@@ -1605,14 +1613,16 @@ cudaError_t sample_chunked(const DrawArgs& a, Workspace ws) {
   if (grid < 3) grid = 3;
   // split pipeline: the panel launch is CTA 0 and one helper per chunk of the
   // outer block; the rows below go to k_below on `grid` CTAs
+  // (the panel launch keeps the stream's CTA share: the CTAs beyond CTA 0 and
+  // the helpers serve the FP64 recomputes)
   const bool split_rows = g_tuning.panel_pipeline == 3;
   const int below_grid = grid;
-  if (split_rows) grid = kMaxOuterBlock / 32;
+  if (split_rows && grid < kMaxOuterBlock / 32) grid = kMaxOuterBlock / 32;
   // CTA 0 decides, CTAs 1..nh own the outer block's chunks, the rest the
   // chunks beyond it; slots hold the chunks a CTA precomputes per panel
   // (one CTA per chunk on a full grid; on a small grid a helper owns
   // several chunks, so that most CTAs stay workers)
-  int nh = split_rows ? grid - 1 : (grid - 2) / 8;
+  int nh = split_rows ? kMaxOuterBlock / 32 - 1 : (grid - 2) / 8;
   if (nh > kMaxOuterBlock / 32 - 1) nh = kMaxOuterBlock / 32 - 1;
   if (nh < 1) nh = 1;
   const int64_t nwk = split_rows ? below_grid : grid - 1 - nh;
@@ -1657,6 +1667,7 @@ cudaError_t sample_chunked(const DrawArgs& a, Workspace ws) {
     la.nh = nh;
     la.slots = slots;
     la.withhold = g_tuning.fault_withhold;
+    la.no_rows = split_rows ? 1 : 0;
     la.lr.rc = recompute_args(L.rs, K, a.ld, L.A32, L.ld32, L.piv, a.keep, n, q, a.result);
     la.lr.rc.grid = grid;
     la.lr.yw = L.yw;
