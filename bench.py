@@ -61,13 +61,15 @@ def parse():
                         "the 64x64 grid; LU n=8192; batched L-ensembles)")
     p.add_argument("--batch", type=int, default=4096,
                    help="L-ensembles in the batched measurement (n ~ U{64..1024})")
+    p.add_argument("--update-variant", type=int, default=-1,
+                   help="with --case: DPP_TUNE_UPDATE_VARIANT for the draws (-1: default)")
     p.add_argument("--case", default="", choices=["", "herm", "lu", "cplx", "batched", "adjoint"],
                    help="run one path alone (a small loop for profiling): mixed Hermitian, "
                         "mixed LU, mixed complex Hermitian, batched sampler or batched adjoint")
     return p.parse_args()
 
 
-def tc_traffic_per_launch(n: int, kb: int = 256):
+def tc_traffic_per_launch(n: int, split: str = "3xtf32", kb: int = 256):
     """Mean DRAM bytes of one 3xTF32 k_update_tc launch of an order-n draw:
     bytes per m^2 from the one-launch ncu capture summarised in profiles/
     (n = 8192), times the mean m^2 over the draw's launches (m = n - kb,
@@ -77,7 +79,8 @@ def tc_traffic_per_launch(n: int, kb: int = 256):
         src = os.path.join(ROOT, "paper_1905_00165_gb300", "csrc", "dpp_tc.cu")
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         vals = {}
-        with open(os.path.join(ROOT, "profiles", "k_update_tc_3xtf32_traffic_n8192.txt")) as f:
+        name = f"k_update_tc_{split}_traffic_n8192.txt"
+        with open(os.path.join(ROOT, "profiles", name)) as f:
             for ln in f:
                 if ": " in ln:  # keys may hold a colon themselves ("sha256[:16]")
                     k, v = ln.split(": ", 1)
@@ -432,6 +435,8 @@ def run_case(args):
     n = args.n
     prec = "3xtf32" if args.precision == "auto" else args.precision
     steps = args.steps if args.steps is not None else 4
+    if args.update_variant >= 0:
+        _lib.set_tuning(_lib.DPP_TUNE_UPDATE_VARIANT, args.update_variant)
     if args.case in ("batched", "adjoint"):
         Ks = W.lensemble_batch_torch(args.batch, seed=0, device=str(dev))
         b = dpp.BatchedSampler(Ks)
@@ -633,9 +638,18 @@ def main():
     L = dpp.load()
     n = args.n
     prec_name = args.precision
+    cache = os.path.join(ROOT, "paper_1905_00165_gb300", "tune_gb300.json")
+    if os.path.exists(cache):
+        _lib.tune_load(cache)
     if prec_name == "auto":
-        # 3xTF32: measured faster than BF16x6 over the whole draw on GB300
-        prec_name = "3xtf32" if dpp.workspace_size(0, n, 0, 1, 1) > 0 else "fp64"
+        # the operand split (3xTF32 or BF16x6, both FP32-accurate) whose tuned
+        # configuration drew faster on this GPU; 3xTF32 without a tuning entry
+        best = None
+        for cand in ("3xtf32", "bf16x6"):
+            e = _lib.tune_lookup(0, n, 0, dpp.PRECISIONS[cand])
+            if e is not None and (best is None or e["samples_per_s"] > best[1]):
+                best = (cand, e["samples_per_s"])
+        prec_name = best[0] if best else "3xtf32"
     prec = dpp.PRECISIONS[prec_name]
     _lib.set_tuning(_lib.DPP_TUNE_UPDATE_KERNEL, 0 if args.update == "tc" else 1)
     steps = args.steps if args.steps is not None else (40 if prec_name != "fp64" else 4)
@@ -663,9 +677,6 @@ def main():
         # the autotuner's entry for this GPU and key (the committed table, or a
         # tuning run on this kernel now); the library applies its outer block,
         # panel pipeline and CTA cap to every draw below
-        cache = os.path.join(ROOT, "paper_1905_00165_gb300", "tune_gb300.json")
-        if os.path.exists(cache):
-            _lib.tune_load(cache)
         tuning = _lib.tune_lookup(0, n, 0, prec)
         source = "tuning table"
         if tuning is None:
@@ -760,7 +771,7 @@ def main():
             ach = per_launch_flops / (avg_ms / 1e3) / 1e12
             roof = {"kernel": dom, "bound": "tensor", "achieved": ach, "peak": tf32 / 3.0,
                     "unit": "TFLOP/s", "frac": ach / (tf32 / 3.0),
-                    "traffic": tc_traffic_per_launch(n),
+                    "traffic": tc_traffic_per_launch(n, "3xtf32", int(tuning["outer_block"]) if tuning else 256),
                     "traffic_source": "ncu one launch at n = 8192, scaled by m^2 (profiles/)",
                     "executed_tensor_frac": 3.0 * ach / tf32,
                     "peak_source": "measured bf16 x nominal tf32/bf16 (2.25:1.1), / 3 products",
@@ -771,7 +782,8 @@ def main():
             ach = per_launch_flops / (avg_ms / 1e3) / 1e12
             roof = {"kernel": dom, "bound": "tensor", "achieved": ach, "peak": bf16 / 6.0,
                     "unit": "TFLOP/s", "frac": ach / (bf16 / 6.0),
-                    "traffic": None,
+                    "traffic": tc_traffic_per_launch(n, "bf16x6", int(tuning["outer_block"]) if tuning else 256),
+                    "traffic_source": "ncu one launch at n = 8192, scaled by m^2 (profiles/)",
                     "executed_tensor_frac": 6.0 * ach / bf16,
                     "peak_source": "MEASURED_PEAKS bf16_tflops (burst), / 6 products"}
         else:
