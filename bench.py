@@ -61,6 +61,8 @@ def parse():
                         "the 64x64 grid; LU n=8192; batched L-ensembles)")
     p.add_argument("--batch", type=int, default=4096,
                    help="L-ensembles in the batched measurement (n ~ U{64..1024})")
+    p.add_argument("--pipeline", type=int, default=-1,
+                   help="with --case: DPP_TUNE_PANEL_PIPELINE for the draws (-1: default)")
     p.add_argument("--update-variant", type=int, default=-1,
                    help="with --case: DPP_TUNE_UPDATE_VARIANT for the draws (-1: default)")
     p.add_argument("--case", default="", choices=["", "herm", "lu", "cplx", "batched", "adjoint"],
@@ -437,6 +439,8 @@ def run_case(args):
     steps = args.steps if args.steps is not None else 4
     if args.update_variant >= 0:
         _lib.set_tuning(_lib.DPP_TUNE_UPDATE_VARIANT, args.update_variant)
+    if args.pipeline >= 0:
+        _lib.set_tuning(_lib.DPP_TUNE_PANEL_PIPELINE, args.pipeline)
     if args.case in ("batched", "adjoint"):
         Ks = W.lensemble_batch_torch(args.batch, seed=0, device=str(dev))
         b = dpp.BatchedSampler(Ks)
