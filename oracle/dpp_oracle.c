@@ -38,6 +38,7 @@
 #include <complex.h>
 #include <math.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 
 /* ------------------------------------------------------------------------- */
@@ -242,6 +243,98 @@ int64_t oracle_dpp_ldl_greedy_r64(int64_t n, double* A, int64_t ld,
   }
   *logp = lp;
   return kept;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Algorithm 2 (Theorem 2): elementary (projection) DPP sampling by k steps of */
+/* left-looking, diagonally-pivoted Cholesky. K (real symmetric, an orthogonal */
+/* projection of rank k) is copied into A (n x n, column-major, ld n) and     */
+/* factored in place with symmetric row/column swaps; d holds the remaining   */
+/* diagonal by position, perm the original index at each position.            */
+/* Step j: S = sum over positions p >= j of max(d_p, 0) (= k - j in exact    */
+/* arithmetic); the position t is the first p >= j whose running sum of       */
+/* max(d, 0) exceeds u_j S (the last position with d > 0 if rounding leaves   */
+/* none); positions j and t are swapped in A (rows and columns), d and perm;  */
+/* A_jj = sqrt(d_j); then A[j+1:n, j] -= A[j+1:n, 0:j] A[j, 0:j]^T, the       */
+/* column is divided by A_jj and each d_i loses A_ij^2.                       */
+/* Outputs: sample[0:k] = perm[0:k] (selection order), chol (k x k, ld k) the */
+/* lower-triangular Cholesky factor of K_Y in that order, logp = 2 sum_j      */
+/* log A_jj (Theorem 2: P(Y) = product of the squared pivots). Returns 0, or  */
+/* -1 if a pivot was not positive.                                           */
+/* ------------------------------------------------------------------------- */
+int oracle_dpp_elementary_r64(int64_t n, const double* K, int64_t ldk, int64_t k,
+                              const double* u, int64_t* sample, double* chol,
+                              double* logp) {
+  double* A = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * (size_t)(n > 0 ? n : 1));
+  double* d = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  int64_t* perm = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  int bad = 0;
+  double lp = 0.0;
+  for (int64_t c = 0; c < n; ++c)
+    for (int64_t i = 0; i < n; ++i) A[i + c * n] = K[i + c * ldk];
+  for (int64_t i = 0; i < n; ++i) {
+    d[i] = A[i + i * n];
+    perm[i] = i;
+  }
+  for (int64_t j = 0; j < k; ++j) {
+    /* draw the position */
+    double S = 0.0;
+    for (int64_t p = j; p < n; ++p) S += d[p] > 0.0 ? d[p] : 0.0;
+    const double target = u[j] * S;
+    int64_t t = -1, last = -1;
+    double acc = 0.0;
+    for (int64_t p = j; p < n; ++p) {
+      if (d[p] > 0.0) last = p;
+      acc += d[p] > 0.0 ? d[p] : 0.0;
+      if (acc > target) {
+        t = p;
+        break;
+      }
+    }
+    if (t < 0) t = last >= 0 ? last : j;
+    /* symmetric swap of positions j and t */
+    if (t != j) {
+      for (int64_t c = 0; c < n; ++c) {
+        const double x = A[j + c * n];
+        A[j + c * n] = A[t + c * n];
+        A[t + c * n] = x;
+      }
+      for (int64_t i = 0; i < n; ++i) {
+        const double x = A[i + j * n];
+        A[i + j * n] = A[i + t * n];
+        A[i + t * n] = x;
+      }
+      const double dx = d[j];
+      d[j] = d[t];
+      d[t] = dx;
+      const int64_t px = perm[j];
+      perm[j] = perm[t];
+      perm[t] = px;
+    }
+    if (!(d[j] > 0.0)) bad = 1;
+    const double ajj = sqrt(d[j] > 0.0 ? d[j] : 0.0);
+    A[j + j * n] = ajj;
+    lp += 2.0 * log(ajj);
+    if (j == k - 1) break;
+    /* new column (left-looking) and diagonal downdate */
+#pragma omp parallel for schedule(static)
+    for (int64_t i = j + 1; i < n; ++i) {
+      double v = A[i + j * n];
+      for (int64_t s = 0; s < j; ++s) v -= A[i + s * n] * A[j + s * n];
+      v /= ajj;
+      A[i + j * n] = v;
+      d[i] -= v * v;
+    }
+  }
+  for (int64_t j = 0; j < k; ++j) {
+    sample[j] = perm[j];
+    for (int64_t i = 0; i < k; ++i) chol[i + j * k] = i >= j ? A[i + j * n] : 0.0;
+  }
+  *logp = lp;
+  free(A);
+  free(d);
+  free(perm);
+  return bad ? -1 : 0;
 }
 
 int oracle_num_threads(void) {

@@ -8,7 +8,8 @@ Two kinds of function live here:
 
 * ctypes wrappers over ``dpp_oracle.c`` — Algorithm 1 (LU form, real and
   complex), its Hermitian LDL^H specialisation, the greedy maximum-likelihood
-  variant, and the Philox4x32-10 uniforms (the counter-based generator both
+  variant, Algorithm 2 (the elementary sampler of projection kernels), and the
+  Philox4x32-10 uniforms (the counter-based generator both
   sides implement independently from its published definition);
 * closed forms written from their plain definitions with numpy library
   primitives (det, solve, inv):
@@ -69,6 +70,8 @@ def _load():
         f.restype = i64
     lib.oracle_dpp_ldl_greedy_r64.argtypes = [i64, dp, i64, u8p, dp, dp]
     lib.oracle_dpp_ldl_greedy_r64.restype = i64
+    lib.oracle_dpp_elementary_r64.argtypes = [i64, dp, i64, i64, dp, dp, dp, dp]
+    lib.oracle_dpp_elementary_r64.restype = ctypes.c_int
     lib.oracle_num_threads.argtypes = []
     lib.oracle_num_threads.restype = ctypes.c_int
     _lib = lib
@@ -164,6 +167,40 @@ def greedy_ldl(K: np.ndarray) -> Draw:
     lp = np.zeros(1)
     _load().oracle_dpp_ldl_greedy_r64(n, _ptr(A), n, _ptr(keep), _ptr(piv), _ptr(lp))
     return Draw(keep, piv, float(lp[0]), A)
+
+
+class ElementaryDraw:
+    """One draw of Algorithm 2: the k sampled indices in selection order, the
+    Cholesky factor of K_Y in that order, log P(Y) and whether every pivot was
+    positive."""
+
+    def __init__(self, n, sample, chol, logp, ok):
+        self.n = n
+        self.sample = sample
+        self.chol = chol
+        self.logp = logp
+        self.ok = ok
+
+    @property
+    def keep(self) -> np.ndarray:
+        m = np.zeros(self.n, dtype=np.uint8)
+        m[self.sample] = 1
+        return m
+
+
+def sample_elementary(K: np.ndarray, k: int, u: np.ndarray) -> ElementaryDraw:
+    """Algorithm 2 (Theorem 2) on a real symmetric projection K of rank k with
+    one uniform per step (u[0:k])."""
+    A = _prep(K, np.float64)
+    n = A.shape[0]
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    assert u.shape[0] >= k and 0 <= k <= n
+    sample = np.zeros(max(k, 1), dtype=np.int64)
+    chol = np.zeros((max(k, 1), max(k, 1)), dtype=np.float64, order="F")
+    lp = np.zeros(1)
+    rc = _load().oracle_dpp_elementary_r64(n, _ptr(A), n, k, _ptr(u), _ptr(sample), _ptr(chol),
+                                           _ptr(lp))
+    return ElementaryDraw(n, sample[:k].copy(), np.array(chol[:k, :k]), float(lp[0]), rc == 0)
 
 
 def forced_uniforms(keep: np.ndarray) -> np.ndarray:

@@ -299,3 +299,74 @@ def test_logprob_grad_matches_finite_differences(complex_):
             fdi = (O.subset_logprob(K + 1j * h * E, keep)
                    - O.subset_logprob(K - 1j * h * E, keep)) / (2 * h)
             assert abs(fdi - np.imag(G[i, j])) < 1e-6 * max(1.0, abs(fdi))
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 2 (Theorem 2): the elementary sampler of projection kernels
+# ---------------------------------------------------------------------------
+def _projection(n, k, seed):
+    return W.hermitian_kernel(n, seed=seed, kind="projection", rank=k)
+
+
+def test_elementary_sample_size_likelihood_and_factor():
+    """Every draw has exactly k distinct indices (Theorem 2); log P(Y) is
+    log det(K_Y) (library slogdet), and the returned factor is the Cholesky
+    factor of K_Y in selection order."""
+    for n, k, seed in [(40, 1, 1), (40, 10, 2), (120, 30, 3), (64, 64, 4)]:
+        K = _projection(n, k, seed)
+        for s in range(4):
+            d = O.sample_elementary(K, k, O.uniforms(s, 7, k))
+            assert d.ok
+            assert len(set(d.sample.tolist())) == k and d.sample.min() >= 0 and d.sample.max() < n
+            KY = K[np.ix_(d.sample, d.sample)]
+            sign, ld = np.linalg.slogdet(KY)
+            assert sign > 0 and abs(d.logp - ld) <= 1e-9 * max(1.0, abs(ld))
+            assert np.allclose(np.tril(d.chol), d.chol)
+            assert np.abs(d.chol @ d.chol.T - KY).max() < 1e-10
+
+
+def test_elementary_distribution_chi2():
+    """n = 8, rank 3: the empirical frequencies of 30 000 draws against
+    P(Y) = det(K_Y) for all 56 subsets of size 3 (the DPP of a projection
+    kernel has only samples of size k, Theorem 2)."""
+    import itertools
+    from scipy import stats
+    n, k = 8, 3
+    K = _projection(n, k, 11)
+    subsets = list(itertools.combinations(range(n), k))
+    p = np.array([np.linalg.det(K[np.ix_(c, c)]) for c in subsets])
+    assert abs(p.sum() - 1.0) < 1e-12
+    index = {c: i for i, c in enumerate(subsets)}
+    counts = np.zeros(len(subsets))
+    draws = 30000
+    for s in range(draws):
+        d = O.sample_elementary(K, k, O.uniforms(s, 0, k))
+        counts[index[tuple(sorted(d.sample.tolist()))]] += 1
+    keep = p * draws >= 5
+    chi2 = ((counts[keep] - draws * p[keep]) ** 2 / (draws * p[keep])).sum()
+    pval = stats.chi2.sf(chi2, keep.sum() - 1)
+    assert pval > 1e-3, (chi2, pval)
+
+
+def test_elementary_inclusion_marginals():
+    """Inclusion frequencies approach diag(K) (P[i in Y] = K_ii)."""
+    n, k = 30, 9
+    K = _projection(n, k, 5)
+    draws = 8000
+    freq = np.zeros(n)
+    for s in range(draws):
+        freq[O.sample_elementary(K, k, O.uniforms(s, 3, k)).sample] += 1
+    freq /= draws
+    se = np.sqrt(np.diag(K) * (1 - np.diag(K)) / draws) + 1e-3
+    assert np.all(np.abs(freq - np.diag(K)) < 5 * se)
+
+
+def test_elementary_edge_cases():
+    """k = 0 draws nothing; the identity (rank n) keeps every index with
+    probability one."""
+    K = _projection(10, 3, 6)
+    d = O.sample_elementary(K, 0, np.zeros(1))
+    assert d.sample.size == 0 and d.logp == 0.0
+    n = 12
+    d = O.sample_elementary(np.eye(n), n, O.uniforms(1, 0, n))
+    assert sorted(d.sample.tolist()) == list(range(n)) and abs(d.logp) < 1e-12
