@@ -226,6 +226,36 @@ dpp_status dpp_greedy_lu(const void* K, int64_t n, int64_t ld, int32_t dtype, in
                          uint8_t* keep, void* factor_out, double* pivots, dpp_result* result,
                          void* workspace, size_t workspace_bytes, void* stream);
 
+/* Elementary DPP sampler (Algorithm 2, Theorem 2): for a real symmetric
+ * marginal kernel K that is an orthogonal projection of rank k, k steps of
+ * left-looking, diagonally pivoted Cholesky factorization in which the pivot
+ * of step j is drawn from the remaining diagonal d with probability
+ * d_t / (k - j) give a sample of DPP(K); its size is k, and
+ * P(Y) = prod_j A_jj^2 over the k pivots. FP64, O(n k^2), in ONE cooperative
+ * launch (bounded grid barriers; DPP_RES_TIMEOUT if one runs out).
+ * Step j uses one uniform u_j (Philox as above, counter j, or uniforms[j]):
+ * with the positions in the order of the algorithm's symmetric swaps, the
+ * position t is the first p >= j whose running sum of max(d_p, 0) exceeds
+ * u_j S, S the sum over all p >= j (k - j in exact arithmetic); the last
+ * position with d > 0 if rounding leaves none.
+ *   K          device, n x ld column-major FP64 (read; K is symmetric).
+ *   k          the rank (0 <= k <= n); exactly k steps are run.
+ *   sample     device, k int64: the sampled indices in selection order.
+ *   keep       device, n bytes, or NULL: keep[i] = 1 iff i is sampled.
+ *   chol       device, k x k column-major (ld k), or NULL: the lower
+ *              Cholesky factor of K_Y in selection order (pivots A_jj on the
+ *              diagonal), as the listing of Algorithm 2 returns it.
+ *   result     device; logp = 2 sum_j log A_jj, n_kept = k; a pivot that is
+ *              not positive sets DPP_RES_INADMISSIBLE (K is not a projection
+ *              of rank k) or DPP_RES_NONFINITE.
+ *   workspace  >= dpp_elementary_workspace_size(n, k) bytes (8 n k bytes for
+ *              the factor columns plus O(n)). */
+size_t dpp_elementary_workspace_size(int64_t n, int64_t k);
+dpp_status dpp_sample_elementary(const double* K, int64_t n, int64_t ld, int64_t k, uint64_t seed,
+                                 uint64_t instance, const double* uniforms, int64_t* sample,
+                                 uint8_t* keep, double* chol, dpp_result* result, void* workspace,
+                                 size_t workspace_bytes, void* stream);
+
 /* Many independent draws, one per Hermitian (real symmetric) kernel of its own
  * order, in ONE persistent launch (no host synchronisation). Each CTA takes
  * the next instance from a device work queue (largest n first) and draws it

@@ -259,12 +259,14 @@ int64_t oracle_dpp_ldl_greedy_r64(int64_t n, double* A, int64_t ld,
 /* column is divided by A_jj and each d_i loses A_ij^2.                       */
 /* Outputs: sample[0:k] = perm[0:k] (selection order), chol (k x k, ld k) the */
 /* lower-triangular Cholesky factor of K_Y in that order, logp = 2 sum_j      */
-/* log A_jj (Theorem 2: P(Y) = product of the squared pivots). Returns 0, or  */
-/* -1 if a pivot was not positive.                                           */
+/* log A_jj (Theorem 2: P(Y) = product of the squared pivots). margin (k or   */
+/* NULL) receives, per step, the distance of u_j S to the nearest running sum */
+/* divided by S: where it is tiny, another summation order may pick the      */
+/* neighbouring position. Returns 0, or -1 if a pivot was not positive.       */
 /* ------------------------------------------------------------------------- */
 int oracle_dpp_elementary_r64(int64_t n, const double* K, int64_t ldk, int64_t k,
                               const double* u, int64_t* sample, double* chol,
-                              double* logp) {
+                              double* logp, double* margin) {
   double* A = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * (size_t)(n > 0 ? n : 1));
   double* d = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
   int64_t* perm = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
@@ -292,6 +294,15 @@ int oracle_dpp_elementary_r64(int64_t n, const double* K, int64_t ldk, int64_t k
       }
     }
     if (t < 0) t = last >= 0 ? last : j;
+    if (margin) {
+      double m = fabs(target), run = 0.0;
+      for (int64_t p = j; p < n; ++p) {
+        run += d[p] > 0.0 ? d[p] : 0.0;
+        const double dist = fabs(run - target);
+        if (dist < m) m = dist;
+      }
+      margin[j] = S > 0.0 ? m / S : 0.0;
+    }
     /* symmetric swap of positions j and t */
     if (t != j) {
       for (int64_t c = 0; c < n; ++c) {

@@ -70,7 +70,7 @@ def _load():
         f.restype = i64
     lib.oracle_dpp_ldl_greedy_r64.argtypes = [i64, dp, i64, u8p, dp, dp]
     lib.oracle_dpp_ldl_greedy_r64.restype = i64
-    lib.oracle_dpp_elementary_r64.argtypes = [i64, dp, i64, i64, dp, dp, dp, dp]
+    lib.oracle_dpp_elementary_r64.argtypes = [i64, dp, i64, i64, dp, dp, dp, dp, dp]
     lib.oracle_dpp_elementary_r64.restype = ctypes.c_int
     lib.oracle_num_threads.argtypes = []
     lib.oracle_num_threads.restype = ctypes.c_int
@@ -174,8 +174,9 @@ class ElementaryDraw:
     Cholesky factor of K_Y in that order, log P(Y) and whether every pivot was
     positive."""
 
-    def __init__(self, n, sample, chol, logp, ok):
+    def __init__(self, n, sample, chol, logp, ok, margin):
         self.n = n
+        self.margin = margin
         self.sample = sample
         self.chol = chol
         self.logp = logp
@@ -198,9 +199,11 @@ def sample_elementary(K: np.ndarray, k: int, u: np.ndarray) -> ElementaryDraw:
     sample = np.zeros(max(k, 1), dtype=np.int64)
     chol = np.zeros((max(k, 1), max(k, 1)), dtype=np.float64, order="F")
     lp = np.zeros(1)
+    margin = np.zeros(max(k, 1))
     rc = _load().oracle_dpp_elementary_r64(n, _ptr(A), n, k, _ptr(u), _ptr(sample), _ptr(chol),
-                                           _ptr(lp))
-    return ElementaryDraw(n, sample[:k].copy(), np.array(chol[:k, :k]), float(lp[0]), rc == 0)
+                                           _ptr(lp), _ptr(margin))
+    return ElementaryDraw(n, sample[:k].copy(), np.array(chol[:k, :k]), float(lp[0]), rc == 0,
+                          margin[:k].copy())
 
 
 def forced_uniforms(keep: np.ndarray) -> np.ndarray:

@@ -16,7 +16,7 @@ from ._lib import (DPP_C128, DPP_OP_LOGPROB_BACKWARD, DPP_OP_SAMPLE_HERMITIAN,
 
 __all__ = ["sample_hermitian", "sample_hermitian_static", "sample_lu", "greedy_hermitian",
            "greedy_lu", "sample_batched", "BatchedSampler", "autotune",
-           "lensemble_to_marginal",
+           "lensemble_to_marginal", "sample_elementary",
            "logprob_backward", "uniforms", "Sample", "DPPLogProb", "DPPError", "load",
            "workspace_size"]
 
@@ -295,6 +295,47 @@ def sample_batched(Ks, seed: int = 0, instance=None, want_pivots: bool = False, 
     b = BatchedSampler(Ks, instance=instance, want_pivots=want_pivots, uniforms=uniforms)
     b.draw(seed)
     return b
+
+
+class ElementarySample:
+    """Device-resident outcome of one elementary draw. ``result()`` synchronises."""
+
+    def __init__(self, sample, keep, chol, raw):
+        self.sample = sample
+        self.keep = keep
+        self.chol = chol
+        self.raw = raw
+
+    def result(self) -> dict:
+        return decode_result(bytes(self.raw.cpu().numpy().tobytes()))
+
+
+def sample_elementary(K, k: int, seed: int = 0, instance: int = 0, uniforms=None,
+                      chol: bool = False, workspace=None) -> ElementarySample:
+    """Algorithm 2: a sample of DPP(K) for a real symmetric projection K of rank k."""
+    torch = _torch()
+    L = load()
+    if not K.is_cuda or K.dtype != torch.float64:
+        raise TypeError("K must be a float64 CUDA tensor")
+    Kc, ld = colmajor(K)
+    n = K.shape[0]
+    dev = K.device
+    sample = torch.empty(max(k, 1), dtype=torch.int64, device=dev)
+    keep = torch.empty(max(n, 1), dtype=torch.uint8, device=dev)
+    ch = empty_colmajor(max(k, 1), torch.float64, dev) if chol else None
+    raw = torch.zeros(_lib.RESULT_BYTES, dtype=torch.uint8, device=dev)
+    need = int(L.dpp_elementary_workspace_size(n, k))
+    if need == 0:
+        raise DPPError(_lib.DPP_ERR_INVALID_ARG, "bad n or k")
+    ws = workspace if workspace is not None else torch.empty(need, dtype=torch.uint8, device=dev)
+    if uniforms is not None:
+        uniforms = uniforms.to(device=dev, dtype=torch.float64).contiguous()
+    _lib.check(L.dpp_sample_elementary(
+        Kc.data_ptr() if n else None, n, ld, k, seed, instance,
+        None if uniforms is None else uniforms.data_ptr(), sample.data_ptr(), keep.data_ptr(),
+        None if ch is None else ch.data_ptr(), raw.data_ptr(), ws.data_ptr(), ws.numel(),
+        _stream(dev)))
+    return ElementarySample(sample[:k], keep[:n], ch, raw)
 
 
 def lensemble_to_marginal(Ls):

@@ -103,6 +103,10 @@ def load(path: Optional[str] = None):
     L.dpp_tune_load.restype = i32
     L.dpp_lensemble_to_marginal_batched.argtypes = [i32, vp, vp, vp, vp, vp, vp, sz, vp]
     L.dpp_lensemble_to_marginal_batched.restype = i32
+    L.dpp_elementary_workspace_size.argtypes = [i64, i64]
+    L.dpp_elementary_workspace_size.restype = sz
+    L.dpp_sample_elementary.argtypes = [vp, i64, i64, i64, u64, u64, vp, vp, vp, vp, vp, vp, sz, vp]
+    L.dpp_sample_elementary.restype = i32
     L.dpp_tune_clear.argtypes = []
     L.dpp_tune_clear.restype = None
     _lib = L

@@ -221,6 +221,37 @@ dpp_status dpp_greedy_lu(const void* K, int64_t n, int64_t ld, int32_t dtype, in
                        workspace, workspace_bytes, stream);
 }
 
+size_t dpp_elementary_workspace_size(int64_t n, int64_t k) {
+  if (n < 0 || k < 0 || k > n || n > (int64_t)0x7fffffff) return 0;
+  return ws_elementary(n, k);
+}
+
+dpp_status dpp_sample_elementary(const double* K, int64_t n, int64_t ld, int64_t k, uint64_t seed,
+                                 uint64_t instance, const double* uniforms, int64_t* sample,
+                                 uint8_t* keep, double* chol, dpp_result* result, void* workspace,
+                                 size_t workspace_bytes, void* stream) {
+  g_last_error.clear();
+  if (n < 0 || n > (int64_t)0x7fffffff) return fail(DPP_ERR_INVALID_ARG, "bad n");
+  if (k < 0 || k > n) return fail(DPP_ERR_INVALID_ARG, "k must be in [0, n]");
+  if (ld < (n > 1 ? n : 1)) return fail(DPP_ERR_INVALID_ARG, "ld must be >= max(1, n)");
+  if (!result || !aligned(result, 8)) return fail(DPP_ERR_INVALID_ARG, "result NULL or misaligned");
+  if (n > 0 && (!K || !aligned(K, 8))) return fail(DPP_ERR_INVALID_ARG, "K NULL or misaligned");
+  if (k > 0 && (!sample || !aligned(sample, 8)))
+    return fail(DPP_ERR_INVALID_ARG, "sample NULL or misaligned");
+  if (chol && !aligned(chol, 8)) return fail(DPP_ERR_INVALID_ARG, "chol misaligned");
+  if (!workspace || !aligned(workspace, 256))
+    return fail(DPP_ERR_WORKSPACE, "workspace must be non-NULL and 256-byte aligned");
+  if (workspace_bytes < ws_elementary(n, k)) return fail(DPP_ERR_WORKSPACE, "workspace too small");
+  begin_call(DPP_OP_SAMPLE_HERMITIAN, n, DPP_R64, DPP_PREC_FP64);
+  Workspace ws;
+  ws.base = static_cast<char*>(workspace);
+  ws.size = workspace_bytes;
+  cudaError_t e = sample_elementary(K, n, ld, k, seed, instance, uniforms, sample, keep, chol,
+                                    result, ws, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return fail_cuda(e, "dpp_sample_elementary");
+  return DPP_OK;
+}
+
 size_t dpp_batched_workspace_size(int32_t batch, int64_t n_max, int32_t precision) {
   if (batch < 0 || n_max < 0 || precision != DPP_PREC_FP32) return 0;
   return ws_batched(batch, n_max, batched_default_ctas());

@@ -133,6 +133,13 @@ size_t ws_batched_per_cta(int64_t n_max);
 int batched_default_ctas();
 cudaError_t sample_batched(const BatchedArgs& b, Workspace ws);
 
+// Elementary (projection) sampler, Algorithm 2 (dpp_elementary.cu).
+size_t ws_elementary(int64_t n, int64_t k);
+cudaError_t sample_elementary(const double* K, int64_t n, int64_t ld, int64_t k, uint64_t seed,
+                              uint64_t instance, const double* uniforms, int64_t* sample,
+                              uint8_t* keep, double* chol, dpp_result* result, Workspace ws,
+                              cudaStream_t s);
+
 // Adjoint (dpp_backward.cu).
 size_t ws_backward(int64_t n, int32_t dtype, bool hermitian);
 cudaError_t logprob_backward(const void* K, int64_t n, int64_t ld, int32_t dtype,

@@ -30,7 +30,7 @@ std::atomic<unsigned long long> g_launches{0};
 const char* kNames[kProfCategories] = {"panel_decide_solve", "update_fp64", "update_f32_simt",
                                        "update_tc", "convert", "recompute", "other",
                                        "batched", "adjoint_batched", "lensemble_batched",
-                                       "panel_rows_below"};
+                                       "panel_rows_below", "elementary"};
 
 cudaEvent_t get_event() {
   if (!g_pool.empty()) {

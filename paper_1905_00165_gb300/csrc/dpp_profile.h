@@ -17,7 +17,8 @@ enum ProfCat {
   kProfAdjoint = 8,
   kProfLEnsemble = 9,
   kProfBelow = 10,
-  kProfCategories = 11
+  kProfElementary = 11,
+  kProfCategories = 12
 };
 
 // Counts one launch; while profiling is on, records an event pair around the

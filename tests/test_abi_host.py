@@ -233,3 +233,20 @@ def test_autotune_rejects_bad_arguments_on_host(L):
     assert f(0, fake, 100, 100, 0, 1, 2, 0, fake, need, None, None) == _lib.DPP_ERR_INVALID_ARG
     assert f(0, fake, 1000, 1000, 0, 1, 2, 4, fake, 1024, None, None) == _lib.DPP_ERR_WORKSPACE
     assert f(1, fake, 100, 100, 1, 1, 2, 4, fake, need, None, None) == _lib.DPP_ERR_UNSUPPORTED
+
+
+def test_elementary_arguments_checked_on_host(L):
+    fake = 4096
+    f = L.dpp_sample_elementary
+    need = L.dpp_elementary_workspace_size(100, 10)
+    assert need >= 8 * 100 * 10
+    assert L.dpp_elementary_workspace_size(100, 101) == 0
+    assert L.dpp_elementary_workspace_size(-1, 0) == 0
+    assert f(fake, 100, 100, 101, 0, 0, None, fake, None, None, fake, fake, need, None) == \
+        _lib.DPP_ERR_INVALID_ARG  # k > n
+    assert f(fake, 100, 99, 10, 0, 0, None, fake, None, None, fake, fake, need, None) == \
+        _lib.DPP_ERR_INVALID_ARG  # ld < n
+    assert f(fake, 100, 100, 10, 0, 0, None, None, None, None, fake, fake, need, None) == \
+        _lib.DPP_ERR_INVALID_ARG  # no sample buffer
+    assert f(fake, 100, 100, 10, 0, 0, None, fake, None, None, fake, fake, 64, None) == \
+        _lib.DPP_ERR_WORKSPACE
