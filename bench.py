@@ -54,7 +54,7 @@ def parse():
                    help="draws in flight on this many streams, each launch capped at "
                         "SMs / streams CTAs (0: the autotuner's choice)")
     p.add_argument("--suite-only", default="",
-                   help="with --suite: comma-separated subset of C1,C2,C3,C4")
+                   help="with --suite: comma-separated subset of C1,C2,C3,C4,E")
     p.add_argument("--suite", action="store_true",
                    help="one JSON line per workload of the paper-shaped configurations "
                         "(FP64 n=512; n=4096 real/complex, projection/Beta; spanning trees of "
@@ -410,6 +410,37 @@ def run_suite(args):
         line("C4", dict(cfg4, streams=nst), "bf16x6", ms, 2 * n ** 3 / 3, {},
              {"timing": "wall clock over all streams, after a device synchronize"})
 
+    # E: the elementary sampler (Algorithm 2) on projection kernels: the
+    # paper's n = 5000 ranks 10 / 100 / 500, and the rank-n/4 projections of
+    # the Hermitian configuration (n = 4096 and 16384)
+    def suite_e():
+        L = dpp.load()
+        for n, k in ((5000, 10), (5000, 100), (5000, 500), (4096, 1024), (16384, 4096)):
+            Kd = W.hermitian_kernel(n, seed=0, kind="projection", rank=k, device=str(dev),
+                                    return_torch=True).contiguous()
+            need = int(L.dpp_elementary_workspace_size(n, k))
+            ws = torch.empty(need, dtype=torch.uint8, device=dev)
+            sample = torch.empty(k, dtype=torch.int64, device=dev)
+            raw = torch.zeros(_lib.RESULT_BYTES, dtype=torch.uint8, device=dev)
+
+            def fn(seed, Kd=Kd, n=n, k=k, ws=ws, sample=sample, raw=raw, need=need):
+                _lib.check(L.dpp_sample_elementary(Kd.data_ptr(), n, n, k, seed, 0, None,
+                                                   sample.data_ptr(), None, None, raw.data_ptr(),
+                                                   ws.data_ptr(), need, stream.cuda_stream))
+            draws = 8 if n * k * k < 5e10 else 2
+            ms, prof = timed(fn, draws, warm=1)
+            res = _lib.decode_result(bytes(raw.cpu().numpy().tobytes()))
+            tf = n * k * k / (ms / 1e3) / 1e12
+            print(json.dumps({"suite": "E", "config": {"n": n, "rank": k, "kernel": "projection"},
+                              "precision": "fp64", "samples_per_s": 1e3 / ms, "ms_per_draw": ms,
+                              "tflops_algorithmic": tf, "flops_convention": "n k^2 (multiply-adds x 2 / 2)",
+                              "last_draw_kept": res["n_kept"], "last_draw_status": res["status"]}),
+                  flush=True)
+            del Kd, ws
+            torch.cuda.empty_cache()
+
+    if want("E"):
+        suite_e()
     if want("C1"):
         suite_c1()
     if want("C2"):
