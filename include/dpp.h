@@ -249,7 +249,9 @@ dpp_status dpp_greedy_lu(const void* K, int64_t n, int64_t ld, int32_t dtype, in
  *              not positive sets DPP_RES_INADMISSIBLE (K is not a projection
  *              of rank k) or DPP_RES_NONFINITE.
  *   workspace  >= dpp_elementary_workspace_size(n, k) bytes (8 n k bytes for
- *              the factor columns plus O(n)). */
+ *              the factor columns plus O(n)).
+ * Limit: n <= 2048 x (number of SMs) (each CTA owns at most 2048 positions);
+ * a larger n returns DPP_ERR_CUDA. */
 size_t dpp_elementary_workspace_size(int64_t n, int64_t k);
 dpp_status dpp_sample_elementary(const double* K, int64_t n, int64_t ld, int64_t k, uint64_t seed,
                                  uint64_t instance, const double* uniforms, int64_t* sample,

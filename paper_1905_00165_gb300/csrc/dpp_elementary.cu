@@ -135,8 +135,16 @@ __device__ void elem_partial(const ElemArgs& a, int64_t j, double* red) {
   }
 }
 
+constexpr int kEMaxCtas = 1024;   // partials staged in shared memory
+constexpr int kEMaxChunk = 2048;  // positions per CTA (the owner's staged range)
+
 __global__ void __launch_bounds__(kEThreads) k_elementary(ElemArgs a) {
   __shared__ double red[kEThreads / 32];
+  __shared__ double s_part[kEMaxCtas];
+  __shared__ int s_lastp[kEMaxCtas];
+  __shared__ double s_d[kEMaxChunk];
+  __shared__ int s_owner;
+  __shared__ double s_acc, s_target;
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const int64_t n = a.n, k = a.k;
   const int64_t lo = (int64_t)blockIdx.x * a.chunk;
@@ -154,15 +162,22 @@ __global__ void __launch_bounds__(kEThreads) k_elementary(ElemArgs a) {
   for (int64_t j = 0; j < k; ++j) {
     if (!elem_barrier(a)) return;
     // ---- B: the position t (all CTAs agree on the CTA that holds it) ----
+    // the partials are staged in shared memory by all threads (independent
+    // loads), then thread 0 forms the running sums in CTA order
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += kEThreads) {
+      s_part[b] = __ldcg(&a.part[b]);
+      s_lastp[b] = __ldcg(&a.lastpos[b]);
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
       double S = 0.0;
-      for (unsigned b = 0; b < gridDim.x; ++b) S += __ldcg(&a.part[b]);
+      for (unsigned b = 0; b < gridDim.x; ++b) S += s_part[b];
       const double u = a.uniforms ? a.uniforms[j] : philox_uniform(a.seed, a.inst, (uint64_t)j);
       const double target = u * S;
       double acc = 0.0;
       int owner = -1;
       for (unsigned b = 0; b < gridDim.x; ++b) {
-        const double pb = __ldcg(&a.part[b]);
+        const double pb = s_part[b];
         if (acc + pb > target && pb > 0.0) {
           owner = (int)b;
           break;
@@ -171,18 +186,29 @@ __global__ void __launch_bounds__(kEThreads) k_elementary(ElemArgs a) {
       }
       if (owner < 0) {  // rounding left the target at the end: last positive position
         int best = -1;
-        for (unsigned b = 0; b < gridDim.x; ++b)
-          best = max(best, __ldcg(&a.lastpos[b]));
+        for (unsigned b = 0; b < gridDim.x; ++b) best = max(best, s_lastp[b]);
         owner = best >= 0 ? (int)(best / a.chunk) : (int)(j / a.chunk);
         acc = -1.0;  // marks "take the last positive position"
       }
-      if ((int)blockIdx.x == owner) {
+      s_owner = owner;
+      s_acc = acc;
+      s_target = target;
+    }
+    __syncthreads();
+    if ((int)blockIdx.x == s_owner) {
+      // the owner's remaining diagonal, staged by all threads, scanned in order
+      const int64_t p0 = lo > j ? lo : j;
+      for (int64_t p = p0 + threadIdx.x; p < hi; p += kEThreads)
+        s_d[p - p0] = __ldcg(&a.d[__ldcg(&a.perm[p])]);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const int owner = s_owner;
+        const double target = s_target;
         int64_t t = -1;
-        if (acc >= 0.0) {
-          double run = acc;
-          const int64_t p0 = lo > j ? lo : j;
+        if (s_acc >= 0.0) {
+          double run = s_acc;
           for (int64_t p = p0; p < hi; ++p) {
-            const double dp = __ldcg(&a.d[__ldcg(&a.perm[p])]);
+            const double dp = s_d[p - p0];
             if (dp > 0.0) {
               run += dp;
               if (run > target) {
@@ -193,7 +219,7 @@ __global__ void __launch_bounds__(kEThreads) k_elementary(ElemArgs a) {
           }
         }
         if (t < 0) {
-          const int lp_owner = __ldcg(&a.lastpos[owner]);
+          const int lp_owner = s_lastp[owner];
           t = lp_owner >= 0 ? lp_owner : j;
         }
         const int32_t pj = __ldcg(&a.perm[j]), pt = __ldcg(&a.perm[t]);
@@ -314,8 +340,11 @@ cudaError_t sample_elementary(const double* K, int64_t n, int64_t ld, int64_t k,
   if (g_tuning.max_ctas > 0 && grid > g_tuning.max_ctas) grid = g_tuning.max_ctas;
   int64_t by_n = (n + 31) / 32;
   if (grid > by_n) grid = by_n;
-  if (grid > 4096) grid = 4096;
+  if (grid > kEMaxCtas) grid = kEMaxCtas;
+  const int64_t min_grid = (n + kEMaxChunk - 1) / kEMaxChunk;
+  if (grid < min_grid) grid = min_grid;
   if (grid < 1) grid = 1;
+  if (grid > caps[dev] || grid > kEMaxCtas) return cudaErrorInvalidValue;  // n too large
   a.chunk = (n + grid - 1) / grid;
   grid = (n + a.chunk - 1) / a.chunk;  // every CTA owns at least one position
   void* args[] = {&a};
