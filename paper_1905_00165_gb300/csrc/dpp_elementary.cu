@@ -241,23 +241,30 @@ __global__ void __launch_bounds__(kEThreads) k_elementary(ElemArgs a) {
     if (blockIdx.x == 0 && threadIdx.x == 0) lp += 2.0 * log(piv);
     if (j == k - 1) break;
     // ---- C: column j for this CTA's positions > j, then phase A of j + 1 ----
-    // eight lanes per index (four indices per warp at once), so the latency
+    // four lanes per index (eight indices per warp at once), so the latency
     // chain of one index (permutation, K entry and factor row, reduction,
     // diagonal) overlaps with the other indices'
     const double* Fs = a.F + sel * k;
-    const int grp = threadIdx.x >> 3, gl = threadIdx.x & 7;
+    const int grp = threadIdx.x >> 2, gl = threadIdx.x & 3;
     const int64_t p0 = lo > j + 1 ? lo : j + 1;
     // (the loop bound is the warp's, so every lane reaches the shuffles)
-    for (int64_t pb = p0 + (grp & ~3); pb < hi; pb += kEThreads / 8) {
-      const int64_t p = pb + (grp & 3);
+    for (int64_t pb = p0 + (grp & ~7); pb < hi; pb += kEThreads / 4) {
+      const int64_t p = pb + (grp & 7);
       const bool act = p < hi;
       const int64_t i = act ? __ldcg(&a.perm[p]) : 0;
       const double* Fi = a.F + i * k;
       const double kis = (act && gl == 0) ? a.K[i + sel * a.ld] : 0.0;
-      double dot = 0.0;
-      if (act)
-        for (int64_t s2 = gl; s2 < j; s2 += 8) dot = fma(__ldcg(&Fi[s2]), __ldcg(&Fs[s2]), dot);
-      dot += __shfl_xor_sync(kEFull, dot, 4);
+      double dot = 0.0, dot2 = 0.0;
+      if (act) {
+        int64_t s2 = gl;
+#pragma unroll 4
+        for (; s2 + 4 < j; s2 += 8) {
+          dot = fma(__ldcg(&Fi[s2]), __ldcg(&Fs[s2]), dot);
+          dot2 = fma(__ldcg(&Fi[s2 + 4]), __ldcg(&Fs[s2 + 4]), dot2);
+        }
+        if (s2 < j) dot = fma(__ldcg(&Fi[s2]), __ldcg(&Fs[s2]), dot);
+      }
+      dot += dot2;
       dot += __shfl_xor_sync(kEFull, dot, 2);
       dot += __shfl_xor_sync(kEFull, dot, 1);
       if (act && gl == 0) {
