@@ -370,3 +370,19 @@ def test_elementary_edge_cases():
     n = 12
     d = O.sample_elementary(np.eye(n), n, O.uniforms(1, 0, n))
     assert sorted(d.sample.tolist()) == list(range(n)) and abs(d.logp) < 1e-12
+
+
+def test_complex_lu_logp_on_nonhermitian_kernel():
+    """The complex LU form on a non-Hermitian K = D^{-1} S D (D with complex
+    phases): log P equals log|det(K - 1_{Y^c})| (LAPACK slogdet), and the
+    decisions equal those of the Hermitian LDL^H form on S (Prop. 2)."""
+    n = 60
+    K, S = W.lu_similarity_kernel(n, seed=12, complex_=True)
+    assert np.abs(K - K.conj().T).max() > 1e-3  # genuinely non-Hermitian
+    for seed in range(3):
+        u = O.uniforms(seed, 4, n)
+        d = O.sample_lu(K, u)
+        assert abs(d.logp - O.subset_logprob(K, d.keep)) <= 1e-10 * max(1.0, abs(d.logp))
+        h = O.sample_ldl(S, u)
+        assert np.array_equal(d.keep, h.keep)
+        assert abs(d.logp - h.logp) <= 1e-10 * max(1.0, abs(h.logp))
