@@ -505,6 +505,29 @@ def run_case(args):
     return 0
 
 
+def replica_seed_base(rank: int) -> int:
+    """Philox seed of a rank's first draw: ranks draw disjoint seed ranges
+    (independent replicas; no collective on the data path)."""
+    return rank * 1000003
+
+
+def job_time_ms(ms_local: float, ws_n: int, device=None) -> float:
+    """The job's time: the maximum over ranks of each rank's timed region."""
+    if ws_n <= 1:
+        return ms_local
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms_local], dtype=torch.float64,
+                     device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: int, ws_n: int, ms: float) -> float:
+    """Whole-job throughput: every rank's units over the job's time."""
+    return ws_n * units_per_rank / (ms / 1e3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -736,7 +759,7 @@ def main():
                                     stv.cuda_stream)
         _lib.check(st)
 
-    base_seed = rank * 1000003
+    base_seed = replica_seed_base(rank)
     for w in range(warmup):
         draw(base_seed + 900000 + w)
     torch.cuda.synchronize()
@@ -768,14 +791,11 @@ def main():
     launches = _lib.launch_count() - l0
     prof = _lib.profile_stop()
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
+    ms = job_time_ms(ev0.elapsed_time(ev1), ws_n, dev)
     if ws_n > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
         torch.distributed.barrier()
     res = _lib.decode_result(bytes(raw.cpu().numpy().tobytes()))
-    value = ws_n * steps / (ms / 1e3)
+    value = job_rate(steps, ws_n, ms)
     algo_flops = n ** 3 / 3.0
     # the last timed draw on the first stream, kept for the oracle comparison
     s_par = max(s for s in range(steps) if s % nst == 0)
@@ -917,12 +937,8 @@ def main():
                 stream.wait_event(done)
         a1.record(stream)
         torch.cuda.synchronize()
-        e_ms = a0.elapsed_time(a1)
-        if ws_n > 1:
-            t = torch.tensor([e_ms], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e_ms = float(t.item())
-        e2e = {"value": ws_n * e2e_steps / (e_ms / 1e3), "unit": "samples/s",
+        e_ms = job_time_ms(a0.elapsed_time(a1), ws_n, dev)
+        e2e = {"value": job_rate(e2e_steps, ws_n, e_ms), "unit": "samples/s",
                "h2d_bytes_per_step": 8 * n * n, "d2h_bytes_per_step": n + _lib.RESULT_BYTES,
                "steps": e2e_steps,
                "overlap": f"H2D on a copy stream into {nbuf} rotating buffers; draws on {nst} streams"}
