@@ -380,6 +380,11 @@ __device__ __forceinline__ void dec_fast(int b, int lane, float tau0, float (&r)
     if (fabsf(uj - ph) <= tau) {
       stop = J;
     } else {
+      // FP32 comparison of the FP32 uniform with the pivot's high part: u and
+      // the double-float pivot in [-1, 2] each lose at most 2^-24 to the
+      // rounding (u < 1, |hi| < 2, half an ulp each), and tau >= 2^-22 (its
+      // floor), so outside the band the FP64 comparison of u with the pivot
+      // gives the same decision
       const bool kp = uj < ph;
       const float df = kp ? ph : ph - 1.0f;
       if (lane == J && !kp) dd = f2_add_f(dd, -1.0f);

@@ -128,3 +128,21 @@ def test_hermitian_complex_identity_second_order(seed):
     naive = kgg - np.sum(np.abs(lrow) ** 2 * d)
     assert abs(d2 - exact) < 50 * EPS ** 2 * (1 + abs(exact)), (d2, exact)
     assert abs(naive - exact) > abs(d2 - exact)
+
+
+def test_fp32_decision_outside_the_band_equals_fp64():
+    """The mixed chains decide in FP32 outside the borderline band: u (FP64) and
+    the pivot's FP32 high part are each rounded to FP32. Every |u - d| > 2^-22
+    (the band's floor) gives the same decision in FP32 as in FP64, since each
+    rounding moves a value in (0, 2) by at most 2^-24; checked on a grid that
+    crowds the band's edge."""
+    import numpy as np
+    rng = np.random.default_rng(0)
+    u = rng.uniform(0.0, 1.0, 200000)
+    for scale in (1.0, 1.000001, 0.999999):
+        off = np.where(rng.random(u.size) < 0.5, 1.0, -1.0) * 2.0 ** -22 * scale * (1 + rng.random(u.size))
+        d = np.clip(u + off, -1.0, 1.999)
+        keep64 = u < d
+        far = np.abs(u - d) > 2.0 ** -22
+        keep32 = u.astype(np.float32) < d.astype(np.float32)
+        assert np.array_equal(keep64[far], keep32[far])
