@@ -1303,12 +1303,39 @@ __global__ void __launch_bounds__(kLuThreads, 1) k_lu_outer(LuArgs a) {
 // are those of the left-looking worker steps, accumulated panel by panel. At
 // the end it stores L (and M^T), the W and M operand rows with their
 // tensor-core splits, and subtracts sum_c W M from each running diagonal.
-constexpr int kBR = 64;  // indices per CTA of k_below
+constexpr int kBR = 32;  // indices per CTA of k_below
+
+constexpr int kBelowLdp = kNB + 4;  // row length of the staged panel operands
 
 inline size_t below_smem(bool sym) {
   const size_t x = sizeof(float) * kBR * (kNB + 1);
-  const size_t ps = sizeof(float) * kNB * 33;
+  const size_t ps = sizeof(float) * 32 * kBelowLdp;
   return (sym ? x : 2 * x) + (sym ? ps : 2 * ps) + sizeof(float) * (2 * 32 * 33 + 32 + kNB);
+}
+
+// Substitution of R rows of one side against the panel's 32 x 32 unit lower
+// block T (row c, column c' < c), the rows interleaved so that their chains
+// overlap: lane c holds column c of every row; step c0 broadcasts the final
+// value of column c0 and every later column subtracts its multiple.
+template <int R>
+__device__ __forceinline__ void below_solve(float* base, int ldx, const int* rows, int D, int b,
+                                            const float* T, const float* scale) {
+  const int lane = threadIdx.x & 31;
+  float x[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) x[r] = lane < b ? base[rows[r] * ldx + D + lane] : 0.f;
+  for (int c0 = 0; c0 < b - 1; ++c0) {
+    const float t = lane > c0 ? T[lane * 33 + c0] : 0.f;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float y = __shfl_sync(kLuFull, x[r], c0);
+      x[r] = fmaf(-y, t, x[r]);
+    }
+  }
+  const float sc = scale ? scale[lane] : 1.f;
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    if (lane < b) base[rows[r] * ldx + D + lane] = x[r] * sc;
 }
 
 template <bool SYM>
@@ -1316,18 +1343,20 @@ __global__ void __launch_bounds__(kLuThreads) k_below(LuArgs a) {
   constexpr int ldx = kNB + 1;
   float* X = reinterpret_cast<float*>(g_lu_dyn);   // [kBR][ldx]: A rows, then W
   float* Zs = SYM ? X : X + kBR * ldx;             // [kBR][ldx]: A columns, then M (LU)
-  float* Ps = (SYM ? X : Zs) + kBR * ldx;          // [kNB][33]: M rows of the outer block
-  float* Qs = SYM ? Ps : Ps + kNB * 33;            // [kNB][33]: W rows of the outer block (LU)
-  float* T11 = Qs + kNB * 33;                      // [32][33]: M of the panel's diagonal block
+  // [32][kBelowLdp], panel column t by outer-block index j: M (and, for LU, W)
+  // of the outer block's rows, 16-byte aligned rows for vector loads
+  float* Ps = (SYM ? X : Zs) + kBR * ldx;
+  float* Qs = SYM ? Ps : Ps + 32 * kBelowLdp;
+  float* T11 = Qs + 32 * kBelowLdp;                // [32][33]: M of the panel's diagonal block
   float* U11 = T11 + 32 * 33;                      // [32][33]: L of it (LU)
   float* rdp = U11 + 32 * 33;                      // [32]: 1 / d of the panel
   float* rda = rdp + 32;                           // [kNB]: 1 / d of the outer block
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, wp = tid >> 5;
   const int kb = a.kb, np = (kb + 31) / 32;
   const int64_t q = a.q, qe = q + kb, n = a.n, lda = a.lda;
   const float* A = a.A;
   float* Aw = a.A;
-  const int ty = tid >> 4, tx = tid & 15;  // update: rows 4 ty.., columns 4 tx.. of a 64-wide chunk
+  const int ty = tid >> 5, tx = tid & 31;  // update: rows 4 ty.., columns 4 tx.. of a 128-wide chunk
   for (int64_t i0 = qe + (int64_t)kBR * blockIdx.x; i0 < n; i0 += (int64_t)kBR * gridDim.x) {
     const int nr = (int)((n - i0) < kBR ? (n - i0) : kBR);
     for (int idx = tid; idx < kBR * kb; idx += kLuThreads) {
@@ -1362,32 +1391,20 @@ __global__ void __launch_bounds__(kLuThreads) k_below(LuArgs a) {
         rda[D + tid] = r;
       }
       __syncthreads();
-      if (tid < kBR) {
-        float* xr = X + tid * ldx + D;
-        float y[32];
+      // solves: side 0 (W) and, for LU, side 1 (M = U / d); eight warps
+      if (SYM) {
+        int rows[4] = {wp, wp + 8, wp + 16, wp + 24};
+        below_solve<4>(X, ldx, rows, D, b, T11, nullptr);
+      } else if (wp < 4) {
+        int rows[8];
 #pragma unroll
-        for (int c = 0; c < 32; ++c) y[c] = c < b ? xr[c] : 0.f;
+        for (int r = 0; r < 8; ++r) rows[r] = wp + 4 * r;
+        below_solve<8>(X, ldx, rows, D, b, T11, nullptr);
+      } else {
+        int rows[8];
 #pragma unroll
-        for (int c = 1; c < 32; ++c) {
-#pragma unroll
-          for (int kk = 0; kk < c; ++kk) y[c] = fmaf(-y[kk], T11[c * 33 + kk], y[c]);
-        }
-#pragma unroll
-        for (int c = 0; c < 32; ++c)
-          if (c < b) xr[c] = y[c];
-      } else if (!SYM && tid < 2 * kBR) {
-        float* zr = Zs + (tid - kBR) * ldx + D;
-        float u[32];
-#pragma unroll
-        for (int c = 0; c < 32; ++c) u[c] = c < b ? zr[c] : 0.f;
-#pragma unroll
-        for (int c = 1; c < 32; ++c) {
-#pragma unroll
-          for (int kk = 0; kk < c; ++kk) u[c] = fmaf(-U11[c * 33 + kk], u[kk], u[c]);
-        }
-#pragma unroll
-        for (int c = 0; c < 32; ++c)
-          if (c < b) zr[c] = u[c] * rdp[c];
+        for (int r = 0; r < 8; ++r) rows[r] = (wp - 4) + 4 * r;
+        below_solve<8>(Zs, ldx, rows, D, b, U11, rdp);
       }
       __syncthreads();
       const int C0 = D + 32;
@@ -1395,11 +1412,13 @@ __global__ void __launch_bounds__(kLuThreads) k_below(LuArgs a) {
         for (int idx = tid; idx < (kb - C0) * 32; idx += kLuThreads) {
           const int j = C0 + (idx >> 5), t = idx & 31;
           const int64_t off = (q + j) * (int64_t)kNB + D + t;
-          Ps[j * 33 + t] = t < b ? __ldcg(&a.Mk[off]) : 0.f;
-          if (!SYM) Qs[j * 33 + t] = t < b ? __ldcg(&a.Wk[off]) : 0.f;
+          Ps[t * kBelowLdp + j] = t < b ? __ldcg(&a.Mk[off]) : 0.f;
+          if (!SYM) Qs[t * kBelowLdp + j] = t < b ? __ldcg(&a.Wk[off]) : 0.f;
         }
         __syncthreads();
-        for (int j0 = C0; j0 < kb; j0 += 64) {
+        // (kb is the full outer block here, a multiple of 32: when jb < kb the
+        // four columns jb..jb+3 all exist)
+        for (int j0 = C0; j0 < kb; j0 += 128) {
           float ax[4][4], az[4][4];
 #pragma unroll
           for (int i = 0; i < 4; ++i)
@@ -1408,21 +1427,23 @@ __global__ void __launch_bounds__(kLuThreads) k_below(LuArgs a) {
           const int jb = j0 + 4 * tx;
 #pragma unroll 4
           for (int t = 0; t < 32; ++t) {
-            float w[4], m[4];
+            float w[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) w[i] = X[(4 * ty + i) * ldx + D + t];
-#pragma unroll
-            for (int jj = 0; jj < 4; ++jj) m[jj] = (jb + jj < kb) ? Ps[(jb + jj) * 33 + t] : 0.f;
+            const float4 m4 = jb < kb ? *reinterpret_cast<const float4*>(&Ps[t * kBelowLdp + jb])
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float m[4] = {m4.x, m4.y, m4.z, m4.w};
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
               for (int jj = 0; jj < 4; ++jj) ax[i][jj] = fmaf(w[i], m[jj], ax[i][jj]);
             if (!SYM) {
-              float mr[4], wq[4];
+              float mr[4];
 #pragma unroll
               for (int i = 0; i < 4; ++i) mr[i] = Zs[(4 * ty + i) * ldx + D + t];
-#pragma unroll
-              for (int jj = 0; jj < 4; ++jj) wq[jj] = (jb + jj < kb) ? Qs[(jb + jj) * 33 + t] : 0.f;
+              const float4 q4 = jb < kb ? *reinterpret_cast<const float4*>(&Qs[t * kBelowLdp + jb])
+                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+              const float wq[4] = {q4.x, q4.y, q4.z, q4.w};
 #pragma unroll
               for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -1438,8 +1459,8 @@ __global__ void __launch_bounds__(kLuThreads) k_below(LuArgs a) {
                 if (!SYM) Zs[(4 * ty + i) * ldx + jb + jj] -= az[i][jj];
               }
             }
-          __syncthreads();
         }
+        __syncthreads();
       }
     }
     // stores: L below the outer block (column-major, rows fastest) ...
@@ -1461,18 +1482,31 @@ __global__ void __launch_bounds__(kLuThreads) k_below(LuArgs a) {
         write_split(a.split, a.Mop, off, m);
       }
     }
-    // running diagonal and band scale of each index
-    if (tid < nr) {
+    // running diagonal and band scale: eight lanes per index, each summing a
+    // 32-column slice, then a fixed-order tree over the slices
+    {
+      const int r = tid >> 3, part = tid & 7;
       f2 dsum = {0.f, 0.f};
       float ssum = 0.f;
-      for (int c = 0; c < kb; ++c) {
-        const float w = X[tid * ldx + c];
-        const float m = SYM ? w * rda[c] : Zs[tid * ldx + c];
+      for (int c = 32 * part; c < 32 * part + 32 && c < kb; ++c) {
+        const float w = X[r * ldx + c];
+        const float m = SYM ? w * rda[c] : Zs[r * ldx + c];
         dsum = f2_add_prod(dsum, w, m);
         ssum += fabsf(w * m);
       }
-      a.kd[i0 + tid] -= f2_to_double(dsum);
-      a.s[i0 + tid] += (double)ssum;
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1) {
+        const f2 other = {__shfl_down_sync(kLuFull, dsum.hi, o), __shfl_down_sync(kLuFull, dsum.lo, o)};
+        const float os = __shfl_down_sync(kLuFull, ssum, o);
+        if (part < o) {
+          dsum = f2_add(dsum, other);
+          ssum += os;
+        }
+      }
+      if (part == 0 && r < nr) {
+        a.kd[i0 + r] -= f2_to_double(dsum);
+        a.s[i0 + r] += (double)ssum;
+      }
     }
     __syncthreads();
   }
@@ -1688,7 +1722,7 @@ cudaError_t sample_chunked(const DrawArgs& a, Workspace ws) {
       // flops for the Hermitian form, twice that for LU)
       const double fl = (SYM ? 1.0 : 2.0) * (double)(n - r0) * (double)kb * (double)kb;
       int64_t bg = (n - r0 + kBR - 1) / kBR;
-      const int64_t bcap = (int64_t)below_grid * (SYM ? 2 : 1);  // CTAs resident per SM
+      const int64_t bcap = (int64_t)below_grid * (SYM ? 3 : 1);  // CTAs resident per SM
       if (bg > bcap) bg = bcap;
       ProfScope ps(kProfBelow, a.stream, fl, 0.0);
       k_below<SYM><<<(unsigned)bg, kLuThreads, below_smem(SYM), a.stream>>>(la);
