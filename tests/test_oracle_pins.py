@@ -386,3 +386,71 @@ def test_complex_lu_logp_on_nonhermitian_kernel():
         h = O.sample_ldl(S, u)
         assert np.array_equal(d.keep, h.keep)
         assert abs(d.logp - h.logp) <= 1e-10 * max(1.0, abs(h.logp))
+
+
+# ---------------------------------------------------------------------------
+# Domino tilings of the Aztec diamond (complex, non-Hermitian; Figs. 3 and 4)
+# ---------------------------------------------------------------------------
+def _count_perfect_matchings(edges, n_black):
+    """Brute force: perfect matchings of the bipartite graph, black by black."""
+    adj = [[] for _ in range(n_black)]
+    for b, w in edges:
+        adj[int(b)].append(int(w))
+
+    def rec(b, used):
+        if b == n_black:
+            return 1
+        return sum(rec(b + 1, used | (1 << w)) for w in adj[b] if not used >> w & 1)
+
+    return rec(0, 0)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
+def test_aztec_kasteleyn_counts_tilings(d):
+    """The number of tilings by brute force is 2^{d(d+1)/2}, and so is
+    |det Kast| (Kasteleyn's theorem pins the weights)."""
+    Kast, edges = W.aztec_kasteleyn(d)
+    assert len(edges) == 4 * d * d
+    count = _count_perfect_matchings(edges, Kast.shape[0])
+    assert count == 2 ** (d * (d + 1) // 2)
+    assert abs(np.linalg.slogdet(Kast)[1] - W.aztec_log_tilings(d)) < 1e-12
+
+
+def test_aztec_kernel_enumeration_order2():
+    """Order 2 (n = 16): P(Y) = |det(K - 1_{Y^c})| over all 2^16 subsets sums
+    to one and is 1/8 on exactly the 8 tilings, 0 elsewhere."""
+    K, edges, nb = W.aztec_kernel(2)
+    assert np.abs(K - K.conj().T).max() > 1e-3  # genuinely non-Hermitian
+    probs = O.enumerate_probs(K)
+    assert abs(probs.sum() - 1.0) < 1e-12
+    support = np.flatnonzero(probs > 1e-9)
+    assert len(support) == 8
+    for mask in support:
+        keep = np.array([(mask >> j) & 1 for j in range(16)], dtype=np.uint8)
+        assert W.is_perfect_matching(edges, keep, nb)
+        assert abs(probs[mask] - 0.125) < 1e-12
+
+
+@pytest.mark.parametrize("d", [2, 5, 8])
+def test_aztec_oracle_draws_are_uniform_tilings(d):
+    """Every LU draw of the Kenyon kernel is a tiling with log P equal to
+    -log(#tilings) = -(d(d+1)/2) ln 2."""
+    K, edges, nb = W.aztec_kernel(d)
+    n = K.shape[0]
+    for seed in range(4):
+        dr = O.sample_lu(K, O.uniforms(seed, 0, n))
+        assert W.is_perfect_matching(edges, dr.keep, nb)
+        assert abs(dr.logp + W.aztec_log_tilings(d)) <= 1e-9 * W.aztec_log_tilings(d)
+
+
+def test_aztec_order10_likelihood_matches_paper():
+    """Fig. 3: both samples of the order-10 diamond have likelihood
+    exp(-38.1231)."""
+    val, tol = _golden_likelihoods()["aztec_10"]
+    K, edges, nb = W.aztec_kernel(10)
+    for seed in range(2):
+        dr = O.sample_lu(K, O.uniforms(seed, 0, K.shape[0]))
+        assert W.is_perfect_matching(edges, dr.keep, nb)
+        assert abs(dr.logp - val) <= tol
+    val80, tol80 = _golden_likelihoods()["aztec_80"]
+    assert abs(-W.aztec_log_tilings(80) - val80) <= tol80

@@ -19,6 +19,12 @@ Kernels (all FP64 / complex128, returned as dense n x n arrays):
 * ``lu_similarity_kernel``: K = D^{-1} S D with S Hermitian as above and D a
   log-normal diagonal; diagonal similarity preserves every principal minor, so
   DPP(K) = DPP(S) (Prop. 2 of the paper).
+* ``aztec_kernel``: the domino tilings of the Aztec diamond of order d as a
+  DPP over the 4 d^2 edges of its dual graph: Kasteleyn weights (1 on
+  horizontal, i on vertical adjacencies) and Kenyon's local-statistics formula
+  K(e, e') = Kast(b, w) Kast^{-1}(w, b') for e = (b, w), e' = (b', w'); a
+  complex, non-Hermitian projection of rank d (d + 1) whose draws are uniform
+  tilings (Section 1 of the paper, the Aztec diamond figures).
 * ``lensemble_kernel``: K = L (L + I)^{-1}, L = Phi Phi^T, Phi with unit-norm
   Gaussian rows scaled by LogUniform(0.1, 10) qualities, formed through the
   push-through identity K = Phi (Phi^T Phi + I)^{-1} Phi^T.
@@ -143,6 +149,78 @@ def grid_spanning_tree_log_count(d: int) -> float:
     s = lam[:, None] + lam[None, :]
     s = s.ravel()[1:]  # drop the (0, 0) zero eigenvalue
     return float(np.sum(np.log(s)) - math.log(d * d))
+
+
+# --------------------------------------------------------------------------
+# Domino tilings of the Aztec diamond
+# --------------------------------------------------------------------------
+def aztec_squares(d: int):
+    """Unit squares of the Aztec diamond of order d, by lower-left corner
+    (x, y), centre (x + 1/2, y + 1/2) with |x + 1/2| + |y + 1/2| <= d; split by
+    checkerboard colour (black: x + y even), each list ordered by (y, x)."""
+    sq = [(x, y) for y in range(-d, d) for x in range(-d, d)
+          if abs(x + 0.5) + abs(y + 0.5) <= d]
+    black = [s for s in sq if (s[0] + s[1]) % 2 == 0]
+    white = [s for s in sq if (s[0] + s[1]) % 2 != 0]
+    return black, white
+
+
+def aztec_kasteleyn(d: int):
+    """(Kast, edges): the Kasteleyn matrix of the Aztec diamond's dual graph,
+    rows black squares, columns white squares, weight 1 for a horizontal
+    neighbour and i for a vertical one (every inner face is a 4-cycle with
+    two of each, so the alternating product is -1, Kasteleyn's condition);
+    edges (black index, white index) ordered by black square, then by the
+    directions east, west, north, south. |det Kast| = 2^{d (d + 1) / 2}."""
+    black, white = aztec_squares(d)
+    wi = {s: i for i, s in enumerate(white)}
+    nb = len(black)
+    Kast = np.zeros((nb, nb), dtype=np.complex128)
+    edges = []
+    for b, (x, y) in enumerate(black):
+        for dx, dy, wgt in ((1, 0, 1.0), (-1, 0, 1.0), (0, 1, 1j), (0, -1, 1j)):
+            w = wi.get((x + dx, y + dy))
+            if w is not None:
+                Kast[b, w] = wgt
+                edges.append((b, w))
+    return Kast, np.array(edges, dtype=np.int64)
+
+
+def aztec_kernel(d: int, device: Optional[str] = None):
+    """(K, edges, n_black): the edge-inclusion kernel of uniform domino
+    tilings of the Aztec diamond of order d (n = 4 d^2 edges, complex,
+    non-Hermitian, rank d (d + 1)). K[e, e'] = Kast(b, w) Kast^{-1}(w, b');
+    every principal minor is an inclusion probability (Kenyon), every draw a
+    perfect matching of probability 2^{-d (d + 1) / 2}. The inverse is taken
+    with torch on ``device`` when given (a library routine; rounding only)."""
+    Kast, edges = aztec_kasteleyn(d)
+    b, w = edges[:, 0], edges[:, 1]
+    wt = Kast[b, w]
+    if device is not None and device != "cpu":
+        import torch
+        Ki = torch.linalg.inv(torch.from_numpy(Kast).to(device))
+        bi = torch.from_numpy(b).to(device)
+        wi_ = torch.from_numpy(w).to(device)
+        K = torch.from_numpy(wt).to(device)[:, None] * Ki[wi_][:, bi]
+        return K.cpu().numpy(), edges, Kast.shape[0]
+    Ki = np.linalg.inv(Kast)
+    K = wt[:, None] * Ki[w][:, b]
+    return K, edges, Kast.shape[0]
+
+
+def aztec_log_tilings(d: int) -> float:
+    """log of the number of domino tilings of the Aztec diamond of order d,
+    2^{d (d + 1) / 2} (Elkies-Kuperberg-Larsen-Propp)."""
+    return d * (d + 1) / 2 * math.log(2.0)
+
+
+def is_perfect_matching(edges: np.ndarray, keep: np.ndarray, n_black: int) -> bool:
+    """The kept edges cover every black and every white square exactly once."""
+    k = np.asarray(keep).astype(bool)
+    e = edges[k]
+    if len(e) != n_black:
+        return False
+    return len(np.unique(e[:, 0])) == n_black and len(np.unique(e[:, 1])) == n_black
 
 
 # --------------------------------------------------------------------------
