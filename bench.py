@@ -54,7 +54,7 @@ def parse():
                    help="draws in flight on this many streams, each launch capped at "
                         "SMs / streams CTAs (0: the autotuner's choice)")
     p.add_argument("--suite-only", default="",
-                   help="with --suite: comma-separated subset of C1,C2,C3,C4,E")
+                   help="with --suite: comma-separated subset of C1,C2,C3,C4,E,A")
     p.add_argument("--suite", action="store_true",
                    help="one JSON line per workload of the paper-shaped configurations "
                         "(FP64 n=512; n=4096 real/complex, projection/Beta; spanning trees of "
@@ -65,9 +65,11 @@ def parse():
                    help="with --case: DPP_TUNE_PANEL_PIPELINE for the draws (-1: default)")
     p.add_argument("--update-variant", type=int, default=-1,
                    help="with --case: DPP_TUNE_UPDATE_VARIANT for the draws (-1: default)")
-    p.add_argument("--case", default="", choices=["", "herm", "lu", "cplx", "batched", "adjoint"],
+    p.add_argument("--case", default="",
+                   choices=["", "herm", "lu", "cplx", "aztec", "batched", "adjoint"],
                    help="run one path alone (a small loop for profiling): mixed Hermitian, "
-                        "mixed LU, mixed complex Hermitian, batched sampler or batched adjoint")
+                        "mixed LU, mixed complex Hermitian, mixed complex LU on an Aztec "
+                        "diamond, batched sampler or batched adjoint")
     return p.parse_args()
 
 
@@ -439,6 +441,41 @@ def run_suite(args):
             del Kd, ws
             torch.cuda.empty_cache()
 
+    # A: uniform domino tilings of the Aztec diamond (complex non-Hermitian
+    # Kenyon kernel, n = 4 d^2 edges), the paper's complex LU workload
+    def suite_a():
+        L = dpp.load()
+        for d in (30, 50):
+            Kd, edges, nb = W.aztec_kernel(d, device=str(dev), return_torch=True)
+            n = Kd.shape[0]
+            lt = W.aztec_log_tilings(d)
+            cfg = {"aztec_order": d, "n": n, "kernel": "Kenyon over the Kasteleyn matrix"}
+            for prec_name, draws in (("fp64", 1 if d >= 50 else 2), ("3xtf32", 8), ("bf16x6", 8)):
+                prec = dpp.PRECISIONS[prec_name]
+                need = dpp.workspace_size(1, n, 1, prec, 0)
+                ws = torch.empty(need, dtype=torch.uint8, device=dev)
+                keep = torch.empty(n, dtype=torch.uint8, device=dev)
+                raw = torch.zeros(_lib.RESULT_BYTES, dtype=torch.uint8, device=dev)
+
+                def fn(seed, ws=ws, keep=keep, raw=raw, need=need, prec=prec, n=n):
+                    _lib.check(L.dpp_sample_lu(Kd.data_ptr(), n, n, 1, prec, seed, 0, None,
+                                               keep.data_ptr(), None, None, raw.data_ptr(),
+                                               ws.data_ptr(), need, stream.cuda_stream))
+                ms, prof = timed(fn, draws, warm=1)
+                res = _lib.decode_result(bytes(raw.cpu().numpy().tobytes()))
+                line("A", cfg, prec_name, ms, 8 * n ** 3 / 3, prof,
+                     {"last_draw_is_tiling": bool(W.is_perfect_matching(
+                         edges, keep.cpu().numpy(), nb)),
+                      "last_draw_logp_err": res["logp"] + lt,
+                      "last_draw_borderline": res["n_borderline"],
+                      "last_draw_status": res["status"]})
+                del ws
+                torch.cuda.empty_cache()
+            del Kd
+            torch.cuda.empty_cache()
+
+    if want("A"):
+        suite_a()
     if want("E"):
         suite_e()
     if want("C1"):
@@ -484,6 +521,12 @@ def run_case(args):
         if args.case == "lu":
             K, _ = W.lu_similarity_kernel(n, seed=0, device=str(dev))
             Kd = torch.from_numpy(np.ascontiguousarray(K.T)).to(dev).t()
+            fn = lambda s: dpp.sample_lu(Kd, seed=s, precision=prec)
+        elif args.case == "aztec":
+            # the Aztec diamond whose edge count 4 d^2 is closest to --n
+            d = max(1, int(round((n / 4) ** 0.5)))
+            Kd, _, _ = W.aztec_kernel(d, device=str(dev), return_torch=True)
+            n = Kd.shape[0]
             fn = lambda s: dpp.sample_lu(Kd, seed=s, precision=prec)
         else:
             Kd = W.hermitian_kernel(n, seed=0, kind=args.kind, complex_=args.case == "cplx",

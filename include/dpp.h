@@ -192,11 +192,14 @@ dpp_status dpp_sample_hermitian_static(const void* K, int64_t n, int64_t ld,
  * of K is read, factor_out receives L (strictly lower, unit diagonal) and U
  * (upper, with the pivots on the diagonal), and `pivots`, when not NULL,
  * receives n doubles for DPP_R64 and 2n doubles (re, im) for DPP_C128.
- * Precision: DPP_PREC_FP64 (R64, C128), DPP_PREC_3XTF32 or DPP_PREC_BF16X6
- * (R64). The mixed precisions keep an FP32 copy of K, make every decision
- * on an FP64 pivot (recomputed from K when it lies within the borderline
- * band of its uniform) and apply the trailing updates on the tensor cores;
- * factor_out then receives the FP32 factor (FP64 pivots) and may not equal K. */
+ * Precision: DPP_PREC_FP64, DPP_PREC_3XTF32 or DPP_PREC_BF16X6 (R64 and
+ * C128). The mixed precisions keep an FP32 copy of K (planar real and
+ * imaginary copies for C128), make every decision on an FP64 pivot
+ * (recomputed from K when it lies within the borderline band of its uniform;
+ * for C128 the decision compares u_j with Re d_j) and apply the trailing
+ * updates on the tensor cores (two real contractions of depth 2 kb per
+ * complex update, outer blocks of at most 128 columns); factor_out then
+ * receives the FP32 factor (FP64 pivots) and may not equal K. */
 dpp_status dpp_sample_lu(const void* K, int64_t n, int64_t ld, int32_t dtype,
                          int32_t precision, uint64_t seed, uint64_t instance,
                          const double* uniforms, uint8_t* keep,

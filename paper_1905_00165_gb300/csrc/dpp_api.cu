@@ -99,6 +99,8 @@ size_t dpp_workspace_size(int32_t op, int64_t n, int32_t dtype, int32_t precisio
       if (precision == DPP_PREC_FP64) return ws_fp64(n, dtype, false, true);
       if ((precision == DPP_PREC_3XTF32 || precision == DPP_PREC_BF16X6) && dtype == DPP_R64)
         return ws_mixed_lu(n);
+      if ((precision == DPP_PREC_3XTF32 || precision == DPP_PREC_BF16X6) && dtype == DPP_C128)
+        return ws_mixed_cxlu(n);
       return 0;
     case DPP_OP_LOGPROB_BACKWARD:
       if (precision == DPP_PREC_FP64) return ws_backward(n, dtype, hermitian != 0);
@@ -152,7 +154,9 @@ static dpp_status sample_common(bool hermitian, const void* K, int64_t n, int64_
       // the mixed path reads K in FP64 for recomputes: it must stay intact
       return fail(DPP_ERR_INVALID_ARG, "mixed precision cannot factor in place (factor_out == K)");
     }
-    if (!hermitian)
+    if (!hermitian && dtype == DPP_C128)
+      e = sample_mixed_cxlu(a, ws);
+    else if (!hermitian)
       e = sample_mixed_lu(a, ws);
     else if (dtype == DPP_C128)
       e = sample_mixed_cx(a, ws);

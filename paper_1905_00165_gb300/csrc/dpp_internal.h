@@ -98,6 +98,10 @@ cudaError_t sample_mixed_chunked(const DrawArgs& a, Workspace ws);
 size_t ws_mixed_cx(int64_t n);
 cudaError_t sample_mixed_cx(const DrawArgs& a, Workspace ws);
 
+// Mixed-precision LU sampler for complex, non-Hermitian K (dpp_mixed_cxlu.cu).
+size_t ws_mixed_cxlu(int64_t n);
+cudaError_t sample_mixed_cxlu(const DrawArgs& a, Workspace ws);
+
 // Operand splits of the tensor-core trailing update.
 enum { kSplit3xTf32 = 0, kSplitBf16x6 = 1 };
 

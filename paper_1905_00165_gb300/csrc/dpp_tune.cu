@@ -362,7 +362,9 @@ dpp_status dpp_autotune(int32_t op, const void* K, int64_t n, int64_t ld, int32_
     const int cap = so == 1 ? 0 : (id.sms / so < 8 ? 8 : id.sms / so);
     const int nouter = mixed ? 2 : 1;
     for (int oi = 0; oi < nouter; ++oi) {
-      const int outer = mixed ? (oi == 0 ? 256 : 128) : 0;
+      // (the complex LU path takes outer blocks of at most 128 columns)
+      const bool cxlu = op == DPP_OP_SAMPLE_LU && dtype == DPP_C128;
+      const int outer = mixed ? (oi == 0 ? (cxlu ? 128 : 256) : (cxlu ? 64 : 128)) : 0;
       // panel pipelines: single helper, chunked and split for real Hermitian
       // draws; chunked (0) and split for real LU draws; none to choose else
       int pipes[3] = {0, 0, 0}, npipe = 1;

@@ -49,10 +49,10 @@ def test_workspace_sizes(L):
     assert dpp.workspace_size(0, 0, 0, 0, 1) > 0
     assert dpp.workspace_size(0, 100, 7, 0, 1) == 0  # unknown dtype
     assert dpp.workspace_size(9, 100, 0, 0, 1) == 0  # unknown op
-    # mixed LU: real only; its FP32 copy of K is full square
+    # mixed LU: its FP32 copy of K is full square (planar for complex)
     assert dpp.workspace_size(1, 100, 0, 1, 0) > 100 * 100 * 4
     assert dpp.workspace_size(1, 100, 0, 2, 0) == dpp.workspace_size(1, 100, 0, 1, 0)
-    assert dpp.workspace_size(1, 100, 1, 1, 0) == 0  # no complex mixed LU
+    assert dpp.workspace_size(1, 100, 1, 1, 0) > 100 * 100 * 8
     # complex mixed Hermitian: planar FP32 copy (8 B per element)
     assert dpp.workspace_size(0, 100, 1, 2, 1) > 100 * 100 * 8
 
@@ -149,14 +149,15 @@ def test_tuning_keys_validated_on_host(L):
 
 def test_mixed_workspace_sizes_per_form():
     """Mixed precision: real Hermitian (either panel pipeline), complex
-    Hermitian (planar copy, 8 B per element) and real LU (full square) have
-    workspaces; complex LU has none."""
+    Hermitian (planar copy, 8 B per element), real LU (full square) and
+    complex LU (planar full square) have workspaces."""
     n = 1000
     herm = dpp.workspace_size(0, n, _lib.DPP_R64, _lib.DPP_PREC_3XTF32, 1)
     cplx = dpp.workspace_size(0, n, _lib.DPP_C128, _lib.DPP_PREC_3XTF32, 1)
     lu = dpp.workspace_size(1, n, _lib.DPP_R64, _lib.DPP_PREC_BF16X6, 0)
-    assert herm >= 4 * n * n and lu >= 4 * n * n and cplx >= 8 * n * n
-    assert dpp.workspace_size(1, n, _lib.DPP_C128, _lib.DPP_PREC_BF16X6, 0) == 0
+    cxlu = dpp.workspace_size(1, n, _lib.DPP_C128, _lib.DPP_PREC_BF16X6, 0)
+    assert herm >= 4 * n * n and lu >= 4 * n * n and cplx >= 8 * n * n and cxlu >= 8 * n * n
+    assert cxlu == dpp.workspace_size(1, n, _lib.DPP_C128, _lib.DPP_PREC_3XTF32, 0)
 
 
 def test_greedy_workspace_and_arguments(L):
@@ -166,7 +167,8 @@ def test_greedy_workspace_and_arguments(L):
         for prec in (0, 1, 2):
             ws = dpp.workspace_size(op_s, 1000, 0, prec, herm)
             assert dpp.workspace_size(op_g, 1000, 0, prec, herm) == ws + 8000 + 192
-    assert dpp.workspace_size(4, 100, 1, 1, 0) == 0  # no complex mixed LU
+    cx = dpp.workspace_size(1, 100, 1, 1, 0)
+    assert dpp.workspace_size(4, 100, 1, 1, 0) == cx + 800 + 224  # complex mixed LU
     fake = 4096
     f = L.dpp_greedy_hermitian
     assert f(fake, -1, 4, 0, 0, fake, None, None, fake, fake, 1 << 20, None) == _lib.DPP_ERR_INVALID_ARG
@@ -232,7 +234,9 @@ def test_autotune_rejects_bad_arguments_on_host(L):
     assert f(0, fake, 100, 100, 0, 1, 0, 4, fake, need, None, None) == _lib.DPP_ERR_INVALID_ARG
     assert f(0, fake, 100, 100, 0, 1, 2, 0, fake, need, None, None) == _lib.DPP_ERR_INVALID_ARG
     assert f(0, fake, 1000, 1000, 0, 1, 2, 4, fake, 1024, None, None) == _lib.DPP_ERR_WORKSPACE
-    assert f(1, fake, 100, 100, 1, 1, 2, 4, fake, need, None, None) == _lib.DPP_ERR_UNSUPPORTED
+    # complex LU in a mixed precision is tunable too: a too small workspace is refused
+    assert L.dpp_autotune_workspace_size(1, 100, 1, 1, 2) > 2 * dpp.workspace_size(1, 100, 1, 1, 0)
+    assert f(1, fake, 100, 100, 1, 1, 2, 4, fake, 1024, None, None) == _lib.DPP_ERR_WORKSPACE
 
 
 def test_elementary_arguments_checked_on_host(L):

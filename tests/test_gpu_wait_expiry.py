@@ -75,3 +75,24 @@ def test_withheld_panel_times_out_and_next_draw_is_exact(dpp, precision, hermiti
     assert r2["status"] & (_lib.DPP_RES_TIMEOUT | _lib.DPP_RES_NONFINITE) == 0, r2
     tol = 1e-10 if precision == "fp64" else 1e-6
     compare_draw(s2.keep.cpu().numpy(), r2["logp"], None, ref, u, logp_rtol=tol)
+
+
+def test_withheld_block_complex_lu_times_out_and_next_draw_is_exact(dpp):
+    """The complex LU path: CTA 0 never publishes its outer block, the other
+    CTAs' waits run out after 5 ms, and the next draw is the oracle's."""
+    import torch
+    from paper_1905_00165_gb300 import _lib
+    n = 500
+    K, _ = W.lu_similarity_kernel(n, seed=19, complex_=True)
+    Kd = torch.from_numpy(K).cuda()
+    s, dt = _withheld(dpp, lambda: dpp.sample_lu(Kd, seed=2, precision="3xtf32"))
+    r = s.result()
+    assert r["status"] & _lib.DPP_RES_TIMEOUT, r
+    assert dt < 10.0, dt
+    u = O.uniforms(2, 0, n)
+    ref = O.sample_lu(K, u)
+    s2 = dpp.sample_lu(Kd, seed=2, precision="3xtf32")
+    torch.cuda.synchronize()
+    r2 = s2.result()
+    assert r2["status"] & (_lib.DPP_RES_TIMEOUT | _lib.DPP_RES_NONFINITE) == 0, r2
+    compare_draw(s2.keep.cpu().numpy(), r2["logp"], None, ref, u, logp_rtol=1e-6)

@@ -186,23 +186,27 @@ def aztec_kasteleyn(d: int):
     return Kast, np.array(edges, dtype=np.int64)
 
 
-def aztec_kernel(d: int, device: Optional[str] = None):
+def aztec_kernel(d: int, device: Optional[str] = None, return_torch: bool = False):
     """(K, edges, n_black): the edge-inclusion kernel of uniform domino
     tilings of the Aztec diamond of order d (n = 4 d^2 edges, complex,
     non-Hermitian, rank d (d + 1)). K[e, e'] = Kast(b, w) Kast^{-1}(w, b');
     every principal minor is an inclusion probability (Kenyon), every draw a
     perfect matching of probability 2^{-d (d + 1) / 2}. The inverse is taken
-    with torch on ``device`` when given (a library routine; rounding only)."""
+    with torch on ``device`` when given (a library routine; rounding only);
+    ``return_torch`` then returns K on the device with column-major storage."""
     Kast, edges = aztec_kasteleyn(d)
     b, w = edges[:, 0], edges[:, 1]
     wt = Kast[b, w]
     if device is not None and device != "cpu":
         import torch
-        Ki = torch.linalg.inv(torch.from_numpy(Kast).to(device))
+        KiT = torch.linalg.inv(torch.from_numpy(Kast).to(device)).T
         bi = torch.from_numpy(b).to(device)
         wi_ = torch.from_numpy(w).to(device)
-        K = torch.from_numpy(wt).to(device)[:, None] * Ki[wi_][:, bi]
-        return K.cpu().numpy(), edges, Kast.shape[0]
+        # K^T[e', e] = Kast^{-1}(w_e, b_e') Kast(b_e, w_e), stored row-major
+        Kt = KiT[bi][:, wi_] * torch.from_numpy(wt).to(device)[None, :]
+        if return_torch:
+            return Kt.t(), edges, Kast.shape[0]
+        return Kt.t().cpu().numpy(), edges, Kast.shape[0]
     Ki = np.linalg.inv(Kast)
     K = wt[:, None] * Ki[w][:, b]
     return K, edges, Kast.shape[0]
