@@ -471,7 +471,39 @@ def run_suite(args):
                       "last_draw_status": res["status"]})
                 del ws
                 torch.cuda.empty_cache()
-            del Kd
+            # several mixed draws in flight, each launch on a quarter of the SMs
+            nst = 4
+            sms = torch.cuda.get_device_properties(dev).multi_processor_count
+            old_cap = _lib.get_tuning(_lib.DPP_TUNE_MAX_CTAS)
+            _lib.set_tuning(_lib.DPP_TUNE_MAX_CTAS, max(8, sms // nst))
+            try:
+                prec = dpp.PRECISIONS["3xtf32"]
+                need = dpp.workspace_size(1, n, 1, prec, 0)
+                streams = [torch.cuda.Stream(dev) for _ in range(nst)]
+                bufs = [(torch.empty(need, dtype=torch.uint8, device=dev),
+                         torch.empty(n, dtype=torch.uint8, device=dev),
+                         torch.zeros(_lib.RESULT_BYTES, dtype=torch.uint8, device=dev))
+                        for _ in range(nst)]
+
+                def fs(seed, i):
+                    ws, keep, raw = bufs[i]
+                    _lib.check(L.dpp_sample_lu(Kd.data_ptr(), n, n, 1, prec, seed, 0, None,
+                                               keep.data_ptr(), None, None, raw.data_ptr(),
+                                               ws.data_ptr(), need, streams[i].cuda_stream))
+                for i in range(nst):
+                    fs(10**6 + i, i)
+                torch.cuda.synchronize()
+                draws = 16
+                t0 = time.perf_counter()
+                for dd in range(draws):
+                    fs(dd, dd % nst)
+                torch.cuda.synchronize()
+                ms = (time.perf_counter() - t0) * 1e3 / draws
+            finally:
+                _lib.set_tuning(_lib.DPP_TUNE_MAX_CTAS, old_cap)
+            line("A", dict(cfg, streams=nst), "3xtf32", ms, 8 * n ** 3 / 3, {},
+                 {"timing": "wall clock over all streams, after a device synchronize"})
+            del bufs, Kd
             torch.cuda.empty_cache()
 
     if want("A"):
@@ -524,8 +556,11 @@ def run_case(args):
             fn = lambda s: dpp.sample_lu(Kd, seed=s, precision=prec)
         elif args.case == "aztec":
             # the Aztec diamond whose edge count 4 d^2 is closest to --n
+            # (built on the host: under a profiler torch's device linear algebra
+            # may be unavailable)
             d = max(1, int(round((n / 4) ** 0.5)))
-            Kd, _, _ = W.aztec_kernel(d, device=str(dev), return_torch=True)
+            K, _, _ = W.aztec_kernel(d)
+            Kd = torch.from_numpy(np.ascontiguousarray(K.T)).to(dev).t()
             n = Kd.shape[0]
             fn = lambda s: dpp.sample_lu(Kd, seed=s, precision=prec)
         else:

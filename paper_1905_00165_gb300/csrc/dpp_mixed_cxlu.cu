@@ -96,6 +96,17 @@ __device__ __forceinline__ double2 drecip(double2 a) {
   return make_double2(ar / den, -ai / den);
 }
 __device__ __forceinline__ double2 tod(cf a) { return make_double2((double)a.x, (double)a.y); }
+// 1 / a in FP32, scaled so that tiny pivots neither underflow nor overflow
+// (the FP64 pipe of this GPU is narrow: per-thread FP64 divisions in the
+// decision loop cost more than the rest of a step)
+__device__ __forceinline__ cf crecipf(cf a) {
+  const float s = fmaxf(fabsf(a.x), fabsf(a.y));
+  const float is = 1.f / s;
+  const float ar = a.x * is, ai = a.y * is;
+  const float den = 1.f / (s * fmaf(ar, ar, ai * ai));
+  return {ar * den, -ai * den};
+}
+__device__ __forceinline__ float cabsf_(cf a) { return hypotf(a.x, a.y); }
 
 // ---------------------------------------------------------------------------
 // FP64 recompute, complex LU form
@@ -624,13 +635,18 @@ struct XArgs {
 extern __shared__ __align__(16) unsigned char g_x_dyn[];
 
 // CTA 0's per-index state of the diagonal block (after the two planes).
+// Double-float (FP32 pairs) throughout: the decision loop runs on every
+// thread of the CTA, and FP64 instructions issue slowly on this GPU.
 struct XDiag {
-  double u[kXB];
-  double kdr[kXB], kdi[kXB];  // running pivots
-  double ds[kXB];             // band scales
-  double pr[kXB], pi[kXB];    // final pivots
-  double2 pe;
-  float kabs[kXB];
+  double2 pe;                    // a recomputed pivot
+  float uh[kXB], ul[kXB];        // uniforms
+  float krh[kXB], krl[kXB];      // running pivots, real part
+  float kih[kXB], kil[kXB];      // imaginary part
+  float ds[kXB];                 // band scales
+  float prh[kXB], prl[kXB];      // final pivots
+  float pih[kXB], pil[kXB];
+  float kabs[kXB];               // |K_jj|
+  int kpx;                       // decision after a recompute
   unsigned char kp[kXB];
 };
 constexpr size_t kXPlane = sizeof(float) * kXB * kXBp;
@@ -684,54 +700,72 @@ __device__ __noinline__ void xl_diag_block(const XArgs& a) {
   }
   for (int j = tid; j < kb; j += kXT) {
     const int64_t i = q + j;
-    S.u[j] = a.uniforms ? a.uniforms[i] : philox_uniform(a.seed, a.inst, (uint64_t)i);
+    // (a given uniform is clamped to +-1e30, which decides like +-infinity
+    // against any finite FP32 pivot and keeps the double-float finite)
+    double ud = a.uniforms ? a.uniforms[i] : philox_uniform(a.seed, a.inst, (uint64_t)i);
+    ud = fmin(fmax(ud, -1e30), 1e30);
+    const f2 u = f2_from_double(ud);
     const double2 k = a.kd[i];
-    S.kdr[j] = k.x;
-    S.kdi[j] = k.y;
-    S.ds[j] = a.s[i];
+    const f2 kr = f2_from_double(k.x), ki = f2_from_double(k.y);
+    S.uh[j] = u.hi;
+    S.ul[j] = u.lo;
+    S.krh[j] = kr.hi;
+    S.krl[j] = kr.lo;
+    S.kih[j] = ki.hi;
+    S.kil[j] = ki.lo;
+    S.ds[j] = (float)a.s[i];
     S.kabs[j] = (float)dabs(a.K[i + i * a.ldk]);
   }
   __syncthreads();
   int border = 0, rc_failed = 0, seq = 0;
   float max_ratio = 0.f;
   for (int j = 0; j < kb; ++j) {
-    const double uj = S.u[j];
-    const double2 ph = make_double2(S.kdr[j], S.kdi[j]);
-    const double tau =
-        (double)a.tau0 * sqrt((double)(q + j + 1)) * ((double)S.kabs[j] + S.ds[j]) + 0x1.0p-22;
-    double2 pe = ph;
-    // every thread takes the same test on the same shared values
-    if (fabs(uj - ph.x) <= tau) {
-      __threadfence();  // the factor entries stored so far, before the request
+    f2 pr = make_f2(S.krh[j], S.krl[j]), pim = make_f2(S.kih[j], S.kil[j]);
+    const float uh = S.uh[j], ul = S.ul[j];
+    const float tau = a.tau0 * sqrtf((float)(q + j + 1)) * (S.kabs[j] + S.ds[j]) + 0x1.0p-22f;
+    // u - Re d in double-float (exact where the two are close); every thread
+    // takes the same test on the same shared values
+    const float du = (uh - pr.hi) + (ul - pr.lo);
+    bool kp = du < 0.f;
+    if (fabsf(du) <= tau) {
+      // the pivots so far, out to global memory for the recompute
+      for (int c = tid; c < j; c += kXT)
+        a.piv[q + c] = make_double2(f2_to_double(make_f2(S.prh[c], S.prl[c])),
+                                    f2_to_double(make_f2(S.pih[c], S.pil[c])));
+      __threadfence();  // with the factor entries stored so far, before the request
       __syncthreads();
       if (wp == 0) {
+        const double2 ph = make_double2(f2_to_double(pr), f2_to_double(pim));
+        const double ud = (double)uh + (double)ul;
         double2 p2 = ph;
         double est = 0.0;
         const bool ok = xl_leader(a.xr, q + j, a.epoch, &seq, &p2, &est);
         if (lane == 0) {
           S.pe = ok ? p2 : ph;
+          S.kpx = ud < (ok ? p2.x : ph.x) ? 1 : 0;
           border += 1;
-          const float ratio = (float)(dabs(dsub(p2, ph)) / tau);
+          const float ratio = (float)(dabs(dsub(p2, ph)) / (double)tau);
           if (ok && ratio > max_ratio) max_ratio = ratio;
-          if (!ok || est > fabs(uj - p2.x)) rc_failed = 1;
+          if (!ok || est > fabs(ud - p2.x)) rc_failed = 1;
         }
       }
       __syncthreads();
-      pe = S.pe;
+      pr = f2_from_double(S.pe.x);
+      pim = f2_from_double(S.pe.y);
+      kp = S.kpx != 0;
     }
-    const bool kp = uj < pe.x;
-    if (!kp) pe.x -= 1.0;
-    const double2 rpd = drecip(pe);
-    const cf rp = cmk((float)rpd.x, (float)rpd.y);
+    if (!kp) pr = f2_add_f(pr, -1.f);
+    const cf rp = crecipf(cmk(pr.hi, pim.hi));
     if (tid == 0) {
-      a.piv[q + j] = pe;
       a.keep[q + j] = kp ? 1 : 0;
-      S.pr[j] = pe.x;
-      S.pi[j] = pe.y;
+      S.prh[j] = pr.hi;
+      S.prl[j] = pr.lo;
+      S.pih[j] = pim.hi;
+      S.pil[j] = pim.lo;
       S.kp[j] = kp ? 1 : 0;
       const int64_t o = (q + j) * (1 + lda);
-      Ar[o] = (float)pe.x;
-      Ai[o] = (float)pe.y;
+      Ar[o] = pr.hi;
+      Ai[o] = pim.hi;
     }
     const int m = kb - j - 1;
     // column j of L and row j of U~ out; the running pivots of the later indices
@@ -745,10 +779,17 @@ __device__ __noinline__ void xl_diag_block(const XArgs& a) {
       Ai[oc] = l.y;
       Ar[orow] = ut.x;
       Ai[orow] = ut.y;
-      const double2 pr = dmul(tod(l), tod(ujk));  // d_k -= L(k, j) U(j, k)
-      S.kdr[k] -= pr.x;
-      S.kdi[k] -= pr.y;
-      S.ds[k] += dabs(pr);
+      // d_k -= L(k, j) U(j, k), the products formed exactly
+      f2 kr = make_f2(S.krh[k], S.krl[k]), ki = make_f2(S.kih[k], S.kil[k]);
+      kr = f2_sub_prod(kr, l.x, ujk.x);
+      kr = f2_add_prod(kr, l.y, ujk.y);
+      ki = f2_sub_prod(ki, l.x, ujk.y);
+      ki = f2_sub_prod(ki, l.y, ujk.x);
+      S.krh[k] = kr.hi;
+      S.krl[k] = kr.lo;
+      S.kih[k] = ki.hi;
+      S.kil[k] = ki.lo;
+      S.ds[k] += cabsf_(l) * cabsf_(ujk);
     }
     // the rest of the block: B[i][k] -= L(i, j) U(j, k), i, k > j
     {
@@ -770,7 +811,9 @@ __device__ __noinline__ void xl_diag_block(const XArgs& a) {
   double lp = 0.0;
   int kept = 0, oor = 0, bad = 0;
   for (int j = tid; j < kb; j += kXT) {
-    const double2 d = make_double2(S.pr[j], S.pi[j]);
+    const double2 d = make_double2(f2_to_double(make_f2(S.prh[j], S.prl[j])),
+                                   f2_to_double(make_f2(S.pih[j], S.pil[j])));
+    a.piv[q + j] = d;
     const double2 pre = S.kp[j] ? d : make_double2(d.x + 1.0, d.y);
     lp += log(dabs(d));
     kept += S.kp[j];
@@ -867,9 +910,10 @@ __device__ __noinline__ void xl_tiles(const XArgs& a) {
   const float* Ar = a.Ar;
   const float* Ai = a.Ai;
   for (int c = tid; c < kb; c += kXT) {
-    const double2 r = drecip(a.piv[q + c]);
-    rdr[c] = (float)r.x;
-    rdi[c] = (float)r.y;
+    const double2 d = a.piv[q + c];
+    const cf r = crecipf(cmk((float)d.x, (float)d.y));
+    rdr[c] = r.x;
+    rdi[c] = r.y;
   }
   const int64_t ntiles = (n - qe + 31) / 32;
   for (int64_t tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
@@ -929,7 +973,9 @@ __device__ __noinline__ void xl_tiles(const XArgs& a) {
       __syncthreads();
       if (nc > 0) {
         // S[r][C0 + j] -= sum_c0 S[r][D + c0] P[c0][j]; rows 4 ty.., columns tx + 32 jj
+        // for the ncj 32-column chunks that exist
         const int ty = wp, tx = lane;
+        const int ncj = (nc + 31) >> 5;
 #pragma unroll 1
         for (int side = 0; side < 2; ++side) {
           float* Sr = side ? Zr : Xr;
@@ -949,13 +995,13 @@ __device__ __noinline__ void xl_tiles(const XArgs& a) {
               w[i] = cmk(Sr[(4 * ty + i) * kXBp + D + c0], Si[(4 * ty + i) * kXBp + D + c0]);
 #pragma unroll
             for (int jj = 0; jj < 3; ++jj) {
-              const int j = tx + 32 * jj;
-              m[jj] = j < nc ? cmk(Or[c0 * kXPc + j], Oi[c0 * kXPc + j]) : cmk(0.f, 0.f);
+              if (jj < ncj) {
+                const int j = tx + 32 * jj;
+                m[jj] = j < nc ? cmk(Or[c0 * kXPc + j], Oi[c0 * kXPc + j]) : cmk(0.f, 0.f);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc[i][jj] = cfma(acc[i][jj], w[i], m[jj]);
+              }
             }
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-              for (int jj = 0; jj < 3; ++jj) acc[i][jj] = cfma(acc[i][jj], w[i], m[jj]);
           }
 #pragma unroll
           for (int i = 0; i < 4; ++i)
@@ -1003,31 +1049,35 @@ __device__ __noinline__ void xl_tiles(const XArgs& a) {
     }
     // running pivots and band scales: eight lanes per index, fixed-order tree
     {
+      // (double-float sums of the exact FP32 products; the FP64 pipe is narrow)
       const int r = tid >> 3, part = tid & 7;
-      double2 acc = make_double2(0.0, 0.0);
-      double ssum = 0.0;
+      f2 ax = make_f2(0.f, 0.f), ay = make_f2(0.f, 0.f);
+      float ssum = 0.f;
       for (int c = part; c < kb; c += 8) {
         const cf w = cmk(Xr[r * kXBp + c], Xi[r * kXBp + c]);
         const cf mv = cmul(cmk(Zr[r * kXBp + c], Zi[r * kXBp + c]), cmk(rdr[c], rdi[c]));
-        const double2 pr = dmul(tod(w), tod(mv));
-        acc = dadd(acc, pr);
-        ssum += dabs(pr);
+        ax = f2_add_prod(ax, w.x, mv.x);
+        ax = f2_add_prod(ax, -w.y, mv.y);
+        ay = f2_add_prod(ay, w.x, mv.y);
+        ay = f2_add_prod(ay, w.y, mv.x);
+        ssum += cabsf_(w) * cabsf_(mv);
       }
 #pragma unroll
       for (int o = 4; o > 0; o >>= 1) {
-        const double ox = __shfl_down_sync(kXF, acc.x, o), oy = __shfl_down_sync(kXF, acc.y, o);
-        const double os = __shfl_down_sync(kXF, ssum, o);
+        const f2 ox = make_f2(__shfl_down_sync(kXF, ax.hi, o), __shfl_down_sync(kXF, ax.lo, o));
+        const f2 oy = make_f2(__shfl_down_sync(kXF, ay.hi, o), __shfl_down_sync(kXF, ay.lo, o));
+        const float os = __shfl_down_sync(kXF, ssum, o);
         if (part < o) {
-          acc.x += ox;
-          acc.y += oy;
+          ax = f2_add(ax, ox);
+          ay = f2_add(ay, oy);
           ssum += os;
         }
       }
       if (part == 0 && r < nr) {
         const int64_t i = i0 + r;
         const double2 k = a.kd[i];
-        a.kd[i] = dsub(k, acc);
-        a.s[i] += ssum;
+        a.kd[i] = make_double2(k.x - f2_to_double(ax), k.y - f2_to_double(ay));
+        a.s[i] += (double)ssum;
       }
     }
     __syncthreads();
