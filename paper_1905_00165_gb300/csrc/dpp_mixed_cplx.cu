@@ -168,7 +168,8 @@ __device__ __noinline__ bool cx_serve(const CxRc& c, unsigned id) {
       cf acc[32];
 #pragma unroll
       for (int k = 0; k < 32; ++k) acc[k] = mkc(0.f, 0.f);
-      for (int64_t s = t + 1 + wp; s < nblk; s += 8) {
+      for (int64_t s = t + 1 + wp + (t + 1 + wp < nblk ? ((nblk - 2 - t - wp) / 8) * 8 : 0);
+         s > t && s < nblk; s -= 8) {  // latest-published source last
         const int ns = (int)((g - 32 * s) < 32 ? (g - 32 * s) : 32);
         cf tile[32];
 #pragma unroll

@@ -101,9 +101,9 @@ __device__ __forceinline__ double2 tod(cf a) { return make_double2((double)a.x, 
 // decision loop cost more than the rest of a step)
 __device__ __forceinline__ cf crecipf(cf a) {
   const float s = fmaxf(fabsf(a.x), fabsf(a.y));
-  const float is = 1.f / s;
+  const float is = __frcp_rn(s);
   const float ar = a.x * is, ai = a.y * is;
-  const float den = 1.f / (s * fmaf(ar, ar, ai * ai));
+  const float den = __frcp_rn(s * fmaf(ar, ar, ai * ai));
   return {ar * den, -ai * den};
 }
 __device__ __forceinline__ float cabsf_(cf a) { return hypotf(a.x, a.y); }
@@ -232,7 +232,8 @@ __device__ __forceinline__ void xl_r1_block(const XRc& X, float* inv, unsigned l
   if (TRANS) {
     // lane = column 32 t + lane: F(32 s + k, 32 t + lane) = A[(32 t + lane) + (32 s + k) lda]
     cf acc = cmk(0.f, 0.f);
-    for (int64_t s = t + 1 + wp; s < nblk; s += 8) {
+    for (int64_t s = t + 1 + wp + (t + 1 + wp < nblk ? ((nblk - 2 - t - wp) / 8) * 8 : 0);
+         s > t && s < nblk; s -= 8) {  // latest-published source last
       const int ns = (int)((g - 32 * s) < 32 ? (g - 32 * s) : 32);
       cf v[32];
 #pragma unroll
@@ -253,7 +254,8 @@ __device__ __forceinline__ void xl_r1_block(const XRc& X, float* inv, unsigned l
     for (int h = 0; h < 2; ++h)
 #pragma unroll
       for (int k = 0; k < 16; ++k) acc[h][k] = cmk(0.f, 0.f);
-    for (int64_t s = t + 1 + wp; s < nblk; s += 8) {
+    for (int64_t s = t + 1 + wp + (t + 1 + wp < nblk ? ((nblk - 2 - t - wp) / 8) * 8 : 0);
+         s > t && s < nblk; s -= 8) {  // latest-published source last
       const int ns = (int)((g - 32 * s) < 32 ? (g - 32 * s) : 32);
       cf xs = cmk(0.f, 0.f);
       *live = __all_sync(kXF, *live);  // warp-uniform before the collective wait
@@ -791,17 +793,33 @@ __device__ __noinline__ void xl_diag_block(const XArgs& a) {
       S.kil[k] = ki.lo;
       S.ds[k] += cabsf_(l) * cabsf_(ujk);
     }
-    // the rest of the block: B[i][k] -= L(i, j) U(j, k), i, k > j
+    // the rest of the block: B[i][k] -= L(i, j) U(j, k), i, k > j; warp w
+    // takes rows j + 1 + w + 8 r, lane l the columns j + 1 + l + 32 c (four
+    // independent updates per row)
     {
-      const int cidx = tid & 127, rh = tid >> 7;
-      if (cidx < m) {
-        const int k = j + 1 + cidx;
-        const cf ujk = cmk(Br[j * kXBp + k], Bi[j * kXBp + k]);
-        for (int i = j + 1 + rh; i < kb; i += 2) {
-          const cf l = cmul(cmk(Br[i * kXBp + j], Bi[i * kXBp + j]), rp);
-          const cf v = cfms(cmk(Br[i * kXBp + k], Bi[i * kXBp + k]), l, ujk);
-          Br[i * kXBp + k] = v.x;
-          Bi[i * kXBp + k] = v.y;
+      const int nc = (m + 31) >> 5;
+      cf uk[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int k = j + 1 + lane + 32 * c;
+        uk[c] = (c < nc && k < kb) ? cmk(Br[j * kXBp + k], Bi[j * kXBp + k]) : cmk(0.f, 0.f);
+      }
+#pragma unroll 2
+      for (int i = j + 1 + wp; i < kb; i += 8) {
+        const cf l = cmul(cmk(Br[i * kXBp + j], Bi[i * kXBp + j]), rp);
+        float* br = Br + i * kXBp + j + 1 + lane;
+        float* bi = Bi + i * kXBp + j + 1 + lane;
+        cf v[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          v[c] = (c < nc && j + 1 + lane + 32 * c < kb) ? cmk(br[32 * c], bi[32 * c]) : cmk(0.f, 0.f);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          if (c < nc && j + 1 + lane + 32 * c < kb) {
+            const cf w = cfms(v[c], l, uk[c]);
+            br[32 * c] = w.x;
+            bi[32 * c] = w.y;
+          }
         }
       }
     }

@@ -164,7 +164,8 @@ __device__ __forceinline__ void lu_r1_block(const RecomputeArgs& a, float* inv,
   if (TRANS) {
     // lane = column of block t: F(32 s + k, 32 t + lane) = A[(32 t + lane) + (32 s + k) lda]
     float acc = 0.f;
-    for (int64_t s = t + 1 + wp; s < nblk; s += 8) {
+    for (int64_t s = t + 1 + wp + (t + 1 + wp < nblk ? ((nblk - 2 - t - wp) / 8) * 8 : 0);
+         s > t && s < nblk; s -= 8) {  // latest-published source last
       const int ns = (int)((g - 32 * s) < 32 ? (g - 32 * s) : 32);
       const float* cp = A + (32 * t + lane) + 32 * s * lda;
       float v[32];
@@ -182,7 +183,8 @@ __device__ __forceinline__ void lu_r1_block(const RecomputeArgs& a, float* inv,
     float acc[32];
 #pragma unroll
     for (int c = 0; c < 32; ++c) acc[c] = 0.f;
-    for (int64_t s = t + 1 + wp; s < nblk; s += 8) {
+    for (int64_t s = t + 1 + wp + (t + 1 + wp < nblk ? ((nblk - 2 - t - wp) / 8) * 8 : 0);
+         s > t && s < nblk; s -= 8) {  // latest-published source last
       const int ns = (int)((g - 32 * s) < 32 ? (g - 32 * s) : 32);
       const float* tp = A + (32 * s + lane) + 32 * t * lda;
       float tile[32];
