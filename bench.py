@@ -65,6 +65,8 @@ def parse():
                    help="with --case: DPP_TUNE_PANEL_PIPELINE for the draws (-1: default)")
     p.add_argument("--update-variant", type=int, default=-1,
                    help="with --case: DPP_TUNE_UPDATE_VARIANT for the draws (-1: default)")
+    p.add_argument("--host-inputs", action="store_true",
+                   help="with --case herm/cplx: build the kernel with numpy on the host")
     p.add_argument("--case", default="",
                    choices=["", "herm", "lu", "cplx", "aztec", "batched", "adjoint"],
                    help="run one path alone (a small loop for profiling): mixed Hermitian, "
@@ -563,6 +565,12 @@ def run_case(args):
             Kd = torch.from_numpy(np.ascontiguousarray(K.T)).to(dev).t()
             n = Kd.shape[0]
             fn = lambda s: dpp.sample_lu(Kd, seed=s, precision=prec)
+        elif args.host_inputs:
+            # numpy on the host (under a profiler torch's device linear algebra may
+            # be unavailable)
+            K = W.hermitian_kernel(n, seed=0, kind=args.kind, complex_=args.case == "cplx")
+            Kd = torch.from_numpy(np.ascontiguousarray(K.T)).to(dev).t()
+            fn = lambda s: dpp.sample_hermitian(Kd, seed=s, precision=prec)
         else:
             Kd = W.hermitian_kernel(n, seed=0, kind=args.kind, complex_=args.case == "cplx",
                                     device=str(dev), return_torch=True)

@@ -220,6 +220,20 @@ __device__ inline bool wait_geq(const unsigned* flag, unsigned target,
   }
 }
 
+// Asynchronous 4-byte global -> shared copies (cp.async): every copy of a
+// staging loop is in flight at once instead of one dependent load at a time.
+// A copy with valid == false writes zero and reads nothing (gmem must still be
+// a valid address).
+__device__ __forceinline__ void cp_async4(float* smem, const float* gmem, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(sa), "l"(gmem),
+               "r"(valid ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Status word that any kernel may OR bits into.
 __device__ inline void flag_status(dpp_result* r, int bits) { atomicOr(&r->status, bits); }
 

@@ -697,9 +697,10 @@ __device__ __noinline__ void xl_diag_block(const XArgs& a) {
   for (int idx = tid; idx < kb * kb; idx += kXT) {
     const int r = idx % kb, c = idx / kb;
     const int64_t o = (q + r) + (q + c) * lda;
-    Br[r * kXBp + c] = __ldcg(Ar + o);
-    Bi[r * kXBp + c] = __ldcg(Ai + o);
+    cp_async4(&Br[r * kXBp + c], Ar + o, true);
+    cp_async4(&Bi[r * kXBp + c], Ai + o, true);
   }
+  cp_async_commit();
   for (int j = tid; j < kb; j += kXT) {
     const int64_t i = q + j;
     // (a given uniform is clamped to +-1e30, which decides like +-infinity
@@ -718,6 +719,7 @@ __device__ __noinline__ void xl_diag_block(const XArgs& a) {
     S.ds[j] = (float)a.s[i];
     S.kabs[j] = (float)dabs(a.K[i + i * a.ldk]);
   }
+  cp_async_wait_all();
   __syncthreads();
   int border = 0, rc_failed = 0, seq = 0;
   float max_ratio = 0.f;
@@ -939,29 +941,32 @@ __device__ __noinline__ void xl_tiles(const XArgs& a) {
     const int nr = (int)((n - i0) < 32 ? (n - i0) : 32);
     for (int idx = tid; idx < 32 * kb; idx += kXT) {
       const int r = idx & 31, c = idx >> 5;
-      const int64_t o = (i0 + r) + (q + c) * lda;
-      Xr[r * kXBp + c] = r < nr ? __ldcg(Ar + o) : 0.f;
-      Xi[r * kXBp + c] = r < nr ? __ldcg(Ai + o) : 0.f;
+      const int64_t o = r < nr ? (i0 + r) + (q + c) * lda : 0;
+      cp_async4(&Xr[r * kXBp + c], Ar + o, r < nr);
+      cp_async4(&Xi[r * kXBp + c], Ai + o, r < nr);
     }
     for (int idx = tid; idx < 32 * kb; idx += kXT) {
       const int c = idx % kb, r = idx / kb;
-      const int64_t o = (q + c) + (i0 + r) * lda;
-      Zr[r * kXBp + c] = r < nr ? __ldcg(Ar + o) : 0.f;
-      Zi[r * kXBp + c] = r < nr ? __ldcg(Ai + o) : 0.f;
+      const int64_t o = r < nr ? (q + c) + (i0 + r) * lda : 0;
+      cp_async4(&Zr[r * kXBp + c], Ar + o, r < nr);
+      cp_async4(&Zi[r * kXBp + c], Ai + o, r < nr);
     }
+    cp_async_commit();
     for (int pk = 0; pk < np; ++pk) {
       const int D = 32 * pk;
       const int b = (kb - D) < 32 ? (kb - D) : 32;
       for (int idx = tid; idx < 1024; idx += kXT) {
         const int c = idx >> 5, c0 = idx & 31;
         const bool in = c < b && c0 < c;
-        const int64_t ou = (q + D + c0) + (q + D + c) * lda;  // U~(D + c0, D + c)
-        const int64_t ol = (q + D + c) + (q + D + c0) * lda;  // L(D + c, D + c0)
-        Tur[c * 33 + c0] = in ? __ldcg(Ar + ou) : 0.f;
-        Tui[c * 33 + c0] = in ? __ldcg(Ai + ou) : 0.f;
-        Tlr[c * 33 + c0] = in ? __ldcg(Ar + ol) : 0.f;
-        Tli[c * 33 + c0] = in ? __ldcg(Ai + ol) : 0.f;
+        const int64_t ou = in ? (q + D + c0) + (q + D + c) * lda : 0;  // U~(D + c0, D + c)
+        const int64_t ol = in ? (q + D + c) + (q + D + c0) * lda : 0;  // L(D + c, D + c0)
+        cp_async4(&Tur[c * 33 + c0], Ar + ou, in);
+        cp_async4(&Tui[c * 33 + c0], Ai + ou, in);
+        cp_async4(&Tlr[c * 33 + c0], Ar + ol, in);
+        cp_async4(&Tli[c * 33 + c0], Ai + ol, in);
       }
+      cp_async_commit();
+      cp_async_wait_all();
       __syncthreads();
       {
         int rows[8];
@@ -977,16 +982,18 @@ __device__ __noinline__ void xl_tiles(const XArgs& a) {
       if (nc > 0) {
         for (int idx = tid; idx < 32 * nc; idx += kXT) {
           const int c0 = idx & 31, j = idx >> 5;
-          const int64_t o = (q + D + c0) + (q + C0 + j) * lda;  // U~(D + c0, C0 + j)
-          Pr[c0 * kXPc + j] = c0 < b ? __ldcg(Ar + o) : 0.f;
-          Pi[c0 * kXPc + j] = c0 < b ? __ldcg(Ai + o) : 0.f;
+          const int64_t o = c0 < b ? (q + D + c0) + (q + C0 + j) * lda : 0;  // U~(D + c0, C0 + j)
+          cp_async4(&Pr[c0 * kXPc + j], Ar + o, c0 < b);
+          cp_async4(&Pi[c0 * kXPc + j], Ai + o, c0 < b);
         }
         for (int idx = tid; idx < 32 * nc; idx += kXT) {
           const int j = idx % nc, c0 = idx / nc;
-          const int64_t o = (q + C0 + j) + (q + D + c0) * lda;  // L(C0 + j, D + c0)
-          Qr[c0 * kXPc + j] = c0 < b ? __ldcg(Ar + o) : 0.f;
-          Qi[c0 * kXPc + j] = c0 < b ? __ldcg(Ai + o) : 0.f;
+          const int64_t o = c0 < b ? (q + C0 + j) + (q + D + c0) * lda : 0;  // L(C0 + j, D + c0)
+          cp_async4(&Qr[c0 * kXPc + j], Ar + o, c0 < b);
+          cp_async4(&Qi[c0 * kXPc + j], Ai + o, c0 < b);
         }
+        cp_async_commit();
+        cp_async_wait_all();
       }
       __syncthreads();
       if (nc > 0) {

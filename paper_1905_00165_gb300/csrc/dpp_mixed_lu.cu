@@ -1307,13 +1307,19 @@ __global__ void __launch_bounds__(kLuThreads, 1) k_lu_outer(LuArgs a) {
 // tensor-core splits, and subtracts sum_c W M from each running diagonal.
 constexpr int kBR = 32;  // indices per CTA of k_below
 
-constexpr int kBelowLdp = kNB + 4;  // row length of the staged panel operands
+// row length of the staged panel operands (odd: the transposing fill and the
+// product's row reads are both free of bank conflicts)
+constexpr int kBelowLdp = kNB + 1;
 
+// (double-buffered panel operands: the next panel's arrive by cp.async while
+// this panel's product runs)
 inline size_t below_smem(bool sym) {
   const size_t x = sizeof(float) * kBR * (kNB + 1);
-  const size_t ps = sizeof(float) * 32 * kBelowLdp;
-  return (sym ? x : 2 * x) + (sym ? ps : 2 * ps) + sizeof(float) * (2 * 32 * 33 + 32 + kNB);
+  const size_t ps = 2 * sizeof(float) * 32 * kBelowLdp;
+  const size_t t = 2 * sizeof(float) * 32 * 33;
+  return (sym ? x + ps + t : 2 * (x + ps + t)) + sizeof(float) * (2 * 32 + kNB + 3 * 256);
 }
+
 
 // Substitution of R rows of one side against the panel's 32 x 32 unit lower
 // block T (row c, column c' < c), the rows interleaved so that their chains
@@ -1345,14 +1351,15 @@ __global__ void __launch_bounds__(kLuThreads) k_below(LuArgs a) {
   constexpr int ldx = kNB + 1;
   float* X = reinterpret_cast<float*>(g_lu_dyn);   // [kBR][ldx]: A rows, then W
   float* Zs = SYM ? X : X + kBR * ldx;             // [kBR][ldx]: A columns, then M (LU)
-  // [32][kBelowLdp], panel column t by outer-block index j: M (and, for LU, W)
-  // of the outer block's rows, 16-byte aligned rows for vector loads
-  float* Ps = (SYM ? X : Zs) + kBR * ldx;
-  float* Qs = SYM ? Ps : Ps + 32 * kBelowLdp;
-  float* T11 = Qs + 32 * kBelowLdp;                // [32][33]: M of the panel's diagonal block
-  float* U11 = T11 + 32 * 33;                      // [32][33]: L of it (LU)
-  float* rdp = U11 + 32 * 33;                      // [32]: 1 / d of the panel
-  float* rda = rdp + 32;                           // [kNB]: 1 / d of the outer block
+  // [2][32][kBelowLdp], panel column t by outer-block index j: M (and, for LU,
+  // W) of the outer block's rows, 16-byte aligned rows for vector loads
+  float* Ps0 = (SYM ? X : Zs) + kBR * ldx;
+  float* Qs0 = SYM ? Ps0 : Ps0 + 2 * 32 * kBelowLdp;
+  float* T0 = Qs0 + 2 * 32 * kBelowLdp;            // [2][32][33]: M of the panel's diagonal block
+  float* U0 = SYM ? T0 : T0 + 2 * 32 * 33;          // [2][32][33]: L of it (LU)
+  float* rdp0 = U0 + 2 * 32 * 33;                  // [2][32]: 1 / d of the panel
+  float* rda = rdp0 + 2 * 32;                      // [kNB]: 1 / d of the outer block
+  float* red = rda + kNB;                          // [3][8][32]: running-diagonal partials
   const int tid = threadIdx.x, wp = tid >> 5;
   const int kb = a.kb, np = (kb + 31) / 32;
   const int64_t q = a.q, qe = q + kb, n = a.n, lda = a.lda;
@@ -1361,38 +1368,63 @@ __global__ void __launch_bounds__(kLuThreads) k_below(LuArgs a) {
   const int ty = tid >> 5, tx = tid & 31;  // update: rows 4 ty.., columns 4 tx.. of a 128-wide chunk
   for (int64_t i0 = qe + (int64_t)kBR * blockIdx.x; i0 < n; i0 += (int64_t)kBR * gridDim.x) {
     const int nr = (int)((n - i0) < kBR ? (n - i0) : kBR);
+    // the rows (and, for LU, columns) by cp.async: every load in flight at once
     for (int idx = tid; idx < kBR * kb; idx += kLuThreads) {
       const int r = idx % kBR, c = idx / kBR;
-      X[r * ldx + c] = r < nr ? __ldcg(&A[(i0 + r) + (q + c) * lda]) : 0.f;
+      cp_async4(&X[r * ldx + c], r < nr ? &A[(i0 + r) + (q + c) * lda] : A, r < nr);
     }
     if (!SYM) {
       for (int idx = tid; idx < kBR * kb; idx += kLuThreads) {
         const int c = idx % kb, r = idx / kb;
-        Zs[r * ldx + c] = r < nr ? __ldcg(&A[(q + c) + (i0 + r) * lda]) : 0.f;
+        cp_async4(&Zs[r * ldx + c], r < nr ? &A[(q + c) + (i0 + r) * lda] : A, r < nr);
       }
+    }
+    cp_async_commit();
+    // Panel k's operands (its diagonal block and the M (W) rows of the outer
+    // block for the later columns) go to buffer k & 1 by cp.async, issued
+    // while panel k - 1's product runs; 1 / d through a register.
+    auto issue = [&](int k) {
+      const int64_t p = q + 32 * k;
+      const int b = (int)((qe - p) < 32 ? (qe - p) : 32);
+      const int D = 32 * k, C0 = D + 32, bf = k & 1;
+      float* T11 = T0 + bf * 32 * 33;
+      float* U11 = U0 + bf * 32 * 33;
+      float* Ps = Ps0 + bf * 32 * kBelowLdp;
+      float* Qs = Qs0 + bf * 32 * kBelowLdp;
+      for (int idx = tid; idx < 1024; idx += kLuThreads) {
+        const int rr = idx >> 5, cc = idx & 31;
+        const bool in = rr < b && cc < b && rr > cc;
+        // M(p + rr, p + cc) (LDL^T: L = M) and, for LU, L(p + rr, p + cc)
+        cp_async4(&T11[rr * 33 + cc], in ? (SYM ? &A[(p + rr) + (p + cc) * lda]
+                                                 : &A[(p + cc) + (p + rr) * lda]) : A, in);
+        if (!SYM) cp_async4(&U11[rr * 33 + cc], in ? &A[(p + rr) + (p + cc) * lda] : A, in);
+      }
+      const int cnt = C0 < kb ? (kb - C0) * 32 : 0;
+      for (int idx = tid; idx < cnt; idx += kLuThreads) {
+        const int j = C0 + (idx >> 5), t = idx & 31;
+        const int64_t off = (q + j) * (int64_t)kNB + D + t;
+        cp_async4(&Ps[t * kBelowLdp + j], t < b ? &a.Mk[off] : a.Mk, t < b);
+        if (!SYM) cp_async4(&Qs[t * kBelowLdp + j], t < b ? &a.Wk[off] : a.Wk, t < b);
+      }
+      cp_async_commit();
+      return (tid < 32 && tid < b) ? 1.f / (float)__ldcg(&a.piv[p + tid]) : 0.f;
+    };
+    float rv = issue(0);
+    cp_async_wait_all();
+    if (tid < 32) {
+      rdp0[tid] = rv;
+      rda[tid] = rv;
     }
     __syncthreads();
     for (int k = 0; k < np; ++k) {
       const int64_t p = q + 32 * k;
       const int b = (int)((qe - p) < 32 ? (qe - p) : 32);
-      const int D = 32 * k;
-      for (int idx = tid; idx < 1024; idx += kLuThreads) {
-        const int rr = idx >> 5, cc = idx & 31;
-        const bool in = rr < b && cc < b && rr > cc;
-        const float l = in ? __ldcg(&A[(p + rr) + (p + cc) * lda]) : 0.f;  // L(p + rr, p + cc)
-        if (SYM) {
-          T11[rr * 33 + cc] = l;
-        } else {
-          U11[rr * 33 + cc] = l;
-          T11[rr * 33 + cc] = in ? __ldcg(&A[(p + cc) + (p + rr) * lda]) : 0.f;  // M(p + rr, p + cc)
-        }
-      }
-      if (tid < 32) {
-        const float r = tid < b ? 1.f / (float)__ldcg(&a.piv[p + tid]) : 0.f;
-        rdp[tid] = r;
-        rda[D + tid] = r;
-      }
-      __syncthreads();
+      const int D = 32 * k, bf = k & 1;
+      const float* T11 = T0 + bf * 32 * 33;
+      const float* U11 = U0 + bf * 32 * 33;
+      const float* rdp = rdp0 + bf * 32;
+      const float* Ps = Ps0 + bf * 32 * kBelowLdp;
+      const float* Qs = Qs0 + bf * 32 * kBelowLdp;
       // solves: side 0 (W) and, for LU, side 1 (M = U / d); eight warps
       if (SYM) {
         int rows[4] = {wp, wp + 8, wp + 16, wp + 24};
@@ -1409,61 +1441,65 @@ __global__ void __launch_bounds__(kLuThreads) k_below(LuArgs a) {
         below_solve<8>(Zs, ldx, rows, D, b, U11, rdp);
       }
       __syncthreads();
+      const bool more = k + 1 < np;
+      if (more) rv = issue(k + 1);
       const int C0 = D + 32;
-      if (C0 < kb) {
-        for (int idx = tid; idx < (kb - C0) * 32; idx += kLuThreads) {
-          const int j = C0 + (idx >> 5), t = idx & 31;
-          const int64_t off = (q + j) * (int64_t)kNB + D + t;
-          Ps[t * kBelowLdp + j] = t < b ? __ldcg(&a.Mk[off]) : 0.f;
-          if (!SYM) Qs[t * kBelowLdp + j] = t < b ? __ldcg(&a.Wk[off]) : 0.f;
-        }
-        __syncthreads();
-        // (kb is the full outer block here, a multiple of 32: when jb < kb the
-        // four columns jb..jb+3 all exist)
-        for (int j0 = C0; j0 < kb; j0 += 128) {
-          float ax[4][4], az[4][4];
+      // columns j0 + tx + 32 jj of a 128-wide chunk: consecutive lanes touch
+      // consecutive words (no bank conflicts in the loads or the updates)
+      for (int j0 = C0; j0 < kb; j0 += 128) {
+        float ax[4][4], az[4][4];
 #pragma unroll
-          for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int jj = 0; jj < 4; ++jj) ax[i][jj] = az[i][jj] = 0.f;
-          const int jb = j0 + 4 * tx;
+          for (int jj = 0; jj < 4; ++jj) ax[i][jj] = az[i][jj] = 0.f;
 #pragma unroll 4
-          for (int t = 0; t < 32; ++t) {
-            float w[4];
+        for (int t = 0; t < 32; ++t) {
+          float w[4], m[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) w[i] = X[(4 * ty + i) * ldx + D + t];
-            const float4 m4 = jb < kb ? *reinterpret_cast<const float4*>(&Ps[t * kBelowLdp + jb])
-                                      : make_float4(0.f, 0.f, 0.f, 0.f);
-            const float m[4] = {m4.x, m4.y, m4.z, m4.w};
+          for (int i = 0; i < 4; ++i) w[i] = X[(4 * ty + i) * ldx + D + t];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-              for (int jj = 0; jj < 4; ++jj) ax[i][jj] = fmaf(w[i], m[jj], ax[i][jj]);
-            if (!SYM) {
-              float mr[4];
-#pragma unroll
-              for (int i = 0; i < 4; ++i) mr[i] = Zs[(4 * ty + i) * ldx + D + t];
-              const float4 q4 = jb < kb ? *reinterpret_cast<const float4*>(&Qs[t * kBelowLdp + jb])
-                                        : make_float4(0.f, 0.f, 0.f, 0.f);
-              const float wq[4] = {q4.x, q4.y, q4.z, q4.w};
-#pragma unroll
-              for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int jj = 0; jj < 4; ++jj) az[i][jj] = fmaf(mr[i], wq[jj], az[i][jj]);
-            }
+          for (int jj = 0; jj < 4; ++jj) {
+            const int j = j0 + tx + 32 * jj;
+            m[jj] = j < kb ? Ps[t * kBelowLdp + j] : 0.f;
           }
 #pragma unroll
           for (int i = 0; i < 4; ++i)
 #pragma unroll
+            for (int jj = 0; jj < 4; ++jj) ax[i][jj] = fmaf(w[i], m[jj], ax[i][jj]);
+          if (!SYM) {
+            float mr[4], wq[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) mr[i] = Zs[(4 * ty + i) * ldx + D + t];
+#pragma unroll
             for (int jj = 0; jj < 4; ++jj) {
-              if (jb + jj < kb) {
-                X[(4 * ty + i) * ldx + jb + jj] -= ax[i][jj];
-                if (!SYM) Zs[(4 * ty + i) * ldx + jb + jj] -= az[i][jj];
-              }
+              const int j = j0 + tx + 32 * jj;
+              wq[jj] = j < kb ? Qs[t * kBelowLdp + j] : 0.f;
             }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+              for (int jj = 0; jj < 4; ++jj) az[i][jj] = fmaf(mr[i], wq[jj], az[i][jj]);
+          }
         }
-        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) {
+            const int j = j0 + tx + 32 * jj;
+            if (j < kb) {
+              X[(4 * ty + i) * ldx + j] -= ax[i][jj];
+              if (!SYM) Zs[(4 * ty + i) * ldx + j] -= az[i][jj];
+            }
+          }
       }
+      if (more) {
+        cp_async_wait_all();
+        if (tid < 32) {
+          rdp0[(bf ^ 1) * 32 + tid] = rv;
+          rda[D + 32 + tid] = rv;
+        }
+      }
+      __syncthreads();
     }
     // stores: L below the outer block (column-major, rows fastest) ...
     for (int idx = tid; idx < kBR * kb; idx += kLuThreads) {
@@ -1484,10 +1520,10 @@ __global__ void __launch_bounds__(kLuThreads) k_below(LuArgs a) {
         write_split(a.split, a.Mop, off, m);
       }
     }
-    // running diagonal and band scale: eight lanes per index, each summing a
-    // 32-column slice, then a fixed-order tree over the slices
+    // running diagonal and band scale: lane = index, warp = 32-column slice,
+    // then warp 0 adds the eight slices in a fixed order
     {
-      const int r = tid >> 3, part = tid & 7;
+      const int r = tid & 31, part = tid >> 5;
       f2 dsum = {0.f, 0.f};
       float ssum = 0.f;
       for (int c = 32 * part; c < 32 * part + 32 && c < kb; ++c) {
@@ -1496,18 +1532,21 @@ __global__ void __launch_bounds__(kLuThreads) k_below(LuArgs a) {
         dsum = f2_add_prod(dsum, w, m);
         ssum += fabsf(w * m);
       }
-#pragma unroll
-      for (int o = 4; o > 0; o >>= 1) {
-        const f2 other = {__shfl_down_sync(kLuFull, dsum.hi, o), __shfl_down_sync(kLuFull, dsum.lo, o)};
-        const float os = __shfl_down_sync(kLuFull, ssum, o);
-        if (part < o) {
-          dsum = f2_add(dsum, other);
-          ssum += os;
+      red[part * 32 + r] = dsum.hi;
+      red[256 + part * 32 + r] = dsum.lo;
+      red[512 + part * 32 + r] = ssum;
+      __syncthreads();
+      if (part == 0) {
+        f2 tot = make_f2(red[r], red[256 + r]);
+        float st = red[512 + r];
+        for (int k = 1; k < 8; ++k) {
+          tot = f2_add(tot, make_f2(red[k * 32 + r], red[256 + k * 32 + r]));
+          st += red[512 + k * 32 + r];
         }
-      }
-      if (part == 0 && r < nr) {
-        a.kd[i0 + r] -= f2_to_double(dsum);
-        a.s[i0 + r] += (double)ssum;
+        if (r < nr) {
+          a.kd[i0 + r] -= f2_to_double(tot);
+          a.s[i0 + r] += (double)st;
+        }
       }
     }
     __syncthreads();
@@ -1724,7 +1763,7 @@ cudaError_t sample_chunked(const DrawArgs& a, Workspace ws) {
       // flops for the Hermitian form, twice that for LU)
       const double fl = (SYM ? 1.0 : 2.0) * (double)(n - r0) * (double)kb * (double)kb;
       int64_t bg = (n - r0 + kBR - 1) / kBR;
-      const int64_t bcap = (int64_t)below_grid * (SYM ? 3 : 1);  // CTAs resident per SM
+      const int64_t bcap = (int64_t)below_grid * (SYM ? 2 : 1);  // CTAs resident per SM
       if (bg > bcap) bg = bcap;
       ProfScope ps(kProfBelow, a.stream, fl, 0.0);
       k_below<SYM><<<(unsigned)bg, kLuThreads, below_smem(SYM), a.stream>>>(la);
