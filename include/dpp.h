@@ -416,6 +416,14 @@ dpp_status dpp_lensemble_to_marginal_batched(int32_t batch, const int64_t* n,
  *                         is drained into FP32 registers instead of 32 / 16;
  *                         bit 1 = 3xTF32 only: 16-deep operand stages, six of
  *                         them, instead of three 32-deep ones
+ *   DPP_TUNE_PANEL_CTAS   split panel pipeline (DPP_TUNE_PANEL_PIPELINE 3):
+ *                         CTAs of each outer block's cooperative decision
+ *                         launch (0 = default: the launch cap DPP_TUNE_MAX_CTAS,
+ *                         at least 8; else 8..4096). CTA 0 and seven helpers
+ *                         decide and solve the block; the others only serve
+ *                         FP64 recomputes, so a smaller grid leaves SMs to the
+ *                         other draws in flight and a larger one recomputes
+ *                         faster.
  *   DPP_TUNE_USE_CACHE    1 (default): when the autotuner's table (below) has
  *                         an entry for a call's key, that entry's outer block,
  *                         panel pipeline and CTA cap replace the three knobs
@@ -430,7 +438,8 @@ typedef enum {
   DPP_TUNE_WAIT_NS = 5,
   DPP_TUNE_FAULT_WITHHOLD = 6,
   DPP_TUNE_USE_CACHE = 7,
-  DPP_TUNE_UPDATE_VARIANT = 8
+  DPP_TUNE_UPDATE_VARIANT = 8,
+  DPP_TUNE_PANEL_CTAS = 9
 } dpp_tune_key;
 
 dpp_status dpp_set_tuning(int32_t key, double value);

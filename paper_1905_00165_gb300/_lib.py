@@ -162,6 +162,7 @@ DPP_TUNE_TAU_SAFETY, DPP_TUNE_OUTER_BLOCK, DPP_TUNE_UPDATE_KERNEL, DPP_TUNE_MAX_
 DPP_TUNE_PANEL_PIPELINE = 4
 DPP_TUNE_WAIT_NS, DPP_TUNE_FAULT_WITHHOLD, DPP_TUNE_USE_CACHE = 5, 6, 7
 DPP_TUNE_UPDATE_VARIANT = 8
+DPP_TUNE_PANEL_CTAS = 9
 
 
 class TuneEntry(ctypes.Structure):

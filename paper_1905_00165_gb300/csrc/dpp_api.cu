@@ -451,6 +451,13 @@ dpp_status dpp_set_tuning(int32_t key, double value) {
       g_settings.update_variant = v;
       return DPP_OK;
     }
+    case DPP_TUNE_PANEL_CTAS: {
+      const int v = (int)value;
+      if ((double)v != value || (v != 0 && (v < 8 || v > 4096)))
+        return fail(DPP_ERR_INVALID_ARG, "panel CTAs must be 0 or in [8, 4096]");
+      g_settings.panel_ctas = v;
+      return DPP_OK;
+    }
     default:
       return fail(DPP_ERR_INVALID_ARG, "unknown tuning key");
   }
@@ -467,6 +474,7 @@ double dpp_get_tuning(int32_t key) {
     case DPP_TUNE_FAULT_WITHHOLD: return (double)g_settings.fault_withhold;
     case DPP_TUNE_USE_CACHE: return (double)g_settings.use_cache;
     case DPP_TUNE_UPDATE_VARIANT: return (double)g_settings.update_variant;
+    case DPP_TUNE_PANEL_CTAS: return (double)g_settings.panel_ctas;
     default: return -1.0;
   }
 }

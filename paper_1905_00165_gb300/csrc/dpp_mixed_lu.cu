@@ -1692,6 +1692,7 @@ cudaError_t sample_chunked(const DrawArgs& a, Workspace ws) {
   // the helpers serve the FP64 recomputes)
   const bool split_rows = g_tuning.panel_pipeline == 3;
   const int below_grid = grid;
+  if (split_rows && g_tuning.panel_ctas > 0) grid = g_tuning.panel_ctas < cap ? g_tuning.panel_ctas : cap;
   if (split_rows && grid < kMaxOuterBlock / 32) grid = kMaxOuterBlock / 32;
   // CTA 0 decides, CTAs 1..nh own the outer block's chunks, the rest the
   // chunks beyond it; slots hold the chunks a CTA precomputes per panel

@@ -132,6 +132,7 @@ def test_tuning_keys_validated_on_host(L):
         (_lib.DPP_TUNE_FAULT_WITHHOLD, [1, 0], [2, -1]),
         (_lib.DPP_TUNE_USE_CACHE, [0, 1], [2, -1]),
         (_lib.DPP_TUNE_UPDATE_VARIANT, [0, 1, 2, 3], [4, -1, 0.5]),
+        (_lib.DPP_TUNE_PANEL_CTAS, [0, 8, 16], [4, 5000, 9.5]),
     ]
     for key, good, bad in cases:
         old = _lib.get_tuning(key)
