@@ -990,6 +990,18 @@ def main():
             f.data_ptr() == k.data_ptr() for f, k in zip(Kinf, Kin))
         ncopy = 2
         cuts = [n * n * i // ncopy for i in range(ncopy + 1)]
+        # the host link alone: one K-sized pinned H2D copy, timed twice (best)
+        h2d_ms = []
+        for _ in range(2):
+            b0 = torch.cuda.Event(enable_timing=True)
+            b1 = torch.cuda.Event(enable_timing=True)
+            b0.record(stream)
+            with torch.cuda.stream(stream):
+                Kinf[0].copy_(Khf, non_blocking=True)
+            b1.record(stream)
+            torch.cuda.synchronize()
+            h2d_ms.append(b0.elapsed_time(b1))
+        h2d_gbs = 8 * n * n / (min(h2d_ms) / 1e3) / 1e9
         keep_h = [torch.empty(n, dtype=torch.uint8, pin_memory=True) for _ in range(nst)]
         raw_h = [torch.empty(_lib.RESULT_BYTES, dtype=torch.uint8, pin_memory=True)
                  for _ in range(nst)]
@@ -1044,6 +1056,8 @@ def main():
         e2e = {"value": job_rate(e2e_steps, ws_n, e_ms), "unit": "samples/s",
                "h2d_bytes_per_step": 8 * n * n, "d2h_bytes_per_step": n + _lib.RESULT_BYTES,
                "steps": e2e_steps,
+               "h2d_alone_gbs": h2d_gbs,
+               "h2d_bound_samples_per_s": h2d_gbs * 1e9 / (8 * n * n),
                "overlap": (f"H2D (pinned host copy with the device buffer's layout, "
                            f"{ncopy} ranges on {ncopy} copy streams) into {nbuf} rotating "
                            f"buffers; draws on {nst} streams")}
