@@ -1034,8 +1034,9 @@ def main():
         keep_h = [torch.empty(n, dtype=torch.uint8, pin_memory=True) for _ in range(nst)]
         raw_h = [torch.empty(_lib.RESULT_BYTES, dtype=torch.uint8, pin_memory=True)
                  for _ in range(nst)]
-        # enough steps for the pipeline of copies and draws in flight to fill
-        e2e_steps = min(steps, max(12, 3 * nst))
+        # as many steps as the timed region, so that the pipeline of copies and
+        # draws in flight fills as it does there
+        e2e_steps = steps
         copy_streams = [torch.cuda.Stream(dev) for _ in range(ncopy)]
         copied = [[torch.cuda.Event() for _ in range(ncopy)] for _ in range(nbuf)]
         consumed = [torch.cuda.Event() for _ in range(nbuf)]
