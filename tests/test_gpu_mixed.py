@@ -315,3 +315,37 @@ def test_update_variants_match_oracle(dpp, precision, variant):
     finally:
         _lib.set_tuning(_lib.DPP_TUNE_UPDATE_VARIANT, old)
         _lib.set_tuning(_lib.DPP_TUNE_OUTER_BLOCK, oldb)
+
+
+@pytest.mark.parametrize("panel_ctas", [8, 16])
+def test_split_pipeline_small_decision_grid(dpp, panel_ctas):
+    """Split pipeline with the decision launch cut to 8 or 16 CTAs
+    (DPP_TUNE_PANEL_CTAS): seven or fifteen recompute servers; borderline
+    pivots deep into the kernel are still recomputed exactly."""
+    from paper_1905_00165_gb300 import _lib
+    n = 3000
+    K = W.hermitian_kernel(n, seed=5, kind="beta")
+    u = O.uniforms(9, 0, n)
+    ref = O.sample_ldl(K, u)
+    pre = pre_decision_pivots(ref)
+    targets = [700, 1279, 2047, 2999]
+    for j in targets:
+        u[j] = pre[j] - 1e-8 if ref.keep[j] else pre[j] + 1e-8
+    ref2 = O.sample_ldl(K, u)
+    keys = (_lib.DPP_TUNE_PANEL_PIPELINE, _lib.DPP_TUNE_PANEL_CTAS, _lib.DPP_TUNE_MAX_CTAS)
+    old = {k: _lib.get_tuning(k) for k in keys}
+    _lib.set_tuning(_lib.DPP_TUNE_PANEL_PIPELINE, 3)
+    _lib.set_tuning(_lib.DPP_TUNE_PANEL_CTAS, panel_ctas)
+    _lib.set_tuning(_lib.DPP_TUNE_MAX_CTAS, 38)
+    try:
+        s = _run(dpp, K, uniforms=u, precision="bf16x6")
+    finally:
+        for k, v in old.items():
+            _lib.set_tuning(k, v)
+    r = s.result()
+    assert r["status"] & (_lib.DPP_RES_TIMEOUT | _lib.DPP_RES_RECOMPUTE) == 0, r
+    assert r["n_borderline"] >= len(targets), r
+    assert np.array_equal(s.keep.cpu().numpy(), ref2.keep)
+    gp = s.pivots.cpu().numpy()
+    for j in targets:
+        assert abs(gp[j] - ref2.pivots[j]) < 1e-10, (j, gp[j], ref2.pivots[j])
