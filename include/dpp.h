@@ -110,7 +110,8 @@ typedef enum {
   DPP_OP_SAMPLE_LU = 1,
   DPP_OP_LOGPROB_BACKWARD = 2,
   DPP_OP_GREEDY_HERMITIAN = 3,
-  DPP_OP_GREEDY_LU = 4
+  DPP_OP_GREEDY_LU = 4,
+  DPP_OP_SAMPLE_BATCHED = 5  /* tuning-table key of dpp_sample_batched only */
 } dpp_op;
 
 /* Bytes of device workspace needed by one call of `op` at order n.
@@ -424,6 +425,9 @@ dpp_status dpp_lensemble_to_marginal_batched(int32_t batch, const int64_t* n,
  *                         FP64 recomputes, so a smaller grid leaves SMs to the
  *                         other draws in flight and a larger one recomputes
  *                         faster.
+ *   DPP_TUNE_BATCHED_THREADS  dpp_sample_batched: threads per CTA, 128
+ *                         (default: two CTAs, two instances, per SM) or 256
+ *                         (one per SM, twice the threads per instance).
  *   DPP_TUNE_USE_CACHE    1 (default): when the autotuner's table (below) has
  *                         an entry for a call's key, that entry's outer block,
  *                         panel pipeline and CTA cap replace the three knobs
@@ -439,7 +443,8 @@ typedef enum {
   DPP_TUNE_FAULT_WITHHOLD = 6,
   DPP_TUNE_USE_CACHE = 7,
   DPP_TUNE_UPDATE_VARIANT = 8,
-  DPP_TUNE_PANEL_CTAS = 9
+  DPP_TUNE_PANEL_CTAS = 9,
+  DPP_TUNE_BATCHED_THREADS = 10
 } dpp_tune_key;
 
 dpp_status dpp_set_tuning(int32_t key, double value);
@@ -457,7 +462,7 @@ double dpp_get_tuning(int32_t key);
  * to every later call with the entry's key (unless DPP_TUNE_USE_CACHE is 0);
  * keeping `streams` draws in flight is the caller's part. */
 typedef struct {
-  int32_t op;              /* DPP_OP_SAMPLE_HERMITIAN or DPP_OP_SAMPLE_LU      */
+  int32_t op;              /* DPP_OP_SAMPLE_HERMITIAN, _LU or _BATCHED         */
   int32_t dtype;
   int32_t precision;
   int32_t n_bucket;        /* floor(log2 n) of the order it was tuned at       */
@@ -469,7 +474,25 @@ typedef struct {
   double samples_per_s;    /* measured with this configuration                 */
   int32_t candidates;      /* configurations timed to choose it                */
   int32_t update_variant;  /* as DPP_TUNE_UPDATE_VARIANT                       */
+  int32_t batched_threads; /* DPP_OP_SAMPLE_BATCHED entries: as
+                              DPP_TUNE_BATCHED_THREADS (0 in the others)       */
 } dpp_tune_entry;
+
+/* Autotune dpp_sample_batched on the caller's batch (its arguments, with
+ * precision DPP_PREC_FP32, no instance/uniform/pivot arrays): `draws` timed
+ * draws (Philox seeds seed, seed + 1, ...; after one warm-up draw) with CTAs
+ * of 128 and of 256 threads (DPP_TUNE_BATCHED_THREADS), CUDA events on
+ * `stream`; the faster goes into the tuning table under (this GPU,
+ * DPP_OP_SAMPLE_BATCHED, DPP_R64, DPP_PREC_FP32, floor(log2 n_max)), which
+ * every later dpp_sample_batched call with that key uses. `best` (host,
+ * nullable) receives the entry; samples_per_s counts instances per second.
+ * The outputs (keep, results) hold the last timed draw. Blocks the host.
+ * Errors: as dpp_sample_batched; DPP_ERR_INVALID_ARG if draws < 1. */
+dpp_status dpp_autotune_batched(int32_t batch, const int64_t* n, const double* const* K,
+                                const int64_t* ld, int64_t n_max, uint64_t seed,
+                                uint8_t* const* keep, dpp_result* results, void* workspace,
+                                size_t workspace_bytes, int32_t draws, dpp_tune_entry* best,
+                                void* stream);
 
 /* Device workspace for dpp_autotune: max_streams draws' workspaces, keep
  * masks and results (0 for an unsupported combination). */

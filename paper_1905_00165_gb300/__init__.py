@@ -249,6 +249,18 @@ class BatchedSampler:
             self.ws.data_ptr(), self.ws.numel(), _stream(self.device))
         _lib.check(st)
 
+    def autotune(self, draws: int = 4, seed: int = 0) -> dict:
+        """Time this batch's draws with 128- and 256-thread CTAs
+        (dpp_autotune_batched) and keep the faster in the library's tuning
+        table for this batch's key (n_max bucket). Returns the entry."""
+        import ctypes
+        e = _lib.TuneEntry()
+        _lib.check(self.L.dpp_autotune_batched(
+            self.batch, self.n.data_ptr(), self.kptr.data_ptr(), self.ld.data_ptr(), self.n_max,
+            seed, self.keep_ptr.data_ptr(), self.raw.data_ptr(), self.ws.data_ptr(),
+            self.ws.numel(), draws, ctypes.byref(e), _stream(self.device)))
+        return e.as_dict()
+
     def logprob_backward(self, grad_logp=None, count=None):
         """dK_i = g_i (K_i - 1_{Y_i^c})^{-T} for the first ``count`` instances
         (default: all) and their last draw (FP64, one persistent launch over

@@ -18,7 +18,7 @@ DPP_OK, DPP_ERR_INVALID_ARG, DPP_ERR_CUDA, DPP_ERR_WORKSPACE, DPP_ERR_UNSUPPORTE
 DPP_R64, DPP_C128 = 0, 1
 DPP_PREC_FP64, DPP_PREC_3XTF32, DPP_PREC_BF16X6, DPP_PREC_FP32 = 0, 1, 2, 3
 DPP_OP_SAMPLE_HERMITIAN, DPP_OP_SAMPLE_LU, DPP_OP_LOGPROB_BACKWARD = 0, 1, 2
-DPP_OP_GREEDY_HERMITIAN, DPP_OP_GREEDY_LU = 3, 4
+DPP_OP_GREEDY_HERMITIAN, DPP_OP_GREEDY_LU, DPP_OP_SAMPLE_BATCHED = 3, 4, 5
 DPP_STATIC_SCRATCH_BYTES = 4 << 20
 DPP_STATIC_MAX_N_R64, DPP_STATIC_MAX_N_C128 = 15418, 7942
 DPP_RES_NONFINITE, DPP_RES_TIMEOUT, DPP_RES_INADMISSIBLE, DPP_RES_RECOMPUTE = 1, 2, 4, 8
@@ -94,6 +94,8 @@ def load(path: Optional[str] = None):
     L.dpp_autotune_workspace_size.argtypes = [i32, i64, i32, i32, i32]
     L.dpp_autotune_workspace_size.restype = sz
     L.dpp_autotune.argtypes = [i32, vp, i64, i64, i32, i32, i32, i32, vp, sz, vp, vp]
+    L.dpp_autotune_batched.argtypes = [i32, vp, vp, vp, i64, u64, vp, vp, vp, sz, i32, vp, vp]
+    L.dpp_autotune_batched.restype = i32
     L.dpp_autotune.restype = i32
     L.dpp_tune_lookup.argtypes = [i32, i64, i32, i32, vp]
     L.dpp_tune_lookup.restype = i32
@@ -163,6 +165,7 @@ DPP_TUNE_PANEL_PIPELINE = 4
 DPP_TUNE_WAIT_NS, DPP_TUNE_FAULT_WITHHOLD, DPP_TUNE_USE_CACHE = 5, 6, 7
 DPP_TUNE_UPDATE_VARIANT = 8
 DPP_TUNE_PANEL_CTAS = 9
+DPP_TUNE_BATCHED_THREADS = 10
 
 
 class TuneEntry(ctypes.Structure):
@@ -172,7 +175,8 @@ class TuneEntry(ctypes.Structure):
                 ("n", ctypes.c_int64), ("outer_block", ctypes.c_int32),
                 ("panel_pipeline", ctypes.c_int32), ("max_ctas", ctypes.c_int32),
                 ("streams", ctypes.c_int32), ("samples_per_s", ctypes.c_double),
-                ("candidates", ctypes.c_int32), ("update_variant", ctypes.c_int32)]
+                ("candidates", ctypes.c_int32), ("update_variant", ctypes.c_int32),
+                ("batched_threads", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -451,6 +451,13 @@ dpp_status dpp_set_tuning(int32_t key, double value) {
       g_settings.update_variant = v;
       return DPP_OK;
     }
+    case DPP_TUNE_BATCHED_THREADS: {
+      const int v = (int)value;
+      if ((double)v != value || (v != 128 && v != 256))
+        return fail(DPP_ERR_INVALID_ARG, "batched threads are 128 or 256");
+      g_settings.batched_threads = v;
+      return DPP_OK;
+    }
     case DPP_TUNE_PANEL_CTAS: {
       const int v = (int)value;
       if ((double)v != value || (v != 0 && (v < 8 || v > 4096)))
@@ -475,6 +482,7 @@ double dpp_get_tuning(int32_t key) {
     case DPP_TUNE_USE_CACHE: return (double)g_settings.use_cache;
     case DPP_TUNE_UPDATE_VARIANT: return (double)g_settings.update_variant;
     case DPP_TUNE_PANEL_CTAS: return (double)g_settings.panel_ctas;
+    case DPP_TUNE_BATCHED_THREADS: return (double)g_settings.batched_threads;
     default: return -1.0;
   }
 }

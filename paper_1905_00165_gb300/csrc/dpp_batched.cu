@@ -24,7 +24,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kP = 32;         // panel width
-constexpr int kThreadsB = 256;
+// threads per CTA: a template parameter (128 or 256, DPP_TUNE_BATCHED_THREADS)
 constexpr int kLd = 65;        // k-major staging tile stride
 
 struct BatchArgs {
@@ -97,6 +97,7 @@ struct Inst {
 // CTA-local FP64 recompute of the pivot of index g (see the exact identity in
 // dpp_recompute.cuh): x0 = L_P^{-T} l (FP32 solve), r = k - (K_P - 1_G) x0 in
 // FP64, v = L_P^{-1} r, d = K_gg - k.x0 - x0.r - sum v^2/d.
+template <int kThreadsB>
 __device__ __noinline__ double cta_recompute(const Inst& in, int64_t g) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const float* A = in.A;
@@ -201,12 +202,15 @@ __device__ __noinline__ double cta_recompute(const Inst& in, int64_t g) {
 }
 
 // Left-looking update of panel [q, q+b) for rows [q, n):
-// A[i, q+c] -= sum_{t<q} L[i,t] d_t L[q+c,t], 64-row tiles, 32-deep chunks.
+// A[i, q+c] -= sum_{t<q} L[i,t] d_t L[q+c,t], tiles of kThreadsB / 4 rows
+// (two per thread row ty), 32-deep chunks.
+template <int kThreadsB>
 __device__ void panel_update(const Inst& in, int64_t q, int b, float* sA, float* sB, int tid) {
   if (q == 0) return;
+  constexpr int kTH = kThreadsB / 4;
   const int64_t n = in.n;
   const int ty = tid / 8, tx = tid % 8;
-  for (int64_t i0 = q; i0 < n; i0 += 64) {
+  for (int64_t i0 = q; i0 < n; i0 += kTH) {
     float acc[2][4];
 #pragma unroll
     for (int rr = 0; rr < 2; ++rr)
@@ -215,8 +219,8 @@ __device__ void panel_update(const Inst& in, int64_t q, int b, float* sA, float*
     for (int64_t k0 = 0; k0 < q; k0 += 32) {
       const int kc = (int)((q - k0) < 32 ? (q - k0) : 32);
       // sA[t][r] = L[i0 + r, k0 + t] (column-major: rows contiguous)
-      for (int idx = tid; idx < 32 * 64; idx += kThreadsB) {
-        const int r = idx % 64, t = idx / 64;
+      for (int idx = tid; idx < 32 * kTH; idx += kThreadsB) {
+        const int r = idx % kTH, t = idx / kTH;
         const int64_t i = i0 + r;
         sA[t * kLd + r] = (t < kc && i < n) ? in.A[i + (k0 + t) * in.lda] : 0.f;
       }
@@ -251,6 +255,7 @@ __device__ void panel_update(const Inst& in, int64_t q, int b, float* sA, float*
   }
 }
 
+template <int kThreadsB>
 __global__ void __launch_bounds__(kThreadsB) k_batched(BatchArgs a) {
   __shared__ float sA[32 * kLd];
   __shared__ float sB[32 * 33];
@@ -317,7 +322,7 @@ __global__ void __launch_bounds__(kThreadsB) k_batched(BatchArgs a) {
     float max_ratio = 0.f;
     for (int64_t q = 0; q < n; q += kP) {
       const int b = (int)((n - q) < kP ? (n - q) : kP);
-      panel_update(in, q, b, sA, sB, tid);
+      panel_update<kThreadsB>(in, q, b, sA, sB, tid);
       __syncthreads();
       // decisions (warp 0); a borderline pivot suspends the loop, the whole CTA
       // recomputes it in FP64, and warp 0 resumes at that pivot
@@ -457,7 +462,7 @@ __global__ void __launch_bounds__(kThreadsB) k_batched(BatchArgs a) {
         __syncthreads();
         const int pend = s_pending;
         if (pend < 0) break;
-        const double pe = cta_recompute(in, q + pend);
+        const double pe = cta_recompute<kThreadsB>(in, q + pend);
         if (tid == 0) {
           s_pe = pe;
           s_resume = 1;
@@ -582,7 +587,10 @@ cudaError_t sample_batched(const BatchedArgs& b, Workspace ws) {
   a.tol = 1e-3;
   {
     ProfScope ps(kProfBatched, b.stream, b.flops, 0.0);
-    k_batched<<<(unsigned)ctas, kThreadsB, 0, b.stream>>>(a);
+    if (g_tuning.batched_threads == 256)
+      k_batched<256><<<(unsigned)ctas, 256, 0, b.stream>>>(a);
+    else
+      k_batched<128><<<(unsigned)ctas, 128, 0, b.stream>>>(a);
   }
   return cudaGetLastError();
 }

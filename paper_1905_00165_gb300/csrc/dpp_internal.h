@@ -74,6 +74,7 @@ struct Tuning {
   int fault_withhold = 0;   // fault injection: the deciding CTA never releases a panel
   int use_cache = 1;        // apply the autotuner's entry for a call's key
   int panel_ctas = 0;       // split pipeline: CTAs of the decision launch (0 = cap)
+  int batched_threads = 128;  // batched sampler: threads per CTA (128 or 256)
 };
 // The process-wide settings (dpp_set_tuning), and the settings of the call in
 // progress on this host thread: every entry point starts with begin_call,

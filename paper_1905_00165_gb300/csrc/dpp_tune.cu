@@ -113,6 +113,10 @@ bool find(int32_t op, int64_t n, int32_t dtype, int32_t precision, dpp_tune_entr
 }
 
 void apply(const dpp_tune_entry& e, Tuning* t) {
+  if (e.op == kOpBatched) {
+    t->batched_threads = e.batched_threads;
+    return;
+  }
   if (e.outer_block >= 32) t->outer_block = e.outer_block;
   t->panel_pipeline = e.panel_pipeline;
   t->max_ctas = e.max_ctas;
@@ -182,13 +186,18 @@ bool read_entry(const char** pp, Entry* x) {
       else if (key == "samples_per_s") e.samples_per_s = v;
       else if (key == "candidates") e.candidates = (int32_t)v;
       else if (key == "update_variant") e.update_variant = (int32_t)v;
+      else if (key == "batched_threads") e.batched_threads = (int32_t)v;
     }
   }
 }
 
 bool valid(const Entry& x) {
   const dpp_tune_entry& e = x.e;
-  return !x.gpu.empty() && x.sms > 0 && e.op >= 0 && e.op <= 1 && (e.dtype == 0 || e.dtype == 1) &&
+  if (e.op == kOpBatched)
+    return !x.gpu.empty() && x.sms > 0 && e.dtype == DPP_R64 && e.precision == DPP_PREC_FP32 &&
+           e.n_bucket >= 0 && e.n_bucket < 40 && (e.batched_threads == 128 || e.batched_threads == 256);
+  return !x.gpu.empty() && x.sms > 0 && e.batched_threads == 0 && e.op >= 0 && e.op <= 1 &&
+         (e.dtype == 0 || e.dtype == 1) &&
          e.precision >= 0 && e.precision <= 2 && e.n_bucket >= 0 && e.n_bucket < 40 &&
          (e.outer_block == 0 || (e.outer_block >= 32 && e.outer_block <= kMaxOuterBlock &&
                                  e.outer_block % 32 == 0)) &&
@@ -452,6 +461,67 @@ dpp_status dpp_autotune(int32_t op, const void* K, int64_t n, int64_t ld, int32_
   return DPP_OK;
 }
 
+dpp_status dpp_autotune_batched(int32_t batch, const int64_t* n, const double* const* K,
+                                const int64_t* ld, int64_t n_max, uint64_t seed,
+                                uint8_t* const* keep, dpp_result* results, void* workspace,
+                                size_t workspace_bytes, int32_t draws, dpp_tune_entry* best,
+                                void* stream) {
+  clear_last_error();
+  if (draws < 1 || draws > 4096)
+    return set_last_error(DPP_ERR_INVALID_ARG, "dpp_autotune_batched: draws must be in [1, 4096]");
+  if (batch < 1 || n_max < 1)
+    return set_last_error(DPP_ERR_INVALID_ARG, "dpp_autotune_batched: empty batch");
+  GpuId id;
+  if (!gpu_id(&id)) return set_last_error(DPP_ERR_CUDA, "dpp_autotune_batched: no device");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  const int opts[2] = {128, 256};
+  dpp_tune_entry win{};
+  double win_sps = -1.0;
+  dpp_status rs = DPP_OK;
+  for (int i = 0; i < 2 && e == cudaSuccess && rs == DPP_OK; ++i) {
+    dpp_tune_entry c{};
+    c.op = kOpBatched;
+    c.dtype = DPP_R64;
+    c.precision = DPP_PREC_FP32;
+    c.n_bucket = bucket_of(n_max);
+    c.n = n_max;
+    c.streams = 1;
+    c.batched_threads = opts[i];
+    tl_force = &c;
+    auto draw = [&](uint64_t s) {
+      return dpp_sample_batched(batch, n, K, ld, n_max, DPP_PREC_FP32, s, nullptr, keep, nullptr,
+                                nullptr, results, workspace, workspace_bytes, stream);
+    };
+    rs = draw(seed + 1000000u);
+    if (rs == DPP_OK) e = cudaEventRecord(e0, st);
+    for (int d = 0; d < draws && rs == DPP_OK && e == cudaSuccess; ++d) rs = draw(seed + d);
+    if (rs == DPP_OK && e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (rs == DPP_OK && e == cudaSuccess) e = cudaEventSynchronize(e1);
+    tl_force = nullptr;
+    float ms = 0.f;
+    if (rs == DPP_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (rs == DPP_OK && e == cudaSuccess) {
+      const double sps = ms > 0.f ? (double)batch * draws / (ms * 1e-3) : 0.0;
+      if (sps > win_sps) {
+        win_sps = sps;
+        win = c;
+        win.samples_per_s = sps;
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (rs != DPP_OK) return rs;
+  if (e != cudaSuccess) return set_last_cuda_error(e, "dpp_autotune_batched");
+  win.candidates = 2;
+  put(id.name, id.sms, win);
+  if (best) *best = win;
+  return DPP_OK;
+}
+
 dpp_status dpp_tune_lookup(int32_t op, int64_t n, int32_t dtype, int32_t precision,
                            dpp_tune_entry* out) {
   clear_last_error();
@@ -484,10 +554,10 @@ dpp_status dpp_tune_save(const char* path) {
             "%s\n  {\"gpu\": \"%s\", \"sms\": %d, \"op\": %d, \"dtype\": %d, \"precision\": %d, "
             "\"n_bucket\": %d, \"n\": %lld, \"outer_block\": %d, \"panel_pipeline\": %d, "
             "\"max_ctas\": %d, \"streams\": %d, \"samples_per_s\": %.6g, \"candidates\": %d, "
-            "\"update_variant\": %d}",
+            "\"update_variant\": %d, \"batched_threads\": %d}",
             i ? "," : "", gpu.c_str(), copy[i].sms, e.op, e.dtype, e.precision, e.n_bucket,
             (long long)e.n, e.outer_block, e.panel_pipeline, e.max_ctas, e.streams,
-            e.samples_per_s, e.candidates, e.update_variant);
+            e.samples_per_s, e.candidates, e.update_variant, e.batched_threads);
   }
   fprintf(f, "\n]}\n");
   const bool ok = fclose(f) == 0;

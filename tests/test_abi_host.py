@@ -133,6 +133,7 @@ def test_tuning_keys_validated_on_host(L):
         (_lib.DPP_TUNE_USE_CACHE, [0, 1], [2, -1]),
         (_lib.DPP_TUNE_UPDATE_VARIANT, [0, 1, 2, 3], [4, -1, 0.5]),
         (_lib.DPP_TUNE_PANEL_CTAS, [0, 8, 16], [4, 5000, 9.5]),
+        (_lib.DPP_TUNE_BATCHED_THREADS, [256, 128], [0, 64, 200]),
     ]
     for key, good, bad in cases:
         old = _lib.get_tuning(key)
@@ -193,7 +194,13 @@ def test_tune_cache_round_trip(L, tmp_path):
          "n_bucket": 13, "n": 8192, "outer_block": 128, "panel_pipeline": 0,
          "max_ctas": 0, "streams": 1, "samples_per_s": 80.25, "candidates": 6,
          "update_variant": 0},
+        {"gpu": "NVIDIA GB300", "sms": 152, "op": 5, "dtype": 0, "precision": 3,
+         "n_bucket": 10, "n": 1024, "outer_block": 0, "panel_pipeline": 0,
+         "max_ctas": 0, "streams": 1, "samples_per_s": 46089.5, "candidates": 2,
+         "update_variant": 0, "batched_threads": 128},
     ]
+    for e in entries:
+        e.setdefault("batched_threads", 0)
     src = tmp_path / "in.json"
     src.write_text(json.dumps({"version": 1, "entries": entries}))
     _lib.tune_clear()
@@ -209,18 +216,32 @@ def test_tune_cache_round_trip(L, tmp_path):
         _lib.tune_load(str(src))
         _lib.tune_save(str(out))
         got = json.loads(out.read_text())["entries"]
-        assert len(got) == 2 and got[0]["outer_block"] == 128 and got[1] == entries[1]
+        assert len(got) == 3 and got[0]["outer_block"] == 128 and got[1:] == entries[1:]
         # refused: malformed, out of range, missing
         bad = tmp_path / "bad.json"
         bad.write_text('{"entries": [{"gpu": "x", "sms": }]}')
         assert L.dpp_tune_load(str(bad).encode()) == _lib.DPP_ERR_INVALID_ARG
         bad.write_text(json.dumps({"entries": [dict(entries[0], outer_block=100)]}))
         assert L.dpp_tune_load(str(bad).encode()) == _lib.DPP_ERR_INVALID_ARG
+        bad.write_text(json.dumps({"entries": [dict(entries[2], batched_threads=64)]}))
+        assert L.dpp_tune_load(str(bad).encode()) == _lib.DPP_ERR_INVALID_ARG
+        bad.write_text(json.dumps({"entries": [dict(entries[0], batched_threads=128)]}))
+        assert L.dpp_tune_load(str(bad).encode()) == _lib.DPP_ERR_INVALID_ARG
         assert L.dpp_tune_load(str(tmp_path / "none.json").encode()) == _lib.DPP_ERR_INVALID_ARG
         _lib.tune_save(str(out))
-        assert len(json.loads(out.read_text())["entries"]) == 2
+        assert len(json.loads(out.read_text())["entries"]) == 3
     finally:
         _lib.tune_clear()
+
+
+def test_autotune_batched_rejects_bad_arguments_on_host(L):
+    """dpp_autotune_batched refuses a bad draw count or an empty batch before
+    any device work."""
+    fake = 4096
+    f = L.dpp_autotune_batched
+    assert f(4, fake, fake, fake, 64, 0, fake, fake, fake, 1 << 20, 0, None, None) == _lib.DPP_ERR_INVALID_ARG
+    assert f(4, fake, fake, fake, 64, 0, fake, fake, fake, 1 << 20, 5000, None, None) == _lib.DPP_ERR_INVALID_ARG
+    assert f(0, fake, fake, fake, 64, 0, fake, fake, fake, 1 << 20, 2, None, None) == _lib.DPP_ERR_INVALID_ARG
 
 
 def test_autotune_rejects_bad_arguments_on_host(L):

@@ -54,3 +54,31 @@ def test_autotune_then_draw_matches_oracle(dpp, hermitian, precision, n, cands):
         compare_draw(s.keep.cpu().numpy(), r["logp"], None, ref, u, logp_rtol=tol)
     _lib.tune_clear()
     assert _lib.tune_lookup(op, n, _lib.DPP_R64, _lib.PRECISIONS[precision]) is None
+
+
+def test_autotune_batched_then_draw_matches_oracle(dpp):
+    """dpp_autotune_batched times 128- and 256-thread CTAs on the caller's
+    batch, keeps the faster under the batch's n_max bucket, and the draws that
+    follow (with that CTA size) are the oracle's."""
+    import torch
+    from paper_1905_00165_gb300 import _lib
+    _lib.tune_clear()
+    sizes = [40, 96, 130, 257, 64, 200, 33, 300]
+    Ks = [W.hermitian_kernel(m, seed=70 + i, kind="uniform") for i, m in enumerate(sizes)]
+    b = dpp.BatchedSampler([torch.from_numpy(K).cuda() for K in Ks])
+    best = b.autotune(draws=2)
+    assert best["op"] == _lib.DPP_OP_SAMPLE_BATCHED and best["candidates"] == 2
+    assert best["batched_threads"] in (128, 256) and best["samples_per_s"] > 0
+    got = _lib.tune_lookup(_lib.DPP_OP_SAMPLE_BATCHED, 300, _lib.DPP_R64, _lib.DPP_PREC_FP32)
+    assert got == best
+    b.draw(7)
+    torch.cuda.synchronize()
+    for i, K in enumerate(Ks):
+        m = K.shape[0]
+        ref = O.sample_ldl(K, O.uniforms(7, i, m))
+        res = _lib.decode_result(bytes(b.raw[i * _lib.RESULT_BYTES:(i + 1) * _lib.RESULT_BYTES]
+                                       .cpu().numpy().tobytes()))
+        assert res["status"] & (_lib.DPP_RES_TIMEOUT | _lib.DPP_RES_NONFINITE) == 0, res
+        compare_draw(b.keep[i][:m].cpu().numpy(), res["logp"], None, ref, O.uniforms(7, i, m),
+                     logp_rtol=1e-6)
+    _lib.tune_clear()

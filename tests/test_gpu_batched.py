@@ -11,12 +11,18 @@ from tests._parity import compare_draw, pre_decision_pivots
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def dpp():
+@pytest.fixture(scope="module", params=[128, 256], ids=["threads128", "threads256"])
+def dpp(request):
+    """The library, with the batched sampler's CTAs of 128 or 256 threads
+    (DPP_TUNE_BATCHED_THREADS)."""
     import __graft_entry__
     __graft_entry__.build()
     import paper_1905_00165_gb300 as m
-    return m
+    from paper_1905_00165_gb300 import _lib
+    old = _lib.get_tuning(_lib.DPP_TUNE_BATCHED_THREADS)
+    _lib.set_tuning(_lib.DPP_TUNE_BATCHED_THREADS, request.param)
+    yield m
+    _lib.set_tuning(_lib.DPP_TUNE_BATCHED_THREADS, old)
 
 
 def _to_dev(Ks):
