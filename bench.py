@@ -219,6 +219,16 @@ def bench_batched(dpp, _lib, dev, batch: int, draws: int, seed: int = 0):
     torch.cuda.synchronize()
     ms_adj = a0.elapsed_time(a1)
     del dKs
+    # the same in FP32 arithmetic (dpp_logprob_backward_batched_fp32)
+    first32 = b.logprob_backward(count=n_adj, precision="fp32")
+    torch.cuda.synchronize()
+    del first32
+    a0.record(stream)
+    dKs = b.logprob_backward(count=n_adj, precision="fp32")
+    a1.record(stream)
+    torch.cuda.synchronize()
+    ms_adj32 = a0.elapsed_time(a1)
+    del dKs
     return {"metric": f"batched L-ensemble samples/s ({batch} kernels, n~U{{64..1024}})",
             "value": batch / (ms / 1e3), "unit": "samples/s", "ms_per_draw": ms,
             "draws": draws, "tflops_algorithmic": flops / (ms / 1e3) / 1e12,
@@ -232,7 +242,10 @@ def bench_batched(dpp, _lib, dev, batch: int, draws: int, seed: int = 0):
             "adjoint": {"instances_per_s": n_adj / (ms_adj / 1e3), "ms": ms_adj,
                         "instances": n_adj, "precision": "fp64",
                         "note": "dK_i = (K_i - 1_{Y_i^c})^{-T}: forced-decision FP64 "
-                                "refactorization and triangular inverses, one library call"},
+                                "refactorization and triangular inverses, one library call",
+                        "fp32": {"instances_per_s": n_adj / (ms_adj32 / 1e3), "ms": ms_adj32,
+                                 "note": "the same steps in FP32 arithmetic, FP64 dK "
+                                         "(dpp_logprob_backward_batched_fp32)"}},
             "config": {"workload": "lensemble_batch", "batch": batch, "nmin": 64, "nmax": 1024,
                        "features": 64, "quality": "LogUniform(0.1, 10)", "precision": "fp32"}}
 

@@ -330,6 +330,19 @@ dpp_status dpp_logprob_backward(const void* K, int64_t n, int64_t ld,
  * Errors: DPP_ERR_INVALID_ARG / DPP_ERR_WORKSPACE found on the host before
  * anything is enqueued; DPP_ERR_CUDA if a launch fails (earlier instances
  * may then already be enqueued). */
+/* dpp_logprob_backward_batched in FP32 arithmetic: the LDL^T of K_i - 1_{Y^c},
+ * the triangular inverse and Z^T D^{-1} Z run at the FP32 rate (GB300's FP64
+ * rate is a small fraction of it); K, g and dK stay FP64 (dK carries FP32
+ * rounding: about 1e-7 relative times the conditioning of K_i - 1_{Y^c}).
+ * Same arguments, workspace and errors. */
+dpp_status dpp_logprob_backward_batched_fp32(int32_t batch, const int64_t* n,
+                                             const void* const* K, const int64_t* ld,
+                                             const uint8_t* const* keep,
+                                             const double* const* grad_logp,
+                                             void* const* dK, const int64_t* ld_dk,
+                                             void* workspace, size_t workspace_bytes,
+                                             void* stream);
+
 /* Workspace bytes for the one-launch form of dpp_logprob_backward_batched on
  * the current device (one CTA per SM, or DPP_TUNE_MAX_CTAS): a descriptor per
  * instance plus, per CTA, n_max^2 + 33 n_max + 32 n_max doubles (rounded up to

@@ -261,10 +261,12 @@ class BatchedSampler:
             self.ws.numel(), draws, ctypes.byref(e), _stream(self.device)))
         return e.as_dict()
 
-    def logprob_backward(self, grad_logp=None, count=None):
+    def logprob_backward(self, grad_logp=None, count=None, precision: str = "fp64"):
         """dK_i = g_i (K_i - 1_{Y_i^c})^{-T} for the first ``count`` instances
-        (default: all) and their last draw (FP64, one persistent launch over
-        every instance)."""
+        (default: all) and their last draw (one persistent launch over every
+        instance; ``precision`` "fp64" or "fp32" arithmetic, FP64 dK)."""
+        if precision not in ("fp64", "fp32"):
+            raise ValueError("precision must be 'fp64' or 'fp32'")
         import ctypes
         import numpy as np
         torch = _torch()
@@ -287,7 +289,9 @@ class BatchedSampler:
         # the one-launch form: a descriptor per instance and n_max^2 scratch per CTA
         need = self.L.dpp_logprob_backward_batched_workspace(B, max(ns) if ns else 0)
         ws = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
-        st = self.L.dpp_logprob_backward_batched(
+        fn = (self.L.dpp_logprob_backward_batched if precision == "fp64"
+              else self.L.dpp_logprob_backward_batched_fp32)
+        st = fn(
             B, n_h.ctypes.data, ctypes.cast(kp, ctypes.c_void_p), ld_h.ctypes.data,
             ctypes.cast(kk, ctypes.c_void_p), ctypes.cast(gp, ctypes.c_void_p),
             ctypes.cast(dp, ctypes.c_void_p), ldd_h.ctypes.data, ws.data_ptr(), ws.numel(),

@@ -77,6 +77,8 @@ def load(path: Optional[str] = None):
     L.dpp_logprob_backward.restype = i32
     L.dpp_logprob_backward_batched.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
     L.dpp_logprob_backward_batched.restype = i32
+    L.dpp_logprob_backward_batched_fp32.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+    L.dpp_logprob_backward_batched_fp32.restype = i32
     L.dpp_logprob_backward_batched_workspace.argtypes = [i32, i64]
     L.dpp_logprob_backward_batched_workspace.restype = sz
     L.dpp_uniforms.argtypes = [u64, u64, i64, vp, vp]

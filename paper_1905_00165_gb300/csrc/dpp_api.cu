@@ -329,11 +329,11 @@ dpp_status dpp_logprob_backward(const void* K, int64_t n, int64_t ld, int32_t dt
   return DPP_OK;
 }
 
-dpp_status dpp_logprob_backward_batched(int32_t batch, const int64_t* n, const void* const* K,
-                                        const int64_t* ld, const uint8_t* const* keep,
-                                        const double* const* grad_logp, void* const* dK,
-                                        const int64_t* ld_dk, void* workspace,
-                                        size_t workspace_bytes, void* stream) {
+static dpp_status backward_batched_common(int32_t batch, const int64_t* n, const void* const* K,
+                                          const int64_t* ld, const uint8_t* const* keep,
+                                          const double* const* grad_logp, void* const* dK,
+                                          const int64_t* ld_dk, bool fp32, void* workspace,
+                                          size_t workspace_bytes, void* stream) {
   g_last_error.clear();
   if (batch < 0) return fail(DPP_ERR_INVALID_ARG, "batch must be >= 0");
   if (batch == 0) return DPP_OK;
@@ -352,15 +352,34 @@ dpp_status dpp_logprob_backward_batched(int32_t batch, const int64_t* n, const v
   if (workspace_bytes < ws_adjoint_batched(batch, n_max, 1))
     return fail(DPP_ERR_WORKSPACE, "workspace too small for one CTA of the batched adjoint");
   // one persistent launch over all instances, on as many CTAs as the workspace holds
-  begin_call(DPP_OP_LOGPROB_BACKWARD, n_max, DPP_R64, DPP_PREC_FP64);
+  begin_call(DPP_OP_LOGPROB_BACKWARD, n_max, DPP_R64, fp32 ? DPP_PREC_FP32 : DPP_PREC_FP64);
   Workspace ws;
   ws.base = static_cast<char*>(workspace);
   ws.size = workspace_bytes;
   cudaError_t e = adjoint_batched(batch, n, reinterpret_cast<const double* const*>(K), ld, keep,
                                   grad_logp, reinterpret_cast<double* const*>(dK), ld_dk, n_max,
-                                  ws, static_cast<cudaStream_t>(stream));
+                                  fp32, ws, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return fail_cuda(e, "dpp_logprob_backward_batched");
   return DPP_OK;
+}
+
+dpp_status dpp_logprob_backward_batched(int32_t batch, const int64_t* n, const void* const* K,
+                                        const int64_t* ld, const uint8_t* const* keep,
+                                        const double* const* grad_logp, void* const* dK,
+                                        const int64_t* ld_dk, void* workspace,
+                                        size_t workspace_bytes, void* stream) {
+  return backward_batched_common(batch, n, K, ld, keep, grad_logp, dK, ld_dk, false, workspace,
+                                 workspace_bytes, stream);
+}
+
+dpp_status dpp_logprob_backward_batched_fp32(int32_t batch, const int64_t* n,
+                                             const void* const* K, const int64_t* ld,
+                                             const uint8_t* const* keep,
+                                             const double* const* grad_logp, void* const* dK,
+                                             const int64_t* ld_dk, void* workspace,
+                                             size_t workspace_bytes, void* stream) {
+  return backward_batched_common(batch, n, K, ld, keep, grad_logp, dK, ld_dk, true, workspace,
+                                 workspace_bytes, stream);
 }
 
 dpp_status dpp_lensemble_to_marginal_batched(int32_t batch, const int64_t* n,
@@ -389,7 +408,7 @@ dpp_status dpp_lensemble_to_marginal_batched(int32_t batch, const int64_t* n,
   Workspace ws;
   ws.base = static_cast<char*>(workspace);
   ws.size = workspace_bytes;
-  cudaError_t e = adjoint_batched(batch, n, L, ld, nullptr, nullptr, K, ld_k, n_max, ws,
+  cudaError_t e = adjoint_batched(batch, n, L, ld, nullptr, nullptr, K, ld_k, n_max, false, ws,
                                   static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return fail_cuda(e, "dpp_lensemble_to_marginal_batched");
   return DPP_OK;

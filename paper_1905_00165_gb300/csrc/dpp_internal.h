@@ -159,7 +159,7 @@ int adjoint_batched_ctas();
 cudaError_t adjoint_batched(int32_t batch, const int64_t* n, const double* const* K,
                             const int64_t* ld, const uint8_t* const* keep,
                             const double* const* g, double* const* dK, const int64_t* ld_dk,
-                            int64_t n_max, Workspace ws, cudaStream_t s);
+                            int64_t n_max, bool fp32, Workspace ws, cudaStream_t s);
 
 // Result initialisation and uniform generation (dpp_fp64.cu).
 cudaError_t init_result(dpp_result* r, cudaStream_t s);

@@ -149,6 +149,28 @@ def test_batched_adjoint_matches_closed_form(dpp):
         assert err < 1e-9, (i, err)
 
 
+def test_batched_adjoint_fp32_matches_closed_form(dpp):
+    """The FP32 form of the batched adjoint (dpp_logprob_backward_batched_fp32)
+    against the oracle's FP64 closed form, within FP32 inversion accuracy:
+    ||dK - ref||_F <= 3e-5 cond(K - 1_{Y^c}) ||ref||_F."""
+    import torch
+    Ks = W.lensemble_batch(8, seed=5, nmin=32, nmax=400)
+    b = dpp.sample_batched(_to_dev(Ks), seed=4)
+    g = torch.tensor([1.0, -0.5, 2.0, 0.25, 1.5, -1.0, 0.75, 3.0], dtype=torch.float64)
+    dKs = b.logprob_backward(g, precision="fp32")
+    torch.cuda.synchronize()
+    for i, K in enumerate(Ks):
+        n = K.shape[0]
+        keep = b.keep[i][:n].cpu().numpy()
+        ref = O.logprob_grad(K, keep, float(g[i]))
+        A = O.complement_shift(K, keep)
+        cond = np.linalg.cond(A)
+        got = dKs[i].cpu().numpy()
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert err <= 3e-5 * cond, (i, err, cond)
+        assert np.allclose(got, got.T, atol=0.0)  # both triangles written
+
+
 def _adjoint_call(dpp, Ks, keeps, g, ws_bytes):
     """dpp_logprob_backward_batched with an explicit workspace size."""
     import ctypes
