@@ -112,16 +112,18 @@ def test_mixed_complex_small_grid(dpp):
         _lib.set_tuning(_lib.DPP_TUNE_MAX_CTAS, old)
 
 
-def test_mixed_complex_matches_fp64_path_n4096(dpp):
-    """The complex configuration at its measured size (n = 4096, Beta(1/2,1/2)
-    spectrum): the mixed path draws the FP64 GPU path's set up to the first
-    pivot within 1e-9 of its uniform; log P within the mixed tolerance."""
+@pytest.mark.parametrize("n,seeds,kind", [(4096, (0, 1), "beta"), (16384, (0,), "beta"),
+                                          (16384, (1,), "projection")])
+def test_mixed_complex_matches_fp64_path(dpp, n, seeds, kind):
+    """The complex configurations at their measured sizes (n = 4096 and 16384,
+    Beta(1/2,1/2) spectrum or a rank-n/4 projection): the mixed path draws the
+    FP64 GPU path's set up to the first pivot within 1e-9 of its uniform; log P
+    within the mixed tolerance."""
     import torch
     from paper_1905_00165_gb300 import _lib
-    n = 4096
-    Kd = W.hermitian_kernel(n, seed=0, kind="beta", complex_=True, device="cuda",
+    Kd = W.hermitian_kernel(n, seed=0, kind=kind, complex_=True, device="cuda",
                             return_torch=True).contiguous()
-    for seed in (0, 1):
+    for seed in seeds:
         ref = dpp.sample_hermitian(Kd, seed=seed, precision="fp64")
         mix = dpp.sample_hermitian(Kd, seed=seed, precision="bf16x6")
         torch.cuda.synchronize()
@@ -137,3 +139,23 @@ def test_mixed_complex_matches_fp64_path_n4096(dpp):
         assert np.array_equal(km[:j0], kr[:j0]), int(np.flatnonzero(km[:j0] != kr[:j0])[0])
         if j0 == n:
             assert abs(rm["logp"] - rr["logp"]) <= MIXED_LOGP_RTOL * abs(rr["logp"])
+
+
+def test_mixed_complex_projection_matches_oracle_n4096(dpp):
+    """A complex rank-n/4 projection kernel (n = 4096) against one oracle draw:
+    decisions up to the first borderline pivot, |Y| = rank, log P."""
+    import torch
+    from paper_1905_00165_gb300 import _lib
+    n = 4096
+    K = W.hermitian_kernel(n, seed=3, kind="projection", complex_=True, device="cuda")
+    Kd = torch.from_numpy(np.ascontiguousarray(K.T)).cuda().t()
+    u = O.uniforms(2, 0, n)
+    ref = O.sample_ldl(K, u)
+    assert int(ref.keep.sum()) == n // 4
+    s = dpp.sample_hermitian(Kd, seed=2, precision="3xtf32")
+    torch.cuda.synchronize()
+    r = s.result()
+    assert r["status"] & _bad(_lib) == 0, r
+    compare_draw(s.keep.cpu().numpy(), r["logp"], s.pivots.cpu().numpy(), ref, u,
+                 logp_rtol=MIXED_LOGP_RTOL, piv_atol=1e-4)
+    assert r["n_kept"] == n // 4
