@@ -1292,7 +1292,7 @@ __global__ void __launch_bounds__(kLuThreads, 1) k_lu_outer(LuArgs a) {
 // Split pipeline (DPP_TUNE_PANEL_PIPELINE 3): the panel launch holds only CTA 0
 // and the helpers, which factor the outer block's own rows with the decisions;
 // afterwards this kernel, on a wide grid, brings every index below the outer
-// block through its panels. A CTA takes 64 indices i and keeps, in shared
+// block through its panels. A CTA takes kBR = 32 indices i and keeps, in shared
 // memory, their row segments X[i][c] = A[i, q + c] and (LU) their column
 // segments Z[i][c] = A[q + c, i], c < kb, and runs the outer block
 // right-looking, panel by panel (p = q + 32 k):
@@ -1344,6 +1344,61 @@ __device__ __forceinline__ void below_solve(float* base, int ldx, const int* row
 #pragma unroll
   for (int r = 0; r < R; ++r)
     if (lane < b) base[rows[r] * ldx + D + lane] = x[r] * sc;
+}
+
+// Panel product of k_below for rows 4 ty .. 4 ty + 3 of the CTA and columns
+// C0 + tx + 32 jj (jj < JJ, below kb): X -= W_panel M^T and (LU) Z -= M_panel
+// W^T over the panel's 32 columns D .. D + 31. Consecutive lanes touch
+// consecutive words, so neither the operand loads nor the updates conflict.
+template <bool SYM, int JJ>
+__device__ __forceinline__ void below_product(float* X, float* Zs, const float* Ps,
+                                              const float* Qs, int ldx, int D, int C0, int kb,
+                                              int ty, int tx) {
+  float ax[4][JJ], az[SYM ? 1 : 4][SYM ? 1 : JJ];
+  bool in[JJ];
+#pragma unroll
+  for (int jj = 0; jj < JJ; ++jj) in[jj] = C0 + tx + 32 * jj < kb;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int jj = 0; jj < JJ; ++jj) {
+      ax[i][jj] = 0.f;
+      if (!SYM) az[i][jj] = 0.f;
+    }
+#pragma unroll 4
+  for (int t = 0; t < 32; ++t) {
+    float w[4], m[JJ];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) w[i] = X[(4 * ty + i) * ldx + D + t];
+#pragma unroll
+    for (int jj = 0; jj < JJ; ++jj) m[jj] = in[jj] ? Ps[t * kBelowLdp + C0 + tx + 32 * jj] : 0.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int jj = 0; jj < JJ; ++jj) ax[i][jj] = fmaf(w[i], m[jj], ax[i][jj]);
+    if (!SYM) {
+      float mr[4], wq[JJ];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) mr[i] = Zs[(4 * ty + i) * ldx + D + t];
+#pragma unroll
+      for (int jj = 0; jj < JJ; ++jj)
+        wq[jj] = in[jj] ? Qs[t * kBelowLdp + C0 + tx + 32 * jj] : 0.f;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int jj = 0; jj < JJ; ++jj) az[SYM ? 0 : i][SYM ? 0 : jj] =
+            fmaf(mr[i], wq[jj], az[SYM ? 0 : i][SYM ? 0 : jj]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int jj = 0; jj < JJ; ++jj)
+      if (in[jj]) {
+        const int j = C0 + tx + 32 * jj;
+        X[(4 * ty + i) * ldx + j] -= ax[i][jj];
+        if (!SYM) Zs[(4 * ty + i) * ldx + j] -= az[SYM ? 0 : i][SYM ? 0 : jj];
+      }
 }
 
 template <bool SYM>
@@ -1444,53 +1499,17 @@ __global__ void __launch_bounds__(kLuThreads) k_below(LuArgs a) {
       const bool more = k + 1 < np;
       if (more) rv = issue(k + 1);
       const int C0 = D + 32;
-      // columns j0 + tx + 32 jj of a 128-wide chunk: consecutive lanes touch
-      // consecutive words (no bank conflicts in the loads or the updates)
-      for (int j0 = C0; j0 < kb; j0 += 128) {
-        float ax[4][4], az[4][4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int jj = 0; jj < 4; ++jj) ax[i][jj] = az[i][jj] = 0.f;
-#pragma unroll 4
-        for (int t = 0; t < 32; ++t) {
-          float w[4], m[4];
-#pragma unroll
-          for (int i = 0; i < 4; ++i) w[i] = X[(4 * ty + i) * ldx + D + t];
-#pragma unroll
-          for (int jj = 0; jj < 4; ++jj) {
-            const int j = j0 + tx + 32 * jj;
-            m[jj] = j < kb ? Ps[t * kBelowLdp + j] : 0.f;
-          }
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int jj = 0; jj < 4; ++jj) ax[i][jj] = fmaf(w[i], m[jj], ax[i][jj]);
-          if (!SYM) {
-            float mr[4], wq[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) mr[i] = Zs[(4 * ty + i) * ldx + D + t];
-#pragma unroll
-            for (int jj = 0; jj < 4; ++jj) {
-              const int j = j0 + tx + 32 * jj;
-              wq[jj] = j < kb ? Qs[t * kBelowLdp + j] : 0.f;
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-              for (int jj = 0; jj < 4; ++jj) az[i][jj] = fmaf(mr[i], wq[jj], az[i][jj]);
-          }
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int jj = 0; jj < 4; ++jj) {
-            const int j = j0 + tx + 32 * jj;
-            if (j < kb) {
-              X[(4 * ty + i) * ldx + j] -= ax[i][jj];
-              if (!SYM) Zs[(4 * ty + i) * ldx + j] -= az[i][jj];
-            }
-          }
+      // the product over the columns right of the panel, in one pass: lane tx
+      // takes columns C0 + tx + 32 jj, jj < JJ = ceil((kb - C0) / 32)
+      switch ((kb - C0 + 31) >> 5) {
+        case 1: below_product<SYM, 1>(X, Zs, Ps, Qs, ldx, D, C0, kb, ty, tx); break;
+        case 2: below_product<SYM, 2>(X, Zs, Ps, Qs, ldx, D, C0, kb, ty, tx); break;
+        case 3: below_product<SYM, 3>(X, Zs, Ps, Qs, ldx, D, C0, kb, ty, tx); break;
+        case 4: below_product<SYM, 4>(X, Zs, Ps, Qs, ldx, D, C0, kb, ty, tx); break;
+        case 5: below_product<SYM, 5>(X, Zs, Ps, Qs, ldx, D, C0, kb, ty, tx); break;
+        case 6: below_product<SYM, 6>(X, Zs, Ps, Qs, ldx, D, C0, kb, ty, tx); break;
+        case 7: below_product<SYM, 7>(X, Zs, Ps, Qs, ldx, D, C0, kb, ty, tx); break;
+        default: break;
       }
       if (more) {
         cp_async_wait_all();
