@@ -863,6 +863,39 @@ def main():
         draw(base_seed + 900000 + w)
     torch.cuda.synchronize()
 
+    # draws are dealt round-robin to the streams; a last, partial round of m
+    # draws takes sms // m CTAs per launch instead of the tuned share, so that
+    # its launches still cover the GPU (dpp.draw_schedule)
+    if tuning is not None:
+        cap0 = int(tuning["max_ctas"])
+    else:
+        cap0 = int(_lib.get_tuning(_lib.DPP_TUNE_MAX_CTAS))
+
+    def run_schedule(count, one):
+        plan = dpp.draw_schedule(count, nst, sms, cap0)
+        s = 0
+        while s < count:
+            cap, e = plan[s][1], s
+            while e < count and plan[e][1] == cap:
+                e += 1
+            if cap == cap0:
+                for t in range(s, e):
+                    one(t, plan[t][0])
+            else:
+                with dpp.tuning_knobs(entry=tuning, max_ctas=cap):
+                    for t in range(s, e):
+                        one(t, plan[t][0])
+            s = e
+        return plan
+
+    def describe(plan):
+        caps = [c for _, c in plan]
+        tail = [c for c in caps if c != cap0]
+        out = f"{len(caps) - len(tail)} draws at {cap0} CTAs per launch"
+        if tail:
+            out += f", last {len(tail)} at {tail[0]}"
+        return out
+
     # ---- timed region ----------------------------------------------------
     if ws_n > 1:
         torch.distributed.barrier()
@@ -878,8 +911,7 @@ def main():
     for sv in side:
         if sv is not stream:
             sv.wait_event(ev0)
-    for s in range(steps):
-        draw(base_seed + s, si=s % nst)
+    plan = run_schedule(steps, lambda s, j: draw(base_seed + s, si=j))
     for sv in side:
         if sv is not stream:
             done = torch.cuda.Event()
@@ -1077,8 +1109,8 @@ def main():
 
         for s0 in range(min(nbuf, e2e_steps)):
             stage(s0)
-        for s in range(e2e_steps):
-            b, j = s % nbuf, s % nst
+        def e2e_step(s, j):
+            b = s % nbuf
             sv = side[j]
             for ev in copied[b]:
                 sv.wait_event(ev)
@@ -1089,6 +1121,8 @@ def main():
                 raw_h[j].copy_(raws[j], non_blocking=True)
             if s + nbuf < e2e_steps:
                 stage(s + nbuf)
+
+        run_schedule(e2e_steps, e2e_step)
         for sv in side:
             if sv is not stream:
                 done = torch.cuda.Event()
@@ -1141,7 +1175,7 @@ def main():
                        "seeds": f"Philox seed = step index (+ rank offset)",
                        "l2_policy": "inputs larger than L2 (2 GiB FP64 K), no flush",
                        "parallelism": f"replicas x{ws_n}",
-                       "streams": nst, "tuning": tuning},
+                       "streams": nst, "schedule": describe(plan), "tuning": tuning},
             "tflops_algorithmic": value * algo_flops / 1e12,
             "roofline": roof,
             "err_vs_oracle": err,

@@ -410,6 +410,59 @@ def autotune(K, hermitian: bool = True, precision: str = "3xtf32", max_streams: 
     return e.as_dict()
 
 
+def draw_schedule(count: int, streams: int, sms: int, cap: int) -> list:
+    """Stream and per-launch CTA cap of each of `count` independent draws run
+    concurrently on `streams` streams (draw s on stream s mod streams).
+
+    Full rounds of `streams` draws keep `cap` (the tuned share of the `sms`
+    SMs; 0 = one CTA per SM). A last, partial round of m < streams draws
+    would leave streams - m shares idle, so its draws take max(cap, sms // m)
+    CTAs each. Returns [(stream, cap), ...]; pure host arithmetic."""
+    if count < 0 or streams < 1 or sms < 1 or cap < 0:
+        raise ValueError("draw_schedule: count >= 0, streams >= 1, sms >= 1, cap >= 0")
+    full = (count // streams) * streams
+    m = count - full
+    tail_cap = cap
+    if m and cap:
+        share = sms // m
+        tail_cap = 0 if share >= sms else max(cap, share)
+    return [(s % streams, cap if s < full else tail_cap) for s in range(count)]
+
+
+class tuning_knobs:
+    """Context manager: the given DPP_TUNE_* knobs for the calls made inside
+    it, the previous values restored on exit. With `entry` (a tuning-table
+    entry as returned by _lib.tune_lookup) the table is switched off and the
+    entry's outer block, panel pipeline, update variant and CTA cap are set
+    explicitly, `max_ctas` (if given) replacing its cap."""
+
+    def __init__(self, entry=None, max_ctas=None, **knobs):
+        self.want = {}
+        if entry is not None:
+            self.want[_lib.DPP_TUNE_USE_CACHE] = 0
+            if entry["outer_block"] >= 32:
+                self.want[_lib.DPP_TUNE_OUTER_BLOCK] = entry["outer_block"]
+            self.want[_lib.DPP_TUNE_PANEL_PIPELINE] = entry["panel_pipeline"]
+            self.want[_lib.DPP_TUNE_UPDATE_VARIANT] = entry["update_variant"]
+            self.want[_lib.DPP_TUNE_MAX_CTAS] = entry["max_ctas"]
+        if max_ctas is not None:
+            self.want[_lib.DPP_TUNE_MAX_CTAS] = max_ctas
+        for k, v in knobs.items():
+            self.want[getattr(_lib, "DPP_TUNE_" + k.upper())] = v
+        self.old = {}
+
+    def __enter__(self):
+        for k, v in self.want.items():
+            self.old[k] = _lib.get_tuning(k)
+            _lib.set_tuning(k, v)
+        return self
+
+    def __exit__(self, *exc):
+        for k, v in reversed(list(self.old.items())):
+            _lib.set_tuning(k, v)
+        return False
+
+
 def uniforms(seed: int, instance: int, n: int, device="cuda"):
     """The Philox uniforms u_0..u_{n-1} the samplers draw for (seed, instance)."""
     torch = _torch()

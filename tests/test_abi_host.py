@@ -276,3 +276,47 @@ def test_elementary_arguments_checked_on_host(L):
         _lib.DPP_ERR_INVALID_ARG  # no sample buffer
     assert f(fake, 100, 100, 10, 0, 0, None, fake, None, None, fake, fake, 64, None) == \
         _lib.DPP_ERR_WORKSPACE
+
+
+def test_draw_schedule_fills_the_last_round():
+    """Concurrent draws: full rounds keep the tuned cap; a partial last round
+    of m draws takes sms // m CTAs per launch (never fewer than the tuned
+    cap, 0 = one per SM when one draw is left); streams stay round-robin."""
+    plan = dpp.draw_schedule(20, 8, 152, 19)
+    assert [j for j, _ in plan] == [s % 8 for s in range(20)]
+    assert [c for _, c in plan] == [19] * 16 + [38] * 4
+    assert dpp.draw_schedule(40, 8, 152, 19) == [(s % 8, 19) for s in range(40)]
+    assert dpp.draw_schedule(17, 8, 152, 19)[-1] == (0, 0)
+    assert [c for _, c in dpp.draw_schedule(5, 8, 152, 19)] == [30] * 5
+    assert [c for _, c in dpp.draw_schedule(7, 4, 152, 38)][4:] == [50] * 3
+    # untuned (cap 0: one CTA per SM) and single-stream schedules are unchanged
+    assert dpp.draw_schedule(3, 1, 152, 0) == [(0, 0)] * 3
+    assert dpp.draw_schedule(5, 4, 152, 0) == [(s % 4, 0) for s in range(5)]
+    # a tail share below the tuned cap keeps the cap
+    assert dpp.draw_schedule(62, 32, 152, 8)[-1] == (29, 8)
+    assert dpp.draw_schedule(0, 8, 152, 19) == []
+    # every round's launches fit the SMs: sum of caps over a round <= sms
+    for count, streams, cap in ((20, 8, 19), (23, 6, 25), (9, 4, 38), (3, 8, 19)):
+        plan = dpp.draw_schedule(count, streams, 152, cap)
+        for r0 in range(0, count, streams):
+            assert sum(c for _, c in plan[r0:r0 + streams]) <= 152
+    with pytest.raises(ValueError):
+        dpp.draw_schedule(4, 0, 152, 19)
+
+
+def test_tuning_knobs_set_and_restore(L):
+    """The knob context sets a tuning entry's knobs explicitly (table off) and
+    restores every previous value on exit, also after an exception."""
+    keys = (_lib.DPP_TUNE_USE_CACHE, _lib.DPP_TUNE_OUTER_BLOCK, _lib.DPP_TUNE_PANEL_PIPELINE,
+            _lib.DPP_TUNE_UPDATE_VARIANT, _lib.DPP_TUNE_MAX_CTAS)
+    before = [_lib.get_tuning(k) for k in keys]
+    entry = {"outer_block": 128, "panel_pipeline": 3, "update_variant": 1, "max_ctas": 19}
+    with dpp.tuning_knobs(entry=entry, max_ctas=38):
+        assert [_lib.get_tuning(k) for k in keys] == [0, 128, 3, 1, 38]
+    assert [_lib.get_tuning(k) for k in keys] == before
+    with pytest.raises(RuntimeError):
+        with dpp.tuning_knobs(max_ctas=24, panel_pipeline=2):
+            assert _lib.get_tuning(_lib.DPP_TUNE_MAX_CTAS) == 24
+            assert _lib.get_tuning(_lib.DPP_TUNE_PANEL_PIPELINE) == 2
+            raise RuntimeError("inside")
+    assert [_lib.get_tuning(k) for k in keys] == before
