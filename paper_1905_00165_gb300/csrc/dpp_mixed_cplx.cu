@@ -232,6 +232,7 @@ __device__ __noinline__ bool cx_serve(const CxRc& c, unsigned id) {
         const int64_t c0 = 32 * m;
         const int ncol = (int)((g - c0) < 32 ? (g - c0) : 32);
         const cf xl = lane < ncol ? word_c(c, c0 + lane, id, &live) : mkc(0.f, 0.f);
+        const double xlr = (double)xl.x, xli = (double)xl.y;  // widened once per lane
         for (int k = 0; k < 32; ++k) {
           const int64_t col = c0 + k;
           double2 kv = make_double2(0.0, 0.0);
@@ -243,7 +244,7 @@ __device__ __noinline__ bool cx_serve(const CxRc& c, unsigned id) {
               kv = make_double2(q.x, -q.y);
             }
           }
-          const double xr_ = (double)__shfl_sync(kCF, xl.x, k), xi_ = (double)__shfl_sync(kCF, xl.y, k);
+          const double xr_ = __shfl_sync(kCF, xlr, k), xi_ = __shfl_sync(kCF, xli, k);
           accA.x = fma(kv.x, xr_, fma(-kv.y, xi_, accA.x));
           accA.y = fma(kv.x, xi_, fma(kv.y, xr_, accA.y));
         }

@@ -305,11 +305,12 @@ __device__ __noinline__ void lu_residual(const LuRc& L, unsigned id, int64_t g, 
     const bool vc = lane < nc;
     const float xl = vc ? word_at(a, a.xw, c0 + lane, id, live) : 0.f;
     const float yl = vc ? word_at(a, L.yw, c0 + lane, id, live) : 0.f;
+    const double xd = (double)xl;  // widened once: double shuffles below
     double kv[32];
 #pragma unroll
     for (int k = 0; k < 32; ++k) kv[k] = (vi && k < nc) ? K[i + (c0 + k) * ldk] : 0.0;
 #pragma unroll
-    for (int k = 0; k < 32; ++k) accA = fma(kv[k], (double)__shfl_sync(kLuFull, xl, k), accA);
+    for (int k = 0; k < 32; ++k) accA = fma(kv[k], __shfl_sync(kLuFull, xd, k), accA);
 #pragma unroll
     for (int k = 0; k < 32; ++k) kv[k] = (vc && k < nr) ? K[(c0 + lane) + (32 * t + k) * ldk] : 0.0;
 #pragma unroll

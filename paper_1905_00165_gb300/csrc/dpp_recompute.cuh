@@ -353,7 +353,9 @@ static __device__ __noinline__ void residual_block(const RecomputeArgs& a, unsig
     for (int64_t m = wp; m <= t; m += 8) {
       const int64_t c0 = 32 * m;
       const int nc = (int)((g - c0) < 32 ? (g - c0) : 32);
-      const float xl = lane < nc ? x0_at(a, c0 + lane, id, live) : 0.f;
+      // x0 widened once per lane: the loop below shuffles doubles instead of
+      // converting every broadcast value
+      const double xl = lane < nc ? (double)x0_at(a, c0 + lane, id, live) : 0.0;
       double kv[32];
 #pragma unroll
       for (int k = 0; k < 32; ++k) {
@@ -361,7 +363,7 @@ static __device__ __noinline__ void residual_block(const RecomputeArgs& a, unsig
         kv[k] = (vi && k < nc) ? (c <= i ? K[i + c * ldk] : K[c + i * ldk]) : 0.0;
       }
 #pragma unroll
-      for (int k = 0; k < 32; ++k) acc = fma(kv[k], (double)__shfl_sync(kRcFull, xl, k), acc);
+      for (int k = 0; k < 32; ++k) acc = fma(kv[k], __shfl_sync(kRcFull, xl, k), acc);
     }
     sRedA[wp][lane] = acc;
   }
