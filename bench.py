@@ -55,6 +55,9 @@ def parse():
                         "SMs / streams CTAs (0: the autotuner's choice)")
     p.add_argument("--suite-only", default="",
                    help="with --suite: comma-separated subset of C1,C2,C3,C4,E,A")
+    p.add_argument("--suite-cpu", action="store_true",
+                   help="the oracle, as it stands, timed on the host cores at each "
+                        "configuration of --suite (its own size, a bounded sample)")
     p.add_argument("--suite", action="store_true",
                    help="one JSON line per workload of the paper-shaped configurations "
                         "(FP64 n=512; n=4096 real/complex, projection/Beta; spanning trees of "
@@ -670,6 +673,95 @@ def err_vs_oracle(keep, pivots, res, ref, u, gap=1e-9):
             "n_kept_gpu": res["n_kept"], "n_kept_oracle": int(ref.keep.sum())}
 
 
+def run_suite_cpu(args):
+    """The CPU oracle at the paper-shaped configurations, each at its own size:
+    the same synthetic kernels as --suite, one JSON line per configuration with
+    the oracle's rate on the host cores, timed over a bounded sample (whole
+    draws; for the batched L-ensembles the first instances of the batch, each
+    converted L -> K and drawn). Configurations whose single draw takes more
+    than a few minutes on the host are left to the headline's own measurement
+    (n = 16384) or reported as skipped."""
+    import numpy as np
+    import workloads as W
+    from oracle import oracle as O
+    O.build()
+    dev = None
+    try:
+        import torch
+        if torch.cuda.is_available():
+            dev = "cuda:0"
+    except Exception:
+        dev = None
+    cores = O.num_threads()
+    O.sample_ldl(np.eye(64) * 0.5, O.uniforms(10**6, 0, 64))  # starts the threads
+
+    def emit(name, cfg, rate, unit, sample):
+        print(json.dumps({"suite": name, "impl": "oracle", "config": cfg, "value": rate,
+                          "unit": unit, "cores": cores, "sample": sample}), flush=True)
+
+    def draws(fn, count, budget_s):
+        times = []
+        for s in range(count):
+            t0 = time.perf_counter()
+            fn(s)
+            times.append(time.perf_counter() - t0)
+            if sum(times) > budget_s:
+                break
+        return len(times), sum(times)
+
+    # C1: n = 512 (Haar, lam ~ U(0, 1)), LDL^T form
+    K = W.hermitian_kernel(512, seed=0, kind="uniform")
+    c, t = draws(lambda s: O.sample_ldl(K, O.uniforms(s, 0, 512)), 256, 20.0)
+    emit("C1", {"n": 512, "kernel": "Haar, lam~U(0,1)"}, c / t, "samples/s",
+         f"{c} draws, seeds 0..{c - 1}: {t:.2f} s")
+    # C2: n = 4096, real and complex, projection and Beta spectra
+    for cplx in (False, True):
+        for kind in ("projection", "beta"):
+            K = W.hermitian_kernel(4096, seed=0, kind=kind, complex_=cplx, device=dev)
+            K = np.asarray(K)
+            c, t = draws(lambda s: O.sample_ldl(K, O.uniforms(s, 0, 4096)), 4, 20.0)
+            emit("C2", {"n": 4096, "kind": kind, "dtype": "c128" if cplx else "f64"}, c / t,
+                 "samples/s", f"{c} complete draw(s): {t:.1f} s")
+    # C3: uniform spanning trees of the 64 x 64 grid (n = 8064)
+    K, edges, V = W.ust_grid_kernel(64, device=dev)
+    c, t = draws(lambda s: O.sample_ldl(K, O.uniforms(s, 0, K.shape[0])), 1, 0.0)
+    emit("C3", {"grid": 64, "n": int(K.shape[0])}, c / t, "samples/s",
+         f"{c} complete draw: {t:.1f} s")
+    # C4: real LU, n = 8192, K = D^{-1} S D
+    K, _ = W.lu_similarity_kernel(8192, seed=0, device=dev)
+    c, t = draws(lambda s: O.sample_lu(K, O.uniforms(s, 0, 8192)), 1, 0.0)
+    emit("C4", {"n": 8192, "kind": "D^-1 S D"}, c / t, "samples/s",
+         f"{c} complete draw: {t:.1f} s")
+    # C5: L-ensembles n ~ U{64..1024}: conversion K = L (L + I)^{-1} and a draw,
+    # instance by instance over the first instances of the 4096-instance batch
+    sizes = W.lensemble_sizes(4096, 0)
+    t_all, done = 0.0, 0
+    for i, m in enumerate(sizes):
+        Lm = W.lensemble_L(int(m), 1 + i)
+        t0 = time.perf_counter()
+        Km = np.linalg.solve((Lm + np.eye(int(m))).T, Lm.T).T
+        O.sample_ldl(0.5 * (Km + Km.T), O.uniforms(i, 0, int(m)))
+        t_all += time.perf_counter() - t0
+        done += 1
+        if t_all > 20.0:
+            break
+    emit("C5", {"batch": 4096, "nmin": 64, "nmax": 1024, "instances_timed": done,
+                "mean_n_timed": float(np.mean(sizes[:done]))}, done / t_all, "instances/s",
+         f"the first {done} instances: numpy conversion and an oracle draw each, {t_all:.1f} s")
+    # E: Algorithm 2 on projections of rank 10 / 100 / 500, n = 5000
+    for k in (10, 100, 500):
+        K = np.asarray(W.hermitian_kernel(5000, seed=0, kind="projection", rank=k, device=dev))
+        c, t = draws(lambda s: O.sample_elementary(K, k, O.uniforms(s, 0, 5000)), 8, 10.0)
+        emit("E", {"n": 5000, "rank": k}, c / t, "samples/s", f"{c} draws: {t:.2f} s")
+    # A: Aztec diamond of order 30 (n = 3600), complex LU
+    K, _, _ = W.aztec_kernel(30, device=dev)
+    K = np.asarray(K)
+    c, t = draws(lambda s: O.sample_lu(K, O.uniforms(s, 0, K.shape[0])), 2, 15.0)
+    emit("A", {"aztec_order": 30, "n": int(K.shape[0])}, c / t, "samples/s",
+         f"{c} complete draw(s): {t:.1f} s")
+    return 0
+
+
 def run_reference(args):
     """The oracle arm: the plain FP64 CPU oracle, as it stands, timed on the
     host cores on the full n x n kernel of the headline workload. Each step is
@@ -772,6 +864,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.suite_cpu:
+        return run_suite_cpu(args)
     if args.suite:
         return run_suite(args)
     if args.case:
