@@ -434,7 +434,9 @@ class tuning_knobs:
     it, the previous values restored on exit. With `entry` (a tuning-table
     entry as returned by _lib.tune_lookup) the table is switched off and the
     entry's outer block, panel pipeline, update variant and CTA cap are set
-    explicitly, `max_ctas` (if given) replacing its cap."""
+    explicitly, `max_ctas` (if given) replacing its cap. The knobs are the
+    library's process-wide settings, read when a call is enqueued: a context
+    changes them for every thread of the process while it is open."""
 
     def __init__(self, entry=None, max_ctas=None, **knobs):
         self.want = {}
