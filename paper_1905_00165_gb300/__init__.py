@@ -18,7 +18,7 @@ __all__ = ["sample_hermitian", "sample_hermitian_static", "sample_lu", "greedy_h
            "greedy_lu", "sample_batched", "BatchedSampler", "autotune",
            "lensemble_to_marginal", "sample_elementary",
            "logprob_backward", "uniforms", "Sample", "DPPLogProb", "DPPError", "load",
-           "workspace_size"]
+           "workspace_size", "draw_schedule", "tuning_knobs"]
 
 
 def _torch():
