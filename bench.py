@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--gen", default="gpu", choices=["gpu", "cpu"],
                    help="where the input kernel's Haar factor is computed")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--e2e-buffers", type=int, default=0,
+                   help="device buffers of K in the end-to-end ring (0: streams + 2)")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-fp64-ref", action="store_true")
     p.add_argument("--no-batched", action="store_true")
@@ -1146,7 +1148,7 @@ def main():
         # streams (two copy engines)
         Kh = torch.empty_strided(Kd.shape, Kd.stride(), dtype=torch.float64, pin_memory=True)
         Kh.copy_(Kd)
-        nbuf = nst + 2
+        nbuf = args.e2e_buffers if args.e2e_buffers > 0 else nst + 2
         Kin = [torch.empty_strided(Kd.shape, Kd.stride(), dtype=torch.float64, device=dev)
                for _ in range(nbuf)]
 
